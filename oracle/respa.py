@@ -1,0 +1,94 @@
+"""Single-loop r-RESPA integrator (Algorithm 2, Sec. 4.1) -- oracle, test use only.
+
+The two force fields are split as in the paper: the Lennard-Jones pair force
+F2b is integrated every iteration of step dt, the ATM triplet force F3b only
+with the step-size factor s (a kick of dt*s/(2m) on iterations with i % s == 0
+and after iterations with (i+1) % s == 0).  With s = 1 this is Stormer-Verlet
+(Sec. 4.1, "Performance" item).  Only iterations divisible by s are full steps
+where energies are meaningful.
+
+Readings where the paper leaves a choice:
+  * the public call takes the outer step dt_outer and k = s inner steps, so the
+    paper's dt is dt_outer / k;
+  * positions are folded back into the periodic box after every position
+    update (Cutoff runs use periodic boundaries, Sec. 4.2);
+  * F2b and F3b are cached between calls: Algorithm 2 evaluates them at x^0
+    once, before its loop.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import Callable, Optional
+
+import numpy as np
+
+from . import atm_brute, kinetic, lj_brute, wrap
+
+ForceFn = Callable[[np.ndarray], tuple]  # x -> (F, U, W)
+
+
+@dataclass
+class State:
+    x: np.ndarray
+    v: np.ndarray
+    L: float
+    mass: float = 1.0
+    f2: Optional[np.ndarray] = None
+    f3: Optional[np.ndarray] = None
+    u2: float = 0.0
+    u3: float = 0.0
+    w2: float = 0.0
+    w3: float = 0.0
+    energies: list = field(default_factory=list)  # (e_kin, u2, u3) at each full step
+
+
+def lj_atm_forces(L: float, eps: float, sigma: float, rc2: float, nu: float, rc3: float):
+    """The two brute-force force fields of the method as callables x -> (F, U, W)."""
+    def f2(x):
+        return lj_brute(x, L, eps, sigma, rc2)
+
+    def f3(x):
+        f, u, w, _ = atm_brute(x, L, nu, rc3)
+        return f, u, w
+    return f2, f3
+
+
+def run(state: State, n_outer: int, k_inner: int, dt_outer: float, f2b: ForceFn, f3b: ForceFn,
+        periodic: bool = True, record: bool = False) -> State:
+    """Advance ``state`` by n_outer outer steps of k_inner inner steps (Algorithm 2, s = k_inner,
+    dt = dt_outer / k_inner).  Updates the state in place and returns it."""
+    if n_outer < 0 or k_inner < 1 or not dt_outer > 0:
+        raise ValueError("n_outer >= 0, k_inner >= 1 and dt_outer > 0 required")
+    s = k_inner
+    dt = dt_outer / k_inner
+    m = state.mass
+    x, v = state.x, state.v
+    if state.f2 is None:  # calculate F2b(x^0)
+        state.f2, state.u2, state.w2 = f2b(x)
+    if state.f3 is None:  # calculate F3b(x^0)
+        state.f3, state.u3, state.w3 = f3b(x)
+    f2, f3 = state.f2, state.f3
+    for i in range(n_outer * s):
+        is_respa = (i % s) == 0
+        next_is_respa = ((i + 1) % s) == 0
+        if is_respa:
+            v = v + (dt * s / (2.0 * m)) * f3
+        x_new = x + dt * v + (dt * dt / (2.0 * m)) * f2
+        if periodic:
+            x_new = wrap(x_new, state.L)
+        f2_new, state.u2, state.w2 = f2b(x_new)
+        v = v + (dt / (2.0 * m)) * (f2 + f2_new)
+        x, f2 = x_new, f2_new
+        if next_is_respa:
+            f3, state.u3, state.w3 = f3b(x)
+            v = v + (dt * s / (2.0 * m)) * f3
+            if record:
+                state.energies.append((kinetic(v, m), state.u2, state.u3))
+    state.x, state.v, state.f2, state.f3 = x, v, f2, f3
+    return state
+
+
+def rvite(e_tot: np.ndarray, e_kin: np.ndarray) -> float:
+    """Relative variation in true energy (Eq. 4): mean |e(i) - mean(e)| / mean(K)."""
+    e_tot = np.asarray(e_tot, dtype=np.float64)
+    return float(np.mean(np.abs(e_tot - e_tot.mean())) / np.mean(e_kin))
