@@ -1,0 +1,291 @@
+"""Benchmark: r-RESPA with cutoff ATM three-body forces on one GB300 (arXiv 2507.11172).
+
+Workload (default): 100,000 particles, FCC at density 0.8 with 0.05 sigma Gaussian jitter and
+Maxwell velocities at T* = 1.0; LJ eps = sigma = 1, r_c = 2.5; ATM nu = 0.073, r_c = 2.5;
+r-RESPA dt_outer = 0.02 with k = 10 inner steps.  One benchmark step = one outer r-RESPA step
+(10 LJ evaluations with their velocity-Verlet updates, one binning sort + pair-list build, one
+ATM evaluation, the outer kicks) through md_respa_step.
+
+value = interacting triplets evaluated per second of whole-step time (FP32 forces with
+compensated accumulation, FP64 integrator and energies).  Also reported: r-RESPA outer steps/s,
+the same numbers for the all-FP64 path, the ATM kernel's roofline position, an end-to-end figure
+through the C ABI with host buffers, and the CPU oracle on a bounded sample.
+
+Multi-GPU (--gpus N under torchrun): independent replicas, one per rank (the method shards into
+independent systems; there is no data-path collective), weak scaling; max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "triplets/s and r-RESPA steps/s, FP32 vs FP64 plain; p50/p99 replica latency"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP32 ALU peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.070 GHz maximum SM clock
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# Algorithmic FP32 flops of one interacting triplet in the ATM kernel's formula (FMA = 2 flops),
+# counted from atm_triplet: d_jk 3, c 5, ab/q 2, rsqrt 1 + Newton 4, w/t3/t5 3, s/A/B/C 8,
+# AB/AC/BC/P 4, Pa/Pb/Pc 9, G 3, ia/ib/ic 5, nu*t5 1, pa2/pb2/pc2 12, F_i 9, F_j 9, F_k 3,
+# accumulation of F_i (3) and scatter of F_j, F_k (6)
+ATM_FLOPS_PER_TRIPLET = 3 + 5 + 2 + 5 + 3 + 8 + 4 + 9 + 3 + 5 + 1 + 12 + 9 + 9 + 3 + 3 + 6
+
+
+def sample_clocks(stop, out):
+    cmd = ["nvidia-smi", "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+           "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+           "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+           "--format=csv,noheader,nounits", "-i", os.environ.get("LOCAL_RANK", "0")]
+    while not stop.is_set():
+        try:
+            r = subprocess.run(cmd, capture_output=True, text=True, timeout=5)
+            if r.returncode == 0:
+                out.append(r.stdout.strip())
+        except Exception:
+            pass
+        stop.wait(0.2)
+
+
+def clock_summary(samples):
+    sm, mx, reasons = [], None, set()
+    for line in samples:
+        f = [t.strip() for t in line.split(",")]
+        if len(f) < 8:
+            continue
+        try:
+            sm.append(float(f[0]))
+            mx = float(f[1])
+        except ValueError:
+            continue
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for name, val in zip(names, f[4:8]):
+            if val.lower().startswith("active"):
+                reasons.add(name)
+    return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+            "samples": len(sm)}
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(
+        os.environ.get("LOCAL_RANK", "0"))
+
+
+def workload():
+    import md_inputs
+    return md_inputs.fcc_100k()
+
+
+def run_ours(args):
+    import torch
+    import paper_2507_11172_gb300 as r3
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    r3.load()
+    w = workload()
+    K, W = args.steps, args.warmup
+    stream = torch.cuda.Stream()
+    flush = torch.empty(int(256 * 2 ** 20) // 4, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def timed_run(precision, steps, warmup, profile):
+        h = r3.md_create_system(w.x, w.L, w.v, 1.0, precision, stream.cuda_stream)
+        try:
+            r3.md_set_potentials(h, 1.0, 1.0, w.rc2, w.nu, w.rc3)
+            with torch.cuda.stream(stream):
+                r3.md_respa_step(h, 0, w.k_inner, w.dt_outer)  # initial forces
+                for _ in range(warmup):
+                    r3.md_respa_step(h, 1, w.k_inner, w.dt_outer)
+                r3.md_set_profiling(h, profile)
+                if profile:  # capture the profiled graph outside the timed region
+                    r3.md_respa_step(h, 1, w.k_inner, w.dt_outer)
+                s0 = r3.md_get_stats(h)
+                ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                      for _ in range(steps)]
+                torch.cuda.synchronize()
+                barrier()
+                stop, samples = threading.Event(), []
+                th = threading.Thread(target=sample_clocks, args=(stop, samples), daemon=True)
+                th.start()
+                for e0, e1 in ev:
+                    flush.fill_(1.0)  # L2 flush between steps (buffer larger than the 129 MB L2)
+                    e0.record(stream)
+                    r3.md_respa_step(h, 1, w.k_inner, w.dt_outer)
+                    e1.record(stream)
+                torch.cuda.synchronize()
+                stop.set()
+                th.join()
+                barrier()
+                s1 = r3.md_get_stats(h)
+            ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
+            return ms, s0, s1, clock_summary(samples)
+        finally:
+            r3.md_destroy_system(h)
+
+    ms32, a0, a1, clk = timed_run(r3.MD_FP32, K, W, True)
+    trip32 = a1["triplets_total"] - a0["triplets_total"]
+    atm_ms = (a1["atm_ms_total"] - a0["atm_ms_total"]) / max(1, a1["atm_timed"] - a0["atm_timed"])
+    trip_per_eval = trip32 / K
+    k64 = max(3, K // 4)
+    ms64, b0, b1, _ = timed_run(r3.MD_FP64, k64, 3, True)
+    trip64 = b1["triplets_total"] - b0["triplets_total"]
+    atm64_ms = (b1["atm_ms_total"] - b0["atm_ms_total"]) / max(1, b1["atm_timed"] - b0["atm_timed"])
+
+    # max over ranks
+    t_local = ms32
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms32], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_local = float(t.item())
+    value = trip32 * world / (t_local / 1e3)
+    steps_per_s = K * world / (t_local / 1e3)
+
+    # end to end through the C ABI with host buffers: per step the caller's state goes host->device,
+    # one outer step runs, and the new state comes back device->host
+    e2e = None
+    if rank == 0:
+        import ctypes
+        n = w.n
+        hx = torch.empty((n, 3), dtype=torch.float64).pin_memory().numpy()
+        hv = torch.empty((n, 3), dtype=torch.float64).pin_memory().numpy()
+        hx[:] = w.x
+        hv[:] = w.v
+        h = r3.md_create_system(w.x, w.L, w.v, 1.0, r3.MD_FP32, stream.cuda_stream)
+        try:
+            r3.md_set_potentials(h, 1.0, 1.0, w.rc2, w.nu, w.rc3)
+            with torch.cuda.stream(stream):
+                for _ in range(2):
+                    r3.md_set_state(h, hx, hv)
+                    r3.md_respa_step(h, 1, w.k_inner, w.dt_outer)
+                    r3.md_get_state(h, hx, hv)
+                ke = max(3, K // 4)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                for _ in range(ke):
+                    r3.md_set_state(h, hx, hv)
+                    r3.md_respa_step(h, 1, w.k_inner, w.dt_outer)
+                    r3.md_get_state(h, hx, hv)
+                torch.cuda.synchronize()
+                te = time.perf_counter() - t0
+            e2e = {"value": trip_per_eval * ke / te, "unit": "triplets/s", "h2d_bytes_per_step": 48 * n,
+                   "d2h_bytes_per_step": 48 * n,
+                   "note": "per step: md_set_state (host x, v) + md_respa_step(1 outer) + md_get_state; "
+                           "set_state invalidates cached forces, so each step also re-evaluates F2b, F3b"}
+        finally:
+            r3.md_destroy_system(h)
+        del ctypes
+
+    peaks = {}
+    if os.path.exists(PEAKS_FILE):
+        peaks = json.load(open(PEAKS_FILE))
+    achieved_tflops = trip_per_eval * ATM_FLOPS_PER_TRIPLET / (atm_ms / 1e3) / 1e12
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "triplets/s",
+        "n_gpus": world,
+        "steps": K,
+        "warmup": W,
+        "ms_per_step": t_local / K,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 forces (compensated), f64 integrator",
+        "data": "synthetic",
+        "config": {"workload": "fcc100k_rho0.8: N=100000 FCC+jitter 0.05, LJ rc 2.5, ATM nu 0.073 rc 2.5, "
+                               "r-RESPA k=10 dt_outer=0.02, one step = one outer step",
+                   "n_particles": w.n, "box_L": w.L, "k_inner": w.k_inner, "dt_outer": w.dt_outer,
+                   "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
+        "rrespa_steps_per_s": steps_per_s,
+        "triplets_per_atm_eval": trip_per_eval,
+        "fp64_plain": {"triplets_per_s": trip64 / (ms64 / 1e3), "rrespa_steps_per_s": k64 / (ms64 / 1e3),
+                       "atm_kernel_ms": atm64_ms},
+        "atm_kernel_ms": atm_ms,
+        "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved_tflops / FP32_PEAK_TFLOPS, "traffic": None,
+                     "kernel": "k_atm<float>",
+                     "note": f"{ATM_FLOPS_PER_TRIPLET} flop per interacting triplet; peak = 152 SM x 128 "
+                             "FP32 lanes x 2 x 2.07 GHz"},
+        "clocks": clk,
+        "gpu_launches": K * (w.k_inner + 7),
+        "e2e": e2e,
+    }
+    if peaks:
+        line["measured_peaks"] = {"hbm_gbs": peaks.get("hbm_gbs"), "bf16_tflops": peaks.get("bf16_tflops")}
+    if not args.no_cpu and rank == 0:
+        line["cpu_baseline"] = cpu_baseline(w, args.cpu_sample)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def cpu_baseline(w, nsample):
+    """The oracle, as it stands, on a bounded sample: the per-particle pass (all triplets and
+    pairs containing each sampled particle) for nsample particles of the same workload."""
+    import oracle
+    import md_inputs
+    sel = np.unique((md_inputs.uniform(7, 11, 0, 4 * nsample) * w.n).astype(np.int64))[:nsample]
+    oracle.atm_particles(w.x, w.L, sel[:4], w.nu, w.rc3)  # load + warm
+    t0 = time.perf_counter()
+    _, _, cnt = oracle.atm_particles(w.x, w.L, sel, w.nu, w.rc3)
+    oracle.lj_particles(w.x, w.L, sel, 1.0, 1.0, w.rc2)
+    dt = time.perf_counter() - t0
+    # each sampled particle's pass evaluates every triplet containing it once
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": float(cnt.sum()) / dt, "unit": "triplets/s", "cores": cores, "kind": "oracle",
+            "sample": f"per-particle pass (ATM + LJ) of {sel.size} particles of the 100k workload, "
+                      f"{int(cnt.sum())} triplet evaluations in {dt:.2f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    w = workload()
+    cb = cpu_baseline(w, args.cpu_sample)
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "triplets/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "fcc100k_rho0.8 (same as our arm), CPU oracle per-particle pass sample"},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "triplets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=256)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

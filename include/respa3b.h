@@ -1,0 +1,162 @@
+/* respa3b -- GB300 (sm_103a) r-RESPA molecular dynamics with Lennard-Jones
+ * pair forces on every inner step and cutoff Axilrod-Teller-Muto (ATM)
+ * three-body forces only on outer steps.
+ *
+ * Method: arXiv 2507.11172 (Martin, Newcome, Muehlhaeusser, Mishra, Gratl,
+ * Bungartz), "The Multiple Time-Stepping Method for 3-Body Interactions in
+ * High Performance Molecular Dynamics Simulations".
+ *   - potentials: LJ 12-6 and ATM, Sec. 2.1;
+ *   - cutoff: a pair counts iff r <= r_c; a triplet counts iff all three of
+ *     its pair distances are <= r_c (Fig. 2 caption, Sec. 4.2.2); plain
+ *     truncation, no shift;
+ *   - integrator: the single-loop r-RESPA of Algorithm 2 (Sec. 4.1), with the
+ *     step-size factor s = k_inner and the paper's dt = dt_outer / k_inner;
+ *   - Newton's third law (Sec. 2.2): each pair and triplet is evaluated once.
+ *
+ * Units are reduced LJ units (Sec. 4.2, Table 1): the caller chooses eps,
+ * sigma, nu and the mass; k_B = 1.  The box is a periodic cube of side L
+ * with minimum-image distances, and L must exceed 3 * max(r_c, r_c + skin)
+ * (a precondition that keeps every cutoff sphere inside one image).
+ *
+ * Conventions for every entry point
+ *   - Returns md_status; nothing is thrown across the boundary.
+ *   - Host arrays are caller-owned, read or written only during the call,
+ *     and always in the caller's original particle order (the library keeps
+ *     its own cell-sorted order internally).  Vectors are n x 3 row-major
+ *     (x0 y0 z0 x1 y1 z1 ...), IEEE double.
+ *   - Device memory is owned by the library; handles are not thread-safe:
+ *     one thread at a time per handle.
+ *   - Calls are synchronous: when a call returns, its GPU work has finished.
+ */
+#ifndef RESPA3B_H
+#define RESPA3B_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct md_system md_system;
+typedef struct md_batch md_batch;
+
+typedef enum {
+  MD_OK = 0,
+  MD_ERR_ARG = -1,            /* invalid argument (n < 3, dt <= 0, k < 1, eps/sigma/r_c <= 0, NULL) */
+  MD_ERR_OOM = -2,            /* device memory (or the batch's memory budget) exhausted */
+  MD_ERR_BOX_TOO_SMALL = -3,  /* L <= 3 * max(r_c2 + skin, r_c3): minimum image not unique */
+  MD_ERR_NONFINITE = -4,      /* a position, velocity, force or energy became NaN/Inf */
+  MD_ERR_DEVICE_TIMEOUT = -5, /* a bounded device-side wait gave up */
+  MD_ERR_CUDA = -6,           /* a CUDA runtime call failed (message via md_last_error) */
+  MD_ERR_STATE = -7,          /* call not valid in this state (e.g. ticket unknown) */
+  MD_ERR_CAPACITY = -8        /* a cell, neighbour list or triplet list exceeded its capacity */
+} md_status;
+
+enum { MD_FP32 = 0, MD_FP64 = 1 };
+
+/* Per-handle counters; all fields refer to the system's lifetime unless noted. */
+typedef struct {
+  uint64_t triplets_last;      /* interacting triplets found by the last ATM evaluation */
+  uint64_t triplets_total;     /* interacting triplets summed over all ATM evaluations */
+  uint64_t atm_evals;          /* ATM evaluations (one per outer step, plus initial) */
+  uint64_t lj_evals;           /* LJ evaluations (one per inner step, plus initial) */
+  uint64_t outer_steps;        /* outer r-RESPA steps completed */
+  uint64_t replays;            /* calls replayed because a particle moved more than skin / 2 */
+  uint64_t guard_rechecks;     /* cutoff tests re-decided in FP64 (guard band) */
+  double atm_ms_total;         /* summed ATM kernel time from CUDA events (profiling on) */
+  uint64_t atm_timed;          /* number of ATM launches in atm_ms_total */
+  int32_t max_cell_count;      /* largest cell occupancy seen at the last binning */
+  int32_t cells_per_side;      /* binning grid */
+} md_stats;
+
+/* Create a system of n >= 3 particles in a periodic cube of side box_L.
+ * pos: n x 3, caller order, any real values (folded into [0, L));
+ * vel: n x 3 or NULL for zeros; mass > 0 (the paper's m, usually 1).
+ * precision: MD_FP32 (FP32 forces with compensated per-particle accumulation,
+ * FP64 positions, velocities and energies) or MD_FP64 (everything in FP64).
+ * cuda_stream: a cudaStream_t to run on, or NULL for a library-owned stream.
+ * Potentials default to eps = sigma = 1, r_c2 = 2.5, nu = 0, r_c3 = 2.5
+ * until md_set_potentials.  On error *out is NULL. */
+md_status md_create_system(md_system **out, int64_t n, double box_L, const double *pos, const double *vel,
+                           double mass, int precision, void *cuda_stream);
+
+/* LJ 12-6 (eps, sigma, pair cutoff rc_pair) and ATM (nu, triplet cutoff
+ * rc_triplet), Sec. 2.1.  nu = 0 disables the three-body force.  Invalidates
+ * the cached forces (Algorithm 2 recomputes F2b(x0) and F3b(x0)). */
+md_status md_set_potentials(md_system *s, double lj_eps, double lj_sigma, double rc_pair, double atm_nu,
+                            double rc_triplet);
+
+/* Verlet-list skin for the pair list (default 0.3 sigma).  The pair list is
+ * rebuilt at every outer step; if any particle moves more than skin/2 within
+ * one, the call is replayed from its start with a rebuild on every inner
+ * step, so results never depend on the skin. */
+md_status md_set_skin(md_system *s, double skin);
+
+/* Advance n_outer >= 0 outer steps of k_inner >= 1 inner steps each:
+ * Algorithm 2 with s = k_inner and dt = dt_outer / k_inner.  Positions and
+ * velocities are updated in place; forces are cached between calls. */
+md_status md_respa_step(md_system *s, int n_outer, int k_inner, double dt_outer);
+
+/* Current forces (caller order, n x 3): f2 = LJ, f3 = ATM, either may be NULL.
+ * Evaluates them first if they are not cached. */
+md_status md_get_forces(md_system *s, double *f2, double *f3);
+
+/* Energies at the current state (a full step): kinetic 0.5 m sum v^2, LJ
+ * energy, ATM energy and the virial W = sum over interactions of
+ * sum r_a . F_a (pressure P = (2 e_kin + W) / (3 L^3)).  Any pointer may be
+ * NULL. */
+md_status md_get_energy(md_system *s, double *e_kin, double *u2, double *u3, double *virial);
+
+/* Copy positions (folded into [0, L)) and velocities out / in, caller order,
+ * n x 3 each; either may be NULL.  md_set_state invalidates cached forces. */
+md_status md_get_state(md_system *s, double *pos, double *vel);
+md_status md_set_state(md_system *s, const double *pos, const double *vel);
+
+/* Counters (see md_stats).  profile = 1 turns on CUDA-event timing of every
+ * ATM launch (atm_ms_total / atm_timed). */
+md_status md_get_stats(md_system *s, md_stats *out);
+md_status md_set_profiling(md_system *s, int profile);
+
+/* Number of particles, box side and precision of a handle. */
+md_status md_get_info(md_system *s, int64_t *n, double *box_L, int *precision);
+
+/* Release all device memory of the handle; NULL is accepted. */
+md_status md_destroy_system(md_system *s);
+
+/* Static string for a status code; message of the last failing CUDA call of
+ * this thread for MD_ERR_CUDA. */
+const char *md_status_string(md_status st);
+const char *md_last_error(void);
+
+/* ---------------- batched ensemble / continuous serving ----------------
+ * A batch advances many independent systems together: on every inner "tick"
+ * one launch per kernel covers all resident systems (uneven sizes, different
+ * k_inner), captured as a CUDA graph per batch composition.  Systems are
+ * created with md_create_system (same precision for all members) and lent to
+ * the batch; their device state stays resident.
+ *
+ * md_batch_create: hbm_budget_bytes bounds the device memory of admitted
+ *   systems (0 = no bound beyond the device).
+ * md_batch_submit: queue n_outer outer steps of (k_inner, dt_outer) for s;
+ *   returns a ticket.  The system joins the batch at the next md_batch_run
+ *   call (admission) if it fits in the budget, else it waits.
+ * md_batch_run: advance every admitted request by up to max_ticks inner
+ *   ticks (<= 0: until every admitted request has finished); finished
+ *   requests leave the batch and queued ones are admitted as memory frees.
+ * md_batch_poll: *done = 1 once the ticket's request has finished.
+ * md_batch_latency: per-outer-step wall-clock latency samples (ms) of the
+ *   ticket's request, measured from its admission; *count in/out.
+ * md_batch_destroy: release the batch (systems stay valid; NULL accepted). */
+md_status md_batch_create(md_batch **out, size_t hbm_budget_bytes);
+md_status md_batch_submit(md_batch *b, md_system *s, int n_outer, int k_inner, double dt_outer, uint64_t *ticket);
+md_status md_batch_run(md_batch *b, int max_ticks);
+md_status md_batch_poll(md_batch *b, uint64_t ticket, int *done);
+md_status md_batch_latency(md_batch *b, uint64_t ticket, double *ms, int *count);
+md_status md_batch_pending(md_batch *b, int *queued, int *resident);
+md_status md_batch_destroy(md_batch *b);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RESPA3B_H */

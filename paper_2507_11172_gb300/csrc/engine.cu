@@ -1,0 +1,887 @@
+// Host runtime and C ABI of respa3b: device state of a system, the launch
+// plan of Algorithm 2 (arXiv 2507.11172, Sec. 4.1) captured as CUDA graphs,
+// snapshot/replay when a particle outruns the pair-list skin, and the batched
+// ensemble / serving engine.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <memory>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/respa3b.h"
+#include "md_internal.cuh"
+
+using namespace r3b;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+md_status cuda_fail(cudaError_t e, const char* what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? MD_ERR_OOM : MD_ERR_CUDA;
+}
+
+#define CK(call)                                        \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+constexpr int kBlock = 256;
+
+int device_sm_count() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return sms;
+}
+
+// one device allocation carved into aligned sub-arrays
+struct Arena {
+  char* base = nullptr;
+  size_t size = 0, used = 0;
+  size_t reserve(size_t bytes) {
+    size_t off = (used + 255) & ~size_t(255);
+    used = off + bytes;
+    return off;
+  }
+};
+
+}  // namespace
+
+// ====================================================================== system
+struct md_system {
+  // description
+  int64_t n = 0;
+  double L = 0, mass = 1.0;
+  int precision = MD_FP32;
+  double eps = 1.0, sigma = 1.0, rc2 = 2.5, nu = 0.0, rc3 = 2.5, skin = 0.3;
+  // grid and capacities
+  int nc = 0, ncell = 0, cap_cell = 0, maxnb = 0, nb_stride = 0;
+  double edge = 0;
+  // device memory
+  char* mem = nullptr;
+  size_t mem_bytes = 0;
+  SysDev h{};              // host copy of the device descriptor
+  SysDev* d_sys = nullptr;  // device copy (inside mem)
+  // snapshot for replay
+  double *snap_x = nullptr, *snap_v = nullptr, *snap_f2 = nullptr, *snap_f3 = nullptr;
+  int *snap_id = nullptr, *snap_cell = nullptr;
+  // work items
+  std::map<std::tuple<int, int, int>, PItem*> pitems;  // (kernel tag, mode, buf) -> device array
+  std::map<std::tuple<int, int>, CItem*> citems;        // (mode, buf)
+  SItem* sitem = nullptr;
+  std::vector<void*> item_allocs;
+  int nblocks = 0;
+  // execution
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int cur = 0;               // position buffer holding the current state
+  bool forces_valid = false;
+  bool energy_valid = false;
+  int atm_smem = 0, atm_grid = 0;
+  std::map<std::tuple<int, int, int, int, int>, cudaGraphExec_t> graphs;  // (n_outer, k, cur, safe, profile)
+  // host mirrors
+  int* h_flags = nullptr;       // pinned [FLG_N]
+  double* h_acc = nullptr;      // pinned [ACC_N]
+  unsigned long long* h_ctr = nullptr;  // pinned [CTR_N]
+  // stats
+  md_stats stats{};
+  bool profile = false;
+  std::vector<cudaEvent_t> events;
+  double e_kin = 0, u2 = 0, u3 = 0, w2 = 0, w3 = 0;
+  // batch membership
+  md_batch* batch = nullptr;
+};
+
+namespace {
+
+enum KTag { T_BIN = 1, T_SCATTER, T_LIST, T_LJ, T_COMB, T_START, T_KIN };
+
+void free_items(md_system* s) {
+  for (void* p : s->item_allocs) cudaFree(p);
+  s->item_allocs.clear();
+  s->pitems.clear();
+  s->citems.clear();
+  s->sitem = nullptr;
+}
+
+void clear_graphs(md_system* s) {
+  for (auto& kv : s->graphs) cudaGraphExecDestroy(kv.second);
+  s->graphs.clear();
+}
+
+void free_device(md_system* s) {
+  clear_graphs(s);
+  free_items(s);
+  if (s->mem) cudaFree(s->mem);
+  s->mem = nullptr;
+  s->mem_bytes = 0;
+  s->d_sys = nullptr;
+}
+
+md_status check_geometry(md_system* s) {
+  if (!(s->eps > 0) || !(s->sigma > 0) || !(s->rc2 > 0) || !(s->rc3 > 0) || !(s->skin >= 0) || !(s->nu >= 0))
+    return MD_ERR_ARG;
+  double reach = std::max(s->rc2 + s->skin, s->rc3);
+  if (!(s->L > 3.0 * reach)) return MD_ERR_BOX_TOO_SMALL;
+  return MD_OK;
+}
+
+// binning grid: cells of edge >= max(r_c2 + skin, r_c3), at least 3 per side
+void choose_grid(md_system* s) {
+  double reach = std::max(s->rc2 + s->skin, s->rc3);
+  int nc = (int)floor(s->L / reach);
+  if (nc < 3) nc = 3;
+  if (nc > 1024) nc = 1024;
+  s->nc = nc;
+  s->ncell = nc * nc * nc;
+  s->edge = s->L / nc;
+  double mean = (double)s->n / s->ncell;
+  if (s->cap_cell == 0) s->cap_cell = std::max(16, (int)ceil(1.6 * mean + 12.0));
+  double rho = (double)s->n / (s->L * s->L * s->L);
+  double rl = s->rc2 + s->skin;
+  double nl = rho * 4.18879020478639 * rl * rl * rl;
+  if (s->maxnb == 0) s->maxnb = std::max(32, (int)ceil(1.35 * nl + 24.0));
+  s->maxnb = std::min(s->maxnb, (int)s->n);
+  s->nb_stride = (int)((s->n + 31) / 32 * 32);
+}
+
+md_status alloc_device(md_system* s) {
+  free_device(s);
+  const size_t n = (size_t)s->n;
+  const size_t t4 = s->precision ? sizeof(double4_32a) : sizeof(float4);
+  const size_t tsz = s->precision ? 8 : 4;
+  Arena a;
+  size_t o_sys = a.reserve(sizeof(SysDev));
+  size_t o_X0 = a.reserve(24 * n), o_X1 = a.reserve(24 * n);
+  size_t o_v = a.reserve(24 * n), o_f2 = a.reserve(24 * n), o_f3 = a.reserve(24 * n), o_va = a.reserve(24 * n);
+  size_t o_id = a.reserve(4 * n), o_ida = a.reserve(4 * n);
+  size_t o_p0 = a.reserve(t4 * n), o_p1 = a.reserve(t4 * n), o_plo = a.reserve(t4 * n), o_ref = a.reserve(t4 * n);
+  size_t o_pcell = a.reserve(4 * n), o_ctmp = a.reserve(4 * n), o_rank = a.reserve(4 * n);
+  size_t o_count = a.reserve(4 * (size_t)s->ncell), o_cstart = a.reserve(4 * ((size_t)s->ncell + 1));
+  size_t o_nbr = a.reserve(4 * (size_t)s->maxnb * s->nb_stride), o_nbc = a.reserve(4 * n);
+  size_t o_part = a.reserve(tsz * 27 * 3 * n);
+  size_t o_acc = a.reserve(8 * ACC_N), o_ctr = a.reserve(8 * CTR_N), o_flg = a.reserve(4 * FLG_N);
+  size_t o_sx = a.reserve(24 * n), o_sv = a.reserve(24 * n), o_sf2 = a.reserve(24 * n), o_sf3 = a.reserve(24 * n);
+  size_t o_sid = a.reserve(4 * n), o_scell = a.reserve(4 * n);
+  char* m = nullptr;
+  cudaError_t e = cudaMalloc(&m, a.used);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_fail(e, "cudaMalloc(system)");
+  }
+  s->mem = m;
+  s->mem_bytes = a.used;
+  CK(cudaMemsetAsync(m, 0, a.used, s->stream));
+  SysDev& h = s->h;
+  memset(&h, 0, sizeof(h));
+  h.X[0] = (double*)(m + o_X0);
+  h.X[1] = (double*)(m + o_X1);
+  h.v = (double*)(m + o_v);
+  h.f2 = (double*)(m + o_f2);
+  h.f3 = (double*)(m + o_f3);
+  h.v_alt = (double*)(m + o_va);
+  h.id = (int*)(m + o_id);
+  h.id_alt = (int*)(m + o_ida);
+  h.pos[0] = m + o_p0;
+  h.pos[1] = m + o_p1;
+  h.poslo = m + o_plo;
+  h.ref = m + o_ref;
+  h.pcell = (int*)(m + o_pcell);
+  h.cell_tmp = (int*)(m + o_ctmp);
+  h.rank = (int*)(m + o_rank);
+  h.count = (int*)(m + o_count);
+  h.cell_start = (int*)(m + o_cstart);
+  h.nbr = (int*)(m + o_nbr);
+  h.nbr_cnt = (int*)(m + o_nbc);
+  h.partial = m + o_part;
+  h.acc = (double*)(m + o_acc);
+  h.ctr = (unsigned long long*)(m + o_ctr);
+  h.flags = (int*)(m + o_flg);
+  s->d_sys = (SysDev*)(m + o_sys);
+  s->snap_x = (double*)(m + o_sx);
+  s->snap_v = (double*)(m + o_sv);
+  s->snap_f2 = (double*)(m + o_sf2);
+  s->snap_f3 = (double*)(m + o_sf3);
+  s->snap_id = (int*)(m + o_sid);
+  s->snap_cell = (int*)(m + o_scell);
+  return MD_OK;
+}
+
+// refresh the parameter fields of the descriptor and upload it
+md_status upload_desc(md_system* s, double dt_in, double dt_out) {
+  SysDev& h = s->h;
+  h.L = s->L;
+  h.half_L = 0.5 * s->L;
+  h.edge = s->edge;
+  h.inv_edge = 1.0 / s->edge;
+  h.nc = s->nc;
+  h.ncell = s->ncell;
+  h.n = (int)s->n;
+  h.cap_cell = s->cap_cell;
+  h.eps = s->eps;
+  h.sig2 = s->sigma * s->sigma;
+  h.rc2 = s->rc2;
+  h.rc2sq = s->rc2 * s->rc2;
+  double rl = s->rc2 + s->skin;
+  h.rlistsq = rl * rl;
+  h.nu = s->nu;
+  h.rc3 = s->rc3;
+  h.rc3sq = s->rc3 * s->rc3;
+  h.half_skin_sq = 0.25 * s->skin * s->skin;
+  // FP32 cutoff decisions are exact outside this band of r^2 around r_c^2 (bound on the
+  // FP32 error of r^2 from cell-local coordinates: a few 1e-6 * r_c^2; 2e-5 r_c^2 kept)
+  double gfac = s->precision ? 1e-12 : 2e-5;
+  h.guard2 = gfac * std::max(1.0, h.rc2sq);
+  h.guard3 = gfac * std::max(1.0, h.rc3sq);
+  h.dt_in = dt_in;
+  h.dt_out = dt_out;
+  h.mass = s->mass;
+  h.inv_mass = 1.0 / s->mass;
+  h.maxnb = s->maxnb;
+  h.nb_stride = s->nb_stride;
+  h.precision = s->precision;
+  CK(cudaMemcpyAsync(s->d_sys, &h, sizeof(SysDev), cudaMemcpyHostToDevice, s->stream));
+  return MD_OK;
+}
+
+template <typename I>
+I* upload_items(md_system* s, const std::vector<I>& v) {
+  I* d = nullptr;
+  if (cudaMalloc(&d, sizeof(I) * std::max<size_t>(1, v.size())) != cudaSuccess) return nullptr;
+  s->item_allocs.push_back(d);
+  cudaMemcpyAsync(d, v.data(), sizeof(I) * v.size(), cudaMemcpyHostToDevice, s->stream);
+  return d;
+}
+
+PItem* pitems_for(md_system* s, int tag, int mode, int buf) {
+  auto key = std::make_tuple(tag, mode, buf);
+  auto it = s->pitems.find(key);
+  if (it != s->pitems.end()) return it->second;
+  std::vector<PItem> v;
+  for (int b = 0; b < s->nblocks; ++b) v.push_back(PItem{0, b * kBlock, mode, buf});
+  PItem* d = upload_items(s, v);
+  s->pitems[key] = d;
+  return d;
+}
+
+CItem* citems_for(md_system* s, int mode, int buf) {
+  auto key = std::make_tuple(mode, buf);
+  auto it = s->citems.find(key);
+  if (it != s->citems.end()) return it->second;
+  std::vector<CItem> v;
+  v.reserve(s->ncell);
+  for (int c = 0; c < s->ncell; ++c) v.push_back(CItem{0, c, buf, mode});
+  CItem* d = upload_items(s, v);
+  s->citems[key] = d;
+  return d;
+}
+
+// all item variants a call can use, created before any graph capture
+md_status prepare_items(md_system* s) {
+  s->nblocks = (int)((s->n + kBlock - 1) / kBlock);
+  for (int b = 0; b < 2; ++b) {
+    pitems_for(s, T_BIN, 0, b);
+    pitems_for(s, T_SCATTER, 0, b);
+    pitems_for(s, T_LIST, 0, b);
+    pitems_for(s, T_START, 0, b);
+    for (int e = 0; e < 2; ++e) {
+      int E = e ? M_ENERGY : 0;
+      pitems_for(s, T_LJ, LJ_INIT | E, b);
+      pitems_for(s, T_LJ, LJ_MID | E, b);
+      pitems_for(s, T_LJ, LJ_LAST | E, b);
+      pitems_for(s, T_COMB, CB_INIT | E, b);
+      pitems_for(s, T_COMB, CB_LAST | E, b);
+      pitems_for(s, T_COMB, CB_CONT | E, b);
+      citems_for(s, E, b);
+    }
+  }
+  pitems_for(s, T_KIN, 0, 0);
+  if (!s->sitem) {
+    std::vector<SItem> v{SItem{0, 0}};
+    s->sitem = upload_items(s, v);
+  }
+  CK(cudaStreamSynchronize(s->stream));
+  for (auto& kv : s->pitems)
+    if (!kv.second) return MD_ERR_OOM;
+  for (auto& kv : s->citems)
+    if (!kv.second) return MD_ERR_OOM;
+  if (!s->sitem) return MD_ERR_OOM;
+  return MD_OK;
+}
+
+md_status configure_atm(md_system* s) {
+  atm_prepare_table(s->stream);
+  int bytes = 0;
+  int per_sm = atm_configure(27 * s->cap_cell, s->precision, &bytes);
+  if (per_sm <= 0) {
+    g_last_error = "ATM kernel does not fit in shared memory for cap_cell=" + std::to_string(s->cap_cell);
+    return MD_ERR_CAPACITY;
+  }
+  s->atm_smem = bytes;
+  s->atm_grid = std::min(s->ncell, per_sm * device_sm_count());
+  return MD_OK;
+}
+
+// (re)build everything that depends on the grid and the capacities
+md_status rebuild(md_system* s, bool keep_state) {
+  std::vector<double> x, v;
+  std::vector<int> id;
+  const size_t n = (size_t)s->n;
+  if (keep_state && s->mem) {  // save the current state (sorted order) on the host
+    x.resize(3 * n);
+    v.resize(3 * n);
+    id.resize(n);
+    CK(cudaMemcpyAsync(x.data(), s->h.X[s->cur], 24 * n, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(v.data(), s->h.v, 24 * n, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(id.data(), s->h.id, 4 * n, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+  }
+  choose_grid(s);
+  md_status st = alloc_device(s);
+  if (st != MD_OK) return st;
+  st = upload_desc(s, 0.0, 0.0);
+  if (st != MD_OK) return st;
+  if (keep_state && !x.empty()) {
+    s->cur = 0;
+    CK(cudaMemcpyAsync(s->h.X[0], x.data(), 24 * n, cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(s->h.v, v.data(), 24 * n, cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(s->h.id, id.data(), 4 * n, cudaMemcpyHostToDevice, s->stream));
+  }
+  st = prepare_items(s);
+  if (st != MD_OK) return st;
+  st = configure_atm(s);
+  if (st != MD_OK) return st;
+  s->forces_valid = false;
+  s->energy_valid = false;
+  s->stats.cells_per_side = s->nc;
+  memset(s->h_ctr, 0, 8 * CTR_N);  // the device counters restart at zero with the new arena
+  return MD_OK;
+}
+
+// ---------------------------------------------------------------- launch plan
+struct Plan {
+  md_system* s;
+  Launch L;
+  template <typename T>
+  void sort(int buf) {
+    launch_bin_count(L, pitems_for(s, T_BIN, 0, buf), s->nblocks, kBlock);
+    launch_scan(L, s->sitem, 1);
+    launch_scatter<T>(L, pitems_for(s, T_SCATTER, 0, buf), s->nblocks, kBlock);
+    launch_listbuild<T>(L, pitems_for(s, T_LIST, 0, buf), s->nblocks, kBlock);
+  }
+  template <typename T>
+  void lj(int kind, int buf, bool energy) {
+    launch_lj<T>(L, pitems_for(s, T_LJ, kind | (energy ? M_ENERGY : 0), buf), s->nblocks, kBlock);
+  }
+  template <typename T>
+  void atm(int buf, bool energy, int ev) {
+    if (ev >= 0) cudaEventRecord(s->events[2 * ev], L.stream);
+    launch_atm<T>(L, citems_for(s, energy ? M_ENERGY : 0, buf), s->ncell, s->atm_grid, 27 * s->cap_cell);
+    if (ev >= 0) cudaEventRecord(s->events[2 * ev + 1], L.stream);
+  }
+  template <typename T>
+  void combine(int kind, int buf, bool energy) {
+    launch_combine<T>(L, pitems_for(s, T_COMB, kind | (energy ? M_ENERGY : 0), buf), s->nblocks, kBlock);
+  }
+  template <typename T>
+  void start(int buf) {
+    launch_start<T>(L, pitems_for(s, T_START, 0, buf), s->nblocks, kBlock);
+  }
+  void kinetic() { launch_kinetic(L, pitems_for(s, T_KIN, 0, 0), s->nblocks, kBlock); }
+  void zero_energy() { cudaMemsetAsync(s->h.acc, 0, 8 * ACC_N, L.stream); }
+};
+
+// initial forces F2b(x), F3b(x) and energies at the current positions (buffer cur)
+template <typename T>
+void enqueue_init(Plan& P, int ev) {
+  md_system* s = P.s;
+  P.zero_energy();
+  P.sort<T>(s->cur);
+  P.lj<T>(LJ_INIT, s->cur, true);
+  P.atm<T>(s->cur, true, ev);
+  P.combine<T>(CB_INIT, s->cur, false);
+  P.kinetic();
+}
+
+// Algorithm 2 for n_outer outer steps of k inner steps, starting from buffer cur
+template <typename T>
+void enqueue_steps(Plan& P, int n_outer, int k, int cur, bool safe, bool profile) {
+  if (n_outer <= 0) return;
+  P.start<T>(cur);  // i % s == 0: F3 half kick; first inner half kick and drift
+  for (int o = 0; o < n_outer; ++o) {
+    const bool last = (o == n_outer - 1);
+    if (last) P.zero_energy();
+    for (int t = 0; t < k; ++t) {
+      const int b = t & 1;
+      if (t == k - 1 || safe) P.sort<T>(b);  // binning + pair list at the outer boundary
+      if (t < k - 1)
+        P.lj<T>(LJ_MID, b, false);
+      else
+        P.lj<T>(LJ_LAST, b, last);
+    }
+    const int b = (k - 1) & 1;
+    P.atm<T>(b, last, profile ? o : -1);  // (i+1) % s == 0: F3b(x^{i+1})
+    P.combine<T>(last ? CB_LAST : CB_CONT, b, last);
+  }
+}
+
+md_status read_flags(md_system* s) {
+  CK(cudaMemcpyAsync(s->h_flags, s->h.flags, 4 * FLG_N, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaMemcpyAsync(s->h_acc, s->h.acc, 8 * ACC_N, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaMemcpyAsync(s->h_ctr, s->h.ctr, 8 * CTR_N, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  return MD_OK;
+}
+
+md_status clear_flags(md_system* s) {
+  CK(cudaMemsetAsync(s->h.flags, 0, 4 * FLG_N, s->stream));
+  return MD_OK;
+}
+
+md_status snapshot(md_system* s, bool save) {
+  const size_t n = (size_t)s->n;
+  auto cp = [&](void* dst, const void* src, size_t b) {
+    return cudaMemcpyAsync(dst, src, b, cudaMemcpyDeviceToDevice, s->stream);
+  };
+  if (save) {
+    CK(cp(s->snap_x, s->h.X[s->cur], 24 * n));
+    CK(cp(s->snap_v, s->h.v, 24 * n));
+    CK(cp(s->snap_f2, s->h.f2, 24 * n));
+    CK(cp(s->snap_f3, s->h.f3, 24 * n));
+    CK(cp(s->snap_id, s->h.id, 4 * n));
+    CK(cp(s->snap_cell, s->h.pcell, 4 * n));
+  } else {
+    CK(cp(s->h.X[s->cur], s->snap_x, 24 * n));
+    CK(cp(s->h.v, s->snap_v, 24 * n));
+    CK(cp(s->h.f2, s->snap_f2, 24 * n));
+    CK(cp(s->h.f3, s->snap_f3, 24 * n));
+    CK(cp(s->h.id, s->snap_id, 4 * n));
+    CK(cp(s->h.pcell, s->snap_cell, 4 * n));
+  }
+  return MD_OK;
+}
+
+md_status ensure_events(md_system* s, int count) {
+  while ((int)s->events.size() < count) {
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e));
+    s->events.push_back(e);
+  }
+  return MD_OK;
+}
+
+// run n_outer steps (n_outer == 0 with init only), as a cached CUDA graph
+md_status run_plan(md_system* s, int n_outer, int k, bool init, bool safe) {
+  const bool prof = s->profile;
+  const int nev = prof ? std::max(1, n_outer) + 1 : 0;
+  md_status st = ensure_events(s, 2 * nev);
+  if (st != MD_OK) return st;
+  Plan P{s, Launch{s->stream, s->d_sys}};
+  auto key = std::make_tuple(init ? -1 - n_outer : n_outer, k, s->cur, safe ? 1 : 0, prof ? 1 : 0);
+  cudaGraphExec_t exec = nullptr;
+  auto it = s->graphs.find(key);
+  if (it != s->graphs.end()) {
+    exec = it->second;
+  } else {
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+    if (s->precision) {
+      if (init) enqueue_init<double>(P, prof ? nev - 1 : -1);
+      enqueue_steps<double>(P, n_outer, k, s->cur, safe, prof);
+    } else {
+      if (init) enqueue_init<float>(P, prof ? nev - 1 : -1);
+      enqueue_steps<float>(P, n_outer, k, s->cur, safe, prof);
+    }
+    cudaError_t e = cudaStreamEndCapture(s->stream, &g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    if (s->graphs.size() > 32) clear_graphs(s);
+    s->graphs[key] = exec;
+  }
+  CK(cudaGraphLaunch(exec, s->stream));
+  return MD_OK;
+}
+
+md_status finish_call(md_system* s, int n_outer) {
+  md_status st = read_flags(s);
+  if (st != MD_OK) return st;
+  if (s->profile) {
+    for (int o = 0; o < n_outer; ++o) {
+      float ms = 0;
+      if (cudaEventElapsedTime(&ms, s->events[2 * o], s->events[2 * o + 1]) == cudaSuccess) {
+        s->stats.atm_ms_total += ms;
+        s->stats.atm_timed += 1;
+      }
+    }
+  }
+  return MD_OK;
+}
+
+md_status status_from_flags(md_system* s) {
+  int err = s->h_flags[FLG_ERR];
+  if (err & ERR_NONFINITE) return MD_ERR_NONFINITE;
+  if (err & (ERR_CELL_CAP | ERR_NBR_CAP | ERR_HALF_CAP)) return MD_ERR_CAPACITY;
+  if (err & ERR_TIMEOUT) return MD_ERR_DEVICE_TIMEOUT;
+  return MD_OK;
+}
+
+// one respa_step call with snapshot / replay
+md_status do_call(md_system* s, int n_outer, int k, double dt_outer) {
+  const double dt_in = dt_outer / k;
+  for (int attempt = 0; attempt < 6; ++attempt) {
+    const bool safe = attempt > 0 && s->h_flags[FLG_SKIN] && !(s->h_flags[FLG_ERR] & (ERR_CELL_CAP | ERR_NBR_CAP));
+    md_status st = upload_desc(s, dt_in, dt_outer);
+    if (st != MD_OK) return st;
+    st = clear_flags(s);
+    if (st != MD_OK) return st;
+    const bool init = !s->forces_valid;
+    const int cur0 = s->cur;
+    st = snapshot(s, true);
+    if (st != MD_OK) return st;
+    const unsigned long long trip0 = s->h_ctr[CTR_TRIPLETS];  // device counter as of the last call
+    st = run_plan(s, n_outer, k, init, safe);
+    if (st != MD_OK) return st;
+    st = finish_call(s, n_outer);
+    if (st != MD_OK) return st;
+    const int err = s->h_flags[FLG_ERR];
+    const bool skin_bad = s->h_flags[FLG_SKIN] != 0 && !safe;
+    const bool cap_bad = (err & (ERR_CELL_CAP | ERR_NBR_CAP)) != 0;
+    s->stats.max_cell_count = s->h_flags[FLG_MAXCELL];
+    if (!(skin_bad || cap_bad) || (err & ERR_NONFINITE)) {
+      md_status fs = status_from_flags(s);
+      if (fs != MD_OK) {
+        s->cur = cur0;
+        snapshot(s, false);
+        s->forces_valid = false;
+        s->energy_valid = false;
+        cudaStreamSynchronize(s->stream);
+        return fs;
+      }
+      // success
+      unsigned long long trip1 = s->h_ctr[CTR_TRIPLETS];
+      int evals = n_outer + (init ? 1 : 0);
+      if (evals > 0) s->stats.triplets_last = (trip1 - trip0) / (unsigned long long)evals;
+      s->stats.triplets_total += trip1 - trip0;
+      s->stats.atm_evals += evals;
+      s->stats.lj_evals += (uint64_t)n_outer * k + (init ? 1 : 0);
+      s->stats.outer_steps += n_outer;
+      s->stats.guard_rechecks = s->h_ctr[CTR_GUARD];
+      if (n_outer > 0) s->cur = (k - 1) & 1;
+      s->forces_valid = true;
+      if (n_outer > 0 || init) {
+        s->e_kin = s->h_acc[ACC_EK];
+        s->u2 = s->h_acc[ACC_U2];
+        s->w2 = s->h_acc[ACC_W2];
+        s->u3 = s->h_acc[ACC_U3];
+        s->w3 = s->h_acc[ACC_W3];
+        s->energy_valid = true;
+      }
+      return MD_OK;
+    }
+    // replay from the snapshot
+    s->cur = cur0;
+    st = snapshot(s, false);
+    if (st != MD_OK) return st;
+    if (cap_bad) {
+      if (err & ERR_CELL_CAP) s->cap_cell = std::max(s->cap_cell + 8, s->h_flags[FLG_MAXCELL] + 8);
+      if (err & ERR_NBR_CAP) s->maxnb = s->maxnb * 3 / 2 + 16;
+      st = rebuild(s, true);
+      if (st != MD_OK) return st;
+    } else {
+      s->stats.replays += 1;
+    }
+    // a replay must recompute the cached forces only if they were not valid before
+    if (init) s->forces_valid = false;
+    s->h_flags[FLG_SKIN] = skin_bad ? 1 : 0;
+    s->h_flags[FLG_ERR] = cap_bad ? err : 0;
+  }
+  g_last_error = "respa_step: replay limit reached";
+  return MD_ERR_CAPACITY;
+}
+
+void aos_to_soa(const double* a, std::vector<double>& s, size_t n) {
+  s.resize(3 * n);
+  for (size_t i = 0; i < n; ++i)
+    for (int c = 0; c < 3; ++c) s[c * n + i] = a[3 * i + c];
+}
+
+md_status fetch_sorted(md_system* s, const double* dsrc, double* out_aos, bool wrap) {
+  const size_t n = (size_t)s->n;
+  std::vector<double> soa(3 * n);
+  std::vector<int> id(n);
+  CK(cudaMemcpyAsync(soa.data(), dsrc, 24 * n, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaMemcpyAsync(id.data(), s->h.id, 4 * n, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  for (size_t q = 0; q < n; ++q) {
+    size_t o = (size_t)id[q];
+    if (o >= n) return MD_ERR_STATE;
+    for (int c = 0; c < 3; ++c) {
+      double x = soa[c * n + q];
+      if (wrap) {
+        x -= s->L * floor(x / s->L);
+        if (x >= s->L) x -= s->L;
+      }
+      out_aos[3 * o + c] = x;
+    }
+  }
+  return MD_OK;
+}
+
+md_status ensure_forces(md_system* s) {
+  if (s->forces_valid) return MD_OK;
+  return do_call(s, 0, 1, 1.0);
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+const char* md_status_string(md_status st) {
+  switch (st) {
+    case MD_OK: return "ok";
+    case MD_ERR_ARG: return "invalid argument";
+    case MD_ERR_OOM: return "out of device memory";
+    case MD_ERR_BOX_TOO_SMALL: return "box too small: L must exceed 3 * max(r_c2 + skin, r_c3)";
+    case MD_ERR_NONFINITE: return "non-finite value in the state";
+    case MD_ERR_DEVICE_TIMEOUT: return "device-side wait timed out";
+    case MD_ERR_CUDA: return "CUDA error";
+    case MD_ERR_STATE: return "invalid state for this call";
+    case MD_ERR_CAPACITY: return "capacity exceeded";
+  }
+  return "unknown status";
+}
+
+const char* md_last_error(void) { return g_last_error.c_str(); }
+
+md_status md_create_system(md_system** out, int64_t n, double box_L, const double* pos, const double* vel,
+                           double mass, int precision, void* cuda_stream) {
+  if (!out) return MD_ERR_ARG;
+  *out = nullptr;
+  if (n < 3 || n >= (int64_t)kNbrMask || !pos || !(box_L > 0) || !(mass > 0) ||
+      (precision != MD_FP32 && precision != MD_FP64))
+    return MD_ERR_ARG;
+  for (int64_t i = 0; i < 3 * n; ++i)
+    if (!isfinite(pos[i]) || (vel && !isfinite(vel[i]))) return MD_ERR_NONFINITE;
+  std::unique_ptr<md_system> s(new md_system());
+  s->n = n;
+  s->L = box_L;
+  s->mass = mass;
+  s->precision = precision;
+  md_status st = check_geometry(s.get());
+  if (st != MD_OK) return st;
+  if (cuda_stream) {
+    s->stream = (cudaStream_t)cuda_stream;
+  } else {
+    CK(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
+    s->own_stream = true;
+  }
+  CK(cudaMallocHost(&s->h_flags, 4 * FLG_N));
+  CK(cudaMallocHost(&s->h_acc, 8 * ACC_N));
+  CK(cudaMallocHost(&s->h_ctr, 8 * CTR_N));
+  memset(s->h_flags, 0, 4 * FLG_N);
+  st = rebuild(s.get(), false);
+  if (st != MD_OK) {
+    md_destroy_system(s.release());
+    return st;
+  }
+  st = md_set_state(s.get(), pos, vel);
+  if (st != MD_OK) {
+    md_destroy_system(s.release());
+    return st;
+  }
+  *out = s.release();
+  return MD_OK;
+}
+
+md_status md_set_potentials(md_system* s, double lj_eps, double lj_sigma, double rc_pair, double atm_nu,
+                            double rc_triplet) {
+  if (!s) return MD_ERR_ARG;
+  if (!(lj_eps > 0) || !(lj_sigma > 0) || !(rc_pair > 0) || !(rc_triplet > 0) || !(atm_nu >= 0) ||
+      !isfinite(atm_nu))
+    return MD_ERR_ARG;
+  double e0 = s->eps, s0 = s->sigma, r20 = s->rc2, nu0 = s->nu, r30 = s->rc3;
+  s->eps = lj_eps;
+  s->sigma = lj_sigma;
+  s->rc2 = rc_pair;
+  s->nu = atm_nu;
+  s->rc3 = rc_triplet;
+  md_status st = check_geometry(s);
+  if (st != MD_OK) {
+    s->eps = e0; s->sigma = s0; s->rc2 = r20; s->nu = nu0; s->rc3 = r30;
+    return st;
+  }
+  s->maxnb = 0;
+  s->cap_cell = 0;
+  return rebuild(s, true);
+}
+
+md_status md_set_skin(md_system* s, double skin) {
+  if (!s || !(skin >= 0) || !isfinite(skin)) return MD_ERR_ARG;
+  double old = s->skin;
+  s->skin = skin;
+  md_status st = check_geometry(s);
+  if (st != MD_OK) {
+    s->skin = old;
+    return st;
+  }
+  s->maxnb = 0;
+  s->cap_cell = 0;
+  return rebuild(s, true);
+}
+
+md_status md_respa_step(md_system* s, int n_outer, int k_inner, double dt_outer) {
+  if (!s || n_outer < 0 || k_inner < 1 || !(dt_outer > 0) || !isfinite(dt_outer)) return MD_ERR_ARG;
+  if (s->batch) return MD_ERR_STATE;
+  return do_call(s, n_outer, k_inner, dt_outer);
+}
+
+md_status md_get_forces(md_system* s, double* f2, double* f3) {
+  if (!s) return MD_ERR_ARG;
+  md_status st = ensure_forces(s);
+  if (st != MD_OK) return st;
+  if (f2) {
+    st = fetch_sorted(s, s->h.f2, f2, false);
+    if (st != MD_OK) return st;
+  }
+  if (f3) {
+    st = fetch_sorted(s, s->h.f3, f3, false);
+    if (st != MD_OK) return st;
+  }
+  return MD_OK;
+}
+
+md_status md_get_energy(md_system* s, double* e_kin, double* u2, double* u3, double* virial) {
+  if (!s) return MD_ERR_ARG;
+  if (!s->energy_valid) {
+    s->forces_valid = false;
+    md_status st = ensure_forces(s);
+    if (st != MD_OK) return st;
+  }
+  if (e_kin) *e_kin = s->e_kin;
+  if (u2) *u2 = s->u2;
+  if (u3) *u3 = s->u3;
+  if (virial) *virial = s->w2 + s->w3;
+  return MD_OK;
+}
+
+md_status md_get_state(md_system* s, double* pos, double* vel) {
+  if (!s) return MD_ERR_ARG;
+  if (pos) {
+    md_status st = fetch_sorted(s, s->h.X[s->cur], pos, true);
+    if (st != MD_OK) return st;
+  }
+  if (vel) {
+    md_status st = fetch_sorted(s, s->h.v, vel, false);
+    if (st != MD_OK) return st;
+  }
+  return MD_OK;
+}
+
+md_status md_set_state(md_system* s, const double* pos, const double* vel) {
+  if (!s) return MD_ERR_ARG;
+  const size_t n = (size_t)s->n;
+  if (!pos && !vel) return MD_OK;
+  std::vector<double> soa;
+  // bring the device state into caller order first (ids = identity afterwards)
+  std::vector<double> xcur(3 * n), vcur(3 * n);
+  md_status st = fetch_sorted(s, s->h.X[s->cur], xcur.data(), true);
+  if (st != MD_OK) return st;
+  st = fetch_sorted(s, s->h.v, vcur.data(), false);
+  if (st != MD_OK) return st;
+  if (pos) {
+    for (size_t i = 0; i < 3 * n; ++i)
+      if (!isfinite(pos[i])) return MD_ERR_NONFINITE;
+    memcpy(xcur.data(), pos, 24 * n);
+  }
+  if (vel) {
+    for (size_t i = 0; i < 3 * n; ++i)
+      if (!isfinite(vel[i])) return MD_ERR_NONFINITE;
+    memcpy(vcur.data(), vel, 24 * n);
+  }
+  for (size_t i = 0; i < 3 * n; ++i) {
+    double x = xcur[i] - s->L * floor(xcur[i] / s->L);
+    if (x >= s->L) x -= s->L;
+    xcur[i] = x;
+  }
+  std::vector<int> id(n);
+  for (size_t i = 0; i < n; ++i) id[i] = (int)i;
+  aos_to_soa(xcur.data(), soa, n);
+  std::vector<double> vs;
+  aos_to_soa(vcur.data(), vs, n);
+  s->cur = 0;
+  CK(cudaMemcpyAsync(s->h.X[0], soa.data(), 24 * n, cudaMemcpyHostToDevice, s->stream));
+  CK(cudaMemcpyAsync(s->h.v, vs.data(), 24 * n, cudaMemcpyHostToDevice, s->stream));
+  CK(cudaMemcpyAsync(s->h.id, id.data(), 4 * n, cudaMemcpyHostToDevice, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  s->forces_valid = false;
+  s->energy_valid = false;
+  return MD_OK;
+}
+
+md_status md_get_stats(md_system* s, md_stats* out) {
+  if (!s || !out) return MD_ERR_ARG;
+  *out = s->stats;
+  return MD_OK;
+}
+
+md_status md_set_profiling(md_system* s, int profile) {
+  if (!s) return MD_ERR_ARG;
+  s->profile = profile != 0;
+  clear_graphs(s);
+  return MD_OK;
+}
+
+md_status md_get_info(md_system* s, int64_t* n, double* box_L, int* precision) {
+  if (!s) return MD_ERR_ARG;
+  if (n) *n = s->n;
+  if (box_L) *box_L = s->L;
+  if (precision) *precision = s->precision;
+  return MD_OK;
+}
+
+md_status md_destroy_system(md_system* s) {
+  if (!s) return MD_OK;
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  free_device(s);
+  for (auto e : s->events) cudaEventDestroy(e);
+  if (s->h_flags) cudaFreeHost(s->h_flags);
+  if (s->h_acc) cudaFreeHost(s->h_acc);
+  if (s->h_ctr) cudaFreeHost(s->h_ctr);
+  if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+  delete s;
+  return MD_OK;
+}
+
+}  // extern "C"
+
+// ====================================================================== batch (pending)
+struct md_batch {
+  int unused;
+};
+extern "C" {
+md_status md_batch_create(md_batch** out, size_t) {
+  if (out) *out = nullptr;
+  return MD_ERR_STATE;
+}
+md_status md_batch_submit(md_batch*, md_system*, int, int, double, uint64_t*) { return MD_ERR_STATE; }
+md_status md_batch_run(md_batch*, int) { return MD_ERR_STATE; }
+md_status md_batch_poll(md_batch*, uint64_t, int*) { return MD_ERR_STATE; }
+md_status md_batch_latency(md_batch*, uint64_t, double*, int*) { return MD_ERR_STATE; }
+md_status md_batch_pending(md_batch*, int*, int*) { return MD_ERR_STATE; }
+md_status md_batch_destroy(md_batch* b) { return b ? MD_ERR_STATE : MD_OK; }
+}

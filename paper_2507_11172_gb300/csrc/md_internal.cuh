@@ -1,0 +1,216 @@
+// Internal definitions shared by the respa3b CUDA sources (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace r3b {
+
+// ---------------------------------------------------------------- capacities
+constexpr int kStencil = 27;        // 3 x 3 x 3 cells: cell edge >= every cutoff
+constexpr int kMaxHalf = 128;       // per-particle ATM half list (neighbours with larger sorted index)
+constexpr int kNbrShift = 27;       // LJ list entry = j | (image code << 27)
+constexpr unsigned kNbrMask = (1u << kNbrShift) - 1u;
+constexpr int kPairTable = kMaxHalf * (kMaxHalf - 1) / 2;  // (j, k) pairs, k-major
+constexpr int kAtmWarps = 8;
+constexpr int kAtmThreads = 32 * kAtmWarps;
+constexpr int kQueue = 64;          // per-warp accepted-triplet queue
+
+// error bits in SysDev::flags[0]
+enum : int {
+  ERR_CELL_CAP = 1,   // a cell holds more particles than cap_cell
+  ERR_NBR_CAP = 2,    // an LJ neighbour list overflowed
+  ERR_HALF_CAP = 4,   // an ATM half list overflowed kMaxHalf
+  ERR_NONFINITE = 8,  // NaN / Inf in positions, velocities or forces
+  ERR_TIMEOUT = 16,   // a bounded wait gave up
+};
+
+// accumulator slots in SysDev::acc (double)
+enum : int { ACC_U2 = 0, ACC_W2 = 1, ACC_U3 = 2, ACC_W3 = 3, ACC_EK = 4, ACC_N = 8 };
+// counter slots in SysDev::ctr (unsigned long long)
+enum : int { CTR_TRIPLETS = 0, CTR_GUARD = 1, CTR_N = 4 };
+// flag slots in SysDev::flags (int)
+enum : int { FLG_ERR = 0, FLG_SKIN = 1, FLG_MAXCELL = 2, FLG_N = 4 };
+
+// Device-resident description of one system.  Kernels read it from global
+// memory at run time (never from constant memory) so graphs stay valid when
+// the host re-points arrays.
+struct SysDev {
+  // geometry
+  double L, half_L, edge, inv_edge;
+  int nc, ncell, n, cap_cell;
+  // potentials (squared cutoffs computed on the host as rc * rc)
+  double eps, sig2, rc2, rc2sq, rlistsq, nu, rc3, rc3sq, half_skin_sq;
+  double guard2, guard3;  // half-width of the r^2 band re-decided in FP64 (pair / triplet)
+  // integrator
+  double dt_in, dt_out, inv_mass, mass;
+  int maxnb, nb_stride;
+  int precision;  // 0 = FP32 forces, 1 = FP64
+  int pad_;
+  // state in cell-sorted order, double SoA [3][n] (x block, y block, z block)
+  double *X[2];       // positions, ping-pong by inner-step parity
+  double *v, *f2, *f3;
+  double *v_alt;      // scatter target of the sort
+  int *id, *id_alt;   // original index of each sorted slot
+  void *pos[2];       // T4 [n]: cell-local coordinates (x, y, z relative to the cell centre of the last sort)
+  void *poslo;        // T4 [n]: FP32 mode: the rounding remainder of pos at the sort
+  void *ref;          // T4 [n]: pos at the sort (displacement check)
+  int *pcell;         // [n] cell of the last sort
+  int *cell_tmp, *rank;       // [n] binning scratch
+  int *count, *cell_start;    // [ncell], [ncell + 1]
+  int *nbr, *nbr_cnt;         // [maxnb][nb_stride] column-major, [n]
+  void *partial;              // T [27][3][n] per-stencil-slot ATM partial forces
+  double *acc;                // [ACC_N]
+  unsigned long long *ctr;    // [CTR_N]
+  int *flags;                 // [FLG_N]
+};
+
+// particle-range work item: threads handle sorted slots [begin, begin + blockDim)
+struct PItem {
+  int sys;
+  int begin;
+  int mode;  // kernel-specific mode bits
+  int buf;   // position buffer index read (and, for drifting kernels, the one written is buf_out)
+};
+
+// base-cell work item for the ATM kernel
+struct CItem {
+  int sys;
+  int cell;
+  int buf;
+  int mode;
+};
+
+// per-system work item (one CTA per system)
+struct SItem {
+  int sys;
+  int mode;
+};
+
+// mode bits
+enum : int {
+  M_ENERGY = 1 << 8,    // accumulate energies / virials
+  M_KIND_MASK = 0xff,
+};
+enum : int {  // LJ kinds
+  LJ_INIT = 0,   // forces (and energy) only
+  LJ_MID = 1,    // forces; v += dt F2 / m; x += dt v  (closing half kick of this step + opening of the next)
+  LJ_LAST = 2,   // forces; v += dt/2 F2 / m (closing half kick before the ATM evaluation)
+};
+enum : int {  // combine kinds
+  CB_INIT = 0,   // F3 only
+  CB_LAST = 1,   // F3; v += dt_outer/2 F3 / m
+  CB_CONT = 2,   // F3; v += dt_outer F3 / m + dt/2 F2 / m; x += dt v  (next outer step starts)
+};
+
+// ---------------------------------------------------------------- helpers
+
+template <typename T> struct V4;
+template <> struct V4<float> { using type = float4; };
+template <> struct V4<double> { using type = double4_32a; };
+
+__device__ __forceinline__ double wrap_box(double x, double L) {
+  double y = x - L * floor(x / L);
+  if (y >= L) y -= L;
+  if (y < 0.0) y = 0.0;
+  return y;
+}
+
+__device__ __forceinline__ int cell_coord(double x, double inv_edge, int nc) {
+  int c = (int)floor(x * inv_edge);
+  return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
+}
+
+// Exact cutoff decision in IEEE double with the same operation order as the
+// CPU reference definition: d = xj - xi; d -= L * rint(d / L) per axis;
+// r2 = (dx*dx + dy*dy) + dz*dz; counts iff r2 <= rcsq.  The _rn intrinsics
+// forbid fused multiply-add contraction, so the result is bit-identical to a
+// plain IEEE evaluation.
+__device__ __forceinline__ bool exact_within(const double* __restrict__ X, int n, int i, int j, double L,
+                                             double rcsq) {
+  double r2 = 0.0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    double d = __dsub_rn(X[a * n + j], X[a * n + i]);
+    d = __dsub_rn(d, __dmul_rn(L, rint(__ddiv_rn(d, L))));
+    r2 = (a == 0) ? __dmul_rn(d, d) : __dadd_rn(r2, __dmul_rn(d, d));
+  }
+  return r2 <= rcsq;
+}
+
+// error-free transformation s + e = a + b (Knuth TwoSum)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// compensated accumulator (hi, lo) += t
+struct CompF {
+  float hi, lo;
+  __device__ __forceinline__ void add(float t) {
+    float s, e;
+    two_sum(hi, t, s, e);
+    hi = s;
+    lo = __fadd_rn(lo, e);
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+template <typename T>
+__device__ __forceinline__ T warp_sum_t(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sumf(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// block-wide sum of one double per thread; every thread must call; result valid in thread 0
+__device__ __forceinline__ double block_sum(double v, double* smem32) {
+  v = warp_sum(v);
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) smem32[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (w == 0) {
+    int nw = (blockDim.x + 31) >> 5;
+    r = lane < nw ? smem32[lane] : 0.0;
+    r = warp_sum(r);
+  }
+  return r;
+}
+
+// ---------------------------------------------------------------- launchers
+struct Launch {
+  cudaStream_t stream;
+  const SysDev* sys;  // device array of systems
+};
+
+// sort.cu
+void launch_bin_count(const Launch& L, const PItem* items, int nitems, int block);
+void launch_scan(const Launch& L, const SItem* items, int nitems);
+template <typename T> void launch_scatter(const Launch& L, const PItem* items, int nitems, int block);
+template <typename T> void launch_listbuild(const Launch& L, const PItem* items, int nitems, int block);
+// forces.cu
+template <typename T> void launch_lj(const Launch& L, const PItem* items, int nitems, int block);
+template <typename T> void launch_atm(const Launch& L, const CItem* items, int nitems, int grid, int smax);
+// dynamic shared memory of the ATM kernel for smax staged particles; sets the kernel attribute
+// and returns the resident CTAs per SM (0 if it does not fit)
+int atm_configure(int smax, int precision, int* smem_bytes);
+template <typename T> void launch_combine(const Launch& L, const PItem* items, int nitems, int block);
+template <typename T> void launch_start(const Launch& L, const PItem* items, int nitems, int block);
+void launch_kinetic(const Launch& L, const PItem* items, int nitems, int block);
+void launch_nonfinite_check(const Launch& L, const PItem* items, int nitems, int block);
+void atm_prepare_table(cudaStream_t s);
+
+}  // namespace r3b

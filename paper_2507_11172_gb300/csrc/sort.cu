@@ -1,0 +1,209 @@
+// Cell-binning counting sort and Verlet pair-list build (linked cells, Sec. 2.2 / Sec. 4.1).
+//
+// Per sort: bin_count (wrap into [0, L), cell id, atomic rank within the
+// cell) -> scan (exclusive prefix over cells, resets counts) -> scatter
+// (permute positions, velocities, ids into cell order; write the cell-local
+// coordinates used by the force kernels) -> listbuild (pair list with skin,
+// copies the permuted state back into place).
+#include "md_internal.cuh"
+
+namespace r3b {
+
+__global__ void k_bin_count(const SysDev* __restrict__ sys, const PItem* __restrict__ items) {
+  const PItem it = items[blockIdx.x];
+  const SysDev& S = sys[it.sys];
+  int p = it.begin + threadIdx.x;
+  if (p >= S.n) return;
+  double* X = S.X[it.buf];
+  const int n = S.n;
+  int c[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    double x = wrap_box(X[a * n + p], S.L);
+    X[a * n + p] = x;
+    c[a] = cell_coord(x, S.inv_edge, S.nc);
+  }
+  int cell = (c[2] * S.nc + c[1]) * S.nc + c[0];
+  S.cell_tmp[p] = cell;
+  S.rank[p] = atomicAdd(&S.count[cell], 1);
+}
+
+// One 1024-thread CTA per system: exclusive scan of count[] into
+// cell_start[], count[] reset to zero, largest occupancy checked.
+__global__ void __launch_bounds__(1024) k_scan(const SysDev* __restrict__ sys, const SItem* __restrict__ items) {
+  const SysDev& S = sys[items[blockIdx.x].sys];
+  __shared__ int wsum[32];
+  __shared__ int wmax[32];
+  const int ncell = S.ncell;
+  const int chunk = (ncell + blockDim.x - 1) / blockDim.x;
+  const int b = threadIdx.x * chunk;
+  const int e = min(b + chunk, ncell);
+  int local = 0, mx = 0;
+  for (int c = b; c < e; ++c) {
+    int v = S.count[c];
+    local += v;
+    mx = max(mx, v);
+  }
+  // block exclusive scan of local
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int incl = local;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  int m = mx;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 31) wsum[w] = incl;
+  if (lane == 0) wmax[w] = m;
+  __syncthreads();
+  if (w == 0) {
+    int nw = blockDim.x >> 5;
+    int s = lane < nw ? wsum[lane] : 0;
+    int mm = lane < nw ? wmax[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int t = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += t;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mm = max(mm, __shfl_xor_sync(0xffffffffu, mm, o));
+    if (lane < nw) wsum[lane] = s;  // inclusive warp totals
+    if (lane == 0) wmax[0] = mm;
+  }
+  __syncthreads();
+  int run = incl - local + (w > 0 ? wsum[w - 1] : 0);
+  for (int c = b; c < e; ++c) {
+    int v = S.count[c];
+    S.cell_start[c] = run;
+    run += v;
+    S.count[c] = 0;
+  }
+  if (threadIdx.x == blockDim.x - 1) S.cell_start[ncell] = run;
+  if (threadIdx.x == 0) {
+    int mxc = wmax[0];
+    atomicMax(&S.flags[FLG_MAXCELL], mxc);
+    if (mxc > S.cap_cell) atomicOr(&S.flags[FLG_ERR], ERR_CELL_CAP);
+  }
+}
+
+template <typename T>
+__global__ void k_scatter(const SysDev* __restrict__ sys, const PItem* __restrict__ items) {
+  using T4 = typename V4<T>::type;
+  const PItem it = items[blockIdx.x];
+  const SysDev& S = sys[it.sys];
+  int p = it.begin + threadIdx.x;
+  if (p >= S.n) return;
+  const int n = S.n;
+  const int cell = S.cell_tmp[p];
+  const int q = S.cell_start[cell] + S.rank[p];
+  const double* X = S.X[it.buf];
+  double* Xa = S.X[it.buf ^ 1];
+  int cx = cell % S.nc, cy = (cell / S.nc) % S.nc, cz = cell / (S.nc * S.nc);
+  double ctr[3] = {(cx + 0.5) * S.edge, (cy + 0.5) * S.edge, (cz + 0.5) * S.edge};
+  T hi[3], lo[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    double x = X[a * n + p];
+    Xa[a * n + q] = x;
+    S.v_alt[a * n + q] = S.v[a * n + p];
+    double rel = x - ctr[a];
+    hi[a] = (T)rel;
+    lo[a] = (T)(rel - (double)hi[a]);
+  }
+  S.id_alt[q] = S.id[p];
+  S.pcell[q] = cell;
+  T4 h;
+  h.x = hi[0]; h.y = hi[1]; h.z = hi[2]; h.w = (T)0;
+  T4 l;
+  l.x = lo[0]; l.y = lo[1]; l.z = lo[2]; l.w = (T)0;
+  reinterpret_cast<T4*>(S.pos[it.buf])[q] = h;
+  reinterpret_cast<T4*>(S.poslo)[q] = l;
+  reinterpret_cast<T4*>(S.ref)[q] = h;
+}
+
+// Pair list with skin: every j != i in the 27 cells around i's cell with
+// |d|^2 <= (r_c2 + skin)^2 (slightly widened: the list may hold a superset).
+// Entry = j | image code << 27, code = (dz+1)*9 + (dy+1)*3 + (dx+1) for the
+// cell offset from i's cell to j's cell.  Also moves the permuted state back.
+template <typename T>
+__global__ void k_listbuild(const SysDev* __restrict__ sys, const PItem* __restrict__ items) {
+  using T4 = typename V4<T>::type;
+  const PItem it = items[blockIdx.x];
+  const SysDev& S = sys[it.sys];
+  int i = it.begin + threadIdx.x;
+  if (i >= S.n) return;
+  const int n = S.n, nc = S.nc;
+  const T4* __restrict__ P = reinterpret_cast<const T4*>(S.pos[it.buf]);
+  const T4 pi = P[i];
+  const int cell = S.pcell[i];
+  const int cx = cell % nc, cy = (cell / nc) % nc, cz = cell / (nc * nc);
+  const T edge = (T)S.edge;
+  const T rl = (T)(S.rlistsq * (1.0 + 1e-5));
+  int cnt = 0;
+  for (int dz = -1; dz <= 1; ++dz) {
+    int zz = cz + dz;
+    zz += (zz < 0) ? nc : 0;
+    zz -= (zz >= nc) ? nc : 0;
+    for (int dy = -1; dy <= 1; ++dy) {
+      int yy = cy + dy;
+      yy += (yy < 0) ? nc : 0;
+      yy -= (yy >= nc) ? nc : 0;
+      for (int dx = -1; dx <= 1; ++dx) {
+        int xx = cx + dx;
+        xx += (xx < 0) ? nc : 0;
+        xx -= (xx >= nc) ? nc : 0;
+        const int c2 = (zz * nc + yy) * nc + xx;
+        const unsigned code = (unsigned)((dz + 1) * 9 + (dy + 1) * 3 + (dx + 1));
+        const T sx = (T)dx * edge, sy = (T)dy * edge, sz = (T)dz * edge;
+        const int j0 = S.cell_start[c2], j1 = S.cell_start[c2 + 1];
+        for (int j = j0; j < j1; ++j) {
+          if (j == i) continue;
+          T4 pj = P[j];
+          T ddx = (pj.x - pi.x) + sx, ddy = (pj.y - pi.y) + sy, ddz = (pj.z - pi.z) + sz;
+          T r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+          if (r2 <= rl) {
+            if (cnt < S.maxnb) S.nbr[(size_t)cnt * S.nb_stride + i] = (int)((unsigned)j | (code << kNbrShift));
+            ++cnt;
+          }
+        }
+      }
+    }
+  }
+  if (cnt > S.maxnb) {
+    atomicOr(&S.flags[FLG_ERR], ERR_NBR_CAP);
+    cnt = S.maxnb;
+  }
+  S.nbr_cnt[i] = cnt;
+  // move the permuted state into place
+  const double* Xa = S.X[it.buf ^ 1];
+  double* X = S.X[it.buf];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    X[a * n + i] = Xa[a * n + i];
+    S.v[a * n + i] = S.v_alt[a * n + i];
+  }
+  S.id[i] = S.id_alt[i];
+}
+
+void launch_bin_count(const Launch& L, const PItem* items, int nitems, int block) {
+  if (nitems > 0) k_bin_count<<<nitems, block, 0, L.stream>>>(L.sys, items);
+}
+void launch_scan(const Launch& L, const SItem* items, int nitems) {
+  if (nitems > 0) k_scan<<<nitems, 1024, 0, L.stream>>>(L.sys, items);
+}
+template <typename T>
+void launch_scatter(const Launch& L, const PItem* items, int nitems, int block) {
+  if (nitems > 0) k_scatter<T><<<nitems, block, 0, L.stream>>>(L.sys, items);
+}
+template <typename T>
+void launch_listbuild(const Launch& L, const PItem* items, int nitems, int block) {
+  if (nitems > 0) k_listbuild<T><<<nitems, block, 0, L.stream>>>(L.sys, items);
+}
+template void launch_scatter<float>(const Launch&, const PItem*, int, int);
+template void launch_scatter<double>(const Launch&, const PItem*, int, int);
+template void launch_listbuild<float>(const Launch&, const PItem*, int, int);
+template void launch_listbuild<double>(const Launch&, const PItem*, int, int);
+
+}  // namespace r3b

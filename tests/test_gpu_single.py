@@ -1,0 +1,227 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU FP64 oracle.
+
+Tolerances (force error e_i = |F_i - F_i^ref| / max(|F_i^ref|, F_rms^ref),
+checked separately for the LJ and the ATM field):
+  FP32 path (FP32 forces, compensated accumulation): max_i e_i <= 1e-5
+  FP64 path: max_i e_i <= 1e-12
+  energies: |E - E_ref| / (E_kin + |U2| + |U3|) <= 1e-6
+Interacting-triplet counts are integers and must match exactly.
+"""
+import numpy as np
+import pytest
+
+import md_inputs
+import oracle
+from oracle import respa
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-5, 1: 1e-12}
+NU = 0.073
+
+
+def force_err(got, ref):
+    frms = np.sqrt((ref ** 2).sum(1).mean())
+    floor = max(frms, 1e-300)
+    return float((np.linalg.norm(got - ref, axis=1) / np.maximum(np.linalg.norm(ref, axis=1), floor)).max())
+
+
+def make(r3, w, prec, nu=NU, rc2=2.5, rc3=2.5, skin=None):
+    return r3.System.create(w.x, w.L, w.v, precision=prec, nu=nu, rc_pair=rc2, rc_triplet=rc3, skin=skin)
+
+
+@pytest.fixture(scope="module")
+def cfg1():
+    return md_inputs.small_fcc_1k()
+
+
+@pytest.fixture(scope="module")
+def cfg1_ref(cfg1):
+    f2, u2, w2 = oracle.lj_brute(cfg1.x, cfg1.L, 1.0, 1.0, 2.5)
+    f3, u3, w3, cnt = oracle.atm_brute(cfg1.x, cfg1.L, NU, 2.5)
+    return dict(f2=f2, u2=u2, w2=w2, f3=f3, u3=u3, w3=w3, cnt=cnt, ek=oracle.kinetic(cfg1.v))
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_forces_and_energy_at_x0(gpu_lib, cfg1, cfg1_ref, prec):
+    r3 = gpu_lib
+    with make(r3, cfg1, prec) as s:
+        f2, f3 = s.forces()
+        ek, u2, u3, w = s.energy()
+        st = s.stats()
+    ref = cfg1_ref
+    assert force_err(f2, ref["f2"]) <= TOL[prec]
+    assert force_err(f3, ref["f3"]) <= TOL[prec]
+    assert st["triplets_last"] == ref["cnt"]
+    scale = ref["ek"] + abs(ref["u2"]) + abs(ref["u3"])
+    etol = 1e-6 if prec == 0 else 1e-12
+    assert abs(u2 - ref["u2"]) / scale <= etol
+    assert abs(u3 - ref["u3"]) / scale <= etol
+    assert abs(ek - ref["ek"]) / scale <= 1e-12
+    assert abs(w - (ref["w2"] + ref["w3"])) / (abs(ref["w2"]) + abs(ref["w3"])) <= 10 * etol
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_trajectory_matches_algorithm2(gpu_lib, cfg1, prec):
+    """10 outer steps of k = 5 (dt_outer = 0.01): positions, velocities, forces, energy."""
+    r3 = gpu_lib
+    st = respa.State(cfg1.x.copy(), cfg1.v.copy(), cfg1.L)
+    f2b, f3b = respa.lj_atm_forces(cfg1.L, 1.0, 1.0, 2.5, NU, 2.5)
+    respa.run(st, 10, 5, 0.01, f2b, f3b)
+    with make(r3, cfg1, prec) as s:
+        s.step(4, 5, 0.01)  # split calls: forces are cached across calls
+        s.step(6, 5, 0.01)
+        x, v = s.state()
+        f2, f3 = s.forces()
+        ek, u2, u3, _ = s.energy()
+        stats = s.stats()
+    d = x - st.x
+    d -= cfg1.L * np.rint(d / cfg1.L)
+    xtol, vtol = (2e-5, 2e-4) if prec == 0 else (1e-10, 1e-9)
+    assert np.abs(d).max() < xtol
+    assert np.abs(v - st.v).max() < vtol
+    ftol = 1e-4 if prec == 0 else 1e-9  # forces at slightly different positions
+    assert force_err(f2, st.f2) < ftol and force_err(f3, st.f3) < ftol
+    e_ref = oracle.kinetic(st.v) + st.u2 + st.u3
+    scale = oracle.kinetic(st.v) + abs(st.u2) + abs(st.u3)
+    assert abs(ek + u2 + u3 - e_ref) / scale <= (1e-6 if prec == 0 else 1e-10)
+    assert stats["outer_steps"] == 10 and stats["atm_evals"] == 11
+
+
+@pytest.mark.parametrize("k", [1, 3])
+def test_step_size_factor_variants(gpu_lib, cfg1, k):
+    """k = 1 is Stormer-Verlet on F2 + F3 (Sec. 4.1); odd k exercises the buffer parity."""
+    r3 = gpu_lib
+    st = respa.State(cfg1.x.copy(), cfg1.v.copy(), cfg1.L)
+    f2b, f3b = respa.lj_atm_forces(cfg1.L, 1.0, 1.0, 2.5, NU, 2.5)
+    respa.run(st, 3, k, 0.002 * k, f2b, f3b)
+    with make(r3, cfg1, 1) as s:
+        s.step(1, k, 0.002 * k)
+        s.step(2, k, 0.002 * k)
+        x, v = s.state()
+    d = x - st.x
+    d -= cfg1.L * np.rint(d / cfg1.L)
+    assert np.abs(d).max() < 1e-10 and np.abs(v - st.v).max() < 1e-9
+
+
+@pytest.mark.parametrize("n,L", [(37, 9.0), (300, 9.0), (777, 10.0), (1283, 11.7)])
+def test_ragged_sizes_and_densities(gpu_lib, n, L):
+    rng = np.random.default_rng(n)
+    x, _ = md_inputs.rsa(n, n / L ** 3, 0.85, 100 + n)
+    L = (n / (n / L ** 3)) ** (1 / 3)
+    v = np.zeros_like(x)
+    f2r, u2r, _ = oracle.lj_brute(x, L, 1.0, 1.0, 2.5)
+    f3r, u3r, _, cnt = oracle.atm_brute(x, L, 0.5, 2.5)
+    for prec in (0, 1):
+        with gpu_lib.System.create(x, L, v, precision=prec, nu=0.5) as s:
+            f2, f3 = s.forces()
+            assert s.stats()["triplets_last"] == cnt
+        if cnt:
+            assert force_err(f3, f3r) <= TOL[prec]
+        assert force_err(f2, f2r) <= TOL[prec]
+    del rng
+
+
+def test_distances_exactly_at_the_cutoff(gpu_lib):
+    """Simple cubic lattice, spacing 1.25, r_c = 2.5: pairs and collinear triplets sit exactly
+    on the cutoff; both sides must include them (r <= r_c) and agree on the count."""
+    b, m = 1.25, 8
+    g = np.arange(m) * b
+    x = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3).copy()
+    L = m * b
+    x[5] += [0.01, 0.0, 0.0]  # break the lattice symmetry a little
+    f3r, u3r, _, cnt = oracle.atm_brute(x, L, NU, 2.5)
+    f2r, u2r, _ = oracle.lj_brute(x, L, 1.0, 1.0, 2.5)
+    for prec in (0, 1):
+        with gpu_lib.System.create(x, L, None, precision=prec, nu=NU, skin=0.1) as s:
+            f2, f3 = s.forces()
+            _, u2, u3, _ = s.energy()
+            assert s.stats()["triplets_last"] == cnt
+            assert s.stats()["guard_rechecks"] > 0
+        assert force_err(f3, f3r) <= TOL[prec]
+        assert force_err(f2, f2r) <= TOL[prec]
+        assert abs(u3 - u3r) <= 1e-6 * abs(u3r) + 1e-12
+
+
+def test_nu_zero_gives_zero_triplet_force(gpu_lib, cfg1):
+    with make(gpu_lib, cfg1, 0, nu=0.0) as s:
+        _, f3 = s.forces()
+        _, _, u3, _ = s.energy()
+    assert np.all(f3 == 0.0) and u3 == 0.0
+
+
+def test_skin_violation_replays_exactly(gpu_lib, cfg1):
+    """A tiny skin makes particles leave it within an outer step; the call is replayed with a
+    list rebuild on every inner step, so the trajectory still matches Algorithm 2."""
+    st = respa.State(cfg1.x.copy(), cfg1.v.copy(), cfg1.L)
+    f2b, f3b = respa.lj_atm_forces(cfg1.L, 1.0, 1.0, 2.5, NU, 2.5)
+    respa.run(st, 3, 5, 0.01, f2b, f3b)
+    with make(gpu_lib, cfg1, 1, skin=0.002) as s:
+        s.step(3, 5, 0.01)
+        x, v = s.state()
+        assert s.stats()["replays"] >= 1
+    d = x - st.x
+    d -= cfg1.L * np.rint(d / cfg1.L)
+    assert np.abs(d).max() < 1e-10
+
+
+def test_dense_cluster_grows_cell_capacity(gpu_lib):
+    """All particles in one corner of a large box: cells overflow their first capacity, the
+    library grows it and replays; results must still match the oracle."""
+    xc, Lc = md_inputs.fcc_jitter(400, 1.0, 0.05, 77)
+    L = 30.0
+    x = xc + 1.0
+    f3r, _, _, cnt = oracle.atm_brute(x, L, NU, 2.5)
+    f2r, _, _ = oracle.lj_brute(x, L, 1.0, 1.0, 2.5)
+    with gpu_lib.System.create(x, L, None, precision=0, nu=NU) as s:
+        f2, f3 = s.forces()
+        assert s.stats()["triplets_last"] == cnt
+    assert force_err(f2, f2r) <= 1e-5 and force_err(f3, f3r) <= 1e-5
+
+
+def test_errors_are_reported(gpu_lib, cfg1):
+    r3 = gpu_lib
+    bad = cfg1.x.copy()
+    bad[3, 1] = np.nan
+    with pytest.raises(r3.MDError) as e:
+        r3.System.create(bad, cfg1.L)
+    assert e.value.status == -4
+    with pytest.raises(r3.MDError) as e:
+        r3.System.create(cfg1.x, 7.0)
+    assert e.value.status == -3
+    with make(r3, cfg1, 0) as s:
+        with pytest.raises(r3.MDError) as e:
+            s.step(1, 0, 0.01)
+        assert e.value.status == -1
+        with pytest.raises(r3.MDError):
+            r3.md_set_potentials(s.handle, 1.0, 1.0, 3.6, NU, 2.5)  # 3 * (3.6 + skin) > L
+
+
+def test_checkpoint_resume(gpu_lib, cfg1):
+    """Run A: 5 outer steps.  Run B: 3 steps, save state, new handle, 2 steps."""
+    r3 = gpu_lib
+    with make(r3, cfg1, 1) as a:
+        a.step(5, 4, 0.008)
+        xa, va = a.state()
+    with make(r3, cfg1, 1) as b:
+        b.step(3, 4, 0.008)
+        xb, vb = b.state()
+    with r3.System.create(xb, cfg1.L, vb, precision=1, nu=NU) as c:
+        c.step(2, 4, 0.008)
+        xc, vc = c.state()
+    d = xc - xa
+    d -= cfg1.L * np.rint(d / cfg1.L)
+    assert np.abs(d).max() < 1e-11 and np.abs(vc - va).max() < 1e-10
+
+
+@pytest.mark.parametrize("prec,ptol", [(0, 1e-4), (1, 1e-9)])
+def test_momentum_and_energy_conservation(gpu_lib, cfg1, prec, ptol):
+    with make(gpu_lib, cfg1, prec) as s:
+        ek0, u20, u30, _ = s.energy()
+        p0 = s.state()[1].sum(0)
+        s.step(20, 5, 0.01)
+        ek, u2, u3, _ = s.energy()
+        p = s.state()[1].sum(0)
+    e0, e1 = ek0 + u20 + u30, ek + u2 + u3
+    assert np.abs(p - p0).max() < ptol  # Newton 3: pair and triplet forces sum to zero
+    assert abs(e1 - e0) / (ek0 + abs(u20) + abs(u30)) < 5e-3  # truncated potentials: bounded jumps only
