@@ -113,8 +113,9 @@ md_status md_get_energy(md_system *s, double *e_kin, double *u2, double *u3, dou
 md_status md_get_state(md_system *s, double *pos, double *vel);
 md_status md_set_state(md_system *s, const double *pos, const double *vel);
 
-/* Counters (see md_stats).  profile = 1 turns on CUDA-event timing of every
- * ATM launch (atm_ms_total / atm_timed). */
+/* Counters (see md_stats).  profile = 1 launches a call's kernels one by one
+ * (instead of replaying a captured CUDA graph) with CUDA events recorded on
+ * the system's stream around every ATM launch (atm_ms_total / atm_timed). */
 md_status md_get_stats(md_system *s, md_stats *out);
 md_status md_set_profiling(md_system *s, int profile);
 

@@ -67,7 +67,7 @@ struct md_system {
   int precision = MD_FP32;
   double eps = 1.0, sigma = 1.0, rc2 = 2.5, nu = 0.0, rc3 = 2.5, skin = 0.3;
   // grid and capacities
-  int nc = 0, ncell = 0, cap_cell = 0, maxnb = 0, nb_stride = 0;
+  int nc = 0, ncell = 0, cap_cell = 0, maxnb = 0;
   double edge = 0;
   // device memory
   char* mem = nullptr;
@@ -82,7 +82,7 @@ struct md_system {
   std::map<std::tuple<int, int>, CItem*> citems;        // (mode, buf)
   SItem* sitem = nullptr;
   std::vector<void*> item_allocs;
-  int nblocks = 0;
+  int nblocks = 0, nblocks_lj = 0;
   // execution
   cudaStream_t stream = nullptr;
   bool own_stream = false;
@@ -148,13 +148,12 @@ void choose_grid(md_system* s) {
   s->ncell = nc * nc * nc;
   s->edge = s->L / nc;
   double mean = (double)s->n / s->ncell;
-  if (s->cap_cell == 0) s->cap_cell = std::max(16, (int)ceil(1.6 * mean + 12.0));
+  if (s->cap_cell == 0) s->cap_cell = std::max(16, (int)ceil(1.25 * mean + 10.0));
   double rho = (double)s->n / (s->L * s->L * s->L);
   double rl = s->rc2 + s->skin;
   double nl = rho * 4.18879020478639 * rl * rl * rl;
   if (s->maxnb == 0) s->maxnb = std::max(32, (int)ceil(1.35 * nl + 24.0));
   s->maxnb = std::min(s->maxnb, (int)s->n);
-  s->nb_stride = (int)((s->n + 31) / 32 * 32);
 }
 
 md_status alloc_device(md_system* s) {
@@ -170,7 +169,7 @@ md_status alloc_device(md_system* s) {
   size_t o_p0 = a.reserve(t4 * n), o_p1 = a.reserve(t4 * n), o_plo = a.reserve(t4 * n), o_ref = a.reserve(t4 * n);
   size_t o_pcell = a.reserve(4 * n), o_ctmp = a.reserve(4 * n), o_rank = a.reserve(4 * n);
   size_t o_count = a.reserve(4 * (size_t)s->ncell), o_cstart = a.reserve(4 * ((size_t)s->ncell + 1));
-  size_t o_nbr = a.reserve(4 * (size_t)s->maxnb * s->nb_stride), o_nbc = a.reserve(4 * n);
+  size_t o_nbr = a.reserve(4 * (size_t)s->maxnb * n), o_nbc = a.reserve(4 * n);
   size_t o_part = a.reserve(tsz * 27 * 3 * n);
   size_t o_acc = a.reserve(8 * ACC_N), o_ctr = a.reserve(8 * CTR_N), o_flg = a.reserve(4 * FLG_N);
   size_t o_sx = a.reserve(24 * n), o_sv = a.reserve(24 * n), o_sf2 = a.reserve(24 * n), o_sf3 = a.reserve(24 * n);
@@ -250,7 +249,7 @@ md_status upload_desc(md_system* s, double dt_in, double dt_out) {
   h.mass = s->mass;
   h.inv_mass = 1.0 / s->mass;
   h.maxnb = s->maxnb;
-  h.nb_stride = s->nb_stride;
+  h.cap_stage = 27 * s->cap_cell;
   h.precision = s->precision;
   CK(cudaMemcpyAsync(s->d_sys, &h, sizeof(SysDev), cudaMemcpyHostToDevice, s->stream));
   return MD_OK;
@@ -270,7 +269,9 @@ PItem* pitems_for(md_system* s, int tag, int mode, int buf) {
   auto it = s->pitems.find(key);
   if (it != s->pitems.end()) return it->second;
   std::vector<PItem> v;
-  for (int b = 0; b < s->nblocks; ++b) v.push_back(PItem{0, b * kBlock, mode, buf});
+  const int per = (tag == T_LJ) ? kBlock / kLjTeam : kBlock;  // particles per block
+  const int nb = (tag == T_LJ) ? s->nblocks_lj : s->nblocks;
+  for (int b = 0; b < nb; ++b) v.push_back(PItem{0, b * per, mode, buf});
   PItem* d = upload_items(s, v);
   s->pitems[key] = d;
   return d;
@@ -291,10 +292,11 @@ CItem* citems_for(md_system* s, int mode, int buf) {
 // all item variants a call can use, created before any graph capture
 md_status prepare_items(md_system* s) {
   s->nblocks = (int)((s->n + kBlock - 1) / kBlock);
+  const int per_lj = kBlock / kLjTeam;
+  s->nblocks_lj = (int)((s->n + per_lj - 1) / per_lj);
   for (int b = 0; b < 2; ++b) {
     pitems_for(s, T_BIN, 0, b);
     pitems_for(s, T_SCATTER, 0, b);
-    pitems_for(s, T_LIST, 0, b);
     pitems_for(s, T_START, 0, b);
     for (int e = 0; e < 2; ++e) {
       int E = e ? M_ENERGY : 0;
@@ -330,6 +332,10 @@ md_status configure_atm(md_system* s) {
     return MD_ERR_CAPACITY;
   }
   s->atm_smem = bytes;
+  if (listbuild_configure(27 * s->cap_cell, s->precision) < 0) {
+    g_last_error = "pair-list build does not fit in shared memory for cap_cell=" + std::to_string(s->cap_cell);
+    return MD_ERR_CAPACITY;
+  }
   s->atm_grid = std::min(s->ncell, per_sm * device_sm_count());
   return MD_OK;
 }
@@ -379,11 +385,11 @@ struct Plan {
     launch_bin_count(L, pitems_for(s, T_BIN, 0, buf), s->nblocks, kBlock);
     launch_scan(L, s->sitem, 1);
     launch_scatter<T>(L, pitems_for(s, T_SCATTER, 0, buf), s->nblocks, kBlock);
-    launch_listbuild<T>(L, pitems_for(s, T_LIST, 0, buf), s->nblocks, kBlock);
+    launch_listbuild<T>(L, citems_for(s, 0, buf), s->ncell, 27 * s->cap_cell);
   }
   template <typename T>
   void lj(int kind, int buf, bool energy) {
-    launch_lj<T>(L, pitems_for(s, T_LJ, kind | (energy ? M_ENERGY : 0), buf), s->nblocks, kBlock);
+    launch_lj<T>(L, pitems_for(s, T_LJ, kind | (energy ? M_ENERGY : 0), buf), s->nblocks_lj, kBlock);
   }
   template <typename T>
   void atm(int buf, bool energy, int ev) {
@@ -490,6 +496,19 @@ md_status run_plan(md_system* s, int n_outer, int k, bool init, bool safe) {
   if (st != MD_OK) return st;
   Plan P{s, Launch{s->stream, s->d_sys}};
   auto key = std::make_tuple(init ? -1 - n_outer : n_outer, k, s->cur, safe ? 1 : 0, prof ? 1 : 0);
+  if (prof) {
+    // profiling: direct launches so the ATM kernel can be timed with events recorded on the
+    // stream (events recorded by graph nodes cannot be read back with cudaEventElapsedTime)
+    if (s->precision) {
+      if (init) enqueue_init<double>(P, nev - 1);
+      enqueue_steps<double>(P, n_outer, k, s->cur, safe, true);
+    } else {
+      if (init) enqueue_init<float>(P, nev - 1);
+      enqueue_steps<float>(P, n_outer, k, s->cur, safe, true);
+    }
+    CK(cudaGetLastError());
+    return MD_OK;
+  }
   cudaGraphExec_t exec = nullptr;
   auto it = s->graphs.find(key);
   if (it != s->graphs.end()) {
@@ -498,11 +517,11 @@ md_status run_plan(md_system* s, int n_outer, int k, bool init, bool safe) {
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
     if (s->precision) {
-      if (init) enqueue_init<double>(P, prof ? nev - 1 : -1);
-      enqueue_steps<double>(P, n_outer, k, s->cur, safe, prof);
+      if (init) enqueue_init<double>(P, -1);
+      enqueue_steps<double>(P, n_outer, k, s->cur, safe, false);
     } else {
-      if (init) enqueue_init<float>(P, prof ? nev - 1 : -1);
-      enqueue_steps<float>(P, n_outer, k, s->cur, safe, prof);
+      if (init) enqueue_init<float>(P, -1);
+      enqueue_steps<float>(P, n_outer, k, s->cur, safe, false);
     }
     cudaError_t e = cudaStreamEndCapture(s->stream, &g);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
@@ -522,9 +541,13 @@ md_status finish_call(md_system* s, int n_outer) {
   if (s->profile) {
     for (int o = 0; o < n_outer; ++o) {
       float ms = 0;
-      if (cudaEventElapsedTime(&ms, s->events[2 * o], s->events[2 * o + 1]) == cudaSuccess) {
+      cudaError_t e = cudaEventElapsedTime(&ms, s->events[2 * o], s->events[2 * o + 1]);
+      if (e == cudaSuccess) {
         s->stats.atm_ms_total += ms;
         s->stats.atm_timed += 1;
+      } else {
+        g_last_error = std::string("cudaEventElapsedTime: ") + cudaGetErrorString(e);
+        cudaGetLastError();  // non-fatal: do not leave the error pending for other CUDA users
       }
     }
   }

@@ -96,8 +96,30 @@ __device__ __forceinline__ void store_pos(const SysDev& S, int buf, int i, const
 }
 
 // ============================================================== LJ pair kernel
+// A team of kLjTeam lanes shares one particle i: lane t of the team walks list
+// entries t, t + kLjTeam, ... (unrolled so several gathers are in flight), sums
+// its share in a compensated (hi, lo) accumulator, and the team combines the
+// shares with error-free TwoSum steps.  The team's first lane then applies the
+// velocity-Verlet kick/drift of Algorithm 2 for i.
 template <typename T>
-__global__ void __launch_bounds__(256) k_lj(const SysDev* __restrict__ sys, const PItem* __restrict__ items) {
+__device__ __forceinline__ void team_sum(CompF& c) {
+#pragma unroll
+  for (int o = kLjTeam / 2; o > 0; o >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, c.hi, o);
+    const float ol = __shfl_xor_sync(0xffffffffu, c.lo, o);
+    float s, e;
+    two_sum(c.hi, oh, s, e);
+    c.hi = s;
+    c.lo = c.lo + (ol + e);
+  }
+}
+__device__ __forceinline__ void team_sum_d(double& v) {
+#pragma unroll
+  for (int o = kLjTeam / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256, 4) k_lj(const SysDev* __restrict__ sys, const PItem* __restrict__ items) {
   using T4 = typename V4<T>::type;
   __shared__ double red[32];
   const PItem it = items[blockIdx.x];
@@ -105,24 +127,25 @@ __global__ void __launch_bounds__(256) k_lj(const SysDev* __restrict__ sys, cons
   const int kind = it.mode & M_KIND_MASK;
   const bool energy = (it.mode & M_ENERGY) != 0;
   const int n = S.n;
-  const int i = it.begin + threadIdx.x;
-  double u_out = 0.0, w_out = 0.0;
-  if (i < n) {
-    const T4* __restrict__ P = reinterpret_cast<const T4*>(S.pos[it.buf]);
-    const double* __restrict__ X = S.X[it.buf];
+  const int tl = threadIdx.x % kLjTeam;
+  const int i = it.begin + threadIdx.x / kLjTeam;
+  const bool active = i < n;
+  const T4* __restrict__ P = reinterpret_cast<const T4*>(S.pos[it.buf]);
+  const double* __restrict__ X = S.X[it.buf];
+  Acc3<T> f;
+  AccS<T> u, w;
+  if (active) {
     const T4 pi = P[i];
     const T edge = (T)S.edge;
     const T rcsq = (T)S.rc2sq;
     const T g2 = (T)S.guard2;
     const T sig2 = (T)S.sig2;
     const T eps24 = (T)(24.0 * S.eps), eps4 = (T)(4.0 * S.eps);
-    Acc3<T> f;
-    AccS<T> u, w;
     const int cnt = S.nbr_cnt[i];
-    const int* __restrict__ nb = S.nbr + i;
-    const size_t stride = (size_t)S.nb_stride;
-    for (int t = 0; t < cnt; ++t) {
-      const unsigned e = (unsigned)__ldg(nb + t * stride);
+    const int* __restrict__ row = S.nbr + (size_t)i * S.maxnb;
+#pragma unroll 4
+    for (int t = tl; t < cnt; t += kLjTeam) {
+      const unsigned e = (unsigned)__ldg(row + t);
       const int j = (int)(e & kNbrMask);
       const int code = (int)(e >> kNbrShift);
       const int ox = code % 3 - 1, oy = (code / 3) % 3 - 1, oz = code / 9 - 1;
@@ -147,12 +170,40 @@ __global__ void __launch_bounds__(256) k_lj(const SysDev* __restrict__ sys, cons
         w.add(g * r2);
       }
     }
-    double F[3] = {f.get(0), f.get(1), f.get(2)};
-    double* f2 = S.f2;
+  }
+  // combine the team's shares (all lanes take part in the shuffles)
+  double F[3], uu = 0.0, ww = 0.0;
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      team_sum<T>(f.c[a]);
+      F[a] = f.get(a);
+    }
+    if (energy) {
+      team_sum<T>(u.c);
+      team_sum<T>(w.c);
+      uu = u.get();
+      ww = w.get();
+    }
+  } else {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      F[a] = f.get(a);
+      team_sum_d(F[a]);
+    }
+    if (energy) {
+      uu = u.get();
+      ww = w.get();
+      team_sum_d(uu);
+      team_sum_d(ww);
+    }
+  }
+  double u_out = 0.0, w_out = 0.0;
+  if (active && tl == 0) {
     bool bad = false;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      f2[a * n + i] = F[a];
+      S.f2[a * n + i] = F[a];
       bad |= !isfinite(F[a]);
     }
     if (kind == LJ_MID) {
@@ -178,10 +229,8 @@ __global__ void __launch_bounds__(256) k_lj(const SysDev* __restrict__ sys, cons
       }
     }
     if (bad) atomicOr(&S.flags[FLG_ERR], ERR_NONFINITE);
-    if (energy) {
-      u_out = 0.5 * u.get();  // every pair appears in both members' lists
-      w_out = 0.5 * w.get();
-    }
+    u_out = 0.5 * uu;  // every pair appears in both members' lists
+    w_out = 0.5 * ww;
   }
   if (energy) {
     double us = block_sum(u_out, red);
@@ -443,25 +492,55 @@ __global__ void __launch_bounds__(kAtmThreads, 2)
         m = kMaxHalf;
       }
       __syncwarp();
-      // 2./3. neighbour pairs -> queue -> triplets
+      // 2. neighbour pairs (j, k) of the half list, k-major through the pair table;
+      //    pairs with r_jk <= r_c are compacted into the warp's queue in table order
       T fi0 = 0, fi1 = 0, fi2 = 0;
       const int np = m * (m - 1) / 2;
       int qn = 0;
-      auto process = [&](unsigned entry) {
-        const int j = (int)(entry & 0xffffu), k = (int)(entry >> 16);
-        TripletOut<T> o;
-        atm_triplet<T>(nu, nd[j], nd[k], o);
-        fi0 += o.fi[0];
-        fi1 += o.fi[1];
-        fi2 += o.fi[2];
-        const int sj = nslot[j], sk = nslot[k];
-        atomicAdd(&acc[sj], o.fj[0]);
-        atomicAdd(&acc[smax + sj], o.fj[1]);
-        atomicAdd(&acc[2 * smax + sj], o.fj[2]);
-        atomicAdd(&acc[sk], o.fk[0]);
-        atomicAdd(&acc[smax + sk], o.fk[1]);
-        atomicAdd(&acc[2 * smax + sk], o.fk[2]);
-        if (energy) uacc.add(o.u);
+      // 3. queued triplets: lane l takes a contiguous run of the queue, so its pairs mostly
+      //    share k (k-major order): F_k and d_k stay in registers until k changes; F_j goes
+      //    to the staged accumulator of j (targets rarely coincide across lanes)
+      auto drain = [&](int count) {
+        if (count <= 0) return;
+        const int C = ((count + 31) >> 5) | 1;  // odd run length: lanes start in different banks
+        const int e0 = lane * C, e1 = min(e0 + C, count);
+        int curk = -1, sk = 0;
+        T4 dk;
+        T fk0 = 0, fk1 = 0, fk2 = 0;
+        for (int e = e0; e < e1; ++e) {
+          const unsigned entry = queue[e];
+          const int j = (int)(entry & 0xffffu), k = (int)(entry >> 16);
+          if (k != curk) {
+            if (curk >= 0) {
+              atomicAdd(&acc[sk], fk0);
+              atomicAdd(&acc[smax + sk], fk1);
+              atomicAdd(&acc[2 * smax + sk], fk2);
+            }
+            curk = k;
+            dk = nd[k];
+            sk = nslot[k];
+            fk0 = fk1 = fk2 = 0;
+          }
+          TripletOut<T> o;
+          atm_triplet<T>(nu, nd[j], dk, o);
+          fi0 += o.fi[0];
+          fi1 += o.fi[1];
+          fi2 += o.fi[2];
+          fk0 += o.fk[0];
+          fk1 += o.fk[1];
+          fk2 += o.fk[2];
+          const int sj = nslot[j];
+          atomicAdd(&acc[sj], o.fj[0]);
+          atomicAdd(&acc[smax + sj], o.fj[1]);
+          atomicAdd(&acc[2 * smax + sj], o.fj[2]);
+          if (energy) uacc.add(o.u);
+        }
+        if (curk >= 0) {
+          atomicAdd(&acc[sk], fk0);
+          atomicAdd(&acc[smax + sk], fk1);
+          atomicAdd(&acc[2 * smax + sk], fk2);
+        }
+        ntrip += (unsigned long long)count;
       };
       for (int p0 = 0; p0 < np; p0 += 32) {
         const int p = p0 + lane;
@@ -486,22 +565,15 @@ __global__ void __launch_bounds__(kAtmThreads, 2)
         const unsigned bal = __ballot_sync(0xffffffffu, ok);
         if (ok) queue[qn + __popc(bal & lt)] = entry;
         qn += __popc(bal);
-        if (qn >= 32) {
+        if (qn > kQueue - 32) {  // next round could overflow: evaluate what is queued
           __syncwarp();
-          process(queue[lane]);
-          ntrip += 32;
-          const int rem = qn - 32;
+          drain(qn);
           __syncwarp();
-          const unsigned tmp = (lane < rem) ? queue[32 + lane] : 0u;
-          __syncwarp();
-          if (lane < rem) queue[lane] = tmp;
-          __syncwarp();
-          qn = rem;
+          qn = 0;
         }
       }
       __syncwarp();
-      if (lane < qn) process(queue[lane]);
-      ntrip += (unsigned long long)qn;
+      drain(qn);
       fi0 = warp_sum_t<T>(fi0);
       fi1 = warp_sum_t<T>(fi1);
       fi2 = warp_sum_t<T>(fi2);
@@ -522,7 +594,7 @@ __global__ void __launch_bounds__(kAtmThreads, 2)
       part[(3 * s + 1) * (size_t)n + p] = acc[smax + t];
       part[(3 * s + 2) * (size_t)n + p] = acc[2 * smax + t];
     }
-    if (lane == 0 && ntrip) atomicAdd(&S.ctr[CTR_TRIPLETS], ntrip);
+    if (lane == 0 && ntrip) atomicAdd(&S.ctr[CTR_TRIPLETS], ntrip);  // ntrip is warp-uniform
     if (energy) {
       double us = block_sum(uacc.get(), red);
       if (threadIdx.x == 0) {

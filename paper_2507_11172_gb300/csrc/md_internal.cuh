@@ -13,7 +13,9 @@ constexpr unsigned kNbrMask = (1u << kNbrShift) - 1u;
 constexpr int kPairTable = kMaxHalf * (kMaxHalf - 1) / 2;  // (j, k) pairs, k-major
 constexpr int kAtmWarps = 8;
 constexpr int kAtmThreads = 32 * kAtmWarps;
-constexpr int kQueue = 64;          // per-warp accepted-triplet queue
+constexpr int kQueue = 512;         // per-warp queue of accepted neighbour pairs (j, k)
+constexpr int kLjTeam = 8;          // lanes cooperating on one particle's pair list
+constexpr int kListWarps = 4;       // warps per CTA of the pair-list build
 
 // error bits in SysDev::flags[0]
 enum : int {
@@ -43,7 +45,7 @@ struct SysDev {
   double guard2, guard3;  // half-width of the r^2 band re-decided in FP64 (pair / triplet)
   // integrator
   double dt_in, dt_out, inv_mass, mass;
-  int maxnb, nb_stride;
+  int maxnb, cap_stage;  // pair-list capacity per particle; staged particles per list-build CTA
   int precision;  // 0 = FP32 forces, 1 = FP64
   int pad_;
   // state in cell-sorted order, double SoA [3][n] (x block, y block, z block)
@@ -57,7 +59,7 @@ struct SysDev {
   int *pcell;         // [n] cell of the last sort
   int *cell_tmp, *rank;       // [n] binning scratch
   int *count, *cell_start;    // [ncell], [ncell + 1]
-  int *nbr, *nbr_cnt;         // [maxnb][nb_stride] column-major, [n]
+  int *nbr, *nbr_cnt;         // [n][maxnb] row-major, [n]
   void *partial;              // T [27][3][n] per-stencil-slot ATM partial forces
   double *acc;                // [ACC_N]
   unsigned long long *ctr;    // [CTR_N]
@@ -200,7 +202,8 @@ struct Launch {
 void launch_bin_count(const Launch& L, const PItem* items, int nitems, int block);
 void launch_scan(const Launch& L, const SItem* items, int nitems);
 template <typename T> void launch_scatter(const Launch& L, const PItem* items, int nitems, int block);
-template <typename T> void launch_listbuild(const Launch& L, const PItem* items, int nitems, int block);
+template <typename T> void launch_listbuild(const Launch& L, const CItem* items, int nitems, int smax);
+int listbuild_configure(int smax, int precision);
 // forces.cu
 template <typename T> void launch_lj(const Launch& L, const PItem* items, int nitems, int block);
 template <typename T> void launch_atm(const Launch& L, const CItem* items, int nitems, int grid, int smax);

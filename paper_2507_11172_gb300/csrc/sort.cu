@@ -123,68 +123,104 @@ __global__ void k_scatter(const SysDev* __restrict__ sys, const PItem* __restric
   reinterpret_cast<T4*>(S.ref)[q] = h;
 }
 
-// Pair list with skin: every j != i in the 27 cells around i's cell with
-// |d|^2 <= (r_c2 + skin)^2 (slightly widened: the list may hold a superset).
-// Entry = j | image code << 27, code = (dz+1)*9 + (dy+1)*3 + (dx+1) for the
-// cell offset from i's cell to j's cell.  Also moves the permuted state back.
+// Pair list with skin, one CTA per cell b: the 27 cells around b are staged in
+// shared memory with coordinates relative to b's centre; one warp per particle i
+// of b tests every staged particle and ballot-compacts those within
+// (r_c2 + skin)^2 (slightly widened: the list may hold a superset) into i's row.
+// Entry = j | image code << 27, code = (dz+1)*9 + (dy+1)*3 + (dx+1) for the cell
+// offset from i's cell to j's cell.  The CTA also moves the permuted state of
+// b's particles back into place.
 template <typename T>
-__global__ void k_listbuild(const SysDev* __restrict__ sys, const PItem* __restrict__ items) {
+__global__ void __launch_bounds__(32 * kListWarps)
+    k_listbuild(const SysDev* __restrict__ sys, const CItem* __restrict__ items, int smax) {
   using T4 = typename V4<T>::type;
-  const PItem it = items[blockIdx.x];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T4* sp = reinterpret_cast<T4*>(smem_raw);
+  int* sj = reinterpret_cast<int*>(sp + smax);
+  __shared__ int st_begin[28], st_cnt[27], st_cell[27];
+  const CItem it = items[blockIdx.x];
   const SysDev& S = sys[it.sys];
-  int i = it.begin + threadIdx.x;
-  if (i >= S.n) return;
-  const int n = S.n, nc = S.nc;
-  const T4* __restrict__ P = reinterpret_cast<const T4*>(S.pos[it.buf]);
-  const T4 pi = P[i];
-  const int cell = S.pcell[i];
-  const int cx = cell % nc, cy = (cell / nc) % nc, cz = cell / (nc * nc);
+  const int b = it.cell, nc = S.nc, n = S.n;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  if (warp == 0) {
+    int cnt = 0;
+    if (lane < 27) {
+      const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
+      const int bx = b % nc, by = (b / nc) % nc, bz = b / (nc * nc);
+      const int c = (((bz + dz + nc) % nc) * nc + (by + dy + nc) % nc) * nc + (bx + dx + nc) % nc;
+      cnt = S.cell_start[c + 1] - S.cell_start[c];
+      st_cnt[lane] = cnt;
+      st_cell[lane] = c;
+    }
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    if (lane < 27) st_begin[lane] = incl - cnt;
+    if (lane == 26) st_begin[27] = incl;
+  }
+  __syncthreads();
+  const int nstaged = min(st_begin[27], smax);
   const T edge = (T)S.edge;
-  const T rl = (T)(S.rlistsq * (1.0 + 1e-5));
-  int cnt = 0;
-  for (int dz = -1; dz <= 1; ++dz) {
-    int zz = cz + dz;
-    zz += (zz < 0) ? nc : 0;
-    zz -= (zz >= nc) ? nc : 0;
-    for (int dy = -1; dy <= 1; ++dy) {
-      int yy = cy + dy;
-      yy += (yy < 0) ? nc : 0;
-      yy -= (yy >= nc) ? nc : 0;
-      for (int dx = -1; dx <= 1; ++dx) {
-        int xx = cx + dx;
-        xx += (xx < 0) ? nc : 0;
-        xx -= (xx >= nc) ? nc : 0;
-        const int c2 = (zz * nc + yy) * nc + xx;
-        const unsigned code = (unsigned)((dz + 1) * 9 + (dy + 1) * 3 + (dx + 1));
-        const T sx = (T)dx * edge, sy = (T)dy * edge, sz = (T)dz * edge;
-        const int j0 = S.cell_start[c2], j1 = S.cell_start[c2 + 1];
-        for (int j = j0; j < j1; ++j) {
-          if (j == i) continue;
-          T4 pj = P[j];
-          T ddx = (pj.x - pi.x) + sx, ddy = (pj.y - pi.y) + sy, ddz = (pj.z - pi.z) + sz;
-          T r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-          if (r2 <= rl) {
-            if (cnt < S.maxnb) S.nbr[(size_t)cnt * S.nb_stride + i] = (int)((unsigned)j | (code << kNbrShift));
-            ++cnt;
-          }
-        }
-      }
+  const T4* __restrict__ P = reinterpret_cast<const T4*>(S.pos[it.buf]);
+  for (int l = warp; l < 27; l += kListWarps) {
+    const int cnt = st_cnt[l];
+    const int c0 = S.cell_start[st_cell[l]];
+    const T ox = (T)(l % 3 - 1) * edge, oy = (T)((l / 3) % 3 - 1) * edge, oz = (T)(l / 9 - 1) * edge;
+    for (int e = lane; e < cnt; e += 32) {
+      const int slot = st_begin[l] + e;
+      if (slot >= smax) break;
+      T4 h = P[c0 + e];
+      h.x += ox;
+      h.y += oy;
+      h.z += oz;
+      sp[slot] = h;
+      sj[slot] = (int)((unsigned)(c0 + e) | ((unsigned)l << kNbrShift));
     }
   }
-  if (cnt > S.maxnb) {
-    atomicOr(&S.flags[FLG_ERR], ERR_NBR_CAP);
-    cnt = S.maxnb;
-  }
-  S.nbr_cnt[i] = cnt;
-  // move the permuted state into place
+  __syncthreads();
+  const T rl = (T)(S.rlistsq * (1.0 + 1e-5));
+  const int nbase = min(st_cnt[13], max(0, nstaged - st_begin[13]));
+  const int i0 = S.cell_start[b];
   const double* Xa = S.X[it.buf ^ 1];
   double* X = S.X[it.buf];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    X[a * n + i] = Xa[a * n + i];
-    S.v[a * n + i] = S.v_alt[a * n + i];
+  for (int ib = warp; ib < nbase; ib += kListWarps) {
+    const int islot = st_begin[13] + ib;
+    const int i = i0 + ib;
+    const T4 pi = sp[islot];
+    int cnt = 0;
+    int* row = S.nbr + (size_t)i * S.maxnb;
+    for (int t0 = 0; t0 < nstaged; t0 += 32) {
+      const int t = t0 + lane;
+      bool ok = false;
+      if (t < nstaged && t != islot) {
+        const T4 q = sp[t];
+        const T dx = q.x - pi.x, dy = q.y - pi.y, dz = q.z - pi.z;
+        ok = dx * dx + dy * dy + dz * dz <= rl;
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, ok);
+      const int pos = cnt + __popc(bal & lt);
+      if (ok && pos < S.maxnb) row[pos] = sj[t];
+      cnt += __popc(bal);
+    }
+    if (lane == 0) {
+      if (cnt > S.maxnb) atomicOr(&S.flags[FLG_ERR], ERR_NBR_CAP);
+      S.nbr_cnt[i] = min(cnt, S.maxnb);
+    }
   }
-  S.id[i] = S.id_alt[i];
+  // every particle of b: permuted state back into place
+  for (int ib = threadIdx.x; ib < st_cnt[13]; ib += blockDim.x) {
+    const int i = i0 + ib;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      X[a * n + i] = Xa[a * n + i];
+      S.v[a * n + i] = S.v_alt[a * n + i];
+    }
+    S.id[i] = S.id_alt[i];
+  }
 }
 
 void launch_bin_count(const Launch& L, const PItem* items, int nitems, int block) {
@@ -198,12 +234,21 @@ void launch_scatter(const Launch& L, const PItem* items, int nitems, int block) 
   if (nitems > 0) k_scatter<T><<<nitems, block, 0, L.stream>>>(L.sys, items);
 }
 template <typename T>
-void launch_listbuild(const Launch& L, const PItem* items, int nitems, int block) {
-  if (nitems > 0) k_listbuild<T><<<nitems, block, 0, L.stream>>>(L.sys, items);
+void launch_listbuild(const Launch& L, const CItem* items, int nitems, int smax) {
+  if (nitems <= 0) return;
+  const int bytes = (int)(smax * (sizeof(typename V4<T>::type) + sizeof(int)));
+  k_listbuild<T><<<nitems, 32 * kListWarps, bytes, L.stream>>>(L.sys, items, smax);
+}
+int listbuild_configure(int smax, int precision) {
+  const int bytes = (int)(smax * ((precision ? sizeof(double4_32a) : sizeof(float4)) + sizeof(int)));
+  cudaError_t e = precision
+                      ? cudaFuncSetAttribute(k_listbuild<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
+                      : cudaFuncSetAttribute(k_listbuild<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  return e == cudaSuccess ? bytes : -1;
 }
 template void launch_scatter<float>(const Launch&, const PItem*, int, int);
 template void launch_scatter<double>(const Launch&, const PItem*, int, int);
-template void launch_listbuild<float>(const Launch&, const PItem*, int, int);
-template void launch_listbuild<double>(const Launch&, const PItem*, int, int);
+template void launch_listbuild<float>(const Launch&, const CItem*, int, int);
+template void launch_listbuild<double>(const Launch&, const CItem*, int, int);
 
 }  // namespace r3b

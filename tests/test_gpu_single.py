@@ -138,8 +138,15 @@ def test_distances_exactly_at_the_cutoff(gpu_lib):
             _, u2, u3, _ = s.energy()
             assert s.stats()["triplets_last"] == cnt
             assert s.stats()["guard_rechecks"] > 0
-        assert force_err(f3, f3r) <= TOL[prec]
-        assert force_err(f2, f2r) <= TOL[prec]
+        # nearly every net force cancels to ~0 on this lattice, so errors are measured against
+        # the scale of one triplet's force at the lattice spacing, 9 nu / b^10 (virial identity)
+        scale = 9 * NU / b ** 10
+        err3 = np.linalg.norm(f3 - f3r, axis=1) / np.maximum(np.linalg.norm(f3r, axis=1), scale)
+        assert err3.max() <= TOL[prec]
+        s6 = b ** -6
+        pair_scale = abs(24 * (2 * s6 * s6 - s6) / b)  # one LJ pair at the lattice spacing
+        err2 = np.linalg.norm(f2 - f2r, axis=1) / np.maximum(np.linalg.norm(f2r, axis=1), pair_scale)
+        assert err2.max() <= TOL[prec]
         assert abs(u3 - u3r) <= 1e-6 * abs(u3r) + 1e-12
 
 
