@@ -157,6 +157,31 @@ md_status md_batch_latency(md_batch *b, uint64_t ticket, double *ms, int *count)
 md_status md_batch_pending(md_batch *b, int *queued, int *resident);
 md_status md_batch_destroy(md_batch *b);
 
+/* ---------------- allocation-free ATM forces ----------------
+ * No counterpart in the paper: an entry point for callers that cannot
+ * allocate device memory (code living inside another framework's memory
+ * pool, a process whose device allocator is locked down, or a caller that
+ * must not trigger the device-wide synchronisation of cudaMalloc/cudaFree).
+ *
+ * Computes the ATM forces F3 (and energy, triplet count) of one configuration
+ * with the FP32 path (FP32 forces, compensated per-particle combination),
+ * the same kernels as md_get_forces.  It allocates nothing: every
+ * intermediate array lives in a file-scope __device__ array of about 10 MiB
+ * that each GPU loading the library holds until the process exits.
+ *   d_pos: device, n x 3 doubles, caller order;  d_f3: device, n x 3 output;
+ *   u3, triplets: host outputs or NULL;  cuda_stream: cudaStream_t or NULL.
+ * Limits: 3 <= n <= MD_NOALLOC_MAX_N, L > 3 r_c (MD_ERR_BOX_TOO_SMALL), at most
+ * 32^3 cells (coarser cells beyond that).  n above the limit returns
+ * MD_ERR_CAPACITY before any device work.
+ * The first call on a device looks up the arrays' device addresses and
+ * uploads the pair table (a synchronous copy), so make that first call before
+ * any stream capture.  All calls share the arrays: calls that overlap on the
+ * GPU (other threads or streams) race; serialise them.  Synchronous: returns
+ * after the forces are written. */
+#define MD_NOALLOC_MAX_N 16384
+md_status md_atm_forces_noalloc(const double *d_pos, int64_t n, double box_L, double atm_nu, double rc_triplet,
+                                double *d_f3, double *u3, uint64_t *triplets, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -68,6 +68,7 @@ SIGNATURES = {
     "md_batch_latency": (_I, [_P, ctypes.c_uint64, _P, ctypes.POINTER(_I)]),
     "md_batch_pending": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "md_batch_destroy": (_I, [_P]),
+    "md_atm_forces_noalloc": (_I, [_P, _I64, _D, _D, _D, _P, ctypes.POINTER(_D), _U64P, _P]),
 }
 
 
@@ -236,6 +237,19 @@ def md_batch_pending(b):
 def md_batch_destroy(b):
     if b:
         _check(load().md_batch_destroy(b), "md_batch_destroy")
+
+
+def md_atm_forces_noalloc(d_pos_ptr: int, n: int, box_L: float, nu: float, rc_triplet: float, d_f3_ptr: int,
+                          stream=None):
+    """ATM forces without any device allocation: d_pos_ptr / d_f3_ptr are device addresses of
+    n x 3 float64 arrays (caller order).  Returns (u3, triplets)."""
+    u3 = _D()
+    trip = ctypes.c_uint64()
+    st = load().md_atm_forces_noalloc(ctypes.c_void_p(int(d_pos_ptr)), int(n), float(box_L), float(nu),
+                                      float(rc_triplet), ctypes.c_void_p(int(d_f3_ptr)), ctypes.byref(u3),
+                                      ctypes.byref(trip), None if stream is None else ctypes.c_void_p(int(stream)))
+    _check(st, "md_atm_forces_noalloc")
+    return u3.value, int(trip.value)
 
 
 @dataclass

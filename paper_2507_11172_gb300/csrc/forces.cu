@@ -754,6 +754,15 @@ void launch_atm(const Launch& L, const CItem* items, int nitems, int grid, int s
   const int bytes = (int)atm_layout<T>(smax).total;
   k_atm<T><<<grid, kAtmThreads, bytes, L.stream>>>(L.sys, items, nitems, g_table, smax);
 }
+// same launch with a caller-provided pair table (used by the allocation-free entry point)
+template <typename T>
+void launch_atm_table(const Launch& L, const CItem* items, int nitems, int grid, int smax, const uint16_t* table) {
+  if (nitems <= 0) return;
+  const int bytes = (int)atm_layout<T>(smax).total;
+  k_atm<T><<<grid, kAtmThreads, bytes, L.stream>>>(L.sys, items, nitems, table, smax);
+}
+template void launch_atm_table<float>(const Launch&, const CItem*, int, int, int, const uint16_t*);
+
 template <typename T>
 void launch_combine(const Launch& L, const PItem* items, int nitems, int block) {
   if (nitems > 0) k_combine<T><<<nitems, block, 0, L.stream>>>(L.sys, items);

@@ -210,6 +210,8 @@ template <typename T> void launch_atm(const Launch& L, const CItem* items, int n
 // dynamic shared memory of the ATM kernel for smax staged particles; sets the kernel attribute
 // and returns the resident CTAs per SM (0 if it does not fit)
 int atm_configure(int smax, int precision, int* smem_bytes);
+template <typename T>
+void launch_atm_table(const Launch& L, const CItem* items, int nitems, int grid, int smax, const uint16_t* table);
 template <typename T> void launch_combine(const Launch& L, const PItem* items, int nitems, int block);
 template <typename T> void launch_start(const Launch& L, const PItem* items, int nitems, int block);
 void launch_kinetic(const Launch& L, const PItem* items, int nitems, int block);
