@@ -68,6 +68,8 @@ typedef struct {
   uint64_t atm_timed;          /* number of ATM launches in atm_ms_total */
   int32_t max_cell_count;      /* largest cell occupancy seen at the last binning */
   int32_t cells_per_side;      /* binning grid */
+  int32_t atm_kernel;          /* triplet kernel in use: 0 cell/Newton-3, 1 per-particle, -1 not chosen yet */
+  int32_t reserved_;
 } md_stats;
 
 /* Create a system of n >= 3 particles in a periodic cube of side box_L.
@@ -118,6 +120,15 @@ md_status md_set_state(md_system *s, const double *pos, const double *vel);
  * the system's stream around every ATM launch (atm_ms_total / atm_timed). */
 md_status md_get_stats(md_system *s, md_stats *out);
 md_status md_set_profiling(md_system *s, int profile);
+
+/* Triplet-kernel choice (an autotuning knob; results agree within the FP tolerance):
+ *   0  one CTA per base cell, shared-memory staging, each triplet evaluated once with
+ *      Newton-3 scatter of the three forces;
+ *   1  one warp per particle, neighbours from the pair list, only the force on that
+ *      particle per evaluation (each triplet evaluated from each member, no scatter);
+ *      needs r_c3 <= r_c2 + skin, else 0 is used;
+ *  -1  (default) time both on the system's first evaluation and keep the faster. */
+md_status md_set_atm_kernel(md_system *s, int variant);
 
 /* Number of particles, box side and precision of a handle. */
 md_status md_get_info(md_system *s, int64_t *n, double *box_L, int *precision);

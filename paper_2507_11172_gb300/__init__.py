@@ -35,7 +35,7 @@ class md_stats(ctypes.Structure):
                 ("atm_evals", ctypes.c_uint64), ("lj_evals", ctypes.c_uint64), ("outer_steps", ctypes.c_uint64),
                 ("replays", ctypes.c_uint64), ("guard_rechecks", ctypes.c_uint64), ("atm_ms_total", ctypes.c_double),
                 ("atm_timed", ctypes.c_uint64), ("max_cell_count", ctypes.c_int32),
-                ("cells_per_side", ctypes.c_int32)]
+                ("cells_per_side", ctypes.c_int32), ("atm_kernel", ctypes.c_int32), ("reserved_", ctypes.c_int32)]
 
 
 _lib = None
@@ -57,6 +57,7 @@ SIGNATURES = {
     "md_set_state": (_I, [_P, _P, _P]),
     "md_get_stats": (_I, [_P, ctypes.POINTER(md_stats)]),
     "md_set_profiling": (_I, [_P, _I]),
+    "md_set_atm_kernel": (_I, [_P, _I]),
     "md_get_info": (_I, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_D), ctypes.POINTER(_I)]),
     "md_destroy_system": (_I, [_P]),
     "md_status_string": (ctypes.c_char_p, [_I]),
@@ -187,6 +188,10 @@ def md_get_stats(h) -> dict:
 
 def md_set_profiling(h, on: bool):
     _check(load().md_set_profiling(h, 1 if on else 0), "md_set_profiling")
+
+
+def md_set_atm_kernel(h, variant: int):
+    _check(load().md_set_atm_kernel(h, int(variant)), "md_set_atm_kernel")
 
 
 def md_destroy_system(h):

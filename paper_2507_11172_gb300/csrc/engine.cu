@@ -90,6 +90,9 @@ struct md_system {
   bool forces_valid = false;
   bool energy_valid = false;
   int atm_smem = 0, atm_grid = 0;
+  int atm_variant = -1;       // 0: cell kernel with Newton-3 scatter, 1: per-particle kernel, -1: tune
+  int atm_variant_req = -1;   // requested by md_set_atm_kernel (-1 = autotune)
+  int nblocks_pa = 0;
   std::map<std::tuple<int, int, int, int, int>, cudaGraphExec_t> graphs;  // (n_outer, k, cur, safe, profile)
   // host mirrors
   int* h_flags = nullptr;       // pinned [FLG_N]
@@ -106,7 +109,7 @@ struct md_system {
 
 namespace {
 
-enum KTag { T_BIN = 1, T_SCATTER, T_LIST, T_LJ, T_COMB, T_START, T_KIN };
+enum KTag { T_BIN = 1, T_SCATTER, T_LIST, T_LJ, T_COMB, T_START, T_KIN, T_ATMPA };
 
 void free_items(md_system* s) {
   for (void* p : s->item_allocs) cudaFree(p);
@@ -249,8 +252,24 @@ md_status upload_desc(md_system* s, double dt_in, double dt_out) {
   h.mass = s->mass;
   h.inv_mass = 1.0 / s->mass;
   h.maxnb = s->maxnb;
-  h.cap_stage = 27 * s->cap_cell;
+  h.cap_stage = atm_stage_capacity(s->cap_cell);
   h.precision = s->precision;
+  {
+    const double r = h.rc3 * (1.0 + 1e-5) + 1e-5;
+    h.f_edge = (float)h.edge;
+    h.f_edge_lo = (float)(h.edge - (double)h.f_edge);
+    h.f_half_edge = (float)(0.5 * h.edge);
+    h.f_rc2sq = (float)h.rc2sq;
+    h.f_guard2 = (float)h.guard2;
+    h.f_sig2 = (float)h.sig2;
+    h.f_eps24 = (float)(24.0 * h.eps);
+    h.f_eps4 = (float)(4.0 * h.eps);
+    h.f_rc3sq = (float)h.rc3sq;
+    h.f_guard3 = (float)h.guard3;
+    h.f_nu = (float)h.nu;
+    h.f_reach2 = (float)(r * r);
+    h.f_half_skin_sq = (float)h.half_skin_sq;
+  }
   CK(cudaMemcpyAsync(s->d_sys, &h, sizeof(SysDev), cudaMemcpyHostToDevice, s->stream));
   return MD_OK;
 }
@@ -269,8 +288,8 @@ PItem* pitems_for(md_system* s, int tag, int mode, int buf) {
   auto it = s->pitems.find(key);
   if (it != s->pitems.end()) return it->second;
   std::vector<PItem> v;
-  const int per = (tag == T_LJ) ? kBlock / kLjTeam : kBlock;  // particles per block
-  const int nb = (tag == T_LJ) ? s->nblocks_lj : s->nblocks;
+  const int per = (tag == T_LJ) ? kBlock / kLjTeam : (tag == T_ATMPA ? kPaPerBlock : kBlock);
+  const int nb = (tag == T_LJ) ? s->nblocks_lj : (tag == T_ATMPA ? s->nblocks_pa : s->nblocks);
   for (int b = 0; b < nb; ++b) v.push_back(PItem{0, b * per, mode, buf});
   PItem* d = upload_items(s, v);
   s->pitems[key] = d;
@@ -294,6 +313,7 @@ md_status prepare_items(md_system* s) {
   s->nblocks = (int)((s->n + kBlock - 1) / kBlock);
   const int per_lj = kBlock / kLjTeam;
   s->nblocks_lj = (int)((s->n + per_lj - 1) / per_lj);
+  s->nblocks_pa = (int)((s->n + kPaPerBlock - 1) / kPaPerBlock);
   for (int b = 0; b < 2; ++b) {
     pitems_for(s, T_BIN, 0, b);
     pitems_for(s, T_SCATTER, 0, b);
@@ -306,6 +326,10 @@ md_status prepare_items(md_system* s) {
       pitems_for(s, T_COMB, CB_INIT | E, b);
       pitems_for(s, T_COMB, CB_LAST | E, b);
       pitems_for(s, T_COMB, CB_CONT | E, b);
+      pitems_for(s, T_COMB, CB_INIT | E | M_F3READY, b);
+      pitems_for(s, T_COMB, CB_LAST | E | M_F3READY, b);
+      pitems_for(s, T_COMB, CB_CONT | E | M_F3READY, b);
+      pitems_for(s, T_ATMPA, E, b);
       citems_for(s, E, b);
     }
   }
@@ -326,7 +350,7 @@ md_status prepare_items(md_system* s) {
 md_status configure_atm(md_system* s) {
   atm_prepare_table(s->stream);
   int bytes = 0;
-  int per_sm = atm_configure(27 * s->cap_cell, s->precision, &bytes);
+  int per_sm = atm_configure(atm_stage_capacity(s->cap_cell), s->precision, &bytes);
   if (per_sm <= 0) {
     g_last_error = "ATM kernel does not fit in shared memory for cap_cell=" + std::to_string(s->cap_cell);
     return MD_ERR_CAPACITY;
@@ -372,6 +396,7 @@ md_status rebuild(md_system* s, bool keep_state) {
   s->forces_valid = false;
   s->energy_valid = false;
   s->stats.cells_per_side = s->nc;
+  s->atm_variant = -1;  // re-tune for the new grid / parameters
   memset(s->h_ctr, 0, 8 * CTR_N);  // the device counters restart at zero with the new arena
   return MD_OK;
 }
@@ -394,12 +419,17 @@ struct Plan {
   template <typename T>
   void atm(int buf, bool energy, int ev) {
     if (ev >= 0) cudaEventRecord(s->events[2 * ev], L.stream);
-    launch_atm<T>(L, citems_for(s, energy ? M_ENERGY : 0, buf), s->ncell, s->atm_grid, 27 * s->cap_cell);
+    if (s->atm_variant == 1)
+      launch_atm_pa<T>(L, pitems_for(s, T_ATMPA, energy ? M_ENERGY : 0, buf), s->nblocks_pa);
+    else
+      launch_atm<T>(L, citems_for(s, energy ? M_ENERGY : 0, buf), s->ncell, s->atm_grid,
+                    atm_stage_capacity(s->cap_cell));
     if (ev >= 0) cudaEventRecord(s->events[2 * ev + 1], L.stream);
   }
   template <typename T>
   void combine(int kind, int buf, bool energy) {
-    launch_combine<T>(L, pitems_for(s, T_COMB, kind | (energy ? M_ENERGY : 0), buf), s->nblocks, kBlock);
+    const int ready = (s->atm_variant == 1) ? M_F3READY : 0;
+    launch_combine<T>(L, pitems_for(s, T_COMB, kind | ready | (energy ? M_ENERGY : 0), buf), s->nblocks, kBlock);
   }
   template <typename T>
   void start(int buf) {
@@ -562,8 +592,66 @@ md_status status_from_flags(md_system* s) {
   return MD_OK;
 }
 
+bool variant_allowed(const md_system* s, int v) {
+  // the per-particle kernel reads its neighbours from the pair list: needs r_c3 <= r_c2 + skin
+  return v == 0 || (v == 1 && s->rc3 <= s->rc2 + s->skin);
+}
+
+// Autotuner for the triplet kernel: after one initial evaluation (binning, pair list, forces)
+// each allowed variant is launched a few times on the same configuration with CUDA events
+// around each launch; the faster one is kept for the system.
+md_status tune_atm(md_system* s) {
+  const int req = s->atm_variant_req;
+  if (req >= 0) {
+    s->atm_variant = variant_allowed(s, req) ? req : 0;
+    return MD_OK;
+  }
+  s->atm_variant = 0;
+  if (!variant_allowed(s, 1)) return MD_OK;
+  md_status st = upload_desc(s, 0.0, 0.0);
+  if (st != MD_OK) return st;
+  st = ensure_events(s, 2);
+  if (st != MD_OK) return st;
+  Plan P{s, Launch{s->stream, s->d_sys}};
+  const bool prof = s->profile;
+  s->profile = false;
+  clear_graphs(s);
+  st = run_plan(s, 0, 1, true, false);  // binning + pair list at the current positions
+  if (st != MD_OK) return st;
+  float best = 1e30f;
+  int bestv = 0;
+  for (int v = 0; v < 2; ++v) {
+    s->atm_variant = v;
+    float tot = 0.f;
+    for (int r = 0; r < 4; ++r) {
+      CK(cudaEventRecord(s->events[0], s->stream));
+      if (s->precision) P.atm<double>(s->cur, false, -1); else P.atm<float>(s->cur, false, -1);
+      CK(cudaEventRecord(s->events[1], s->stream));
+      CK(cudaEventSynchronize(s->events[1]));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, s->events[0], s->events[1]));
+      if (r > 0) tot += ms;  // first launch warms caches
+    }
+    if (tot < best) {
+      best = tot;
+      bestv = v;
+    }
+  }
+  s->atm_variant = bestv;
+  s->profile = prof;
+  clear_graphs(s);
+  s->forces_valid = false;  // recompute with the chosen kernel
+  s->energy_valid = false;
+  st = read_flags(s);      // refresh the counter baseline (the trial launches counted triplets)
+  return st;
+}
+
 // one respa_step call with snapshot / replay
 md_status do_call(md_system* s, int n_outer, int k, double dt_outer) {
+  if (s->atm_variant < 0) {
+    md_status st = tune_atm(s);
+    if (st != MD_OK) return st;
+  }
   const double dt_in = dt_outer / k;
   for (int attempt = 0; attempt < 6; ++attempt) {
     const bool safe = attempt > 0 && s->h_flags[FLG_SKIN] && !(s->h_flags[FLG_ERR] & (ERR_CELL_CAP | ERR_NBR_CAP));
@@ -858,6 +946,7 @@ md_status md_set_state(md_system* s, const double* pos, const double* vel) {
 
 md_status md_get_stats(md_system* s, md_stats* out) {
   if (!s || !out) return MD_ERR_ARG;
+  s->stats.atm_kernel = s->atm_variant;
   *out = s->stats;
   return MD_OK;
 }
@@ -866,6 +955,16 @@ md_status md_set_profiling(md_system* s, int profile) {
   if (!s) return MD_ERR_ARG;
   s->profile = profile != 0;
   clear_graphs(s);
+  return MD_OK;
+}
+
+md_status md_set_atm_kernel(md_system* s, int variant) {
+  if (!s || variant < -1 || variant > 1) return MD_ERR_ARG;
+  s->atm_variant_req = variant;
+  s->atm_variant = -1;
+  clear_graphs(s);
+  s->forces_valid = false;
+  s->energy_valid = false;
   return MD_OK;
 }
 

@@ -66,6 +66,11 @@ template <> struct AccS<double> {
   __device__ __forceinline__ double get() const { return c; }
 };
 
+// finiteness from the exponent bits (integer ALU, not the scarce FP64 pipe)
+__device__ __forceinline__ bool finite_bits(double x) {
+  return ((unsigned long long)__double_as_longlong(x) & 0x7ff0000000000000ull) != 0x7ff0000000000000ull;
+}
+
 // cell-local coordinate of an FP64 position relative to the centre of cell
 // `cell`, folded to the nearest image (|rel| <= L/2)
 __device__ __forceinline__ void cell_rel(const SysDev& S, int cell, const double x[3], double rel[3]) {
@@ -88,10 +93,10 @@ __device__ __forceinline__ void store_pos(const SysDev& S, int buf, int i, const
   h.z = (T)rel[2];
   h.w = (T)0;
   reinterpret_cast<T4*>(S.pos[buf])[i] = h;
-  if (check_skin) {
-    T4 r = reinterpret_cast<const T4*>(S.ref)[i];
-    double dx = (double)h.x - (double)r.x, dy = (double)h.y - (double)r.y, dz = (double)h.z - (double)r.z;
-    if (dx * dx + dy * dy + dz * dz > S.half_skin_sq) atomicOr(&S.flags[FLG_SKIN], 1);
+  if (check_skin) {  // displacement since the last sort, in the force precision
+    const T4 r = reinterpret_cast<const T4*>(S.ref)[i];
+    const T dx = h.x - r.x, dy = h.y - r.y, dz = h.z - r.z;
+    if (dx * dx + dy * dy + dz * dz > Par<T>::half_skin_sq(S)) atomicOr(&S.flags[FLG_SKIN], 1);
   }
 }
 
@@ -118,9 +123,23 @@ __device__ __forceinline__ void team_sum_d(double& v) {
   for (int o = kLjTeam / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
 }
 
+// read-only cached load of a 4-vector (the position buffer read by a kernel is never written by it)
+__device__ __forceinline__ float4 ldg4(const float4* p) { return __ldg(p); }
+__device__ __forceinline__ double4_32a ldg4(const double4_32a* p) { return *p; }
+
+template <typename T> __device__ __forceinline__ T recip_fast(T x);
+// FP32: hardware reciprocal refined by one Newton step (no special-value path: r^2 is a
+// normal positive number here)
+template <> __device__ __forceinline__ float recip_fast<float>(float x) {
+  const float y = __fdividef(1.0f, x);
+  return y * fmaf(-x, y, 2.0f);
+}
+template <> __device__ __forceinline__ double recip_fast<double>(double x) { return 1.0 / x; }
+
 template <typename T>
-__global__ void __launch_bounds__(256, 4) k_lj(const SysDev* __restrict__ sys, const PItem* __restrict__ items) {
+__global__ void __launch_bounds__(256, 3) k_lj(const SysDev* __restrict__ sys, const PItem* __restrict__ items) {
   using T4 = typename V4<T>::type;
+  constexpr int kBatch = 4;
   __shared__ double red[32];
   const PItem it = items[blockIdx.x];
   const SysDev& S = sys[it.sys];
@@ -132,112 +151,156 @@ __global__ void __launch_bounds__(256, 4) k_lj(const SysDev* __restrict__ sys, c
   const bool active = i < n;
   const T4* __restrict__ P = reinterpret_cast<const T4*>(S.pos[it.buf]);
   const double* __restrict__ X = S.X[it.buf];
-  Acc3<T> f;
-  AccS<T> u, w;
+  T fx = 0, fy = 0, fz = 0, uu_t = 0, ww_t = 0;  // plain partial sums of <= maxnb / kLjTeam terms
   if (active) {
     const T4 pi = P[i];
-    const T edge = (T)S.edge;
-    const T rcsq = (T)S.rc2sq;
-    const T g2 = (T)S.guard2;
-    const T sig2 = (T)S.sig2;
-    const T eps24 = (T)(24.0 * S.eps), eps4 = (T)(4.0 * S.eps);
+    const T edge = Par<T>::edge(S);
+    const T rcsq = Par<T>::rc2sq(S);
+    const T g2 = Par<T>::guard2(S);
+    const T sig2 = Par<T>::sig2(S);
+    const T eps24 = Par<T>::eps24(S), eps4 = Par<T>::eps4(S);
     const int cnt = S.nbr_cnt[i];
     const int* __restrict__ row = S.nbr + (size_t)i * S.maxnb;
-#pragma unroll 4
-    for (int t = tl; t < cnt; t += kLjTeam) {
-      const unsigned e = (unsigned)__ldg(row + t);
-      const int j = (int)(e & kNbrMask);
-      const int code = (int)(e >> kNbrShift);
-      const int ox = code % 3 - 1, oy = (code / 3) % 3 - 1, oz = code / 9 - 1;
-      const T4 pj = P[j];
-      const T dx = (pj.x - pi.x) + (T)ox * edge;
-      const T dy = (pj.y - pi.y) + (T)oy * edge;
-      const T dz = (pj.z - pi.z) + (T)oz * edge;
-      const T r2 = dx * dx + dy * dy + dz * dz;
-      if (r2 > rcsq + g2) continue;
-      if (r2 >= rcsq - g2) {  // guard band: decide exactly in FP64
-        atomicAdd(&S.ctr[CTR_GUARD], 1ull);
-        if (!exact_within(X, n, i, j, S.L, S.rc2sq)) continue;
+    for (int t0 = tl; t0 < cnt; t0 += kLjTeam * kBatch) {
+      unsigned e[kBatch];
+      T4 pj[kBatch];
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) {
+        const int t = t0 + u * kLjTeam;
+        e[u] = (t < cnt) ? (unsigned)__ldg(row + t) : (unsigned)i;  // padding entry: i itself
       }
-      const T ir2 = recip<T>(r2);
-      const T sr2 = sig2 * ir2;
-      const T sr6 = sr2 * sr2 * sr2;
-      const T sr12 = sr6 * sr6;
-      const T g = eps24 * (sr12 + sr12 - sr6) * ir2;  // F_i = -g d
-      f.add(-g * dx, -g * dy, -g * dz);
-      if (energy) {
-        u.add(eps4 * (sr12 - sr6));
-        w.add(g * r2);
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) pj[u] = ldg4(P + (e[u] & kNbrMask));
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) {
+        const unsigned c = e[u] >> kNbrShift;
+        const T sx = fma((T)(c & 3u), edge, -edge);
+        const T sy = fma((T)((c >> 2) & 3u), edge, -edge);
+        const T sz = fma((T)(c >> 4), edge, -edge);
+        const T dx = (pj[u].x - pi.x) + sx;
+        const T dy = (pj[u].y - pi.y) + sy;
+        const T dz = (pj[u].z - pi.z) + sz;
+        const T r2 = dx * dx + dy * dy + dz * dz;
+        bool in = (r2 <= rcsq - g2) && (t0 + u * kLjTeam < cnt);
+        if ((r2 < rcsq + g2) && (r2 > rcsq - g2) && (t0 + u * kLjTeam < cnt)) {  // guard band: exact FP64
+          atomicAdd(&S.ctr[CTR_GUARD], 1ull);
+          in = exact_within(X, n, i, (int)(e[u] & kNbrMask), S.L, S.rc2sq);
+        }
+        const T r2s = in ? r2 : (T)1;
+        const T ir2 = recip_fast<T>(r2s);
+        const T sr2 = sig2 * ir2;
+        const T sr6 = sr2 * sr2 * sr2;
+        const T sr12 = sr6 * sr6;
+        const T g = in ? eps24 * (sr12 + sr12 - sr6) * ir2 : (T)0;  // F_i = -g d
+        fx = fma(-g, dx, fx);
+        fy = fma(-g, dy, fy);
+        fz = fma(-g, dz, fz);
+        if (energy) {
+          uu_t += in ? eps4 * (sr12 - sr6) : (T)0;
+          ww_t += g * r2;
+        }
       }
     }
   }
-  // combine the team's shares (all lanes take part in the shuffles)
-  double F[3], uu = 0.0, ww = 0.0;
+  Acc3<T> f;
+  AccS<T> u, w;
+  f.add(fx, fy, fz);
+  if (energy) {
+    u.add(uu_t);
+    w.add(ww_t);
+  }
+  // combine the team's shares (all lanes take part in the shuffles); the (hi, lo) results
+  // are parked in shared memory and converted to FP64 by the full-warp epilogue below.
+  // On GB300 an FP64 instruction costs 64 FP32 issue slots, so the FP64 work runs on
+  // full warps: warp 0 updates the block's 32 particles with one lane each.
+  constexpr int kPer = 256 / kLjTeam;
+  __shared__ T sFh[3][kPer], sFl[3][kPer], sEh[2][kPer], sEl[2][kPer];
+  const int team = threadIdx.x / kLjTeam;
   if constexpr (sizeof(T) == 4) {
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      team_sum<T>(f.c[a]);
-      F[a] = f.get(a);
-    }
+    for (int a = 0; a < 3; ++a) team_sum<T>(f.c[a]);
     if (energy) {
       team_sum<T>(u.c);
       team_sum<T>(w.c);
-      uu = u.get();
-      ww = w.get();
+    }
+    if (tl == 0) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        sFh[a][team] = f.c[a].hi;
+        sFl[a][team] = f.c[a].lo;
+      }
+      sEh[0][team] = active && energy ? u.c.hi : 0.f;
+      sEl[0][team] = active && energy ? u.c.lo : 0.f;
+      sEh[1][team] = active && energy ? w.c.hi : 0.f;
+      sEl[1][team] = active && energy ? w.c.lo : 0.f;
     }
   } else {
+    double Fd[3] = {f.get(0), f.get(1), f.get(2)};
+    double ud = energy ? u.get() : 0.0, wd = energy ? w.get() : 0.0;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      F[a] = f.get(a);
-      team_sum_d(F[a]);
-    }
+    for (int a = 0; a < 3; ++a) team_sum_d(Fd[a]);
     if (energy) {
-      uu = u.get();
-      ww = w.get();
-      team_sum_d(uu);
-      team_sum_d(ww);
+      team_sum_d(ud);
+      team_sum_d(wd);
     }
-  }
-  double u_out = 0.0, w_out = 0.0;
-  if (active && tl == 0) {
-    bool bad = false;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      S.f2[a * n + i] = F[a];
-      bad |= !isfinite(F[a]);
-    }
-    if (kind == LJ_MID) {
-      // closing half kick of this inner step + opening half kick of the next, then the drift
-      double xn[3], rel[3];
-      double* Xo = S.X[it.buf ^ 1];
+    if (tl == 0) {
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        double vv = S.v[a * n + i] + S.dt_in * S.inv_mass * F[a];
-        S.v[a * n + i] = vv;
-        xn[a] = X[a * n + i] + S.dt_in * vv;
-        Xo[a * n + i] = xn[a];
-        bad |= !isfinite(vv);
+        sFh[a][team] = Fd[a];
+        sFl[a][team] = 0.0;
       }
-      cell_rel(S, S.pcell[i], xn, rel);
-      store_pos<T>(S, it.buf ^ 1, i, rel, true);
-    } else if (kind == LJ_LAST) {
+      sEh[0][team] = active ? ud : 0.0;
+      sEl[0][team] = 0.0;
+      sEh[1][team] = active ? wd : 0.0;
+      sEl[1][team] = 0.0;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int q = it.begin + threadIdx.x;
+    if (q < n) {
+      double Fq[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) Fq[a] = (double)sFh[a][threadIdx.x] + (double)sFl[a][threadIdx.x];
+      bool bad = false;
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        double vv = S.v[a * n + i] + 0.5 * S.dt_in * S.inv_mass * F[a];
-        S.v[a * n + i] = vv;
-        bad |= !isfinite(vv);
+        S.f2[a * n + q] = Fq[a];
+        bad |= !finite_bits(Fq[a]);
       }
+      if (kind == LJ_MID) {
+        // closing half kick of this inner step + opening half kick of the next, then the drift
+        const double c = S.dt_in * S.inv_mass;
+        double xn[3], rel[3];
+        double* Xo = S.X[it.buf ^ 1];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const double vv = fma(c, Fq[a], S.v[a * n + q]);
+          S.v[a * n + q] = vv;
+          xn[a] = fma(S.dt_in, vv, X[a * n + q]);
+          Xo[a * n + q] = xn[a];
+          bad |= !finite_bits(vv);
+        }
+        cell_rel(S, S.pcell[q], xn, rel);
+        store_pos<T>(S, it.buf ^ 1, q, rel, true);
+      } else if (kind == LJ_LAST) {
+        const double c = 0.5 * S.dt_in * S.inv_mass;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const double vv = fma(c, Fq[a], S.v[a * n + q]);
+          S.v[a * n + q] = vv;
+          bad |= !finite_bits(vv);
+        }
+      }
+      if (bad) atomicOr(&S.flags[FLG_ERR], ERR_NONFINITE);
     }
-    if (bad) atomicOr(&S.flags[FLG_ERR], ERR_NONFINITE);
-    u_out = 0.5 * uu;  // every pair appears in both members' lists
-    w_out = 0.5 * ww;
-  }
-  if (energy) {
-    double us = block_sum(u_out, red);
-    double ws = block_sum(w_out, red);
-    if (threadIdx.x == 0) {
-      atomicAdd(&S.acc[ACC_U2], us);
-      atomicAdd(&S.acc[ACC_W2], ws);
+    if (energy) {  // every pair appears in both members' lists: halve
+      const double us = warp_sum(0.5 * ((double)sEh[0][threadIdx.x] + (double)sEl[0][threadIdx.x]));
+      const double ws = warp_sum(0.5 * ((double)sEh[1][threadIdx.x] + (double)sEl[1][threadIdx.x]));
+      if (threadIdx.x == 0) {
+        atomicAdd(&S.acc[ACC_U2], us);
+        atomicAdd(&S.acc[ACC_W2], ws);
+      }
     }
   }
 }
@@ -267,7 +330,7 @@ __global__ void __launch_bounds__(256, 4) k_lj(const SysDev* __restrict__ sys, c
 // with d_ij = x_j - x_i, d_ik = x_k - x_i, d_jk = x_k - x_j.
 
 struct AtmLayout {
-  size_t table, nd, nslot, nidx, queue, sp, sl, acc, sidx, sst, total;
+  size_t table, nd, nslot, nidx, queue, aq, sp, sl, acc, sidx, sst, total;
 };
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
@@ -277,11 +340,12 @@ __host__ __device__ inline AtmLayout atm_layout(int smax) {
   using T4 = typename V4<T>::type;
   AtmLayout l;
   size_t o = 0;
-  l.table = o; o = al16(o + sizeof(uint16_t) * kPairTable);
+  l.table = o;  // the pair table is read from global memory through L1
   l.nd = o; o = al16(o + sizeof(T4) * kMaxHalf * kAtmWarps);
-  l.nslot = o; o = al16(o + sizeof(int) * kMaxHalf * kAtmWarps);
+  l.nslot = o; o = al16(o + sizeof(unsigned short) * kMaxHalf * kAtmWarps);
   l.nidx = o; o = al16(o + sizeof(int) * kMaxHalf * kAtmWarps);
   l.queue = o; o = al16(o + sizeof(unsigned) * kQueue * kAtmWarps);
+  l.aq = o; o = al16(o + sizeof(T) * 3 * kMaxHalf * kAtmWarps);
   l.sp = o; o = al16(o + sizeof(T4) * smax);
   l.sl = o; o = al16(o + (sizeof(T) == 4 ? sizeof(T4) * smax : 0));
   l.acc = o; o = al16(o + sizeof(T) * 3 * smax);
@@ -334,13 +398,12 @@ __device__ __forceinline__ void atm_triplet(const T nu, const typename V4<T>::ty
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kAtmThreads, 2)
+__global__ void __launch_bounds__(kAtmThreads, 3)
     k_atm(const SysDev* __restrict__ sys, const CItem* __restrict__ items, int nitems,
           const uint16_t* __restrict__ gtable, int smax) {
   using T4 = typename V4<T>::type;
   extern __shared__ __align__(16) unsigned char smem[];
   const AtmLayout Ly = atm_layout<T>(smax);
-  uint16_t* table = reinterpret_cast<uint16_t*>(smem + Ly.table);
   T4* sp = reinterpret_cast<T4*>(smem + Ly.sp);
   T4* sl = reinterpret_cast<T4*>(smem + Ly.sl);
   T* acc = reinterpret_cast<T*>(smem + Ly.acc);
@@ -349,14 +412,16 @@ __global__ void __launch_bounds__(kAtmThreads, 2)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   T4* nd = reinterpret_cast<T4*>(smem + Ly.nd) + warp * kMaxHalf;
-  int* nslot = reinterpret_cast<int*>(smem + Ly.nslot) + warp * kMaxHalf;
+  unsigned short* nslot = reinterpret_cast<unsigned short*>(smem + Ly.nslot) + warp * kMaxHalf;
   int* nidx = reinterpret_cast<int*>(smem + Ly.nidx) + warp * kMaxHalf;
   unsigned* queue = reinterpret_cast<unsigned*>(smem + Ly.queue) + warp * kQueue;
+  // forces on the neighbours of the warp's current base particle, by list position
+  T* aq = reinterpret_cast<T*>(smem + Ly.aq) + warp * 3 * kMaxHalf;
 
   __shared__ int st_begin[28], st_cnt[27], st_cell[27], st_s[27];
   __shared__ double red[32];
+  __shared__ int next_base;
 
-  for (int t = threadIdx.x; t < kPairTable; t += blockDim.x) table[t] = gtable[t];
 
   for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
     const CItem it = items[item];
@@ -389,72 +454,108 @@ __global__ void __launch_bounds__(kAtmThreads, 2)
       if (lane == 26) st_begin[27] = incl;
     }
     __syncthreads();
-    const int nstaged = min(st_begin[27], smax);
-    const int nbase = min(st_cnt[0], nstaged);
-    if (st_begin[27] > smax && threadIdx.x == 0) atomicOr(&S.flags[FLG_ERR], ERR_CELL_CAP);
-    // ---- stage particles (coordinates relative to the base cell centre)
-    const T edge_hi = (T)S.edge;
-    const T edge_lo = (T)(S.edge - (double)edge_hi);
+    // ---- stage particles with coordinates relative to the base cell centre.  The base cell
+    //      fills slots [0, nbase) in sorted order.  A particle of another cell is kept only if
+    //      it lies within r_c of the base cell's box (no triplet of a base particle can include
+    //      the others) and is appended through a shared counter; a dropped particle receives
+    //      zero partial forces from this cell.
+    __shared__ int n_kept;
+    const int nbase = min(st_cnt[0], smax);
+    if (threadIdx.x == 0) {
+      n_kept = nbase;
+      if (st_cnt[0] > smax) atomicOr(&S.flags[FLG_ERR], ERR_CELL_CAP);
+    }
+    __syncthreads();
+    const T edge_hi = Par<T>::edge(S);
+    const T edge_lo = Par<T>::edge_lo(S);
+    const T half_e = Par<T>::half_edge(S);
+    const T reach2 = Par<T>::reach2(S);
+    T* part = reinterpret_cast<T*>(S.partial);
     for (int l = warp; l < 27; l += kAtmWarps) {
       const int cnt = st_cnt[l];
       if (cnt == 0) continue;
       const int s = st_s[l];
       const int c0 = S.cell_start[st_cell[l]];
       const T ox = (T)(s % 3 - 1), oy = (T)((s / 3) % 3 - 1), oz = (T)(s / 9 - 1);
-      for (int e = lane; e < cnt; e += 32) {
-        const int slot = st_begin[l] + e;
-        if (slot >= smax) break;
+      for (int e0 = 0; e0 < cnt; e0 += 32) {
+        const int e = e0 + lane;
+        const bool have = e < cnt;
         const int p = c0 + e;
-        T4 h = reinterpret_cast<const T4*>(S.pos[it.buf])[p];
         T4 hs, ls;
-        if (sizeof(T) == 4) {
-          T4 lo = reinterpret_cast<const T4*>(S.poslo)[p];
-          float sx, ex, sy, ey, sz, ez;
-          two_sum((float)h.x, (float)(ox * edge_hi), sx, ex);
-          two_sum((float)h.y, (float)(oy * edge_hi), sy, ey);
-          two_sum((float)h.z, (float)(oz * edge_hi), sz, ez);
-          hs.x = sx; hs.y = sy; hs.z = sz; hs.w = 0;
-          ls.x = lo.x + (ex + ox * edge_lo);
-          ls.y = lo.y + (ey + oy * edge_lo);
-          ls.z = lo.z + (ez + oz * edge_lo);
-          ls.w = 0;
-          sl[slot] = ls;
-        } else {
-          hs.x = h.x + (T)((double)ox * S.edge);
-          hs.y = h.y + (T)((double)oy * S.edge);
-          hs.z = h.z + (T)((double)oz * S.edge);
-          hs.w = 0;
+        if (have) {
+          T4 h = reinterpret_cast<const T4*>(S.pos[it.buf])[p];
+          if (sizeof(T) == 4) {
+            T4 lo = reinterpret_cast<const T4*>(S.poslo)[p];
+            float sx, ex, sy, ey, sz, ez;
+            two_sum((float)h.x, (float)(ox * edge_hi), sx, ex);
+            two_sum((float)h.y, (float)(oy * edge_hi), sy, ey);
+            two_sum((float)h.z, (float)(oz * edge_hi), sz, ez);
+            hs.x = sx; hs.y = sy; hs.z = sz; hs.w = 0;
+            ls.x = lo.x + (ex + ox * edge_lo);
+            ls.y = lo.y + (ey + oy * edge_lo);
+            ls.z = lo.z + (ez + oz * edge_lo);
+            ls.w = 0;
+          } else {
+            hs.x = h.x + (T)((double)ox * S.edge);
+            hs.y = h.y + (T)((double)oy * S.edge);
+            hs.z = h.z + (T)((double)oz * S.edge);
+            hs.w = 0;
+          }
         }
-        sp[slot] = hs;
-        sidx[slot] = p;
-        sst[slot] = (unsigned char)s;
-        acc[slot] = (T)0;
-        acc[smax + slot] = (T)0;
-        acc[2 * smax + slot] = (T)0;
+        bool keep = have;
+        int slot = e;
+        if (l != 0) {
+          if (have) {
+            const T bx = max(abs(hs.x) - half_e, (T)0), by = max(abs(hs.y) - half_e, (T)0),
+                    bz = max(abs(hs.z) - half_e, (T)0);
+            keep = bx * bx + by * by + bz * bz <= reach2;
+          }
+          const unsigned bal = __ballot_sync(0xffffffffu, keep);
+          int base = 0;
+          if (lane == 0 && bal) base = atomicAdd(&n_kept, __popc(bal));
+          base = __shfl_sync(0xffffffffu, base, 0);
+          slot = base + __popc(bal & lt);
+        }
+        if (keep && slot < smax) {
+          if (sizeof(T) == 4) sl[slot] = ls;
+          sp[slot] = hs;
+          sidx[slot] = p;
+          sst[slot] = (unsigned char)s;
+          acc[slot] = (T)0;
+          acc[smax + slot] = (T)0;
+          acc[2 * smax + slot] = (T)0;
+        } else if (have && !keep) {
+          part[(3 * (size_t)s + 0) * n + p] = (T)0;
+          part[(3 * (size_t)s + 1) * n + p] = (T)0;
+          part[(3 * (size_t)s + 2) * n + p] = (T)0;
+        }
       }
     }
     __syncthreads();
-    const T rcsq = (T)S.rc3sq;
-    const T g3 = (T)S.guard3;
-    const T nu = (T)S.nu;
+    const int nstaged = min(n_kept, smax);
+    if (n_kept > smax && threadIdx.x == 0) atomicOr(&S.flags[FLG_ERR], ERR_CELL_CAP);
+    const T rcsq = Par<T>::rc3sq(S);
+    const T g3 = Par<T>::guard3(S);
+    const T nu = Par<T>::nu(S);
     AccS<T> uacc;
     unsigned long long ntrip = 0;
-    // ---- one warp per base particle i
-    for (int is = warp; is < nbase; is += kAtmWarps) {
+    // ---- one warp per base particle i.  Warps take particles from a shared counter in
+    //      increasing sorted order: the lowest indices own the longest half lists, so the
+    //      longest jobs start first and the CTA's warps finish close together.
+    if (threadIdx.x == 0) next_base = kAtmWarps;
+    __syncthreads();
+    for (int is = warp; is < nbase;) {
       const T4 pi = sp[is];
-      T4 li;
-      if (sizeof(T) == 4) li = sl[is];
       const int gi = sidx[is];
-      // 1. half list
+      // 1. half list: staged particles after i with r_ij <= r_c (hi parts; guard band in FP64)
       int m = 0;
       for (int t0 = is + 1; t0 < nstaged; t0 += 32) {
         const int t = t0 + lane;
         bool ok = false;
-        T4 d4;
         if (t < nstaged) {
           const T4 pt = sp[t];
-          T dx = pt.x - pi.x, dy = pt.y - pi.y, dz = pt.z - pi.z;
-          T r2 = dx * dx + dy * dy + dz * dz;
+          const T dx = pt.x - pi.x, dy = pt.y - pi.y, dz = pt.z - pi.z;
+          const T r2 = dx * dx + dy * dy + dz * dz;
           if (r2 <= rcsq + g3) {
             if (r2 >= rcsq - g3) {
               atomicAdd(&S.ctr[CTR_GUARD], 1ull);
@@ -463,27 +564,11 @@ __global__ void __launch_bounds__(kAtmThreads, 2)
               ok = true;
             }
           }
-          if (ok && sizeof(T) == 4) {  // full-precision difference: (hi_t - hi_i) exactly + lo terms
-            const T4 lt4 = sl[t];
-            float s0, e0, s1, e1, s2, e2;
-            two_sum((float)pt.x, -(float)pi.x, s0, e0);
-            two_sum((float)pt.y, -(float)pi.y, s1, e1);
-            two_sum((float)pt.z, -(float)pi.z, s2, e2);
-            dx = s0 + (e0 + ((float)lt4.x - (float)li.x));
-            dy = s1 + (e1 + ((float)lt4.y - (float)li.y));
-            dz = s2 + (e2 + ((float)lt4.z - (float)li.z));
-            r2 = dx * dx + dy * dy + dz * dz;
-          }
-          d4.x = dx; d4.y = dy; d4.z = dz; d4.w = r2;
         }
         const unsigned bal = __ballot_sync(0xffffffffu, ok);
         if (ok) {
           const int pos = m + __popc(bal & lt);
-          if (pos < kMaxHalf) {
-            nd[pos] = d4;
-            nslot[pos] = t;
-            nidx[pos] = sidx[t];
-          }
+          if (pos < kMaxHalf) nslot[pos] = (unsigned short)t;
         }
         m += __popc(bal);
       }
@@ -492,75 +577,139 @@ __global__ void __launch_bounds__(kAtmThreads, 2)
         m = kMaxHalf;
       }
       __syncwarp();
+      //    full-precision difference vectors of the accepted neighbours: (hi_t - hi_i) exactly
+      //    by TwoSum, plus the lo parts (FP32); plain differences in FP64
+      {
+        T4 li;
+        if (sizeof(T) == 4) li = sl[is];
+        for (int q = lane; q < m; q += 32) {
+          const int t = nslot[q];
+          const T4 pt = sp[t];
+          T dx, dy, dz;
+          if (sizeof(T) == 4) {
+            const T4 lt4 = sl[t];
+            float s0, e0, s1, e1, s2, e2;
+            two_sum((float)pt.x, -(float)pi.x, s0, e0);
+            two_sum((float)pt.y, -(float)pi.y, s1, e1);
+            two_sum((float)pt.z, -(float)pi.z, s2, e2);
+            dx = s0 + (e0 + ((float)lt4.x - (float)li.x));
+            dy = s1 + (e1 + ((float)lt4.y - (float)li.y));
+            dz = s2 + (e2 + ((float)lt4.z - (float)li.z));
+          } else {
+            dx = pt.x - pi.x;
+            dy = pt.y - pi.y;
+            dz = pt.z - pi.z;
+          }
+          T4 d4;
+          d4.x = dx; d4.y = dy; d4.z = dz; d4.w = dx * dx + dy * dy + dz * dz;
+          nd[q] = d4;
+          nidx[q] = sidx[t];
+        }
+      }
+      __syncwarp();
       // 2. neighbour pairs (j, k) of the half list, k-major through the pair table;
       //    pairs with r_jk <= r_c are compacted into the warp's queue in table order
       T fi0 = 0, fi1 = 0, fi2 = 0;
       const int np = m * (m - 1) / 2;
       int qn = 0;
+      for (int q = lane; q < m; q += 32) {
+        aq[q] = (T)0;
+        aq[kMaxHalf + q] = (T)0;
+        aq[2 * kMaxHalf + q] = (T)0;
+      }
+      __syncwarp();
+      // add a force to list position q of the warp-private accumulator.  Plain read-modify-
+      // write; lanes of the warp that target the same q in the same step are detected with
+      // a match and their values summed by shuffles first, so every slot has one writer.
+      auto add_q = [&](unsigned mask, int q, T fx, T fy, T fz) {
+        const unsigned grp = __match_any_sync(mask, q);
+        const int leader = __ffs(grp) - 1;
+        if (grp != (1u << lane)) {
+          unsigned others = grp & ~(1u << leader);
+          while (others) {
+            const int src = __ffs(others) - 1;
+            others &= others - 1;
+            const T ox = __shfl_sync(grp, fx, src), oy = __shfl_sync(grp, fy, src), oz = __shfl_sync(grp, fz, src);
+            if (lane == leader) {
+              fx += ox;
+              fy += oy;
+              fz += oz;
+            }
+          }
+        }
+        if (lane == leader) {
+          aq[q] += fx;
+          aq[kMaxHalf + q] += fy;
+          aq[2 * kMaxHalf + q] += fz;
+        }
+      };
       // 3. queued triplets: lane l takes a contiguous run of the queue, so its pairs mostly
-      //    share k (k-major order): F_k and d_k stay in registers until k changes; F_j goes
-      //    to the staged accumulator of j (targets rarely coincide across lanes)
+      //    share k (k-major order): F_k and d_k stay in registers until k changes
       auto drain = [&](int count) {
         if (count <= 0) return;
         const int C = ((count + 31) >> 5) | 1;  // odd run length: lanes start in different banks
-        const int e0 = lane * C, e1 = min(e0 + C, count);
-        int curk = -1, sk = 0;
+        const int e0 = lane * C, len = max(0, min(e0 + C, count) - e0);
+        // each lane starts its run at a lane-dependent offset: columns list j in ascending
+        // order, so lanes that walked their runs in step would hit the same j together
+        int off = len ? (lane * 5) % len : 0;
+        int curk = -1;
         T4 dk;
         T fk0 = 0, fk1 = 0, fk2 = 0;
-        for (int e = e0; e < e1; ++e) {
-          const unsigned entry = queue[e];
-          const int j = (int)(entry & 0xffffu), k = (int)(entry >> 16);
-          if (k != curk) {
-            if (curk >= 0) {
-              atomicAdd(&acc[sk], fk0);
-              atomicAdd(&acc[smax + sk], fk1);
-              atomicAdd(&acc[2 * smax + sk], fk2);
+        for (int r = 0; r < C; ++r) {  // every lane runs all C steps (warp-wide ballots below)
+          const bool act = r < len;
+          const unsigned amask = __ballot_sync(0xffffffffu, act);
+          if (act) {
+            const int e = e0 + off;
+            if (++off == len) off = 0;
+            const unsigned entry = queue[e];
+            const int j = (int)(entry & 0xffffu), k = (int)(entry >> 16);
+            const bool change = k != curk;
+            const unsigned cmask = __ballot_sync(amask, change && curk >= 0);
+            if (change && curk >= 0) add_q(cmask, curk, fk0, fk1, fk2);
+            if (change) {
+              curk = k;
+              dk = nd[k];
+              fk0 = fk1 = fk2 = 0;
             }
-            curk = k;
-            dk = nd[k];
-            sk = nslot[k];
-            fk0 = fk1 = fk2 = 0;
+            TripletOut<T> o;
+            atm_triplet<T>(nu, nd[j], dk, o);
+            fi0 += o.fi[0];
+            fi1 += o.fi[1];
+            fi2 += o.fi[2];
+            fk0 += o.fk[0];
+            fk1 += o.fk[1];
+            fk2 += o.fk[2];
+            add_q(amask, j, o.fj[0], o.fj[1], o.fj[2]);
+            if (energy) uacc.add(o.u);
           }
-          TripletOut<T> o;
-          atm_triplet<T>(nu, nd[j], dk, o);
-          fi0 += o.fi[0];
-          fi1 += o.fi[1];
-          fi2 += o.fi[2];
-          fk0 += o.fk[0];
-          fk1 += o.fk[1];
-          fk2 += o.fk[2];
-          const int sj = nslot[j];
-          atomicAdd(&acc[sj], o.fj[0]);
-          atomicAdd(&acc[smax + sj], o.fj[1]);
-          atomicAdd(&acc[2 * smax + sj], o.fj[2]);
-          if (energy) uacc.add(o.u);
         }
-        if (curk >= 0) {
-          atomicAdd(&acc[sk], fk0);
-          atomicAdd(&acc[smax + sk], fk1);
-          atomicAdd(&acc[2 * smax + sk], fk2);
-        }
+        __syncwarp();
+        const unsigned fmask = __ballot_sync(0xffffffffu, curk >= 0);
+        if (curk >= 0) add_q(fmask, curk, fk0, fk1, fk2);
+        __syncwarp();
         ntrip += (unsigned long long)count;
       };
       for (int p0 = 0; p0 < np; p0 += 32) {
         const int p = p0 + lane;
-        bool ok = false;
+        bool ok = false, band = false;
         unsigned entry = 0;
+        int jj = 0, kk = 0;
         if (p < np) {
-          const unsigned e = table[p];
-          const int j = (int)(e & 0xffu), k = (int)(e >> 8);
-          const T4 dj = nd[j], dk = nd[k];
+          const unsigned e = __ldg(gtable + p);
+          jj = (int)(e & 0xffu);
+          kk = (int)(e >> 8);
+          const T4 dj = nd[jj], dk = nd[kk];
           const T ex = dk.x - dj.x, ey = dk.y - dj.y, ez = dk.z - dj.z;
           const T c = ex * ex + ey * ey + ez * ez;
-          if (c <= rcsq + g3) {
-            if (c >= rcsq - g3) {
-              atomicAdd(&S.ctr[CTR_GUARD], 1ull);
-              ok = exact_within(X, n, nidx[j], nidx[k], S.L, S.rc3sq);
-            } else {
-              ok = true;
-            }
+          ok = c < rcsq - g3;
+          band = (c >= rcsq - g3) && (c <= rcsq + g3);
+          entry = (unsigned)jj | ((unsigned)kk << 16);
+        }
+        if (__any_sync(0xffffffffu, band)) {  // rare: decide the guard band exactly in FP64
+          if (band) {
+            atomicAdd(&S.ctr[CTR_GUARD], 1ull);
+            ok = exact_within(X, n, nidx[jj], nidx[kk], S.L, S.rc3sq);
           }
-          entry = (unsigned)j | ((unsigned)k << 16);
         }
         const unsigned bal = __ballot_sync(0xffffffffu, ok);
         if (ok) queue[qn + __popc(bal & lt)] = entry;
@@ -574,6 +723,15 @@ __global__ void __launch_bounds__(kAtmThreads, 2)
       }
       __syncwarp();
       drain(qn);
+      __syncwarp();
+      // neighbours' totals for this base particle -> staged accumulators (one atomic per
+      // neighbour and component); F_i by a warp reduction
+      for (int q = lane; q < m; q += 32) {
+        const int sq = nslot[q];
+        atomicAdd(&acc[sq], aq[q]);
+        atomicAdd(&acc[smax + sq], aq[kMaxHalf + q]);
+        atomicAdd(&acc[2 * smax + sq], aq[2 * kMaxHalf + q]);
+      }
       fi0 = warp_sum_t<T>(fi0);
       fi1 = warp_sum_t<T>(fi1);
       fi2 = warp_sum_t<T>(fi2);
@@ -583,10 +741,12 @@ __global__ void __launch_bounds__(kAtmThreads, 2)
         atomicAdd(&acc[2 * smax + is], fi2);
       }
       __syncwarp();
+      int nx = 0;
+      if (lane == 0) nx = atomicAdd(&next_base, 1);
+      is = __shfl_sync(0xffffffffu, nx, 0);
     }
     __syncthreads();
     // ---- partial forces of every staged particle, one slot per stencil offset
-    T* part = reinterpret_cast<T*>(S.partial);
     for (int t = threadIdx.x; t < nstaged; t += blockDim.x) {
       const size_t s = sst[t];
       const int p = sidx[t];
@@ -600,6 +760,257 @@ __global__ void __launch_bounds__(kAtmThreads, 2)
       if (threadIdx.x == 0) {
         atomicAdd(&S.acc[ACC_U3], us);
         atomicAdd(&S.acc[ACC_W3], 9.0 * us);  // phi3 is homogeneous of degree -9: sum r.F = 9 phi3
+      }
+    }
+  }
+}
+
+// ============================================================== ATM, one warp per particle
+//
+// Variant without Newton-3 scatter: warp x gathers x's neighbours within r_c3 from the
+// fresh pair list (a superset: r_c2 + skin >= r_c3 is required), tests every unordered
+// pair (y, z) of them for r_yz <= r_c3 and evaluates only the force on x,
+//   F_x = 2 (phi_a d_xy + phi_b d_xz),  a = r_xy^2, b = r_xz^2, c = r_yz^2,
+// so each triplet is evaluated once from each of its three members.  No shared-memory
+// accumulation, no staging, no partial buffers: F_x is a warp reduction written directly.
+// Energy: each evaluation adds phi / 3.  Triplets are counted where x has the smallest index.
+
+// warp sum of one FP32 value per lane as an error-free (hi, lo) pair (TwoSum tree)
+__device__ __forceinline__ void warp_sum_pair(float v, float& hi, float& lo) {
+  hi = v;
+  lo = 0.f;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, hi, o);
+    const float ol = __shfl_xor_sync(0xffffffffu, lo, o);
+    float s, e;
+    two_sum(hi, oh, s, e);
+    hi = s;
+    lo = lo + (ol + e);
+  }
+}
+
+// warp sum of one value per lane: FP32 with compensation (result valid in every lane);
+// plain FP64 in the FP64 path
+template <typename T> __device__ __forceinline__ double warp_sum_comp(T v);
+template <> __device__ __forceinline__ double warp_sum_comp<float>(float v) {
+  float hi = v, lo = 0.f;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, hi, o);
+    const float ol = __shfl_xor_sync(0xffffffffu, lo, o);
+    float s, e;
+    two_sum(hi, oh, s, e);
+    hi = s;
+    lo = lo + (ol + e);
+  }
+  return (double)hi + (double)lo;
+}
+template <> __device__ __forceinline__ double warp_sum_comp<double>(double v) { return warp_sum(v); }
+
+template <typename T>
+__device__ __forceinline__ void atm_vertex(const T nu, const typename V4<T>::type dy, const typename V4<T>::type dz,
+                                           T& fx, T& fy, T& fz, T& u) {
+  const T ex = dz.x - dy.x, ey = dz.y - dy.y, ez = dz.z - dy.z;  // d_yz
+  const T a = dy.w, b = dz.w;
+  const T c = ex * ex + ey * ey + ez * ez;
+  const T ab = a * b;
+  const T q = ab * c;
+  const T t = rsqrt_acc<T>(q);
+  const T w = t * t;
+  const T t3 = w * t;
+  const T t5 = t3 * w;
+  const T s = a + b + c;
+  const T A = s - (c + c), B = s - (b + b), C = s - (a + a);
+  const T AB = A * B, AC = A * C;
+  const T P = AB * C;
+  const T Pa = (a + a) * C - AB;
+  const T Pb = (b + b) * B - AC;
+  const T G = (T)1.5 * q + (T)0.9375 * P;
+  const T ia = (b * c) * w, ib = (a * c) * w;
+  const T nt5 = nu * t5;
+  const T pa2 = (T)2 * nt5 * ((T)0.375 * Pa - ia * G);
+  const T pb2 = (T)2 * nt5 * ((T)0.375 * Pb - ib * G);
+  fx = pa2 * dy.x + pb2 * dz.x;
+  fy = pa2 * dy.y + pb2 * dz.y;
+  fz = pa2 * dy.z + pb2 * dz.z;
+  u = nu * t3 * ((T)1 + (T)0.375 * P * w);
+}
+
+constexpr int kPaWarps = 4;
+constexpr int kMaxFull = 128;  // neighbours within r_c3 of one particle
+
+template <typename T>
+__global__ void __launch_bounds__(32 * kPaWarps)
+    k_atm_pa(const SysDev* __restrict__ sys, const PItem* __restrict__ items, const uint16_t* __restrict__ gtable) {
+  using T4 = typename V4<T>::type;
+  __shared__ T4 s_nd[kPaWarps][kMaxFull];
+  __shared__ int s_idx[kPaWarps][kMaxFull];
+  __shared__ unsigned s_q[kPaWarps][64];
+  const PItem it = items[blockIdx.x];
+  const SysDev& S = sys[it.sys];
+  const bool energy = (it.mode & M_ENERGY) != 0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const int x = it.begin + warp;
+  if (x >= S.n) return;  // whole warp leaves together
+  const int n = S.n;
+  T4* nd = s_nd[warp];
+  int* nidx = s_idx[warp];
+  unsigned* queue = s_q[warp];
+  const T4* __restrict__ P = reinterpret_cast<const T4*>(S.pos[it.buf]);
+  const T4* __restrict__ PL = reinterpret_cast<const T4*>(S.poslo);
+  const double* __restrict__ X = S.X[it.buf];
+  const T edge = Par<T>::edge(S), edge_lo = Par<T>::edge_lo(S);
+  const T rcsq = Par<T>::rc3sq(S), g3 = Par<T>::guard3(S), nu = Par<T>::nu(S);
+  const T4 px = P[x];
+  T4 lx;
+  if (sizeof(T) == 4) lx = PL[x];
+  // 1. neighbours within r_c3 from the pair list (full-precision differences)
+  const int cnt = S.nbr_cnt[x];
+  const int* __restrict__ row = S.nbr + (size_t)x * S.maxnb;
+  int m = 0;
+  for (int t0 = 0; t0 < cnt; t0 += 32) {
+    const int t = t0 + lane;
+    bool ok = false, band = false;
+    int j = x;
+    T dx = 0, dy = 0, dz = 0;
+    if (t < cnt) {
+      const unsigned e = (unsigned)__ldg(row + t);
+      j = (int)(e & kNbrMask);
+      const unsigned cde = e >> kNbrShift;
+      const T ox = (T)(cde & 3u) - (T)1, oy = (T)((cde >> 2) & 3u) - (T)1, oz = (T)(cde >> 4) - (T)1;
+      const T4 pj = P[j];
+      if (sizeof(T) == 4) {
+        const T4 lj = PL[j];
+        float s1, e1, s2, e2;
+        two_sum((float)pj.x, -(float)px.x, s1, e1);
+        two_sum(s1, (float)(ox * edge), s2, e2);
+        dx = s2 + ((e1 + e2) + (((float)lj.x - (float)lx.x) + (float)(ox * edge_lo)));
+        two_sum((float)pj.y, -(float)px.y, s1, e1);
+        two_sum(s1, (float)(oy * edge), s2, e2);
+        dy = s2 + ((e1 + e2) + (((float)lj.y - (float)lx.y) + (float)(oy * edge_lo)));
+        two_sum((float)pj.z, -(float)px.z, s1, e1);
+        two_sum(s1, (float)(oz * edge), s2, e2);
+        dz = s2 + ((e1 + e2) + (((float)lj.z - (float)lx.z) + (float)(oz * edge_lo)));
+      } else {
+        dx = (pj.x - px.x) + ox * edge;
+        dy = (pj.y - px.y) + oy * edge;
+        dz = (pj.z - px.z) + oz * edge;
+      }
+      const T r2 = dx * dx + dy * dy + dz * dz;
+      ok = r2 < rcsq - g3;
+      band = (r2 >= rcsq - g3) && (r2 <= rcsq + g3);
+    }
+    if (__any_sync(0xffffffffu, band)) {
+      if (band) {
+        atomicAdd(&S.ctr[CTR_GUARD], 1ull);
+        ok = exact_within(X, n, x, j, S.L, S.rc3sq);
+      }
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, ok);
+    if (ok) {
+      const int pos = m + __popc(bal & lt);
+      if (pos < kMaxFull) {
+        T4 d4;
+        d4.x = dx; d4.y = dy; d4.z = dz; d4.w = dx * dx + dy * dy + dz * dz;
+        nd[pos] = d4;
+        nidx[pos] = j;
+      }
+    }
+    m += __popc(bal);
+  }
+  if (m > kMaxFull) {
+    if (lane == 0) atomicOr(&S.flags[FLG_ERR], ERR_HALF_CAP);
+    m = kMaxFull;
+  }
+  __syncwarp();
+  // 2./3. pairs (y, z) of the list through the k-major table; accepted pairs go to a 64-entry
+  //        ring and are evaluated 32 at a time (all lanes busy)
+  T f0 = 0, f1 = 0, f2 = 0, uu = 0;
+  unsigned long long own = 0;
+  const int np = m * (m - 1) / 2;
+  unsigned head = 0, tail = 0;  // warp-uniform ring positions
+  auto eval = [&](unsigned entry) {
+    const int y = (int)(entry & 0xffffu), z = (int)(entry >> 16);
+    T ax, ay, az, au;
+    atm_vertex<T>(nu, nd[y], nd[z], ax, ay, az, au);
+    f0 += ax;
+    f1 += ay;
+    f2 += az;
+    uu += au;
+    own += (x < nidx[y] && x < nidx[z]) ? 1ull : 0ull;
+  };
+  for (int p0 = 0; p0 < np; p0 += 32) {
+    const int p = p0 + lane;
+    bool ok = false, band = false;
+    unsigned entry = 0;
+    if (p < np) {
+      const unsigned e = __ldg(gtable + p);
+      const T4 dy = nd[e & 0xffu], dz = nd[e >> 8];
+      const T ex = dz.x - dy.x, ey = dz.y - dy.y, ez = dz.z - dy.z;
+      const T c = ex * ex + ey * ey + ez * ez;
+      ok = c < rcsq - g3;
+      band = abs(c - rcsq) <= g3;
+      entry = (e & 0xffu) | ((e >> 8) << 16);
+    }
+    const unsigned bband = __ballot_sync(0xffffffffu, band);
+    if (bband) {  // rare: decide the guard band exactly in FP64
+      if (band) {
+        atomicAdd(&S.ctr[CTR_GUARD], 1ull);
+        ok = exact_within(X, n, nidx[entry & 0xffffu], nidx[entry >> 16], S.L, S.rc3sq);
+      }
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, ok);
+    if (ok) queue[(tail + __popc(bal & lt)) & 63u] = entry;
+    tail += __popc(bal);
+    if (tail - head >= 32) {
+      __syncwarp();
+      eval(queue[(head + lane) & 63u]);
+      head += 32;
+      __syncwarp();
+    }
+  }
+  __syncwarp();
+  if (lane < (int)(tail - head)) eval(queue[(head + lane) & 63u]);
+  // F_x and the energy share: per-lane FP32 sums combined by an error-free (TwoSum) warp
+  // reduction; the (hi, lo) pair is converted to FP64 by the combine kernel on full warps
+  // (FP64 arithmetic is scarce on GB300)
+  unsigned long long cnt_own = own;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) cnt_own += __shfl_xor_sync(0xffffffffu, cnt_own, o);
+  if constexpr (sizeof(T) == 4) {
+    float h0, l0, h1, l1, h2, l2, hu = 0.f, lu = 0.f;
+    warp_sum_pair(f0, h0, l0);
+    warp_sum_pair(f1, h1, l1);
+    warp_sum_pair(f2, h2, l2);
+    if (energy) warp_sum_pair(uu, hu, lu);
+    if (lane == 0) {
+      float* pf = reinterpret_cast<float*>(S.partial);  // [6][n]: hi x, y, z then lo x, y, z
+      pf[x] = h0;
+      pf[n + x] = h1;
+      pf[2 * n + x] = h2;
+      pf[3 * n + x] = l0;
+      pf[4 * n + x] = l1;
+      pf[5 * n + x] = l2;
+      if (cnt_own) atomicAdd(&S.ctr[CTR_TRIPLETS], cnt_own);
+      if (energy) {
+        const double U = (double)hu + (double)lu;
+        atomicAdd(&S.acc[ACC_U3], U * (1.0 / 3.0));
+        atomicAdd(&S.acc[ACC_W3], 3.0 * U);  // 9 * U / 3
+      }
+    }
+  } else {
+    const double F0 = warp_sum(f0), F1 = warp_sum(f1), F2 = warp_sum(f2);
+    const double U = energy ? warp_sum(uu) : 0.0;
+    if (lane == 0) {
+      S.f3[x] = F0;
+      S.f3[n + x] = F1;
+      S.f3[2 * n + x] = F2;
+      if (cnt_own) atomicAdd(&S.ctr[CTR_TRIPLETS], cnt_own);
+      if (energy) {
+        atomicAdd(&S.acc[ACC_U3], U / 3.0);
+        atomicAdd(&S.acc[ACC_W3], 3.0 * U);
       }
     }
   }
@@ -621,8 +1032,9 @@ __global__ void __launch_bounds__(256) k_combine(const SysDev* __restrict__ sys,
     const int cx = cell % nc, cy = (cell / nc) % nc, cz = cell / (nc * nc);
     const T* part = reinterpret_cast<const T*>(S.partial);
     Acc3<T> f;
+    const bool ready = (it.mode & M_F3READY) != 0;  // the per-particle triplet kernel wrote f3
 #pragma unroll 1
-    for (int s = 0; s < 27; ++s) {
+    for (int s = 0; s < (ready ? 0 : 27); ++s) {
       const int dx = s % 3 - 1, dy = (s / 3) % 3 - 1, dz = s / 9 - 1;
       const int bx = (cx - dx + nc) % nc, by = (cy - dy + nc) % nc, bz = (cz - dz + nc) % nc;
       const int base = (bz * nc + by) * nc + bx;
@@ -630,6 +1042,18 @@ __global__ void __launch_bounds__(256) k_combine(const SysDev* __restrict__ sys,
       f.add(part[(3 * s + 0) * (size_t)n + p], part[(3 * s + 1) * (size_t)n + p], part[(3 * s + 2) * (size_t)n + p]);
     }
     double F[3] = {f.get(0), f.get(1), f.get(2)};
+    if (ready) {
+      if (sizeof(T) == 4) {
+        const float* pf = reinterpret_cast<const float*>(S.partial);
+        F[0] = (double)pf[p] + (double)pf[3 * n + p];
+        F[1] = (double)pf[n + p] + (double)pf[4 * n + p];
+        F[2] = (double)pf[2 * n + p] + (double)pf[5 * n + p];
+      } else {
+        F[0] = S.f3[p];
+        F[1] = S.f3[n + p];
+        F[2] = S.f3[2 * n + p];
+      }
+    }
     bool bad = false;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -762,6 +1186,13 @@ void launch_atm_table(const Launch& L, const CItem* items, int nitems, int grid,
   k_atm<T><<<grid, kAtmThreads, bytes, L.stream>>>(L.sys, items, nitems, table, smax);
 }
 template void launch_atm_table<float>(const Launch&, const CItem*, int, int, int, const uint16_t*);
+
+template <typename T>
+void launch_atm_pa(const Launch& L, const PItem* items, int nitems) {
+  if (nitems > 0) k_atm_pa<T><<<nitems, 32 * kPaWarps, 0, L.stream>>>(L.sys, items, g_table);
+}
+template void launch_atm_pa<float>(const Launch&, const PItem*, int);
+template void launch_atm_pa<double>(const Launch&, const PItem*, int);
 
 template <typename T>
 void launch_combine(const Launch& L, const PItem* items, int nitems, int block) {

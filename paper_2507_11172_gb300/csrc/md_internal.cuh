@@ -8,12 +8,12 @@ namespace r3b {
 // ---------------------------------------------------------------- capacities
 constexpr int kStencil = 27;        // 3 x 3 x 3 cells: cell edge >= every cutoff
 constexpr int kMaxHalf = 128;       // per-particle ATM half list (neighbours with larger sorted index)
-constexpr int kNbrShift = 27;       // LJ list entry = j | (image code << 27)
+constexpr int kNbrShift = 26;       // LJ list entry = j | (image code << 26), code = 2 bits per axis
 constexpr unsigned kNbrMask = (1u << kNbrShift) - 1u;
 constexpr int kPairTable = kMaxHalf * (kMaxHalf - 1) / 2;  // (j, k) pairs, k-major
 constexpr int kAtmWarps = 8;
 constexpr int kAtmThreads = 32 * kAtmWarps;
-constexpr int kQueue = 512;         // per-warp queue of accepted neighbour pairs (j, k)
+constexpr int kQueue = 256;         // per-warp queue of accepted neighbour pairs (j, k)
 constexpr int kLjTeam = 8;          // lanes cooperating on one particle's pair list
 constexpr int kListWarps = 4;       // warps per CTA of the pair-list build
 
@@ -45,7 +45,11 @@ struct SysDev {
   double guard2, guard3;  // half-width of the r^2 band re-decided in FP64 (pair / triplet)
   // integrator
   double dt_in, dt_out, inv_mass, mass;
-  int maxnb, cap_stage;  // pair-list capacity per particle; staged particles per list-build CTA
+  int maxnb, cap_stage;  // pair-list capacity per particle; staged particles per ATM CTA
+  // FP32 copies of the parameters used by the FP32 kernels, computed on the host (on GB300 an
+  // FP64 conversion in every thread costs as much as a pair evaluation)
+  float f_edge, f_edge_lo, f_half_edge, f_rc2sq, f_guard2, f_sig2, f_eps24, f_eps4;
+  float f_rc3sq, f_guard3, f_nu, f_reach2, f_half_skin_sq, f_pad_;
   int precision;  // 0 = FP32 forces, 1 = FP64
   int pad_;
   // state in cell-sorted order, double SoA [3][n] (x block, y block, z block)
@@ -91,6 +95,7 @@ struct SItem {
 // mode bits
 enum : int {
   M_ENERGY = 1 << 8,    // accumulate energies / virials
+  M_F3READY = 1 << 9,   // combine: f3 already holds complete forces (per-particle triplet kernel)
   M_KIND_MASK = 0xff,
 };
 enum : int {  // LJ kinds
@@ -105,6 +110,42 @@ enum : int {  // combine kinds
 };
 
 // ---------------------------------------------------------------- helpers
+
+// parameter in the kernel's precision: the FP32 copy or the FP64 original
+template <typename T> struct Par;
+template <> struct Par<float> {
+  static __device__ __forceinline__ float edge(const SysDev& S) { return S.f_edge; }
+  static __device__ __forceinline__ float edge_lo(const SysDev& S) { return S.f_edge_lo; }
+  static __device__ __forceinline__ float half_edge(const SysDev& S) { return S.f_half_edge; }
+  static __device__ __forceinline__ float rc2sq(const SysDev& S) { return S.f_rc2sq; }
+  static __device__ __forceinline__ float guard2(const SysDev& S) { return S.f_guard2; }
+  static __device__ __forceinline__ float sig2(const SysDev& S) { return S.f_sig2; }
+  static __device__ __forceinline__ float eps24(const SysDev& S) { return S.f_eps24; }
+  static __device__ __forceinline__ float eps4(const SysDev& S) { return S.f_eps4; }
+  static __device__ __forceinline__ float rc3sq(const SysDev& S) { return S.f_rc3sq; }
+  static __device__ __forceinline__ float guard3(const SysDev& S) { return S.f_guard3; }
+  static __device__ __forceinline__ float nu(const SysDev& S) { return S.f_nu; }
+  static __device__ __forceinline__ float reach2(const SysDev& S) { return S.f_reach2; }
+  static __device__ __forceinline__ float half_skin_sq(const SysDev& S) { return S.f_half_skin_sq; }
+};
+template <> struct Par<double> {
+  static __device__ __forceinline__ double edge(const SysDev& S) { return S.edge; }
+  static __device__ __forceinline__ double edge_lo(const SysDev&) { return 0.0; }
+  static __device__ __forceinline__ double half_edge(const SysDev& S) { return 0.5 * S.edge; }
+  static __device__ __forceinline__ double rc2sq(const SysDev& S) { return S.rc2sq; }
+  static __device__ __forceinline__ double guard2(const SysDev& S) { return S.guard2; }
+  static __device__ __forceinline__ double sig2(const SysDev& S) { return S.sig2; }
+  static __device__ __forceinline__ double eps24(const SysDev& S) { return 24.0 * S.eps; }
+  static __device__ __forceinline__ double eps4(const SysDev& S) { return 4.0 * S.eps; }
+  static __device__ __forceinline__ double rc3sq(const SysDev& S) { return S.rc3sq; }
+  static __device__ __forceinline__ double guard3(const SysDev& S) { return S.guard3; }
+  static __device__ __forceinline__ double nu(const SysDev& S) { return S.nu; }
+  static __device__ __forceinline__ double reach2(const SysDev& S) {
+    const double r = S.rc3 * (1.0 + 1e-5) + 1e-5;
+    return r * r;
+  }
+  static __device__ __forceinline__ double half_skin_sq(const SysDev& S) { return S.half_skin_sq; }
+};
 
 template <typename T> struct V4;
 template <> struct V4<float> { using type = float4; };
@@ -207,9 +248,16 @@ int listbuild_configure(int smax, int precision);
 // forces.cu
 template <typename T> void launch_lj(const Launch& L, const PItem* items, int nitems, int block);
 template <typename T> void launch_atm(const Launch& L, const CItem* items, int nitems, int grid, int smax);
+// staged-particle capacity of an ATM CTA: the particles within r_c of a base cell (edge >= r_c)
+// occupy at most the volume of about 21 cells (16 cells plus margin is sized for the typical mean
+// occupancy); more raises ERR_CELL_CAP and a larger cap_cell
+inline int atm_stage_capacity(int cap_cell) { return 16 * cap_cell + 64; }
 // dynamic shared memory of the ATM kernel for smax staged particles; sets the kernel attribute
 // and returns the resident CTAs per SM (0 if it does not fit)
 int atm_configure(int smax, int precision, int* smem_bytes);
+// per-particle ATM variant: items of 4 particles (one warp each)
+template <typename T> void launch_atm_pa(const Launch& L, const PItem* items, int nitems);
+constexpr int kPaPerBlock = 4;
 template <typename T>
 void launch_atm_table(const Launch& L, const CItem* items, int nitems, int grid, int smax, const uint16_t* table);
 template <typename T> void launch_combine(const Launch& L, const PItem* items, int nitems, int block);

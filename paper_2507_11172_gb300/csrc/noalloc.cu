@@ -174,7 +174,7 @@ extern "C" md_status md_atm_forces_noalloc(const double* d_pos, int64_t n, doubl
   int cap = std::max(16, (int)ceil(1.5 * (double)nn / ncell + 12.0));
   for (int attempt = 0; attempt < 4; ++attempt) {
     int smem = 0;
-    const int per_sm = atm_configure(27 * cap, MD_FP32, &smem);
+    const int per_sm = atm_configure(atm_stage_capacity(cap), MD_FP32, &smem);
     if (per_sm <= 0) {
       g_noalloc_error = "md_atm_forces_noalloc: a cell holds more particles than shared memory can stage";
       return MD_ERR_CAPACITY;
@@ -222,6 +222,22 @@ extern "C" md_status md_atm_forces_noalloc(const double* d_pos, int64_t n, doubl
     h.ctr = reinterpret_cast<unsigned long long*>(m + kOffCtr);
     h.flags = reinterpret_cast<int*>(m + kOffFlags);
 
+  {
+    const double r = h.rc3 * (1.0 + 1e-5) + 1e-5;
+    h.f_edge = (float)h.edge;
+    h.f_edge_lo = (float)(h.edge - (double)h.f_edge);
+    h.f_half_edge = (float)(0.5 * h.edge);
+    h.f_rc2sq = (float)h.rc2sq;
+    h.f_guard2 = (float)h.guard2;
+    h.f_sig2 = (float)h.sig2;
+    h.f_eps24 = (float)(24.0 * h.eps);
+    h.f_eps4 = (float)(4.0 * h.eps);
+    h.f_rc3sq = (float)h.rc3sq;
+    h.f_guard3 = (float)h.guard3;
+    h.f_nu = (float)h.nu;
+    h.f_reach2 = (float)(r * r);
+    h.f_half_skin_sq = (float)h.half_skin_sq;
+  }
 #define NA_CK(call)                                  \
   do {                                               \
     cudaError_t e_ = (call);                         \
@@ -242,7 +258,7 @@ extern "C" md_status md_atm_forces_noalloc(const double* d_pos, int64_t n, doubl
     launch_scan(L, d_sit, 1);
     launch_scatter<float>(L, d_pit, nb, 256);  // sorted positions land in X[1]
     NA_CK(cudaMemcpyAsync(h.X[0], h.X[1], 24ull * nn, cudaMemcpyDeviceToDevice, stream));
-    launch_atm_table<float>(L, d_cit, ncell, grid, 27 * cap, D->table);
+    launch_atm_table<float>(L, d_cit, ncell, grid, atm_stage_capacity(cap), D->table);
     launch_combine<float>(L, d_pit, nb, 256);
     k_noalloc_unpack<<<nb, 256, 0, stream>>>(h.f3, h.id_alt, nn, d_f3);
     NA_CK(cudaGetLastError());

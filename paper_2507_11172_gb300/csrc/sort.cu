@@ -127,8 +127,8 @@ __global__ void k_scatter(const SysDev* __restrict__ sys, const PItem* __restric
 // shared memory with coordinates relative to b's centre; one warp per particle i
 // of b tests every staged particle and ballot-compacts those within
 // (r_c2 + skin)^2 (slightly widened: the list may hold a superset) into i's row.
-// Entry = j | image code << 27, code = (dz+1)*9 + (dy+1)*3 + (dx+1) for the cell
-// offset from i's cell to j's cell.  The CTA also moves the permuted state of
+// Entry = j | image code << 26, code = (dx+1) | (dy+1) << 2 | (dz+1) << 4 for the
+// cell offset from i's cell to j's cell.  The CTA also moves the permuted state of
 // b's particles back into place.
 template <typename T>
 __global__ void __launch_bounds__(32 * kListWarps)
@@ -178,7 +178,9 @@ __global__ void __launch_bounds__(32 * kListWarps)
       h.y += oy;
       h.z += oz;
       sp[slot] = h;
-      sj[slot] = (int)((unsigned)(c0 + e) | ((unsigned)l << kNbrShift));
+      // image code: cell offset (dx, dy, dz) + 1 per axis in 2 bits each
+      const unsigned code = (unsigned)(l % 3) | ((unsigned)((l / 3) % 3) << 2) | ((unsigned)(l / 9) << 4);
+      sj[slot] = (int)((unsigned)(c0 + e) | (code << kNbrShift));
     }
   }
   __syncthreads();

@@ -232,3 +232,29 @@ def test_momentum_and_energy_conservation(gpu_lib, cfg1, prec, ptol):
     e0, e1 = ek0 + u20 + u30, ek + u2 + u3
     assert np.abs(p - p0).max() < ptol  # Newton 3: pair and triplet forces sum to zero
     assert abs(e1 - e0) / (ek0 + abs(u20) + abs(u30)) < 5e-3  # truncated potentials: bounded jumps only
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_both_triplet_kernels_match_oracle(gpu_lib, cfg1, cfg1_ref, variant, prec):
+    """Cell kernel with Newton-3 scatter (0) and per-particle kernel (1): same forces, energy
+    and interacting-triplet count as the oracle, at x0 and after a few outer steps."""
+    r3 = gpu_lib
+    with make(r3, cfg1, prec) as s:
+        r3.md_set_atm_kernel(s.handle, variant)
+        f2, f3 = s.forces()
+        _, u2, u3, _ = s.energy()
+        st = s.stats()
+        assert st["atm_kernel"] == variant
+        assert st["triplets_last"] == cfg1_ref["cnt"]
+        assert force_err(f3, cfg1_ref["f3"]) <= TOL[prec]
+        scale = cfg1_ref["ek"] + abs(cfg1_ref["u2"]) + abs(cfg1_ref["u3"])
+        assert abs(u3 - cfg1_ref["u3"]) / scale <= (1e-6 if prec == 0 else 1e-12)
+        s.step(2, 5, 0.01)
+        x, _ = s.state()
+        _, f3b = s.forces()
+    sel = np.arange(0, cfg1.n, 3)
+    r3f, _, _ = oracle.atm_particles(x, cfg1.L, sel, NU, 2.5)
+    frms = np.sqrt((r3f ** 2).sum(1).mean())
+    err = np.linalg.norm(f3b[sel] - r3f, axis=1) / np.maximum(np.linalg.norm(r3f, axis=1), frms)
+    assert err.max() <= TOL[prec]
