@@ -54,6 +54,9 @@ typedef enum {
 } md_status;
 
 enum { MD_FP32 = 0, MD_FP64 = 1 };
+/* OR into md_create_system's precision: keep the state on the host and allocate device
+ * memory only at first use or when a batch admits the system (serving by memory budget). */
+enum { MD_DEFERRED = 0x100 };
 
 /* Per-handle counters; all fields refer to the system's lifetime unless noted. */
 typedef struct {

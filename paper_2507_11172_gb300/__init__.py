@@ -19,6 +19,7 @@ from . import build_lib
 
 MD_FP32 = 0
 MD_FP64 = 1
+MD_DEFERRED = 0x100
 
 STATUS = {0: "MD_OK", -1: "MD_ERR_ARG", -2: "MD_ERR_OOM", -3: "MD_ERR_BOX_TOO_SMALL", -4: "MD_ERR_NONFINITE",
           -5: "MD_ERR_DEVICE_TIMEOUT", -6: "MD_ERR_CUDA", -7: "MD_ERR_STATE", -8: "MD_ERR_CAPACITY"}

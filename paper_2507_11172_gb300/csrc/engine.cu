@@ -105,6 +105,9 @@ struct md_system {
   double e_kin = 0, u2 = 0, u3 = 0, w2 = 0, w3 = 0;
   // batch membership
   md_batch* batch = nullptr;
+  // deferred allocation: state kept on the host until first use
+  bool deferred = false;
+  std::vector<double> host_x, host_v;
 };
 
 namespace {
@@ -158,6 +161,8 @@ void choose_grid(md_system* s) {
   if (s->maxnb == 0) s->maxnb = std::max(32, (int)ceil(1.35 * nl + 24.0));
   s->maxnb = std::min(s->maxnb, (int)s->n);
 }
+
+size_t arena_bytes(const md_system* s);
 
 md_status alloc_device(md_system* s) {
   free_device(s);
@@ -218,7 +223,48 @@ md_status alloc_device(md_system* s) {
   s->snap_f3 = (double*)(m + o_sf3);
   s->snap_id = (int*)(m + o_sid);
   s->snap_cell = (int*)(m + o_scell);
+  h.snap_x = s->snap_x;
+  h.snap_v = s->snap_v;
+  h.snap_f2 = s->snap_f2;
+  h.snap_f3 = s->snap_f3;
+  h.snap_id = s->snap_id;
+  h.snap_cell = s->snap_cell;
+  h.mode_tab = nullptr;
   return MD_OK;
+}
+
+// device bytes alloc_device would reserve (grid and capacities chosen as for a real build)
+size_t arena_bytes(const md_system* s0) {
+  md_system tmp;
+  tmp.n = s0->n;
+  tmp.L = s0->L;
+  tmp.rc2 = s0->rc2;
+  tmp.rc3 = s0->rc3;
+  tmp.skin = s0->skin;
+  choose_grid(&tmp);
+  const size_t n = (size_t)tmp.n;
+  const size_t t4 = s0->precision ? sizeof(double4_32a) : sizeof(float4);
+  const size_t tsz = s0->precision ? 8 : 4;
+  Arena a;
+  a.reserve(sizeof(SysDev));
+  for (int i = 0; i < 6; ++i) a.reserve(24 * n);
+  a.reserve(4 * n);
+  a.reserve(4 * n);
+  for (int i = 0; i < 4; ++i) a.reserve(t4 * n);
+  for (int i = 0; i < 3; ++i) a.reserve(4 * n);
+  a.reserve(4 * (size_t)tmp.ncell);
+  a.reserve(4 * ((size_t)tmp.ncell + 1));
+  a.reserve(4 * (size_t)tmp.maxnb * n);
+  a.reserve(4 * n);
+  a.reserve(tsz * 27 * 3 * n);
+  a.reserve(8 * ACC_N);
+  a.reserve(8 * CTR_N);
+  a.reserve(4 * FLG_N);
+  for (int i = 0; i < 4; ++i) a.reserve(24 * n);
+  a.reserve(4 * n);
+  a.reserve(4 * n);
+  // work-item arrays (about 30 particle-block variants and 4 cell variants)
+  return a.used + 30 * sizeof(PItem) * (n / 32 + 2) + 4 * sizeof(CItem) * (size_t)tmp.ncell;
 }
 
 // refresh the parameter fields of the descriptor and upload it
@@ -752,159 +798,7 @@ md_status fetch_sorted(md_system* s, const double* dsrc, double* out_aos, bool w
   return MD_OK;
 }
 
-md_status ensure_forces(md_system* s) {
-  if (s->forces_valid) return MD_OK;
-  return do_call(s, 0, 1, 1.0);
-}
-
-}  // namespace
-
-// ====================================================================== C ABI
-extern "C" {
-
-const char* md_status_string(md_status st) {
-  switch (st) {
-    case MD_OK: return "ok";
-    case MD_ERR_ARG: return "invalid argument";
-    case MD_ERR_OOM: return "out of device memory";
-    case MD_ERR_BOX_TOO_SMALL: return "box too small: L must exceed 3 * max(r_c2 + skin, r_c3)";
-    case MD_ERR_NONFINITE: return "non-finite value in the state";
-    case MD_ERR_DEVICE_TIMEOUT: return "device-side wait timed out";
-    case MD_ERR_CUDA: return "CUDA error";
-    case MD_ERR_STATE: return "invalid state for this call";
-    case MD_ERR_CAPACITY: return "capacity exceeded";
-  }
-  return "unknown status";
-}
-
-const char* md_last_error(void) { return g_last_error.c_str(); }
-
-md_status md_create_system(md_system** out, int64_t n, double box_L, const double* pos, const double* vel,
-                           double mass, int precision, void* cuda_stream) {
-  if (!out) return MD_ERR_ARG;
-  *out = nullptr;
-  if (n < 3 || n >= (int64_t)kNbrMask || !pos || !(box_L > 0) || !(mass > 0) ||
-      (precision != MD_FP32 && precision != MD_FP64))
-    return MD_ERR_ARG;
-  for (int64_t i = 0; i < 3 * n; ++i)
-    if (!isfinite(pos[i]) || (vel && !isfinite(vel[i]))) return MD_ERR_NONFINITE;
-  std::unique_ptr<md_system> s(new md_system());
-  s->n = n;
-  s->L = box_L;
-  s->mass = mass;
-  s->precision = precision;
-  md_status st = check_geometry(s.get());
-  if (st != MD_OK) return st;
-  if (cuda_stream) {
-    s->stream = (cudaStream_t)cuda_stream;
-  } else {
-    CK(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
-    s->own_stream = true;
-  }
-  CK(cudaMallocHost(&s->h_flags, 4 * FLG_N));
-  CK(cudaMallocHost(&s->h_acc, 8 * ACC_N));
-  CK(cudaMallocHost(&s->h_ctr, 8 * CTR_N));
-  memset(s->h_flags, 0, 4 * FLG_N);
-  st = rebuild(s.get(), false);
-  if (st != MD_OK) {
-    md_destroy_system(s.release());
-    return st;
-  }
-  st = md_set_state(s.get(), pos, vel);
-  if (st != MD_OK) {
-    md_destroy_system(s.release());
-    return st;
-  }
-  *out = s.release();
-  return MD_OK;
-}
-
-md_status md_set_potentials(md_system* s, double lj_eps, double lj_sigma, double rc_pair, double atm_nu,
-                            double rc_triplet) {
-  if (!s) return MD_ERR_ARG;
-  if (!(lj_eps > 0) || !(lj_sigma > 0) || !(rc_pair > 0) || !(rc_triplet > 0) || !(atm_nu >= 0) ||
-      !isfinite(atm_nu))
-    return MD_ERR_ARG;
-  double e0 = s->eps, s0 = s->sigma, r20 = s->rc2, nu0 = s->nu, r30 = s->rc3;
-  s->eps = lj_eps;
-  s->sigma = lj_sigma;
-  s->rc2 = rc_pair;
-  s->nu = atm_nu;
-  s->rc3 = rc_triplet;
-  md_status st = check_geometry(s);
-  if (st != MD_OK) {
-    s->eps = e0; s->sigma = s0; s->rc2 = r20; s->nu = nu0; s->rc3 = r30;
-    return st;
-  }
-  s->maxnb = 0;
-  s->cap_cell = 0;
-  return rebuild(s, true);
-}
-
-md_status md_set_skin(md_system* s, double skin) {
-  if (!s || !(skin >= 0) || !isfinite(skin)) return MD_ERR_ARG;
-  double old = s->skin;
-  s->skin = skin;
-  md_status st = check_geometry(s);
-  if (st != MD_OK) {
-    s->skin = old;
-    return st;
-  }
-  s->maxnb = 0;
-  s->cap_cell = 0;
-  return rebuild(s, true);
-}
-
-md_status md_respa_step(md_system* s, int n_outer, int k_inner, double dt_outer) {
-  if (!s || n_outer < 0 || k_inner < 1 || !(dt_outer > 0) || !isfinite(dt_outer)) return MD_ERR_ARG;
-  if (s->batch) return MD_ERR_STATE;
-  return do_call(s, n_outer, k_inner, dt_outer);
-}
-
-md_status md_get_forces(md_system* s, double* f2, double* f3) {
-  if (!s) return MD_ERR_ARG;
-  md_status st = ensure_forces(s);
-  if (st != MD_OK) return st;
-  if (f2) {
-    st = fetch_sorted(s, s->h.f2, f2, false);
-    if (st != MD_OK) return st;
-  }
-  if (f3) {
-    st = fetch_sorted(s, s->h.f3, f3, false);
-    if (st != MD_OK) return st;
-  }
-  return MD_OK;
-}
-
-md_status md_get_energy(md_system* s, double* e_kin, double* u2, double* u3, double* virial) {
-  if (!s) return MD_ERR_ARG;
-  if (!s->energy_valid) {
-    s->forces_valid = false;
-    md_status st = ensure_forces(s);
-    if (st != MD_OK) return st;
-  }
-  if (e_kin) *e_kin = s->e_kin;
-  if (u2) *u2 = s->u2;
-  if (u3) *u3 = s->u3;
-  if (virial) *virial = s->w2 + s->w3;
-  return MD_OK;
-}
-
-md_status md_get_state(md_system* s, double* pos, double* vel) {
-  if (!s) return MD_ERR_ARG;
-  if (pos) {
-    md_status st = fetch_sorted(s, s->h.X[s->cur], pos, true);
-    if (st != MD_OK) return st;
-  }
-  if (vel) {
-    md_status st = fetch_sorted(s, s->h.v, vel, false);
-    if (st != MD_OK) return st;
-  }
-  return MD_OK;
-}
-
-md_status md_set_state(md_system* s, const double* pos, const double* vel) {
-  if (!s) return MD_ERR_ARG;
+md_status set_state_impl(md_system* s, const double* pos, const double* vel) {
   const size_t n = (size_t)s->n;
   if (!pos && !vel) return MD_OK;
   std::vector<double> soa;
@@ -942,6 +836,223 @@ md_status md_set_state(md_system* s, const double* pos, const double* vel) {
   s->forces_valid = false;
   s->energy_valid = false;
   return MD_OK;
+}
+
+
+// allocate a deferred system's device state and upload its host copy
+md_status ensure_resident(md_system* s) {
+  if (!s->deferred) return MD_OK;
+  md_status st = rebuild(s, false);
+  if (st != MD_OK) return st;
+  s->deferred = false;
+  st = set_state_impl(s, s->host_x.data(), s->host_v.data());
+  if (st != MD_OK) return st;
+  s->host_x.clear();
+  s->host_x.shrink_to_fit();
+  s->host_v.clear();
+  s->host_v.shrink_to_fit();
+  return MD_OK;
+}
+
+md_status ensure_forces(md_system* s) {
+  md_status st = ensure_resident(s);
+  if (st != MD_OK) return st;
+  if (s->forces_valid) return MD_OK;
+  return do_call(s, 0, 1, 1.0);
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+const char* md_status_string(md_status st) {
+  switch (st) {
+    case MD_OK: return "ok";
+    case MD_ERR_ARG: return "invalid argument";
+    case MD_ERR_OOM: return "out of device memory";
+    case MD_ERR_BOX_TOO_SMALL: return "box too small: L must exceed 3 * max(r_c2 + skin, r_c3)";
+    case MD_ERR_NONFINITE: return "non-finite value in the state";
+    case MD_ERR_DEVICE_TIMEOUT: return "device-side wait timed out";
+    case MD_ERR_CUDA: return "CUDA error";
+    case MD_ERR_STATE: return "invalid state for this call";
+    case MD_ERR_CAPACITY: return "capacity exceeded";
+  }
+  return "unknown status";
+}
+
+const char* md_last_error(void) { return g_last_error.c_str(); }
+
+md_status md_create_system(md_system** out, int64_t n, double box_L, const double* pos, const double* vel,
+                           double mass, int precision, void* cuda_stream) {
+  if (!out) return MD_ERR_ARG;
+  *out = nullptr;
+  const bool deferred = (precision & MD_DEFERRED) != 0;
+  precision &= ~MD_DEFERRED;
+  if (n < 3 || n >= (int64_t)kNbrMask || !pos || !(box_L > 0) || !(mass > 0) ||
+      (precision != MD_FP32 && precision != MD_FP64))
+    return MD_ERR_ARG;
+  for (int64_t i = 0; i < 3 * n; ++i)
+    if (!isfinite(pos[i]) || (vel && !isfinite(vel[i]))) return MD_ERR_NONFINITE;
+  std::unique_ptr<md_system> s(new md_system());
+  s->n = n;
+  s->L = box_L;
+  s->mass = mass;
+  s->precision = precision;
+  md_status st = check_geometry(s.get());
+  if (st != MD_OK) return st;
+  if (cuda_stream) {
+    s->stream = (cudaStream_t)cuda_stream;
+  } else {
+    CK(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
+    s->own_stream = true;
+  }
+  CK(cudaMallocHost(&s->h_flags, 4 * FLG_N));
+  CK(cudaMallocHost(&s->h_acc, 8 * ACC_N));
+  CK(cudaMallocHost(&s->h_ctr, 8 * CTR_N));
+  memset(s->h_flags, 0, 4 * FLG_N);
+  memset(s->h_ctr, 0, 8 * CTR_N);
+  if (deferred) {  // keep the state on the host until first use or batch admission
+    s->deferred = true;
+    s->host_x.assign(pos, pos + 3 * n);
+    s->host_v.assign(3 * n, 0.0);
+    if (vel) s->host_v.assign(vel, vel + 3 * n);
+    for (int64_t i = 0; i < 3 * n; ++i) {
+      double x = s->host_x[i] - box_L * floor(s->host_x[i] / box_L);
+      s->host_x[i] = x >= box_L ? x - box_L : x;
+    }
+    *out = s.release();
+    return MD_OK;
+  }
+  st = rebuild(s.get(), false);
+  if (st != MD_OK) {
+    md_destroy_system(s.release());
+    return st;
+  }
+  st = md_set_state(s.get(), pos, vel);
+  if (st != MD_OK) {
+    md_destroy_system(s.release());
+    return st;
+  }
+  *out = s.release();
+  return MD_OK;
+}
+
+md_status md_set_potentials(md_system* s, double lj_eps, double lj_sigma, double rc_pair, double atm_nu,
+                            double rc_triplet) {
+  if (!s) return MD_ERR_ARG;
+  if (!(lj_eps > 0) || !(lj_sigma > 0) || !(rc_pair > 0) || !(rc_triplet > 0) || !(atm_nu >= 0) ||
+      !isfinite(atm_nu))
+    return MD_ERR_ARG;
+  double e0 = s->eps, s0 = s->sigma, r20 = s->rc2, nu0 = s->nu, r30 = s->rc3;
+  s->eps = lj_eps;
+  s->sigma = lj_sigma;
+  s->rc2 = rc_pair;
+  s->nu = atm_nu;
+  s->rc3 = rc_triplet;
+  md_status st = check_geometry(s);
+  if (st != MD_OK) {
+    s->eps = e0; s->sigma = s0; s->rc2 = r20; s->nu = nu0; s->rc3 = r30;
+    return st;
+  }
+  s->maxnb = 0;
+  s->cap_cell = 0;
+  if (s->deferred) return MD_OK;
+  if (s->batch) return MD_ERR_STATE;
+  return rebuild(s, true);
+}
+
+md_status md_set_skin(md_system* s, double skin) {
+  if (!s || !(skin >= 0) || !isfinite(skin)) return MD_ERR_ARG;
+  double old = s->skin;
+  s->skin = skin;
+  md_status st = check_geometry(s);
+  if (st != MD_OK) {
+    s->skin = old;
+    return st;
+  }
+  s->maxnb = 0;
+  s->cap_cell = 0;
+  if (s->deferred) return MD_OK;
+  if (s->batch) return MD_ERR_STATE;
+  return rebuild(s, true);
+}
+
+md_status md_respa_step(md_system* s, int n_outer, int k_inner, double dt_outer) {
+  if (!s || n_outer < 0 || k_inner < 1 || !(dt_outer > 0) || !isfinite(dt_outer)) return MD_ERR_ARG;
+  if (s->batch) return MD_ERR_STATE;
+  md_status st = ensure_resident(s);
+  if (st != MD_OK) return st;
+  return do_call(s, n_outer, k_inner, dt_outer);
+}
+
+md_status md_get_forces(md_system* s, double* f2, double* f3) {
+  if (!s) return MD_ERR_ARG;
+  if (s->batch) return MD_ERR_STATE;
+  md_status st = ensure_forces(s);
+  if (st != MD_OK) return st;
+  if (f2) {
+    st = fetch_sorted(s, s->h.f2, f2, false);
+    if (st != MD_OK) return st;
+  }
+  if (f3) {
+    st = fetch_sorted(s, s->h.f3, f3, false);
+    if (st != MD_OK) return st;
+  }
+  return MD_OK;
+}
+
+md_status md_get_energy(md_system* s, double* e_kin, double* u2, double* u3, double* virial) {
+  if (!s) return MD_ERR_ARG;
+  if (s->batch) return MD_ERR_STATE;
+  if (!s->energy_valid) {
+    s->forces_valid = false;
+    md_status st = ensure_forces(s);
+    if (st != MD_OK) return st;
+  }
+  if (e_kin) *e_kin = s->e_kin;
+  if (u2) *u2 = s->u2;
+  if (u3) *u3 = s->u3;
+  if (virial) *virial = s->w2 + s->w3;
+  return MD_OK;
+}
+
+md_status md_get_state(md_system* s, double* pos, double* vel) {
+  if (!s) return MD_ERR_ARG;
+  if (s->batch) return MD_ERR_STATE;
+  if (s->deferred) {
+    if (pos) memcpy(pos, s->host_x.data(), 24 * (size_t)s->n);
+    if (vel) memcpy(vel, s->host_v.data(), 24 * (size_t)s->n);
+    return MD_OK;
+  }
+  if (pos) {
+    md_status st = fetch_sorted(s, s->h.X[s->cur], pos, true);
+    if (st != MD_OK) return st;
+  }
+  if (vel) {
+    md_status st = fetch_sorted(s, s->h.v, vel, false);
+    if (st != MD_OK) return st;
+  }
+  return MD_OK;
+}
+
+md_status md_set_state(md_system* s, const double* pos, const double* vel) {
+  if (!s) return MD_ERR_ARG;
+  if (s->batch) return MD_ERR_STATE;
+  if (s->deferred) {
+    const size_t n = (size_t)s->n;
+    for (size_t i = 0; i < 3 * n; ++i)
+      if ((pos && !isfinite(pos[i])) || (vel && !isfinite(vel[i]))) return MD_ERR_NONFINITE;
+    if (pos) {
+      for (size_t i = 0; i < 3 * n; ++i) {
+        double x = pos[i] - s->L * floor(pos[i] / s->L);
+        s->host_x[i] = x >= s->L ? x - s->L : x;
+      }
+    }
+    if (vel) memcpy(s->host_v.data(), vel, 24 * n);
+    return MD_OK;
+  }
+  return set_state_impl(s, pos, vel);
 }
 
 md_status md_get_stats(md_system* s, md_stats* out) {
@@ -991,19 +1102,598 @@ md_status md_destroy_system(md_system* s) {
 
 }  // extern "C"
 
-// ====================================================================== batch (pending)
-struct md_batch {
-  int unused;
+// ====================================================================== batch
+// Batched ensemble / continuous serving.  Resident members share every launch: on each inner
+// tick one launch per kernel covers all members (work items carry the member index).  Members
+// join at cycle boundaries; a cycle is P = lcm(k_j) ticks, so every member starts its outer
+// steps at t = 0 of a cycle.  The cycle is captured once per composition as a CUDA graph;
+// what changes from cycle to cycle (energy on a member's final outer step, closing vs
+// continuing outer kick, skip once finished) is a per-member table of modes, uploaded before
+// each launch.  %globaltimer stamps at tick boundaries give per-outer-step latencies.
+namespace {
+
+enum { KT_SORT = 0, KT_LJ = 1, KT_ATM = 2, KT_COMB = 3, KT_N = 4 };
+enum { RQ_QUEUED = 0, RQ_RESIDENT = 1, RQ_DONE = 2, RQ_FAILED = 3 };
+
+struct Request {
+  md_system* s = nullptr;
+  uint64_t ticket = 0;
+  int n_outer = 0, k = 1;
+  double dt_outer = 0;
+  int outer_done = 0;
+  int state = RQ_QUEUED;
+  md_status status = MD_OK;
+  std::vector<double> lat_ms;
+  unsigned long long trip0 = 0;
 };
+
+struct TickItems {
+  size_t bin = 0, scan = 0, list = 0, lj = 0, atm = 0, comb = 0;  // offsets (items) in the pools
+  int nbin = 0, nscan = 0, nlist = 0, nlj = 0, natm = 0, ncomb = 0;
+};
+
+}  // namespace
+
+struct md_batch {
+  size_t budget = 0;
+  int precision = -1;
+  std::map<uint64_t, Request> req;
+  std::vector<uint64_t> queue, resident;
+  uint64_t next_ticket = 1;
+  cudaStream_t stream = nullptr;
+  // composition
+  bool dirty = true;
+  int P = 1, variant = 1, smax = 0, smax_list = 0, atm_grid = 0;
+  SysDev* d_sys = nullptr;
+  int* d_modes = nullptr;
+  int* h_modes = nullptr;  // pinned [slots][P][KT_N]
+  int* d_flags = nullptr;
+  double* d_acc = nullptr;
+  unsigned long long* d_ctr = nullptr;
+  int* h_flags = nullptr;
+  double* h_acc = nullptr;
+  unsigned long long* h_ctr = nullptr;
+  unsigned long long* d_stamps = nullptr;
+  unsigned long long* h_stamps = nullptr;
+  PItem* d_pitems = nullptr;
+  CItem* d_citems = nullptr;
+  SItem* d_sitems = nullptr;
+  PItem* d_snap = nullptr;
+  int nsnap = 0;
+  std::vector<TickItems> ticks, ticks_safe;
+  cudaGraphExec_t graph = nullptr, graph_safe = nullptr;
+  size_t cap_slots = 0;
+};
+
+namespace {
+
+void batch_free_composition(md_batch* b) {
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  if (b->graph_safe) cudaGraphExecDestroy(b->graph_safe);
+  b->graph = b->graph_safe = nullptr;
+  for (void* p : {(void*)b->d_sys, (void*)b->d_modes, (void*)b->d_flags, (void*)b->d_acc, (void*)b->d_ctr,
+                  (void*)b->d_stamps, (void*)b->d_pitems, (void*)b->d_citems, (void*)b->d_sitems, (void*)b->d_snap})
+    if (p) cudaFree(p);
+  for (void* p : {(void*)b->h_modes, (void*)b->h_flags, (void*)b->h_acc, (void*)b->h_ctr, (void*)b->h_stamps})
+    if (p) cudaFreeHost(p);
+  b->d_sys = nullptr;
+  b->d_modes = b->h_modes = nullptr;
+  b->d_flags = b->h_flags = nullptr;
+  b->d_acc = b->h_acc = nullptr;
+  b->d_ctr = b->h_ctr = nullptr;
+  b->d_stamps = b->h_stamps = nullptr;
+  b->d_pitems = nullptr;
+  b->d_citems = nullptr;
+  b->d_sitems = nullptr;
+  b->d_snap = nullptr;
+  b->ticks.clear();
+  b->ticks_safe.clear();
+}
+
+long long lcm_ll(long long a, long long b) {
+  long long x = a, y = b;
+  while (y) {
+    long long t = x % y;
+    x = y;
+    y = t;
+  }
+  return a / x * b;
+}
+
+// enqueue one cycle; with check set (outside capture) every launch is checked and the first
+// failing one is named in *failed
+template <typename T>
+void enqueue_cycle(md_batch* b, const std::vector<TickItems>& ticks, bool with_stamps, std::string* failed = nullptr) {
+  Launch L{b->stream, b->d_sys};
+  auto chk = [&](const char* what, int t) {
+    if (!failed || !failed->empty()) return;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) *failed = std::string(what) + " at tick " + std::to_string(t) + ": " + cudaGetErrorString(e);
+  };
+  if (with_stamps) launch_stamp(b->stream, b->d_stamps);
+  chk("stamp", -1);
+  for (int t = 0; t < b->P; ++t) {
+    const TickItems& it = ticks[t];
+    launch_bin_count(L, b->d_pitems + it.bin, it.nbin, kBlock);
+    chk("bin_count", t);
+    launch_scan(L, b->d_sitems + it.scan, it.nscan);
+    chk("scan", t);
+    launch_scatter<T>(L, b->d_pitems + it.bin, it.nbin, kBlock);
+    chk("scatter", t);
+    launch_listbuild<T>(L, b->d_citems + it.list, it.nlist, b->smax_list);
+    chk("listbuild", t);
+    launch_lj<T>(L, b->d_pitems + it.lj, it.nlj, kBlock);
+    chk("lj", t);
+    if (b->variant == 1)
+      launch_atm_pa<T>(L, b->d_pitems + it.atm, it.natm);
+    else
+      launch_atm<T>(L, b->d_citems + it.atm, it.natm, b->atm_grid, b->smax);
+    chk("atm", t);
+    launch_combine<T>(L, b->d_pitems + it.comb, it.ncomb, kBlock);
+    chk("combine", t);
+    if (with_stamps) launch_stamp(b->stream, b->d_stamps + t + 1);
+    chk("stamp", t);
+  }
+}
+
+md_status batch_build(md_batch* b) {
+  batch_free_composition(b);
+  const int ns = (int)b->resident.size();
+  if (ns == 0) {
+    b->dirty = false;
+    return MD_OK;
+  }
+  long long P = 1;
+  bool pa = true;
+  int capmax = 0;
+  for (uint64_t tk : b->resident) {
+    const Request& r = b->req[tk];
+    P = lcm_ll(P, r.k);
+    pa = pa && variant_allowed(r.s, 1);
+    capmax = std::max(capmax, r.s->cap_cell);
+  }
+  if (P > 4096) {
+    g_last_error = "batch: lcm of the members' k_inner exceeds 4096 ticks";
+    return MD_ERR_ARG;
+  }
+  b->P = (int)P;
+  b->variant = pa ? 1 : 0;
+  b->smax = atm_stage_capacity(capmax);
+  b->smax_list = 27 * capmax;  // the pair-list build stages the full 27-cell stencil
+  {
+    int bytes = 0;
+    int per_sm = atm_configure(b->smax, b->precision, &bytes);
+    if (per_sm <= 0) return MD_ERR_CAPACITY;
+    if (listbuild_configure(27 * capmax, b->precision) < 0) return MD_ERR_CAPACITY;
+    b->atm_grid = per_sm * device_sm_count();
+  }
+  // device descriptors: each member's own, with batch-owned flags / counters / mode tables
+  CK(cudaMalloc(&b->d_sys, sizeof(SysDev) * ns));
+  CK(cudaMalloc(&b->d_modes, sizeof(int) * ns * P * KT_N));
+  CK(cudaMallocHost(&b->h_modes, sizeof(int) * ns * P * KT_N));
+  CK(cudaMalloc(&b->d_flags, sizeof(int) * ns * FLG_N));
+  CK(cudaMallocHost(&b->h_flags, sizeof(int) * ns * FLG_N));
+  CK(cudaMalloc(&b->d_acc, sizeof(double) * ns * ACC_N));
+  CK(cudaMallocHost(&b->h_acc, sizeof(double) * ns * ACC_N));
+  CK(cudaMalloc(&b->d_ctr, sizeof(unsigned long long) * ns * CTR_N));
+  CK(cudaMallocHost(&b->h_ctr, sizeof(unsigned long long) * ns * CTR_N));
+  CK(cudaMalloc(&b->d_stamps, sizeof(unsigned long long) * (P + 1)));
+  CK(cudaMallocHost(&b->h_stamps, sizeof(unsigned long long) * (P + 1)));
+  CK(cudaMemsetAsync(b->d_ctr, 0, sizeof(unsigned long long) * ns * CTR_N, b->stream));
+  std::vector<SysDev> hs(ns);
+  for (int j = 0; j < ns; ++j) {
+    Request& r = b->req[b->resident[j]];
+    md_system* s = r.s;
+    md_status st = upload_desc(s, r.dt_outer / r.k, r.dt_outer);
+    if (st != MD_OK) return st;
+    SysDev h = s->h;
+    h.flags = b->d_flags + j * FLG_N;
+    h.acc = b->d_acc + j * ACC_N;
+    h.ctr = b->d_ctr + j * CTR_N;
+    h.mode_tab = b->d_modes + (size_t)j * P * KT_N;
+    hs[j] = h;
+    r.trip0 = 0;
+  }
+  CK(cudaMemcpyAsync(b->d_sys, hs.data(), sizeof(SysDev) * ns, cudaMemcpyHostToDevice, b->stream));
+  // work items for every tick of the cycle (normal, and safe: a rebuild on every tick)
+  std::vector<PItem> pit;
+  std::vector<CItem> cit;
+  std::vector<SItem> sit;
+  auto build_ticks = [&](bool safe, std::vector<TickItems>& out) {
+    out.assign(P, TickItems{});
+    for (int t = 0; t < P; ++t) {
+      TickItems& ti = out[t];
+      auto tab = [&](int kt) { return M_TABLE | (t * KT_N + kt); };
+      ti.bin = pit.size();
+      for (int j = 0; j < ns; ++j) {
+        const Request& r = b->req[b->resident[j]];
+        const int tt = t % r.k;
+        if (!(tt == r.k - 1 || safe)) continue;
+        for (int q = 0; q < (int)r.s->n; q += kBlock) pit.push_back(PItem{j, q, tab(KT_SORT), tt & 1});
+      }
+      ti.nbin = (int)(pit.size() - ti.bin);
+      ti.scan = sit.size();
+      for (int j = 0; j < ns; ++j) {
+        const Request& r = b->req[b->resident[j]];
+        const int tt = t % r.k;
+        if (tt == r.k - 1 || safe) sit.push_back(SItem{j, tab(KT_SORT)});
+      }
+      ti.nscan = (int)(sit.size() - ti.scan);
+      ti.list = cit.size();
+      for (int j = 0; j < ns; ++j) {
+        const Request& r = b->req[b->resident[j]];
+        const int tt = t % r.k;
+        if (!(tt == r.k - 1 || safe)) continue;
+        for (int c = 0; c < r.s->ncell; ++c) cit.push_back(CItem{j, c, tt & 1, tab(KT_SORT)});
+      }
+      ti.nlist = (int)(cit.size() - ti.list);
+      ti.lj = pit.size();
+      for (int j = 0; j < ns; ++j) {
+        const Request& r = b->req[b->resident[j]];
+        const int tt = t % r.k;
+        for (int q = 0; q < (int)r.s->n; q += kBlock / kLjTeam) pit.push_back(PItem{j, q, tab(KT_LJ), tt & 1});
+      }
+      ti.nlj = (int)(pit.size() - ti.lj);
+      if (b->variant == 1) {
+        ti.atm = pit.size();
+        for (int j = 0; j < ns; ++j) {
+          const Request& r = b->req[b->resident[j]];
+          if (t % r.k != r.k - 1) continue;
+          for (int q = 0; q < (int)r.s->n; q += kPaPerBlock) pit.push_back(PItem{j, q, tab(KT_ATM), (r.k - 1) & 1});
+        }
+        ti.natm = (int)(pit.size() - ti.atm);
+      } else {
+        ti.atm = cit.size();
+        for (int j = 0; j < ns; ++j) {
+          const Request& r = b->req[b->resident[j]];
+          if (t % r.k != r.k - 1) continue;
+          for (int c = 0; c < r.s->ncell; ++c) cit.push_back(CItem{j, c, (r.k - 1) & 1, tab(KT_ATM)});
+        }
+        ti.natm = (int)(cit.size() - ti.atm);
+      }
+      ti.comb = pit.size();
+      for (int j = 0; j < ns; ++j) {
+        const Request& r = b->req[b->resident[j]];
+        if (t % r.k != r.k - 1) continue;
+        for (int q = 0; q < (int)r.s->n; q += kBlock) pit.push_back(PItem{j, q, tab(KT_COMB), (r.k - 1) & 1});
+      }
+      ti.ncomb = (int)(pit.size() - ti.comb);
+    }
+  };
+  build_ticks(false, b->ticks);
+  build_ticks(true, b->ticks_safe);
+  std::vector<PItem> snap;
+  for (int j = 0; j < ns; ++j) {
+    const Request& r = b->req[b->resident[j]];
+    for (int q = 0; q < (int)r.s->n; q += kBlock) snap.push_back(PItem{j, q, 0, 0});
+  }
+  b->nsnap = (int)snap.size();
+  CK(cudaMalloc(&b->d_pitems, sizeof(PItem) * std::max<size_t>(1, pit.size())));
+  CK(cudaMalloc(&b->d_citems, sizeof(CItem) * std::max<size_t>(1, cit.size())));
+  CK(cudaMalloc(&b->d_sitems, sizeof(SItem) * std::max<size_t>(1, sit.size())));
+  CK(cudaMalloc(&b->d_snap, sizeof(PItem) * std::max<size_t>(1, snap.size())));
+  CK(cudaMemcpyAsync(b->d_pitems, pit.data(), sizeof(PItem) * pit.size(), cudaMemcpyHostToDevice, b->stream));
+  CK(cudaMemcpyAsync(b->d_citems, cit.data(), sizeof(CItem) * cit.size(), cudaMemcpyHostToDevice, b->stream));
+  CK(cudaMemcpyAsync(b->d_sitems, sit.data(), sizeof(SItem) * sit.size(), cudaMemcpyHostToDevice, b->stream));
+  CK(cudaMemcpyAsync(b->d_snap, snap.data(), sizeof(PItem) * snap.size(), cudaMemcpyHostToDevice, b->stream));
+  CK(cudaStreamSynchronize(b->stream));
+  // capture the two cycle graphs
+  for (int safe = 0; safe < 2; ++safe) {
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    if (b->precision)
+      enqueue_cycle<double>(b, safe ? b->ticks_safe : b->ticks, true);
+    else
+      enqueue_cycle<float>(b, safe ? b->ticks_safe : b->ticks, true);
+    cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+    if (e != cudaSuccess) {
+      // name the launch that broke the capture: enqueue the same cycle uncaptured, checked
+      cudaGetLastError();
+      std::string failed;
+      if (b->precision)
+        enqueue_cycle<double>(b, safe ? b->ticks_safe : b->ticks, true, &failed);
+      else
+        enqueue_cycle<float>(b, safe ? b->ticks_safe : b->ticks, true, &failed);
+      cudaStreamSynchronize(b->stream);
+      cudaGetLastError();
+      g_last_error = "batch graph capture failed (" + std::string(cudaGetErrorString(e)) + "); " +
+                     (failed.empty() ? std::string("uncaptured launches succeeded") : failed);
+      return MD_ERR_CUDA;
+    }
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate(batch)");
+    (safe ? b->graph_safe : b->graph) = ex;
+  }
+  b->dirty = false;
+  return MD_OK;
+}
+
+// modes of every member for every tick of the next cycle
+void batch_fill_modes(md_batch* b, bool safe) {
+  const int ns = (int)b->resident.size();
+  const int P = b->P;
+  for (int j = 0; j < ns; ++j) {
+    const Request& r = b->req[b->resident[j]];
+    const int rem = r.n_outer - r.outer_done;
+    const int f3r = (b->variant == 1) ? M_F3READY : 0;
+    int* tab = b->h_modes + (size_t)j * P * KT_N;
+    for (int t = 0; t < P; ++t) {
+      const int q = t / r.k, tt = t % r.k;
+      int* e = tab + t * KT_N;
+      if (q >= rem) {
+        e[KT_SORT] = e[KT_LJ] = e[KT_ATM] = e[KT_COMB] = M_SKIP;
+        continue;
+      }
+      const bool closing = tt == r.k - 1;
+      const bool final_step = closing && q == rem - 1;
+      const int E = final_step ? M_ENERGY : 0;
+      e[KT_SORT] = (closing || safe) ? 0 : M_SKIP;
+      e[KT_LJ] = (closing ? LJ_LAST : LJ_MID) | E;
+      e[KT_ATM] = closing ? E : M_SKIP;
+      e[KT_COMB] = closing ? ((final_step ? CB_LAST : CB_CONT) | E | f3r) : M_SKIP;
+    }
+  }
+}
+
+md_status batch_admit(md_batch* b) {
+  size_t used = 0;
+  for (uint64_t tk : b->resident) used += b->req[tk].s->mem_bytes;
+  while (!b->queue.empty()) {
+    Request& r = b->req[b->queue.front()];
+    md_system* s = r.s;
+    const size_t need = s->deferred ? arena_bytes(s) : s->mem_bytes;
+    if (b->budget && used + need > b->budget) {
+      if (b->resident.empty()) {  // can never fit: fail the request
+        r.state = RQ_FAILED;
+        r.status = MD_ERR_OOM;
+        b->queue.erase(b->queue.begin());
+        continue;
+      }
+      break;
+    }
+    b->queue.erase(b->queue.begin());
+    md_status st = ensure_resident(s);
+    if (st == MD_OK) st = ensure_forces(s);
+    if (st == MD_OK && r.n_outer > 0) {
+      // opening kicks and first drift of the request (Algorithm 2 at i = 0)
+      st = upload_desc(s, r.dt_outer / r.k, r.dt_outer);
+      if (st == MD_OK) {
+        Plan Pl{s, Launch{s->stream, s->d_sys}};
+        if (s->precision) Pl.start<double>(s->cur); else Pl.start<float>(s->cur);
+        cudaError_t e = cudaStreamSynchronize(s->stream);
+        if (e != cudaSuccess) st = cuda_fail(e, "batch start");
+      }
+    }
+    if (st != MD_OK) {
+      r.state = RQ_FAILED;
+      r.status = st;
+      continue;
+    }
+    if (r.n_outer == 0) {
+      r.state = RQ_DONE;
+      continue;
+    }
+    s->batch = b;
+    s->forces_valid = false;
+    r.state = RQ_RESIDENT;
+    used += s->mem_bytes;
+    b->resident.push_back(r.ticket);
+    b->dirty = true;
+  }
+  return MD_OK;
+}
+
+// finished or failed members leave; their state is a full step again
+void batch_retire(md_batch* b, std::vector<uint64_t>& leaving) {
+  if (leaving.empty()) return;
+  std::vector<uint64_t> keep;
+  for (uint64_t tk : b->resident)
+    if (std::find(leaving.begin(), leaving.end(), tk) == leaving.end()) keep.push_back(tk);
+  b->resident.swap(keep);
+  for (uint64_t tk : leaving) {
+    Request& r = b->req[tk];
+    r.s->batch = nullptr;
+    clear_graphs(r.s);
+  }
+  b->dirty = true;
+}
+
+md_status batch_cycle(md_batch* b) {
+  const int ns = (int)b->resident.size();
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    const bool safe = attempt > 0;
+    batch_fill_modes(b, safe);
+    CK(cudaMemcpyAsync(b->d_modes, b->h_modes, sizeof(int) * ns * b->P * KT_N, cudaMemcpyHostToDevice, b->stream));
+    CK(cudaMemsetAsync(b->d_flags, 0, sizeof(int) * ns * FLG_N, b->stream));
+    CK(cudaMemsetAsync(b->d_acc, 0, sizeof(double) * ns * ACC_N, b->stream));
+    Launch L{b->stream, b->d_sys};
+    launch_snapshot(L, b->d_snap, b->nsnap, 0);
+    CK(cudaGraphLaunch(safe ? b->graph_safe : b->graph, b->stream));
+    CK(cudaMemcpyAsync(b->h_flags, b->d_flags, sizeof(int) * ns * FLG_N, cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaMemcpyAsync(b->h_acc, b->d_acc, sizeof(double) * ns * ACC_N, cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaMemcpyAsync(b->h_ctr, b->d_ctr, sizeof(unsigned long long) * ns * CTR_N, cudaMemcpyDeviceToHost,
+                       b->stream));
+    CK(cudaMemcpyAsync(b->h_stamps, b->d_stamps, sizeof(unsigned long long) * (b->P + 1), cudaMemcpyDeviceToHost,
+                       b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    bool skin = false, cap = false;
+    for (int j = 0; j < ns; ++j) {
+      const int* f = b->h_flags + j * FLG_N;
+      if (f[FLG_SKIN] && !safe) skin = true;
+      if (f[FLG_ERR] & (ERR_CELL_CAP | ERR_NBR_CAP)) cap = true;
+    }
+    if (!(skin || cap)) break;
+    launch_snapshot(L, b->d_snap, b->nsnap, 1);  // every member back to the cycle start
+    CK(cudaStreamSynchronize(b->stream));
+    if (cap) {
+      std::vector<uint64_t> grow;
+      for (int j = 0; j < ns; ++j) {
+        const int* f = b->h_flags + j * FLG_N;
+        if (f[FLG_ERR] & (ERR_CELL_CAP | ERR_NBR_CAP)) grow.push_back(b->resident[j]);
+      }
+      for (uint64_t tk : grow) {
+        md_system* s = b->req[tk].s;
+        const int* f = b->h_flags + (std::find(b->resident.begin(), b->resident.end(), tk) - b->resident.begin()) * FLG_N;
+        if (f[FLG_ERR] & ERR_CELL_CAP) s->cap_cell = std::max(s->cap_cell + 8, f[FLG_MAXCELL] + 8);
+        if (f[FLG_ERR] & ERR_NBR_CAP) s->maxnb = s->maxnb * 3 / 2 + 16;
+        // the snapshot restored positions in buffer 0 with the cycle-start order
+        s->cur = 0;
+        md_status st = rebuild(s, true);
+        if (st == MD_OK) st = ensure_forces(s);
+        if (st == MD_OK) {
+          const Request& r = b->req[tk];
+          st = upload_desc(s, r.dt_outer / r.k, r.dt_outer);
+          Plan Pl{s, Launch{s->stream, s->d_sys}};
+          if (s->precision) Pl.start<double>(s->cur); else Pl.start<float>(s->cur);
+          cudaStreamSynchronize(s->stream);
+        }
+        if (st != MD_OK) return st;
+      }
+      md_status st = batch_build(b);
+      if (st != MD_OK) return st;
+      attempt = 0;  // replay in safe mode: the restored members' cell-local coordinates are stale
+    }
+  }
+  // progress, latencies, completion
+  std::vector<uint64_t> leaving;
+  for (int j = 0; j < ns; ++j) {
+    Request& r = b->req[b->resident[j]];
+    const int* f = b->h_flags + j * FLG_N;
+    const int rem = r.n_outer - r.outer_done;
+    const int steps = std::min(rem, b->P / r.k);
+    for (int q = 0; q < steps; ++q) {
+      const unsigned long long t0 = b->h_stamps[q * r.k], t1 = b->h_stamps[(q + 1) * r.k];
+      r.lat_ms.push_back((double)(t1 - t0) * 1e-6);
+    }
+    r.outer_done += steps;
+    md_system* s = r.s;
+    const unsigned long long trip = b->h_ctr[j * CTR_N + CTR_TRIPLETS];
+    s->stats.triplets_total += trip - r.trip0;
+    if (steps > 0) s->stats.triplets_last = (trip - r.trip0) / (unsigned long long)steps;
+    r.trip0 = trip;
+    s->stats.outer_steps += steps;
+    s->stats.atm_evals += steps;
+    s->stats.lj_evals += (uint64_t)steps * r.k;
+    if (f[FLG_ERR] & (ERR_NONFINITE | ERR_HALF_CAP)) {
+      r.state = RQ_FAILED;
+      r.status = (f[FLG_ERR] & ERR_NONFINITE) ? MD_ERR_NONFINITE : MD_ERR_CAPACITY;
+      s->forces_valid = s->energy_valid = false;
+      leaving.push_back(r.ticket);
+      continue;
+    }
+    if (r.outer_done >= r.n_outer) {
+      const double* a = b->h_acc + j * ACC_N;
+      s->e_kin = a[ACC_EK];
+      s->u2 = a[ACC_U2];
+      s->w2 = a[ACC_W2];
+      s->u3 = a[ACC_U3];
+      s->w3 = a[ACC_W3];
+      s->energy_valid = true;
+      s->forces_valid = true;
+      s->cur = (r.k - 1) & 1;
+      r.state = RQ_DONE;
+      leaving.push_back(r.ticket);
+    }
+  }
+  batch_retire(b, leaving);
+  return MD_OK;
+}
+
+}  // namespace
+
 extern "C" {
-md_status md_batch_create(md_batch** out, size_t) {
-  if (out) *out = nullptr;
-  return MD_ERR_STATE;
+
+md_status md_batch_create(md_batch** out, size_t hbm_budget_bytes) {
+  if (!out) return MD_ERR_ARG;
+  *out = nullptr;
+  std::unique_ptr<md_batch> b(new md_batch());
+  b->budget = hbm_budget_bytes;
+  CK(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
+  *out = b.release();
+  return MD_OK;
 }
-md_status md_batch_submit(md_batch*, md_system*, int, int, double, uint64_t*) { return MD_ERR_STATE; }
-md_status md_batch_run(md_batch*, int) { return MD_ERR_STATE; }
-md_status md_batch_poll(md_batch*, uint64_t, int*) { return MD_ERR_STATE; }
-md_status md_batch_latency(md_batch*, uint64_t, double*, int*) { return MD_ERR_STATE; }
-md_status md_batch_pending(md_batch*, int*, int*) { return MD_ERR_STATE; }
-md_status md_batch_destroy(md_batch* b) { return b ? MD_ERR_STATE : MD_OK; }
+
+md_status md_batch_submit(md_batch* b, md_system* s, int n_outer, int k_inner, double dt_outer, uint64_t* ticket) {
+  if (!b || !s || n_outer < 0 || k_inner < 1 || !(dt_outer > 0) || !isfinite(dt_outer)) return MD_ERR_ARG;
+  if (s->batch) return MD_ERR_STATE;
+  for (auto& kv : b->req)
+    if (kv.second.s == s && (kv.second.state == RQ_QUEUED || kv.second.state == RQ_RESIDENT)) return MD_ERR_STATE;
+  if (b->precision < 0) b->precision = s->precision;
+  if (s->precision != b->precision) return MD_ERR_ARG;
+  Request r;
+  r.s = s;
+  r.ticket = b->next_ticket++;
+  r.n_outer = n_outer;
+  r.k = k_inner;
+  r.dt_outer = dt_outer;
+  b->req[r.ticket] = r;
+  b->queue.push_back(r.ticket);
+  if (ticket) *ticket = r.ticket;
+  return MD_OK;
 }
+
+md_status md_batch_run(md_batch* b, int max_ticks) {
+  if (!b) return MD_ERR_ARG;
+  long long done_ticks = 0;
+  for (;;) {
+    md_status st = batch_admit(b);
+    if (st != MD_OK) return st;
+    if (b->resident.empty()) break;
+    if (b->dirty) {
+      st = batch_build(b);
+      if (st != MD_OK) return st;
+    }
+    st = batch_cycle(b);
+    if (st != MD_OK) return st;
+    done_ticks += b->P;
+    if (max_ticks > 0 && done_ticks >= max_ticks) break;
+  }
+  return MD_OK;
+}
+
+md_status md_batch_poll(md_batch* b, uint64_t ticket, int* done) {
+  if (!b || !done) return MD_ERR_ARG;
+  auto it = b->req.find(ticket);
+  if (it == b->req.end()) return MD_ERR_STATE;
+  *done = (it->second.state == RQ_DONE) ? 1 : 0;
+  if (it->second.state == RQ_FAILED) return it->second.status;
+  return MD_OK;
+}
+
+md_status md_batch_latency(md_batch* b, uint64_t ticket, double* ms, int* count) {
+  if (!b || !count) return MD_ERR_ARG;
+  auto it = b->req.find(ticket);
+  if (it == b->req.end()) return MD_ERR_STATE;
+  const std::vector<double>& l = it->second.lat_ms;
+  const int n = std::min<int>(*count, (int)l.size());
+  if (ms)
+    for (int i = 0; i < n; ++i) ms[i] = l[i];
+  *count = ms ? n : (int)l.size();
+  return MD_OK;
+}
+
+md_status md_batch_pending(md_batch* b, int* queued, int* resident) {
+  if (!b) return MD_ERR_ARG;
+  if (queued) *queued = (int)b->queue.size();
+  if (resident) *resident = (int)b->resident.size();
+  return MD_OK;
+}
+
+md_status md_batch_destroy(md_batch* b) {
+  if (!b) return MD_OK;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  for (uint64_t tk : b->resident) {
+    Request& r = b->req[tk];
+    r.s->batch = nullptr;
+    r.s->forces_valid = false;  // interrupted mid-request: the cached forces are not at a full step
+    r.s->energy_valid = false;
+  }
+  batch_free_composition(b);
+  if (b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+  return MD_OK;
+}
+
+}  // extern "C"

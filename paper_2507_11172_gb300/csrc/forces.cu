@@ -143,8 +143,10 @@ __global__ void __launch_bounds__(256, 3) k_lj(const SysDev* __restrict__ sys, c
   __shared__ double red[32];
   const PItem it = items[blockIdx.x];
   const SysDev& S = sys[it.sys];
-  const int kind = it.mode & M_KIND_MASK;
-  const bool energy = (it.mode & M_ENERGY) != 0;
+  const int mode = item_mode(S, it.mode);
+  if (mode & M_SKIP) return;  // block-uniform: a block belongs to one system
+  const int kind = mode & M_KIND_MASK;
+  const bool energy = (mode & M_ENERGY) != 0;
   const int n = S.n;
   const int tl = threadIdx.x % kLjTeam;
   const int i = it.begin + threadIdx.x / kLjTeam;
@@ -426,8 +428,10 @@ __global__ void __launch_bounds__(kAtmThreads, 3)
   for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
     const CItem it = items[item];
     const SysDev& S = sys[it.sys];
+    const int imode = item_mode(S, it.mode);
+    if (imode & M_SKIP) continue;  // CTA-uniform
     const int n = S.n, nc = S.nc, b = it.cell;
-    const bool energy = (it.mode & M_ENERGY) != 0;
+    const bool energy = (imode & M_ENERGY) != 0;
     const double* __restrict__ X = S.X[it.buf];
     __syncthreads();  // previous item fully consumed the shared arrays
     // ---- stencil: lane l of warp 0 handles stencil cell s(l); the base cell is first
@@ -849,7 +853,9 @@ __global__ void __launch_bounds__(32 * kPaWarps)
   __shared__ unsigned s_q[kPaWarps][64];
   const PItem it = items[blockIdx.x];
   const SysDev& S = sys[it.sys];
-  const bool energy = (it.mode & M_ENERGY) != 0;
+  const int imode = item_mode(S, it.mode);
+  if (imode & M_SKIP) return;
+  const bool energy = (imode & M_ENERGY) != 0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   const int x = it.begin + warp;
@@ -1022,8 +1028,10 @@ __global__ void __launch_bounds__(256) k_combine(const SysDev* __restrict__ sys,
   __shared__ double red[32];
   const PItem it = items[blockIdx.x];
   const SysDev& S = sys[it.sys];
-  const int kind = it.mode & M_KIND_MASK;
-  const bool energy = (it.mode & M_ENERGY) != 0;
+  const int mode = item_mode(S, it.mode);
+  if (mode & M_SKIP) return;
+  const int kind = mode & M_KIND_MASK;
+  const bool energy = (mode & M_ENERGY) != 0;
   const int n = S.n, nc = S.nc;
   const int p = it.begin + threadIdx.x;
   double ek = 0.0;
@@ -1032,7 +1040,7 @@ __global__ void __launch_bounds__(256) k_combine(const SysDev* __restrict__ sys,
     const int cx = cell % nc, cy = (cell / nc) % nc, cz = cell / (nc * nc);
     const T* part = reinterpret_cast<const T*>(S.partial);
     Acc3<T> f;
-    const bool ready = (it.mode & M_F3READY) != 0;  // the per-particle triplet kernel wrote f3
+    const bool ready = (mode & M_F3READY) != 0;  // the per-particle triplet kernel wrote f3
 #pragma unroll 1
     for (int s = 0; s < (ready ? 0 : 27); ++s) {
       const int dx = s % 3 - 1, dy = (s / 3) % 3 - 1, dz = s / 9 - 1;
@@ -1153,17 +1161,29 @@ void atm_prepare_table(cudaStream_t s) {
   cudaStreamSynchronize(s);
 }
 
+// The dynamic shared-memory limit is a property of the kernel for the whole process, shared
+// by every system: it is only ever raised, never lowered below what another system needs.
+static int g_atm_smem_attr[2] = {0, 0};
+
 int atm_configure(int smax, int precision, int* smem_bytes) {
   int bytes = (int)(precision ? atm_layout<double>(smax).total : atm_layout<float>(smax).total);
   *smem_bytes = bytes;
   int nb = 0;
-  if (precision) {
-    if (cudaFuncSetAttribute(k_atm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess) return 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_atm<double>, kAtmThreads, bytes);
-  } else {
-    if (cudaFuncSetAttribute(k_atm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess) return 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_atm<float>, kAtmThreads, bytes);
+  const int p = precision ? 1 : 0;
+  if (bytes > g_atm_smem_attr[p]) {
+    cudaError_t e = precision
+                        ? cudaFuncSetAttribute(k_atm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
+                        : cudaFuncSetAttribute(k_atm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    g_atm_smem_attr[p] = bytes;
   }
+  if (precision)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_atm<double>, kAtmThreads, bytes);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_atm<float>, kAtmThreads, bytes);
   return nb;
 }
 

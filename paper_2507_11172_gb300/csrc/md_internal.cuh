@@ -68,7 +68,13 @@ struct SysDev {
   double *acc;                // [ACC_N]
   unsigned long long *ctr;    // [CTR_N]
   int *flags;                 // [FLG_N]
+  // batched ensembles: per-tick modes of this member (NULL for a lone system) and the
+  // snapshot arrays used to replay a batch cycle
+  const int *mode_tab;
+  double *snap_x, *snap_v, *snap_f2, *snap_f3;
+  int *snap_id, *snap_cell;
 };
+
 
 // particle-range work item: threads handle sorted slots [begin, begin + blockDim)
 struct PItem {
@@ -96,6 +102,9 @@ struct SItem {
 enum : int {
   M_ENERGY = 1 << 8,    // accumulate energies / virials
   M_F3READY = 1 << 9,   // combine: f3 already holds complete forces (per-particle triplet kernel)
+  M_SKIP = 1 << 10,     // batch: this member does nothing in this launch
+  M_TABLE = 1 << 30,    // batch: the low bits index SysDev::mode_tab, which holds the real mode
+  M_TABLE_MASK = 0xffff,
   M_KIND_MASK = 0xff,
 };
 enum : int {  // LJ kinds
@@ -108,6 +117,11 @@ enum : int {  // combine kinds
   CB_LAST = 1,   // F3; v += dt_outer/2 F3 / m
   CB_CONT = 2,   // F3; v += dt_outer F3 / m + dt/2 F2 / m; x += dt v  (next outer step starts)
 };
+
+// mode of a work item: its own, or the member's table entry for batched launches
+__device__ __forceinline__ int item_mode(const SysDev& S, int imode) {
+  return (imode & M_TABLE) ? S.mode_tab[imode & M_TABLE_MASK] : imode;
+}
 
 // ---------------------------------------------------------------- helpers
 
@@ -241,6 +255,8 @@ struct Launch {
 
 // sort.cu
 void launch_bin_count(const Launch& L, const PItem* items, int nitems, int block);
+void launch_snapshot(const Launch& L, const PItem* items, int nitems, int restore);
+void launch_stamp(cudaStream_t s, unsigned long long* out);
 void launch_scan(const Launch& L, const SItem* items, int nitems);
 template <typename T> void launch_scatter(const Launch& L, const PItem* items, int nitems, int block);
 template <typename T> void launch_listbuild(const Launch& L, const CItem* items, int nitems, int smax);

@@ -12,6 +12,7 @@ namespace r3b {
 __global__ void k_bin_count(const SysDev* __restrict__ sys, const PItem* __restrict__ items) {
   const PItem it = items[blockIdx.x];
   const SysDev& S = sys[it.sys];
+  if (item_mode(S, it.mode) & M_SKIP) return;
   int p = it.begin + threadIdx.x;
   if (p >= S.n) return;
   double* X = S.X[it.buf];
@@ -32,6 +33,7 @@ __global__ void k_bin_count(const SysDev* __restrict__ sys, const PItem* __restr
 // cell_start[], count[] reset to zero, largest occupancy checked.
 __global__ void __launch_bounds__(1024) k_scan(const SysDev* __restrict__ sys, const SItem* __restrict__ items) {
   const SysDev& S = sys[items[blockIdx.x].sys];
+  if (item_mode(S, items[blockIdx.x].mode) & M_SKIP) return;
   __shared__ int wsum[32];
   __shared__ int wmax[32];
   const int ncell = S.ncell;
@@ -93,6 +95,7 @@ __global__ void k_scatter(const SysDev* __restrict__ sys, const PItem* __restric
   using T4 = typename V4<T>::type;
   const PItem it = items[blockIdx.x];
   const SysDev& S = sys[it.sys];
+  if (item_mode(S, it.mode) & M_SKIP) return;
   int p = it.begin + threadIdx.x;
   if (p >= S.n) return;
   const int n = S.n;
@@ -140,6 +143,7 @@ __global__ void __launch_bounds__(32 * kListWarps)
   __shared__ int st_begin[28], st_cnt[27], st_cell[27];
   const CItem it = items[blockIdx.x];
   const SysDev& S = sys[it.sys];
+  if (item_mode(S, it.mode) & M_SKIP) return;
   const int b = it.cell, nc = S.nc, n = S.n;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
@@ -164,6 +168,7 @@ __global__ void __launch_bounds__(32 * kListWarps)
   }
   __syncthreads();
   const int nstaged = min(st_begin[27], smax);
+  if (st_begin[27] > smax && threadIdx.x == 0) atomicOr(&S.flags[FLG_ERR], ERR_CELL_CAP);
   const T edge = (T)S.edge;
   const T4* __restrict__ P = reinterpret_cast<const T4*>(S.pos[it.buf]);
   for (int l = warp; l < 27; l += kListWarps) {
@@ -225,6 +230,51 @@ __global__ void __launch_bounds__(32 * kListWarps)
   }
 }
 
+// save (mode 0) or restore (mode 1) the state a batch cycle changes: positions of buffer
+// it.buf, velocities, cached forces, ids and cells
+__global__ void k_snapshot(const SysDev* __restrict__ sys, const PItem* __restrict__ items, int restore) {
+  const PItem it = items[blockIdx.x];
+  const SysDev& S = sys[it.sys];
+  const int p = it.begin + threadIdx.x;
+  if (p >= S.n) return;
+  const int n = S.n;
+  double* X = S.X[it.buf];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int q = a * n + p;
+    if (restore) {
+      X[q] = S.snap_x[q];
+      S.v[q] = S.snap_v[q];
+      S.f2[q] = S.snap_f2[q];
+      S.f3[q] = S.snap_f3[q];
+    } else {
+      S.snap_x[q] = X[q];
+      S.snap_v[q] = S.v[q];
+      S.snap_f2[q] = S.f2[q];
+      S.snap_f3[q] = S.f3[q];
+    }
+  }
+  if (restore) {
+    S.id[p] = S.snap_id[p];
+    S.pcell[p] = S.snap_cell[p];
+  } else {
+    S.snap_id[p] = S.id[p];
+    S.snap_cell[p] = S.pcell[p];
+  }
+}
+
+// device time stamp (ns) at a point of the stream
+__global__ void k_stamp(unsigned long long* out) {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  *out = t;
+}
+
+void launch_snapshot(const Launch& L, const PItem* items, int nitems, int restore) {
+  if (nitems > 0) k_snapshot<<<nitems, 256, 0, L.stream>>>(L.sys, items, restore);
+}
+void launch_stamp(cudaStream_t s, unsigned long long* out) { k_stamp<<<1, 1, 0, s>>>(out); }
+
 void launch_bin_count(const Launch& L, const PItem* items, int nitems, int block) {
   if (nitems > 0) k_bin_count<<<nitems, block, 0, L.stream>>>(L.sys, items);
 }
@@ -241,12 +291,22 @@ void launch_listbuild(const Launch& L, const CItem* items, int nitems, int smax)
   const int bytes = (int)(smax * (sizeof(typename V4<T>::type) + sizeof(int)));
   k_listbuild<T><<<nitems, 32 * kListWarps, bytes, L.stream>>>(L.sys, items, smax);
 }
+// the kernel's dynamic shared-memory limit is process-wide: only ever raised
+static int g_list_smem_attr[2] = {0, 0};
+
 int listbuild_configure(int smax, int precision) {
   const int bytes = (int)(smax * ((precision ? sizeof(double4_32a) : sizeof(float4)) + sizeof(int)));
+  const int p = precision ? 1 : 0;
+  if (bytes <= g_list_smem_attr[p]) return bytes;
   cudaError_t e = precision
                       ? cudaFuncSetAttribute(k_listbuild<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
                       : cudaFuncSetAttribute(k_listbuild<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  return e == cudaSuccess ? bytes : -1;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  g_list_smem_attr[p] = bytes;
+  return bytes;
 }
 template void launch_scatter<float>(const Launch&, const PItem*, int, int);
 template void launch_scatter<double>(const Launch&, const PItem*, int, int);

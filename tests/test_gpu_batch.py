@@ -1,0 +1,131 @@
+"""Batched ensemble and continuous serving: every request's result must equal the same request
+run alone (md_respa_step), within the FP tolerances of the single-system tests, whatever else
+shares the launches; the FP64 batch must also follow Algorithm 2 of the oracle."""
+import numpy as np
+import pytest
+
+import md_inputs
+import oracle
+from oracle import respa
+
+pytestmark = pytest.mark.gpu
+
+NU = 0.073
+
+
+def _systems(seed0=11):
+    """Uneven replicas: sizes, densities, temperatures and step-size factors differ."""
+    specs = [(600, 0.8, 1.0, 4), (1100, 0.85, 1.2, 8), (700, 0.7, 0.9, 2), (900, 0.75, 1.4, 1), (1500, 0.8, 1.1, 4)]
+    out = []
+    for i, (n, rho, T, k) in enumerate(specs):
+        w = md_inputs.fcc_system(n, rho, T, 0.05, seed0 + i)
+        w.k_inner = k
+        w.dt_outer = 0.002 * k
+        out.append(w)
+    return out
+
+
+def _alone(r3, w, n_outer, prec):
+    with r3.System.create(w.x, w.L, w.v, precision=prec, nu=NU) as s:
+        s.step(n_outer, w.k_inner, w.dt_outer)
+        x, v = s.state()
+        e = s.energy()
+    return x, v, e
+
+
+def _dist(a, b, L):
+    d = a - b
+    d -= L * np.rint(d / L)
+    return np.abs(d).max()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_each_result_same_alone_and_in_the_mix(gpu_lib, prec):
+    r3 = gpu_lib
+    ws = _systems()
+    n_outer = 5
+    alone = [_alone(r3, w, n_outer, prec) for w in ws]
+    b = r3.md_batch_create(0)
+    hs, tickets = [], []
+    try:
+        for w in ws:
+            h = r3.md_create_system(w.x, w.L, w.v, 1.0, prec)
+            r3.md_set_potentials(h, 1.0, 1.0, 2.5, NU, 2.5)
+            hs.append(h)
+            tickets.append(r3.md_batch_submit(b, h, n_outer, w.k_inner, w.dt_outer))
+        r3.md_batch_run(b, 0)
+        xtol = 1e-6 if prec == 0 else 1e-11
+        for w, h, t, (xa, va, ea) in zip(ws, hs, tickets, alone):
+            assert r3.md_batch_poll(b, t)
+            x, v = r3.md_get_state(h)
+            e = r3.md_get_energy(h)
+            assert _dist(x, xa, w.L) < xtol
+            assert np.abs(v - va).max() < 10 * xtol
+            scale = abs(ea[0]) + abs(ea[1]) + abs(ea[2])
+            assert abs(sum(e[:3]) - sum(ea[:3])) / scale < (1e-6 if prec == 0 else 1e-11)
+            lat = r3.md_batch_latency(b, t)
+            assert lat.size == n_outer and np.all(lat > 0)
+    finally:
+        r3.md_batch_destroy(b)
+        for h in hs:
+            r3.md_destroy_system(h)
+
+
+def test_batch_fp64_follows_algorithm2(gpu_lib):
+    r3 = gpu_lib
+    ws = _systems(31)[:3]
+    b = r3.md_batch_create(0)
+    hs = []
+    try:
+        tickets = []
+        for w in ws:
+            h = r3.md_create_system(w.x, w.L, w.v, 1.0, r3.MD_FP64)
+            r3.md_set_potentials(h, 1.0, 1.0, 2.5, NU, 2.5)
+            hs.append(h)
+            tickets.append(r3.md_batch_submit(b, h, 3, w.k_inner, w.dt_outer))
+        r3.md_batch_run(b, 0)
+        assert all(r3.md_batch_poll(b, t) for t in tickets)
+        for w, h in zip(ws, hs):
+            st = respa.State(w.x.copy(), w.v.copy(), w.L)
+            f2b, f3b = respa.lj_atm_forces(w.L, 1.0, 1.0, 2.5, NU, 2.5)
+            respa.run(st, 3, w.k_inner, w.dt_outer, f2b, f3b)
+            x, v = r3.md_get_state(h)
+            assert _dist(x, st.x, w.L) < 1e-10
+            assert np.abs(v - st.v).max() < 1e-9
+    finally:
+        r3.md_batch_destroy(b)
+        for h in hs:
+            r3.md_destroy_system(h)
+
+
+def test_serving_budget_and_arrivals(gpu_lib):
+    """Deferred systems admitted by a memory budget that holds about two at a time; more
+    requests arrive while others run; all finish and equal their lone runs."""
+    r3 = gpu_lib
+    ws = _systems(51)
+    n_outer = 4
+    alone = [_alone(r3, w, n_outer, 0) for w in ws]
+    hs = []
+    for w in ws:
+        h = r3.md_create_system(w.x, w.L, w.v, 1.0, r3.MD_FP32 | r3.MD_DEFERRED)
+        r3.md_set_potentials(h, 1.0, 1.0, 2.5, NU, 2.5)
+        hs.append(h)
+    # budget: about two of the largest systems
+    b = r3.md_batch_create(2 * 400 * 1024 * 1024 // 100)
+    try:
+        tickets = [r3.md_batch_submit(b, hs[0], n_outer, ws[0].k_inner, ws[0].dt_outer),
+                   r3.md_batch_submit(b, hs[1], n_outer, ws[1].k_inner, ws[1].dt_outer)]
+        r3.md_batch_run(b, 8)  # a partial run, then more arrivals
+        for w, h in zip(ws[2:], hs[2:]):
+            tickets.append(r3.md_batch_submit(b, h, n_outer, w.k_inner, w.dt_outer))
+        q, res = r3.md_batch_pending(b)
+        assert q + res >= 3
+        r3.md_batch_run(b, 0)
+        for w, h, t, (xa, va, _) in zip(ws, hs, tickets, alone):
+            assert r3.md_batch_poll(b, t)
+            x, _ = r3.md_get_state(h)
+            assert _dist(x, xa, w.L) < 1e-6
+    finally:
+        r3.md_batch_destroy(b)
+        for h in hs:
+            r3.md_destroy_system(h)
