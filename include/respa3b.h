@@ -92,7 +92,8 @@ md_status md_create_system(md_system **out, int64_t n, double box_L, const doubl
 md_status md_set_potentials(md_system *s, double lj_eps, double lj_sigma, double rc_pair, double atm_nu,
                             double rc_triplet);
 
-/* Verlet-list skin for the pair list (default 0.3 sigma).  The pair list is
+/* Verlet-list skin for the pair list (default 0.3 sigma, thinner for boxes below
+ * 3 (r_c2 + 0.3) at creation).  The pair list is
  * rebuilt at every outer step; if any particle moves more than skin/2 within
  * one, the call is replayed from its start with a rebuild on every inner
  * step, so results never depend on the skin. */

@@ -228,6 +228,7 @@ def md_batch_poll(b, ticket: int) -> bool:
 
 
 def md_batch_latency(b, ticket: int, cap: int = 4096) -> np.ndarray:
+    """Per-outer-step latencies (ms, device clock) of a ticket's request."""
     buf = np.zeros(cap)
     c = _I(cap)
     _check(load().md_batch_latency(b, ctypes.c_uint64(ticket), _ptr(buf), ctypes.byref(c)), "md_batch_latency")

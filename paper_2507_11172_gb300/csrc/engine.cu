@@ -899,6 +899,8 @@ md_status md_create_system(md_system** out, int64_t n, double box_L, const doubl
   s->L = box_L;
   s->mass = mass;
   s->precision = precision;
+  // a small box gets a thinner default skin (L must exceed 3 (r_c2 + skin))
+  if (!(s->L > 3.0 * (s->rc2 + s->skin))) s->skin = std::max(0.0, s->L / 3.0 - s->rc2 - 1e-6 * s->L);
   md_status st = check_geometry(s.get());
   if (st != MD_OK) return st;
   if (cuda_stream) {
