@@ -358,7 +358,10 @@ def cpu_baseline(w, nsample):
     pairs containing each sampled particle) for nsample particles of the same workload."""
     import oracle
     import md_inputs
-    sel = np.unique((md_inputs.uniform(7, 11, 0, 4 * nsample) * w.n).astype(np.int64))[:nsample]
+    if nsample >= w.n:
+        sel = np.arange(w.n, dtype=np.int64)
+    else:
+        sel = np.unique((md_inputs.uniform(7, 11, 0, 4 * nsample) * w.n).astype(np.int64))[:nsample]
     oracle.atm_particles(w.x, w.L, sel[:4], w.nu, w.rc3)  # load + warm
     t0 = time.perf_counter()
     _, _, cnt = oracle.atm_particles(w.x, w.L, sel, w.nu, w.rc3)
