@@ -200,10 +200,11 @@ def small_fcc_1k() -> Workload:
     return w
 
 
-def fcc_100k() -> Workload:
+def fcc_100k(replica: int = 0) -> Workload:
     """100,000 particles, same lattice/jitter/potentials, k=10, dt_outer=0.02,
-    100 outer steps."""
-    w = fcc_system(100_000, 0.8, 1.0, 0.05, config_seed(2), name="fcc100k_rho0.8")
+    100 outer steps.  `replica` selects an independent seed (one per rank when
+    several GPUs each run their own copy)."""
+    w = fcc_system(100_000, 0.8, 1.0, 0.05, config_seed(2, replica), name="fcc100k_rho0.8")
     w.dt_outer, w.k_inner, w.n_outer = 0.02, 10, 100
     return w
 

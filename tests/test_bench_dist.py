@@ -1,0 +1,73 @@
+"""Multi-rank host logic of bench.py on CPU (gloo, world size 2).
+
+The method shards into independent replicas (one per GPU, no data-path collective); the only
+cross-rank steps are the barrier around the timed region, the max of the timed region and the sum
+of the units processed.  These run here on gloo; the GPU launch uses the same functions on NCCL.
+"""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out_dir):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        # rank r "timed" 10 + r ms and processed 100 (r + 1) triplets
+        ms, units = bench.reduce_over_ranks(10.0 + rank, 100 * (rank + 1), "cpu")
+        dist.barrier()
+        with open(os.path.join(out_dir, f"r{rank}.json"), "w") as f:
+            json.dump({"ms": ms, "units": units}, f)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_reduce_over_ranks_gloo(tmp_path):
+    world = 2
+    mp.start_processes(_rank_main, args=(world, _free_port(), str(tmp_path)), nprocs=world, start_method="spawn")
+    for r in range(world):
+        got = json.load(open(tmp_path / f"r{r}.json"))
+        assert got["ms"] == 11.0  # slowest rank
+        assert got["units"] == 300.0  # all ranks' units
+
+
+def test_reduce_over_ranks_single_process():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.reduce_over_ranks(7.5, 42) == (7.5, 42.0)
+
+
+def test_replica_inputs_differ_per_rank():
+    """Weak scaling: each rank's replica is an independent seed of the same workload recipe."""
+    sys.path.insert(0, ROOT)
+    import md_inputs
+    a, b = md_inputs.fcc_system(500, 0.8, 1.0, 0.05, md_inputs.config_seed(2, 0)), \
+        md_inputs.fcc_system(500, 0.8, 1.0, 0.05, md_inputs.config_seed(2, 1))
+    assert a.L == b.L and a.x.shape == b.x.shape
+    assert not np.array_equal(a.x, b.x)
+
+
+def test_reference_arm_other_ranks_exit_without_work():
+    """Under torchrun only rank 0 runs the reference (oracle) arm; rank 1 prints nothing, exits 0."""
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    p = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2"],
+                       env=env, capture_output=True, text=True, timeout=120)
+    assert p.returncode == 0, p.stderr
+    assert p.stdout.strip() == ""
