@@ -71,7 +71,7 @@ typedef struct {
   uint64_t atm_timed;          /* number of ATM launches in atm_ms_total */
   int32_t max_cell_count;      /* largest cell occupancy seen at the last binning */
   int32_t cells_per_side;      /* binning grid */
-  int32_t atm_kernel;          /* triplet kernel in use: 0 cell/Newton-3, 1 per-particle, -1 not chosen yet */
+  int32_t atm_kernel;          /* triplet kernel in use: 0 cell, 1 per-particle, 2 rotation, -1 not chosen yet */
   int32_t reserved_;
 } md_stats;
 
@@ -130,8 +130,14 @@ md_status md_set_profiling(md_system *s, int profile);
  *      Newton-3 scatter of the three forces;
  *   1  one warp per particle, neighbours from the pair list, only the force on that
  *      particle per evaluation (each triplet evaluated from each member, no scatter);
- *      needs r_c3 <= r_c2 + skin, else 0 is used;
- *  -1  (default) time both on the system's first evaluation and keep the faster. */
+ *   2  one warp per particle and its half list (neighbours that follow it in cell-offset,
+ *      then index, order), every neighbour pair visited once by a cyclic rotation across
+ *      the lanes, each triplet evaluated once (Newton 3) with its forces kept as edge
+ *      weights; per-neighbour sums added with vector atomics (summation order varies
+ *      from run to run at the FP32 rounding level);
+ *      1 and 2 need r_c3 <= r_c2 + skin, else 0 is used;
+ *  -1  (default) time the allowed kernels on the system's first evaluation and keep the
+ *      fastest.  A batch uses its members' common choice, else 2 where allowed, else 0. */
 md_status md_set_atm_kernel(md_system *s, int variant);
 
 /* Number of particles, box side and precision of a handle. */

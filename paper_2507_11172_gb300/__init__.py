@@ -268,12 +268,14 @@ class System:
 
     @classmethod
     def create(cls, pos, box_L, vel=None, mass=1.0, precision=MD_FP32, eps=1.0, sigma=1.0, rc_pair=2.5, nu=0.0,
-               rc_triplet=2.5, skin=None):
+               rc_triplet=2.5, skin=None, atm_kernel=-1):
         h = md_create_system(pos, box_L, vel, mass, precision)
         try:
             if skin is not None:
                 md_set_skin(h, skin)
             md_set_potentials(h, eps, sigma, rc_pair, nu, rc_triplet)
+            if atm_kernel != -1:
+                md_set_atm_kernel(h, atm_kernel)
         except Exception:
             md_destroy_system(h)
             raise

@@ -93,6 +93,7 @@ struct md_system {
   int atm_variant = -1;       // 0: cell kernel with Newton-3 scatter, 1: per-particle kernel, -1: tune
   int atm_variant_req = -1;   // requested by md_set_atm_kernel (-1 = autotune)
   int nblocks_pa = 0;
+  int nblocks_rot = 0;
   std::map<std::tuple<int, int, int, int, int>, cudaGraphExec_t> graphs;  // (n_outer, k, cur, safe, profile)
   // host mirrors
   int* h_flags = nullptr;       // pinned [FLG_N]
@@ -112,7 +113,7 @@ struct md_system {
 
 namespace {
 
-enum KTag { T_BIN = 1, T_SCATTER, T_LIST, T_LJ, T_COMB, T_START, T_KIN, T_ATMPA };
+enum KTag { T_BIN = 1, T_SCATTER, T_LIST, T_LJ, T_COMB, T_START, T_KIN, T_ATMPA, T_ATMROT };
 
 void free_items(md_system* s) {
   for (void* p : s->item_allocs) cudaFree(p);
@@ -179,6 +180,7 @@ md_status alloc_device(md_system* s) {
   size_t o_count = a.reserve(4 * (size_t)s->ncell), o_cstart = a.reserve(4 * ((size_t)s->ncell + 1));
   size_t o_nbr = a.reserve(4 * (size_t)s->maxnb * n), o_nbc = a.reserve(4 * n);
   size_t o_part = a.reserve(tsz * 27 * 3 * n);
+  size_t o_f3a = a.reserve(4 * tsz * n);
   size_t o_acc = a.reserve(8 * ACC_N), o_ctr = a.reserve(8 * CTR_N), o_flg = a.reserve(4 * FLG_N);
   size_t o_sx = a.reserve(24 * n), o_sv = a.reserve(24 * n), o_sf2 = a.reserve(24 * n), o_sf3 = a.reserve(24 * n);
   size_t o_sid = a.reserve(4 * n), o_scell = a.reserve(4 * n);
@@ -213,6 +215,7 @@ md_status alloc_device(md_system* s) {
   h.nbr = (int*)(m + o_nbr);
   h.nbr_cnt = (int*)(m + o_nbc);
   h.partial = m + o_part;
+  h.f3acc = m + o_f3a;
   h.acc = (double*)(m + o_acc);
   h.ctr = (unsigned long long*)(m + o_ctr);
   h.flags = (int*)(m + o_flg);
@@ -257,6 +260,7 @@ size_t arena_bytes(const md_system* s0) {
   a.reserve(4 * (size_t)tmp.maxnb * n);
   a.reserve(4 * n);
   a.reserve(tsz * 27 * 3 * n);
+  a.reserve(4 * tsz * n);
   a.reserve(8 * ACC_N);
   a.reserve(8 * CTR_N);
   a.reserve(4 * FLG_N);
@@ -334,8 +338,14 @@ PItem* pitems_for(md_system* s, int tag, int mode, int buf) {
   auto it = s->pitems.find(key);
   if (it != s->pitems.end()) return it->second;
   std::vector<PItem> v;
-  const int per = (tag == T_LJ) ? kBlock / kLjTeam : (tag == T_ATMPA ? kPaPerBlock : kBlock);
-  const int nb = (tag == T_LJ) ? s->nblocks_lj : (tag == T_ATMPA ? s->nblocks_pa : s->nblocks);
+  const int per = (tag == T_LJ)      ? kBlock / kLjTeam
+                  : (tag == T_ATMPA)  ? kPaPerBlock
+                  : (tag == T_ATMROT) ? rot_warps(s->precision)
+                                      : kBlock;
+  const int nb = (tag == T_LJ)       ? s->nblocks_lj
+                 : (tag == T_ATMPA)  ? s->nblocks_pa
+                 : (tag == T_ATMROT) ? s->nblocks_rot
+                                     : s->nblocks;
   for (int b = 0; b < nb; ++b) v.push_back(PItem{0, b * per, mode, buf});
   PItem* d = upload_items(s, v);
   s->pitems[key] = d;
@@ -360,6 +370,7 @@ md_status prepare_items(md_system* s) {
   const int per_lj = kBlock / kLjTeam;
   s->nblocks_lj = (int)((s->n + per_lj - 1) / per_lj);
   s->nblocks_pa = (int)((s->n + kPaPerBlock - 1) / kPaPerBlock);
+  s->nblocks_rot = (int)((s->n + rot_warps(s->precision) - 1) / rot_warps(s->precision));
   for (int b = 0; b < 2; ++b) {
     pitems_for(s, T_BIN, 0, b);
     pitems_for(s, T_SCATTER, 0, b);
@@ -375,7 +386,11 @@ md_status prepare_items(md_system* s) {
       pitems_for(s, T_COMB, CB_INIT | E | M_F3READY, b);
       pitems_for(s, T_COMB, CB_LAST | E | M_F3READY, b);
       pitems_for(s, T_COMB, CB_CONT | E | M_F3READY, b);
+      pitems_for(s, T_COMB, CB_INIT | E | M_F3ACC, b);
+      pitems_for(s, T_COMB, CB_LAST | E | M_F3ACC, b);
+      pitems_for(s, T_COMB, CB_CONT | E | M_F3ACC, b);
       pitems_for(s, T_ATMPA, E, b);
+      pitems_for(s, T_ATMROT, E, b);
       citems_for(s, E, b);
     }
   }
@@ -465,7 +480,9 @@ struct Plan {
   template <typename T>
   void atm(int buf, bool energy, int ev) {
     if (ev >= 0) cudaEventRecord(s->events[2 * ev], L.stream);
-    if (s->atm_variant == 1)
+    if (s->atm_variant == 2)
+      launch_atm_rot<T>(L, pitems_for(s, T_ATMROT, energy ? M_ENERGY : 0, buf), s->nblocks_rot);
+    else if (s->atm_variant == 1)
       launch_atm_pa<T>(L, pitems_for(s, T_ATMPA, energy ? M_ENERGY : 0, buf), s->nblocks_pa);
     else
       launch_atm<T>(L, citems_for(s, energy ? M_ENERGY : 0, buf), s->ncell, s->atm_grid,
@@ -474,7 +491,7 @@ struct Plan {
   }
   template <typename T>
   void combine(int kind, int buf, bool energy) {
-    const int ready = (s->atm_variant == 1) ? M_F3READY : 0;
+    const int ready = (s->atm_variant == 1) ? M_F3READY : (s->atm_variant == 2 ? M_F3ACC : 0);
     launch_combine<T>(L, pitems_for(s, T_COMB, kind | ready | (energy ? M_ENERGY : 0), buf), s->nblocks, kBlock);
   }
   template <typename T>
@@ -639,8 +656,8 @@ md_status status_from_flags(md_system* s) {
 }
 
 bool variant_allowed(const md_system* s, int v) {
-  // the per-particle kernel reads its neighbours from the pair list: needs r_c3 <= r_c2 + skin
-  return v == 0 || (v == 1 && s->rc3 <= s->rc2 + s->skin);
+  // the per-particle and rotation kernels read neighbours from the pair list: r_c3 <= r_c2 + skin
+  return v == 0 || ((v == 1 || v == 2) && s->rc3 <= s->rc2 + s->skin);
 }
 
 // Autotuner for the triplet kernel: after one initial evaluation (binning, pair list, forces)
@@ -666,7 +683,8 @@ md_status tune_atm(md_system* s) {
   if (st != MD_OK) return st;
   float best = 1e30f;
   int bestv = 0;
-  for (int v = 0; v < 2; ++v) {
+  for (int v = 0; v < 3; ++v) {
+    if (!variant_allowed(s, v)) continue;
     s->atm_variant = v;
     float tot = 0.f;
     for (int r = 0; r < 4; ++r) {
@@ -685,6 +703,8 @@ md_status tune_atm(md_system* s) {
   }
   s->atm_variant = bestv;
   s->profile = prof;
+  // the rotation kernel's trial launches left sums that no combine cleared
+  CK(cudaMemsetAsync(s->h.f3acc, 0, (size_t)(s->precision ? 32 : 16) * (size_t)s->n, s->stream));
   clear_graphs(s);
   s->forces_valid = false;  // recompute with the chosen kernel
   s->energy_valid = false;
@@ -717,8 +737,10 @@ md_status do_call(md_system* s, int n_outer, int k, double dt_outer) {
     const int err = s->h_flags[FLG_ERR];
     const bool skin_bad = s->h_flags[FLG_SKIN] != 0 && !safe;
     const bool cap_bad = (err & (ERR_CELL_CAP | ERR_NBR_CAP)) != 0;
+    // the rotation and per-particle kernels hold shorter half lists than the cell kernel
+    const bool half_bad = (err & ERR_HALF_CAP) != 0 && s->atm_variant != 0;
     s->stats.max_cell_count = s->h_flags[FLG_MAXCELL];
-    if (!(skin_bad || cap_bad) || (err & ERR_NONFINITE)) {
+    if (!(skin_bad || cap_bad || half_bad) || (err & ERR_NONFINITE)) {
       md_status fs = status_from_flags(s);
       if (fs != MD_OK) {
         s->cur = cur0;
@@ -758,13 +780,17 @@ md_status do_call(md_system* s, int n_outer, int k, double dt_outer) {
       if (err & ERR_NBR_CAP) s->maxnb = s->maxnb * 3 / 2 + 16;
       st = rebuild(s, true);
       if (st != MD_OK) return st;
+    } else if (half_bad) {
+      s->atm_variant = 0;  // kept for this system until the next tuning
+      clear_graphs(s);
+      s->forces_valid = false;  // the failed attempt re-sorted: rebuild the lists from the snapshot
     } else {
       s->stats.replays += 1;
     }
     // a replay must recompute the cached forces only if they were not valid before
     if (init) s->forces_valid = false;
     s->h_flags[FLG_SKIN] = skin_bad ? 1 : 0;
-    s->h_flags[FLG_ERR] = cap_bad ? err : 0;
+    s->h_flags[FLG_ERR] = cap_bad ? (err & ~ERR_HALF_CAP) : 0;
   }
   g_last_error = "respa_step: replay limit reached";
   return MD_ERR_CAPACITY;
@@ -1072,7 +1098,7 @@ md_status md_set_profiling(md_system* s, int profile) {
 }
 
 md_status md_set_atm_kernel(md_system* s, int variant) {
-  if (!s || variant < -1 || variant > 1) return MD_ERR_ARG;
+  if (!s || variant < -1 || variant > 2) return MD_ERR_ARG;
   s->atm_variant_req = variant;
   s->atm_variant = -1;
   clear_graphs(s);
@@ -1146,6 +1172,7 @@ struct md_batch {
   // composition
   bool dirty = true;
   int P = 1, variant = 1, smax = 0, smax_list = 0, atm_grid = 0;
+  bool cell_only = false;  // a member's half list overflowed the rotation kernel: cell kernel from now on
   SysDev* d_sys = nullptr;
   int* d_modes = nullptr;
   int* h_modes = nullptr;  // pinned [slots][P][KT_N]
@@ -1226,7 +1253,9 @@ void enqueue_cycle(md_batch* b, const std::vector<TickItems>& ticks, bool with_s
     chk("listbuild", t);
     launch_lj<T>(L, b->d_pitems + it.lj, it.nlj, kBlock);
     chk("lj", t);
-    if (b->variant == 1)
+    if (b->variant == 2)
+      launch_atm_rot<T>(L, b->d_pitems + it.atm, it.natm);
+    else if (b->variant == 1)
       launch_atm_pa<T>(L, b->d_pitems + it.atm, it.natm);
     else
       launch_atm<T>(L, b->d_citems + it.atm, it.natm, b->atm_grid, b->smax);
@@ -1247,11 +1276,13 @@ md_status batch_build(md_batch* b) {
   }
   long long P = 1;
   bool pa = true;
+  int req = -2;  // the members' common requested triplet kernel (-3: they differ)
   int capmax = 0;
   for (uint64_t tk : b->resident) {
     const Request& r = b->req[tk];
     P = lcm_ll(P, r.k);
     pa = pa && variant_allowed(r.s, 1);
+    req = (req == -2 || req == r.s->atm_variant_req) ? r.s->atm_variant_req : -3;
     capmax = std::max(capmax, r.s->cap_cell);
   }
   if (P > 4096) {
@@ -1259,7 +1290,9 @@ md_status batch_build(md_batch* b) {
     return MD_ERR_ARG;
   }
   b->P = (int)P;
-  b->variant = pa ? 1 : 0;
+  // the members' common request where every member allows it, else the rotation kernel where the
+  // pair list covers the triplet cutoff, else the cell kernel
+  b->variant = b->cell_only ? 0 : ((req >= 0 && (req == 0 || pa)) ? req : (pa ? 2 : 0));
   b->smax = atm_stage_capacity(capmax);
   b->smax_list = 27 * capmax;  // the pair-list build stages the full 27-cell stencil
   {
@@ -1336,12 +1369,13 @@ md_status batch_build(md_batch* b) {
         for (int q = 0; q < (int)r.s->n; q += kBlock / kLjTeam) pit.push_back(PItem{j, q, tab(KT_LJ), tt & 1});
       }
       ti.nlj = (int)(pit.size() - ti.lj);
-      if (b->variant == 1) {
+      if (b->variant >= 1) {
+        const int per = (b->variant == 1) ? kPaPerBlock : rot_warps(b->precision);
         ti.atm = pit.size();
         for (int j = 0; j < ns; ++j) {
           const Request& r = b->req[b->resident[j]];
           if (t % r.k != r.k - 1) continue;
-          for (int q = 0; q < (int)r.s->n; q += kPaPerBlock) pit.push_back(PItem{j, q, tab(KT_ATM), (r.k - 1) & 1});
+          for (int q = 0; q < (int)r.s->n; q += per) pit.push_back(PItem{j, q, tab(KT_ATM), (r.k - 1) & 1});
         }
         ti.natm = (int)(pit.size() - ti.atm);
       } else {
@@ -1419,7 +1453,7 @@ void batch_fill_modes(md_batch* b, bool safe) {
   for (int j = 0; j < ns; ++j) {
     const Request& r = b->req[b->resident[j]];
     const int rem = r.n_outer - r.outer_done;
-    const int f3r = (b->variant == 1) ? M_F3READY : 0;
+    const int f3r = (b->variant == 1) ? M_F3READY : (b->variant == 2 ? M_F3ACC : 0);
     int* tab = b->h_modes + (size_t)j * P * KT_N;
     for (int t = 0; t < P; ++t) {
       const int q = t / r.k, tt = t % r.k;
@@ -1520,15 +1554,21 @@ md_status batch_cycle(md_batch* b) {
     CK(cudaMemcpyAsync(b->h_stamps, b->d_stamps, sizeof(unsigned long long) * (b->P + 1), cudaMemcpyDeviceToHost,
                        b->stream));
     CK(cudaStreamSynchronize(b->stream));
-    bool skin = false, cap = false;
+    bool skin = false, cap = false, half = false;
     for (int j = 0; j < ns; ++j) {
       const int* f = b->h_flags + j * FLG_N;
       if (f[FLG_SKIN] && !safe) skin = true;
       if (f[FLG_ERR] & (ERR_CELL_CAP | ERR_NBR_CAP)) cap = true;
+      if ((f[FLG_ERR] & ERR_HALF_CAP) && b->variant != 0) half = true;
     }
-    if (!(skin || cap)) break;
+    if (!(skin || cap || half)) break;
     launch_snapshot(L, b->d_snap, b->nsnap, 1);  // every member back to the cycle start
     CK(cudaStreamSynchronize(b->stream));
+    if (half && !cap) {  // the cell kernel takes longer half lists; replay the cycle with it
+      b->cell_only = true;
+      md_status st = batch_build(b);
+      if (st != MD_OK) return st;
+    }
     if (cap) {
       std::vector<uint64_t> grow;
       for (int j = 0; j < ns; ++j) {

@@ -1022,6 +1022,275 @@ __global__ void __launch_bounds__(32 * kPaWarps)
   }
 }
 
+// ============================================================== rotation triplet kernel
+// One warp per base particle i.  Its half list holds the neighbours j within r_c3 that follow i in
+// the order (cell offset from i's cell, lexicographic in z, y, x; then sorted index), so that every
+// triplet is owned by exactly one member, its first one in that order (Newton 3: each triplet is
+// evaluated once).  Virtual lane v (lane + 32 h) holds neighbour v.  Step s of a cyclic rotation
+// pairs v with (v + s) mod m; steps 1 .. floor(m / 2) visit every unordered neighbour pair once.
+// The forces are kept as edge weights: with d_j = x_j - x_i, d_k = x_k - x_i, e = d_k - d_j and
+// pa2 = 2 dphi/da, pb2 = 2 dphi/db, pc2 = 2 dphi/dc (a, b, c the squared lengths of d_j, d_k, e),
+//   F_i = pa2 d_j + pb2 d_k,  F_j = -pa2 d_j + pc2 e,  F_k = -pb2 d_k - pc2 e,
+// so neighbour v accumulates one scalar W_v (its i-edge weight) and one vector G_v (its j-k edges):
+// F_v = G_v - W_v d_v and F_i = sum_v W_v d_v.  The lane of j keeps j's share in registers; k's
+// share goes to k's shared-memory slot, written by exactly one lane per step (the rotation is a
+// permutation), with a warp barrier between steps.  Per-(i, neighbour) totals are added to the
+// neighbour's force with one vector atomic; the combine kernel reads and clears them.
+constexpr int kRotMax = 64;  // neighbours in one half list (longer lists: the cell kernel)
+
+// scalar core: the three edge weights (zero unless ok) and, with kE, the triplet energy
+template <typename T, bool kE>
+__device__ __forceinline__ void atm_weights(const T a, const T b, const T c, const T nu, const T nu2, const bool ok,
+                                            T& pa2, T& pb2, T& pc2, T& u) {
+  const T ab = a * b;
+  const T q = ok ? ab * c : (T)1;
+  const T t = rsqrt_acc<T>(q);
+  const T w = t * t;    // 1 / (abc)
+  const T t3 = w * t;   // (abc)^(-3/2)
+  const T t5 = t3 * w;  // (abc)^(-5/2)
+  const T s = a + b + c;
+  const T A = s - (c + c), B = s - (b + b), C = s - (a + a);
+  const T AB = A * B, AC = A * C, BC = B * C;
+  const T P = AB * C;  // (a + b - c)(a - b + c)(-a + b + c) = 8 abc cos(g1) cos(g2) cos(g3)
+  const T Pa = (a + a) * C - AB, Pb = (b + b) * B - AC, Pc = (c + c) * A - BC;  // dP/da, dP/db, dP/dc
+  const T Pw = P * w;
+  const T H = (T)1.5 + (T)0.9375 * Pw;
+  const T k = ok ? nu2 * t5 : (T)0;  // 2 nu (abc)^(-5/2)
+  pa2 = k * ((T)0.375 * Pa - (b * c) * H);
+  pb2 = k * ((T)0.375 * Pb - (a * c) * H);
+  pc2 = k * ((T)0.375 * Pc - ab * H);
+  if (kE) u = ok ? nu * t3 * ((T)1 + (T)0.375 * Pw) : (T)0;
+}
+
+template <typename T> struct RotCfg { static constexpr int warps = (sizeof(T) == 4) ? 8 : 4; };
+
+// the rotation over one half list of m <= 32 VL neighbours (nd: d_v and |d_v|^2; sacc zeroed)
+template <typename T, int VL, bool kE>
+__device__ __forceinline__ void atm_rotate(const SysDev& S, const double* __restrict__ X,
+                                           const typename V4<T>::type* nd, const int* nidx,
+                                           typename V4<T>::type* sacc, const int m, const int lane, T& fix,
+                                           T& fiy, T& fiz, T& uu, unsigned& cnt) {
+  using T4 = typename V4<T>::type;
+  const T rcsq = Par<T>::rc3sq(S), g3 = Par<T>::guard3(S), nu = Par<T>::nu(S);
+  const T nu2 = nu + nu;
+  const T hi = rcsq + g3, lo = rcsq - g3;
+  T4 dj[VL];
+  T Wj[VL], gx[VL], gy[VL], gz[VL];
+#pragma unroll
+  for (int h = 0; h < VL; ++h) {
+    dj[h] = nd[lane + 32 * h];
+    Wj[h] = gx[h] = gy[h] = gz[h] = (T)0;
+  }
+  const int smax = m >> 1;
+#pragma unroll 1
+  for (int s = 1; s <= smax; ++s) {
+    const bool half_step = (s + s == m);
+#pragma unroll
+    for (int h = 0; h < VL; ++h) {
+      const int v = lane + 32 * h;
+      const bool valid = v < m && (!half_step || v < s);
+      int p = v + s;
+      if (p >= m) p -= m;
+      if (v >= m) p = v;  // idle lanes touch only their own (unused) slot
+      const T4 dk = nd[p];
+      const T ex = dk.x - dj[h].x, ey = dk.y - dj[h].y, ez = dk.z - dj[h].z;
+      const T c = ex * ex + ey * ey + ez * ez;
+      bool ok = valid && c <= hi;
+      const bool band = ok && c >= lo;
+      if (__any_sync(0xffffffffu, band)) {  // rare: decide the guard band exactly in FP64
+        if (band) {
+          atomicAdd(&S.ctr[CTR_GUARD], 1ull);
+          ok = exact_within(X, S.n, nidx[v], nidx[p], S.L, S.rc3sq);
+        }
+      }
+      T pa2, pb2, pc2, u = (T)0;
+      atm_weights<T, kE>(dj[h].w, dk.w, c, nu, nu2, ok, pa2, pb2, pc2, u);
+      cnt += ok ? 1u : 0u;
+      if (kE) uu += u;
+      Wj[h] += pa2;
+      const T hx = pc2 * ex, hy = pc2 * ey, hz = pc2 * ez;
+      gx[h] += hx;
+      gy[h] += hy;
+      gz[h] += hz;
+      T4 a = sacc[p];
+      a.x -= hx;
+      a.y -= hy;
+      a.z -= hz;
+      a.w += pb2;
+      sacc[p] = a;
+    }
+    __syncwarp();
+  }
+#pragma unroll
+  for (int h = 0; h < VL; ++h) {
+    const int v = lane + 32 * h;
+    if (v < m) {
+      const T4 a = sacc[v];
+      const T W = Wj[h] + a.w;
+      const T Fx = (gx[h] + a.x) - W * dj[h].x;
+      const T Fy = (gy[h] + a.y) - W * dj[h].y;
+      const T Fz = (gz[h] + a.z) - W * dj[h].z;
+      fix += W * dj[h].x;
+      fiy += W * dj[h].y;
+      fiz += W * dj[h].z;
+      const int j = nidx[v];
+      if constexpr (sizeof(T) == 4) {
+        atomicAdd(reinterpret_cast<float4*>(S.f3acc) + j, make_float4(Fx, Fy, Fz, 0.f));
+      } else {
+        double* q = reinterpret_cast<double*>(S.f3acc) + 4 * (size_t)j;
+        atomicAdd(q, Fx);
+        atomicAdd(q + 1, Fy);
+        atomicAdd(q + 2, Fz);
+      }
+    }
+  }
+}
+
+template <typename T, bool kE>
+__device__ __forceinline__ void atm_rot_base(const SysDev& S, const int buf, const int x, const int lane,
+                                             typename V4<T>::type* nd, int* nidx, typename V4<T>::type* sacc) {
+  using T4 = typename V4<T>::type;
+  const int n = S.n;
+  const unsigned lt = (1u << lane) - 1u;
+  const T4* __restrict__ P = reinterpret_cast<const T4*>(S.pos[buf]);
+  const T4* __restrict__ PL = reinterpret_cast<const T4*>(S.poslo);
+  const double* __restrict__ X = S.X[buf];
+  const T edge = Par<T>::edge(S), edge_lo = Par<T>::edge_lo(S);
+  const T rcsq = Par<T>::rc3sq(S), g3 = Par<T>::guard3(S);
+  const T4 px = P[x];
+  T4 lx;
+  if (sizeof(T) == 4) lx = PL[x];
+  // 1. half list from the pair list: offset code > centre, or the same cell and a larger index
+  const int cnt_list = S.nbr_cnt[x];
+  const int* __restrict__ row = S.nbr + (size_t)x * S.maxnb;
+  constexpr unsigned kCentre = (1u << 4) | (1u << 2) | 1u;  // code of the offset (0, 0, 0)
+  int m = 0;
+  for (int t0 = 0; t0 < cnt_list; t0 += 32) {
+    const int t = t0 + lane;
+    bool ok = false, band = false;
+    int j = x;
+    T dx = 0, dy = 0, dz = 0;
+    if (t < cnt_list) {
+      const unsigned e = (unsigned)__ldg(row + t);
+      j = (int)(e & kNbrMask);
+      const unsigned cde = e >> kNbrShift;
+      if (cde > kCentre || (cde == kCentre && j > x)) {
+        const T ox = (T)(cde & 3u) - (T)1, oy = (T)((cde >> 2) & 3u) - (T)1, oz = (T)(cde >> 4) - (T)1;
+        const T4 pj = P[j];
+        if (sizeof(T) == 4) {
+          const T4 lj = PL[j];
+          float s1, e1, s2, e2;
+          two_sum((float)pj.x, -(float)px.x, s1, e1);
+          two_sum(s1, (float)(ox * edge), s2, e2);
+          dx = s2 + ((e1 + e2) + (((float)lj.x - (float)lx.x) + (float)(ox * edge_lo)));
+          two_sum((float)pj.y, -(float)px.y, s1, e1);
+          two_sum(s1, (float)(oy * edge), s2, e2);
+          dy = s2 + ((e1 + e2) + (((float)lj.y - (float)lx.y) + (float)(oy * edge_lo)));
+          two_sum((float)pj.z, -(float)px.z, s1, e1);
+          two_sum(s1, (float)(oz * edge), s2, e2);
+          dz = s2 + ((e1 + e2) + (((float)lj.z - (float)lx.z) + (float)(oz * edge_lo)));
+        } else {
+          dx = (pj.x - px.x) + ox * edge;
+          dy = (pj.y - px.y) + oy * edge;
+          dz = (pj.z - px.z) + oz * edge;
+        }
+        const T r2 = dx * dx + dy * dy + dz * dz;
+        ok = r2 < rcsq - g3;
+        band = (r2 >= rcsq - g3) && (r2 <= rcsq + g3);
+      }
+    }
+    if (__any_sync(0xffffffffu, band)) {
+      if (band) {
+        atomicAdd(&S.ctr[CTR_GUARD], 1ull);
+        ok = exact_within(X, n, x, j, S.L, S.rc3sq);
+      }
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, ok);
+    if (ok) {
+      const int pos = m + __popc(bal & lt);
+      if (pos < kRotMax) {
+        T4 d4;
+        d4.x = dx;
+        d4.y = dy;
+        d4.z = dz;
+        d4.w = dx * dx + dy * dy + dz * dz;
+        nd[pos] = d4;
+        nidx[pos] = j;
+      }
+    }
+    m += __popc(bal);
+  }
+  if (m > kRotMax) {
+    if (lane == 0) atomicOr(&S.flags[FLG_ERR], ERR_HALF_CAP);
+    m = kRotMax;
+  }
+  const int vlu = m <= 32 ? 1 : 2;  // virtual lanes per lane
+  // idle virtual lanes hold a harmless finite neighbour; every slot starts at zero
+  for (int v = lane; v < 32 * vlu; v += 32) {
+    if (v >= m) {
+      T4 d4;
+      d4.x = d4.y = d4.z = (T)0;
+      d4.w = (T)1;
+      nd[v] = d4;
+    }
+    T4 z;
+    z.x = z.y = z.z = z.w = (T)0;
+    sacc[v] = z;
+  }
+  __syncwarp();
+  // 2. the rotation
+  T fix = 0, fiy = 0, fiz = 0, uu = 0;
+  unsigned cnt = 0;
+  if (m >= 2) {
+    if (vlu == 1)
+      atm_rotate<T, 1, kE>(S, X, nd, nidx, sacc, m, lane, fix, fiy, fiz, uu, cnt);
+    else
+      atm_rotate<T, 2, kE>(S, X, nd, nidx, sacc, m, lane, fix, fiy, fiz, uu, cnt);
+  }
+  // 3. F_i, the count and the energy (per-lane sums combined by compensated warp reductions)
+  unsigned ctot = cnt;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) ctot += __shfl_xor_sync(0xffffffffu, ctot, o);
+  const double F0 = warp_sum_comp<T>(fix), F1 = warp_sum_comp<T>(fiy), F2 = warp_sum_comp<T>(fiz);
+  const double U = kE ? warp_sum_comp<T>(uu) : 0.0;
+  if (lane == 0) {
+    if constexpr (sizeof(T) == 4) {
+      atomicAdd(reinterpret_cast<float4*>(S.f3acc) + x, make_float4((float)F0, (float)F1, (float)F2, 0.f));
+    } else {
+      double* q = reinterpret_cast<double*>(S.f3acc) + 4 * (size_t)x;
+      atomicAdd(q, F0);
+      atomicAdd(q + 1, F1);
+      atomicAdd(q + 2, F2);
+    }
+    if (ctot) atomicAdd(&S.ctr[CTR_TRIPLETS], (unsigned long long)ctot);
+    if (kE) {
+      atomicAdd(&S.acc[ACC_U3], U);
+      atomicAdd(&S.acc[ACC_W3], 9.0 * U);  // sum_a r_a . F_a = 9 phi (phi is homogeneous of degree -9)
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(32 * RotCfg<T>::warps)
+    k_atm_rot(const SysDev* __restrict__ sys, const PItem* __restrict__ items) {
+  using T4 = typename V4<T>::type;
+  constexpr int W = RotCfg<T>::warps;
+  __shared__ T4 s_nd[W][kRotMax];
+  __shared__ T4 s_acc[W][kRotMax];
+  __shared__ int s_idx[W][kRotMax];
+  const PItem it = items[blockIdx.x];
+  const SysDev& S = sys[it.sys];
+  const int imode = item_mode(S, it.mode);
+  if (imode & M_SKIP) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int x = it.begin + warp;
+  if (x >= S.n) return;  // whole warp leaves together
+  if (imode & M_ENERGY)
+    atm_rot_base<T, true>(S, it.buf, x, lane, s_nd[warp], s_idx[warp], s_acc[warp]);
+  else
+    atm_rot_base<T, false>(S, it.buf, x, lane, s_nd[warp], s_idx[warp], s_acc[warp]);
+}
+
 // ============================================================== combine + outer kicks
 template <typename T>
 __global__ void __launch_bounds__(256) k_combine(const SysDev* __restrict__ sys, const PItem* __restrict__ items) {
@@ -1041,8 +1310,9 @@ __global__ void __launch_bounds__(256) k_combine(const SysDev* __restrict__ sys,
     const T* part = reinterpret_cast<const T*>(S.partial);
     Acc3<T> f;
     const bool ready = (mode & M_F3READY) != 0;  // the per-particle triplet kernel wrote f3
+    const bool summed = (mode & M_F3ACC) != 0;   // the rotation kernel's atomic sums
 #pragma unroll 1
-    for (int s = 0; s < (ready ? 0 : 27); ++s) {
+    for (int s = 0; s < ((ready || summed) ? 0 : 27); ++s) {
       const int dx = s % 3 - 1, dy = (s / 3) % 3 - 1, dz = s / 9 - 1;
       const int bx = (cx - dx + nc) % nc, by = (cy - dy + nc) % nc, bz = (cz - dz + nc) % nc;
       const int base = (bz * nc + by) * nc + bx;
@@ -1050,6 +1320,22 @@ __global__ void __launch_bounds__(256) k_combine(const SysDev* __restrict__ sys,
       f.add(part[(3 * s + 0) * (size_t)n + p], part[(3 * s + 1) * (size_t)n + p], part[(3 * s + 2) * (size_t)n + p]);
     }
     double F[3] = {f.get(0), f.get(1), f.get(2)};
+    if (summed) {
+      if (sizeof(T) == 4) {
+        float4* a4 = reinterpret_cast<float4*>(S.f3acc) + p;
+        const float4 a = *a4;
+        F[0] = (double)a.x;
+        F[1] = (double)a.y;
+        F[2] = (double)a.z;
+        *a4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      } else {
+        double* a = reinterpret_cast<double*>(S.f3acc) + 4 * (size_t)p;
+        F[0] = a[0];
+        F[1] = a[1];
+        F[2] = a[2];
+        a[0] = a[1] = a[2] = 0.0;
+      }
+    }
     if (ready) {
       if (sizeof(T) == 4) {
         const float* pf = reinterpret_cast<const float*>(S.partial);
@@ -1211,6 +1497,13 @@ template <typename T>
 void launch_atm_pa(const Launch& L, const PItem* items, int nitems) {
   if (nitems > 0) k_atm_pa<T><<<nitems, 32 * kPaWarps, 0, L.stream>>>(L.sys, items, g_table);
 }
+template <typename T>
+void launch_atm_rot(const Launch& L, const PItem* items, int nitems) {
+  static_assert(RotCfg<T>::warps == rot_warps(sizeof(T) == 8 ? 1 : 0), "items and kernel disagree");
+  if (nitems > 0) k_atm_rot<T><<<nitems, 32 * RotCfg<T>::warps, 0, L.stream>>>(L.sys, items);
+}
+template void launch_atm_rot<float>(const Launch&, const PItem*, int);
+template void launch_atm_rot<double>(const Launch&, const PItem*, int);
 template void launch_atm_pa<float>(const Launch&, const PItem*, int);
 template void launch_atm_pa<double>(const Launch&, const PItem*, int);
 

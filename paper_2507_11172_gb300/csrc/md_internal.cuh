@@ -65,6 +65,8 @@ struct SysDev {
   int *count, *cell_start;    // [ncell], [ncell + 1]
   int *nbr, *nbr_cnt;         // [n][maxnb] row-major, [n]
   void *partial;              // T [27][3][n] per-stencil-slot ATM partial forces
+  void *f3acc;                // [n] float4 (FP32) or double [n][4]: rotation-kernel ATM force sums,
+                              // zero between evaluations (the combine kernel clears what it reads)
   double *acc;                // [ACC_N]
   unsigned long long *ctr;    // [CTR_N]
   int *flags;                 // [FLG_N]
@@ -103,6 +105,7 @@ enum : int {
   M_ENERGY = 1 << 8,    // accumulate energies / virials
   M_F3READY = 1 << 9,   // combine: f3 already holds complete forces (per-particle triplet kernel)
   M_SKIP = 1 << 10,     // batch: this member does nothing in this launch
+  M_F3ACC = 1 << 11,    // combine: read (and clear) the rotation kernel's per-particle sums
   M_TABLE = 1 << 30,    // batch: the low bits index SysDev::mode_tab, which holds the real mode
   M_TABLE_MASK = 0xffff,
   M_KIND_MASK = 0xff,
@@ -274,6 +277,9 @@ int atm_configure(int smax, int precision, int* smem_bytes);
 // per-particle ATM variant: items of 4 particles (one warp each)
 template <typename T> void launch_atm_pa(const Launch& L, const PItem* items, int nitems);
 constexpr int kPaPerBlock = 4;
+// rotation variant: items of rot_warps(precision) particles (one warp each)
+template <typename T> void launch_atm_rot(const Launch& L, const PItem* items, int nitems);
+constexpr int rot_warps(int precision) { return precision ? 4 : 8; }
 template <typename T>
 void launch_atm_table(const Launch& L, const CItem* items, int nitems, int grid, int smax, const uint16_t* table);
 template <typename T> void launch_combine(const Launch& L, const PItem* items, int nitems, int block);

@@ -26,8 +26,9 @@ def force_err(got, ref):
     return float((np.linalg.norm(got - ref, axis=1) / np.maximum(np.linalg.norm(ref, axis=1), floor)).max())
 
 
-def make(r3, w, prec, nu=NU, rc2=2.5, rc3=2.5, skin=None):
-    return r3.System.create(w.x, w.L, w.v, precision=prec, nu=nu, rc_pair=rc2, rc_triplet=rc3, skin=skin)
+def make(r3, w, prec, nu=NU, rc2=2.5, rc3=2.5, skin=None, kernel=-1):
+    return r3.System.create(w.x, w.L, w.v, precision=prec, nu=nu, rc_pair=rc2, rc_triplet=rc3, skin=skin,
+                            atm_kernel=kernel)
 
 
 @pytest.fixture(scope="module")
@@ -104,8 +105,9 @@ def test_step_size_factor_variants(gpu_lib, cfg1, k):
     assert np.abs(d).max() < 1e-10 and np.abs(v - st.v).max() < 1e-9
 
 
+@pytest.mark.parametrize("kernel", [-1, 2])
 @pytest.mark.parametrize("n,L", [(37, 9.0), (300, 9.0), (777, 10.0), (1283, 11.7)])
-def test_ragged_sizes_and_densities(gpu_lib, n, L):
+def test_ragged_sizes_and_densities(gpu_lib, n, L, kernel):
     rng = np.random.default_rng(n)
     x, _ = md_inputs.rsa(n, n / L ** 3, 0.85, 100 + n)
     L = (n / (n / L ** 3)) ** (1 / 3)
@@ -113,7 +115,7 @@ def test_ragged_sizes_and_densities(gpu_lib, n, L):
     f2r, u2r, _ = oracle.lj_brute(x, L, 1.0, 1.0, 2.5)
     f3r, u3r, _, cnt = oracle.atm_brute(x, L, 0.5, 2.5)
     for prec in (0, 1):
-        with gpu_lib.System.create(x, L, v, precision=prec, nu=0.5) as s:
+        with gpu_lib.System.create(x, L, v, precision=prec, nu=0.5, atm_kernel=kernel) as s:
             f2, f3 = s.forces()
             assert s.stats()["triplets_last"] == cnt
         if cnt:
@@ -122,7 +124,8 @@ def test_ragged_sizes_and_densities(gpu_lib, n, L):
     del rng
 
 
-def test_distances_exactly_at_the_cutoff(gpu_lib):
+@pytest.mark.parametrize("kernel", [0, 1, 2])
+def test_distances_exactly_at_the_cutoff(gpu_lib, kernel):
     """Simple cubic lattice, spacing 1.25, r_c = 2.5: pairs and collinear triplets sit exactly
     on the cutoff; both sides must include them (r <= r_c) and agree on the count."""
     b, m = 1.25, 8
@@ -133,7 +136,7 @@ def test_distances_exactly_at_the_cutoff(gpu_lib):
     f3r, u3r, _, cnt = oracle.atm_brute(x, L, NU, 2.5)
     f2r, u2r, _ = oracle.lj_brute(x, L, 1.0, 1.0, 2.5)
     for prec in (0, 1):
-        with gpu_lib.System.create(x, L, None, precision=prec, nu=NU, skin=0.1) as s:
+        with gpu_lib.System.create(x, L, None, precision=prec, nu=NU, skin=0.1, atm_kernel=kernel) as s:
             f2, f3 = s.forces()
             _, u2, u3, _ = s.energy()
             assert s.stats()["triplets_last"] == cnt
@@ -172,7 +175,8 @@ def test_skin_violation_replays_exactly(gpu_lib, cfg1):
     assert np.abs(d).max() < 1e-10
 
 
-def test_dense_cluster_grows_cell_capacity(gpu_lib):
+@pytest.mark.parametrize("kernel", [-1, 2])
+def test_dense_cluster_grows_cell_capacity(gpu_lib, kernel):
     """All particles in one corner of a large box: cells overflow their first capacity, the
     library grows it and replays; results must still match the oracle."""
     xc, Lc = md_inputs.fcc_jitter(400, 1.0, 0.05, 77)
@@ -180,10 +184,25 @@ def test_dense_cluster_grows_cell_capacity(gpu_lib):
     x = xc + 1.0
     f3r, _, _, cnt = oracle.atm_brute(x, L, NU, 2.5)
     f2r, _, _ = oracle.lj_brute(x, L, 1.0, 1.0, 2.5)
-    with gpu_lib.System.create(x, L, None, precision=0, nu=NU) as s:
+    with gpu_lib.System.create(x, L, None, precision=0, nu=NU, atm_kernel=kernel) as s:
         f2, f3 = s.forces()
         assert s.stats()["triplets_last"] == cnt
     assert force_err(f2, f2r) <= 1e-5 and force_err(f3, f3r) <= 1e-5
+
+
+def test_long_half_lists_fall_back_to_the_cell_kernel(gpu_lib):
+    """At density 1.8 about 250 of 1500 particles have more than 64 neighbours within r_c = 2.5
+    on their side, more than the rotation kernel's half list holds: the call is replayed with
+    the cell kernel and the results still match the oracle."""
+    x, L = md_inputs.fcc_jitter(1500, 1.8, 0.02, 91)
+    f3r, u3r, _, cnt = oracle.atm_brute(x, L, NU, 2.5)
+    with gpu_lib.System.create(x, L, None, precision=0, nu=NU, skin=0.1, atm_kernel=2) as s:
+        _, f3 = s.forces()
+        assert s.stats()["triplets_last"] == cnt
+        assert s.stats()["atm_kernel"] == 0
+        s.step(1, 2, 0.001)
+        assert s.stats()["atm_kernel"] == 0
+    assert force_err(f3, f3r) <= 1e-5
 
 
 def test_errors_are_reported(gpu_lib, cfg1):
@@ -234,11 +253,12 @@ def test_momentum_and_energy_conservation(gpu_lib, cfg1, prec, ptol):
     assert abs(e1 - e0) / (ek0 + abs(u20) + abs(u30)) < 5e-3  # truncated potentials: bounded jumps only
 
 
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 2])
 @pytest.mark.parametrize("prec", [0, 1])
 def test_both_triplet_kernels_match_oracle(gpu_lib, cfg1, cfg1_ref, variant, prec):
-    """Cell kernel with Newton-3 scatter (0) and per-particle kernel (1): same forces, energy
-    and interacting-triplet count as the oracle, at x0 and after a few outer steps."""
+    """Cell kernel with Newton-3 scatter (0), per-particle kernel (1) and rotation kernel (2):
+    same forces, energy and interacting-triplet count as the oracle, at x0 and after a few
+    outer steps."""
     r3 = gpu_lib
     with make(r3, cfg1, prec) as s:
         r3.md_set_atm_kernel(s.handle, variant)
