@@ -161,6 +161,7 @@ void choose_grid(md_system* s) {
   double nl = rho * 4.18879020478639 * rl * rl * rl;
   if (s->maxnb == 0) s->maxnb = std::max(32, (int)ceil(1.35 * nl + 24.0));
   s->maxnb = std::min(s->maxnb, (int)s->n);
+  s->maxnb = (s->maxnb + 3) & ~3;  // rows start on 16-byte boundaries (bulk row copies)
 }
 
 size_t arena_bytes(const md_system* s);
@@ -181,6 +182,7 @@ md_status alloc_device(md_system* s) {
   size_t o_nbr = a.reserve(4 * (size_t)s->maxnb * n), o_nbc = a.reserve(4 * n);
   size_t o_part = a.reserve(tsz * 27 * 3 * n);
   size_t o_f3a = a.reserve(4 * tsz * n);
+  size_t o_ipos = a.reserve(16 * n);
   size_t o_acc = a.reserve(8 * ACC_N), o_ctr = a.reserve(8 * CTR_N), o_flg = a.reserve(4 * FLG_N);
   size_t o_sx = a.reserve(24 * n), o_sv = a.reserve(24 * n), o_sf2 = a.reserve(24 * n), o_sf3 = a.reserve(24 * n);
   size_t o_sid = a.reserve(4 * n), o_scell = a.reserve(4 * n);
@@ -216,6 +218,7 @@ md_status alloc_device(md_system* s) {
   h.nbr_cnt = (int*)(m + o_nbc);
   h.partial = m + o_part;
   h.f3acc = m + o_f3a;
+  h.ipos = (int4*)(m + o_ipos);
   h.acc = (double*)(m + o_acc);
   h.ctr = (unsigned long long*)(m + o_ctr);
   h.flags = (int*)(m + o_flg);
@@ -261,6 +264,7 @@ size_t arena_bytes(const md_system* s0) {
   a.reserve(4 * n);
   a.reserve(tsz * 27 * 3 * n);
   a.reserve(4 * tsz * n);
+  a.reserve(16 * n);
   a.reserve(8 * ACC_N);
   a.reserve(8 * CTR_N);
   a.reserve(4 * FLG_N);
@@ -278,6 +282,7 @@ md_status upload_desc(md_system* s, double dt_in, double dt_out) {
   h.half_L = 0.5 * s->L;
   h.edge = s->edge;
   h.inv_edge = 1.0 / s->edge;
+  h.qinv = 4294967296.0 / s->L;
   h.nc = s->nc;
   h.ncell = s->ncell;
   h.n = (int)s->n;
@@ -319,6 +324,7 @@ md_status upload_desc(md_system* s, double dt_in, double dt_out) {
     h.f_nu = (float)h.nu;
     h.f_reach2 = (float)(r * r);
     h.f_half_skin_sq = (float)h.half_skin_sq;
+    h.f_qscale = (float)(s->L / 4294967296.0);
   }
   CK(cudaMemcpyAsync(s->d_sys, &h, sizeof(SysDev), cudaMemcpyHostToDevice, s->stream));
   return MD_OK;
@@ -340,7 +346,7 @@ PItem* pitems_for(md_system* s, int tag, int mode, int buf) {
   std::vector<PItem> v;
   const int per = (tag == T_LJ)      ? kBlock / kLjTeam
                   : (tag == T_ATMPA)  ? kPaPerBlock
-                  : (tag == T_ATMROT) ? rot_warps(s->precision)
+                  : (tag == T_ATMROT) ? rot_bases_per_item(s->precision)
                                       : kBlock;
   const int nb = (tag == T_LJ)       ? s->nblocks_lj
                  : (tag == T_ATMPA)  ? s->nblocks_pa
@@ -370,7 +376,7 @@ md_status prepare_items(md_system* s) {
   const int per_lj = kBlock / kLjTeam;
   s->nblocks_lj = (int)((s->n + per_lj - 1) / per_lj);
   s->nblocks_pa = (int)((s->n + kPaPerBlock - 1) / kPaPerBlock);
-  s->nblocks_rot = (int)((s->n + rot_warps(s->precision) - 1) / rot_warps(s->precision));
+  s->nblocks_rot = (int)((s->n + rot_bases_per_item(s->precision) - 1) / rot_bases_per_item(s->precision));
   for (int b = 0; b < 2; ++b) {
     pitems_for(s, T_BIN, 0, b);
     pitems_for(s, T_SCATTER, 0, b);
@@ -1370,7 +1376,7 @@ md_status batch_build(md_batch* b) {
       }
       ti.nlj = (int)(pit.size() - ti.lj);
       if (b->variant >= 1) {
-        const int per = (b->variant == 1) ? kPaPerBlock : rot_warps(b->precision);
+        const int per = (b->variant == 1) ? kPaPerBlock : rot_bases_per_item(b->precision);
         ti.atm = pit.size();
         for (int j = 0; j < ns; ++j) {
           const Request& r = b->req[b->resident[j]];

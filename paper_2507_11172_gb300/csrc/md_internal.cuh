@@ -39,6 +39,7 @@ enum : int { FLG_ERR = 0, FLG_SKIN = 1, FLG_MAXCELL = 2, FLG_N = 4 };
 struct SysDev {
   // geometry
   double L, half_L, edge, inv_edge;
+  double qinv;  // 2^32 / L: fixed-point position units per length unit
   int nc, ncell, n, cap_cell;
   // potentials (squared cutoffs computed on the host as rc * rc)
   double eps, sig2, rc2, rc2sq, rlistsq, nu, rc3, rc3sq, half_skin_sq;
@@ -49,7 +50,7 @@ struct SysDev {
   // FP32 copies of the parameters used by the FP32 kernels, computed on the host (on GB300 an
   // FP64 conversion in every thread costs as much as a pair evaluation)
   float f_edge, f_edge_lo, f_half_edge, f_rc2sq, f_guard2, f_sig2, f_eps24, f_eps4;
-  float f_rc3sq, f_guard3, f_nu, f_reach2, f_half_skin_sq, f_pad_;
+  float f_rc3sq, f_guard3, f_nu, f_reach2, f_half_skin_sq, f_qscale;  // f_qscale = L / 2^32
   int precision;  // 0 = FP32 forces, 1 = FP64
   int pad_;
   // state in cell-sorted order, double SoA [3][n] (x block, y block, z block)
@@ -65,6 +66,8 @@ struct SysDev {
   int *count, *cell_start;    // [ncell], [ncell + 1]
   int *nbr, *nbr_cnt;         // [n][maxnb] row-major, [n]
   void *partial;              // T [27][3][n] per-stencil-slot ATM partial forces
+  int4 *ipos;                 // [n] FP32 mode: positions of the last binning in fixed point (box = 2^32
+                              // units; x, y, z as wrapping 32-bit integers), NULL where unused
   void *f3acc;                // [n] float4 (FP32) or double [n][4]: rotation-kernel ATM force sums,
                               // zero between evaluations (the combine kernel clears what it reads)
   double *acc;                // [ACC_N]
@@ -277,9 +280,9 @@ int atm_configure(int smax, int precision, int* smem_bytes);
 // per-particle ATM variant: items of 4 particles (one warp each)
 template <typename T> void launch_atm_pa(const Launch& L, const PItem* items, int nitems);
 constexpr int kPaPerBlock = 4;
-// rotation variant: items of rot_warps(precision) particles (one warp each)
+// rotation variant: items of rot_bases_per_item(precision) particles (4 warps of 8 particles each)
 template <typename T> void launch_atm_rot(const Launch& L, const PItem* items, int nitems);
-constexpr int rot_warps(int precision) { return precision ? 4 : 8; }
+constexpr int rot_bases_per_item(int) { return 32; }
 template <typename T>
 void launch_atm_table(const Launch& L, const CItem* items, int nitems, int grid, int smax, const uint16_t* table);
 template <typename T> void launch_combine(const Launch& L, const PItem* items, int nitems, int block);

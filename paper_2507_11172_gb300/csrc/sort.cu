@@ -124,6 +124,14 @@ __global__ void k_scatter(const SysDev* __restrict__ sys, const PItem* __restric
   reinterpret_cast<T4*>(S.pos[it.buf])[q] = h;
   reinterpret_cast<T4*>(S.poslo)[q] = l;
   reinterpret_cast<T4*>(S.ref)[q] = h;
+  if (sizeof(T) == 4 && S.ipos) {  // fixed point: the 64-bit rounding wraps modulo 2^32 for any x
+    int4 iq;
+    iq.x = (int)(unsigned)(unsigned long long)__double2ll_rn(X[p] * S.qinv);
+    iq.y = (int)(unsigned)(unsigned long long)__double2ll_rn(X[n + p] * S.qinv);
+    iq.z = (int)(unsigned)(unsigned long long)__double2ll_rn(X[2 * n + p] * S.qinv);
+    iq.w = 0;
+    S.ipos[q] = iq;
+  }
 }
 
 // Pair list with skin, one CTA per cell b: the 27 cells around b are staged in

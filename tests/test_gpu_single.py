@@ -191,10 +191,12 @@ def test_dense_cluster_grows_cell_capacity(gpu_lib, kernel):
 
 
 def test_long_half_lists_fall_back_to_the_cell_kernel(gpu_lib):
-    """At density 1.8 about 250 of 1500 particles have more than 64 neighbours within r_c = 2.5
-    on their side, more than the rotation kernel's half list holds: the call is replayed with
-    the cell kernel and the results still match the oracle."""
-    x, L = md_inputs.fcc_jitter(1500, 1.8, 0.02, 91)
+    """At density 1.7 some of 1500 particles have more than 64 neighbours within r_c = 2.5 on
+    their side, more than the rotation kernel's half list holds: the call is replayed with the
+    cell kernel and the results still match the oracle.  (At most 122 neighbours in all, so
+    even a particle of the cell kernel's first cell, which sees every neighbour as following
+    it, stays within that kernel's 128-entry list.)"""
+    x, L = md_inputs.fcc_jitter(1500, 1.7, 0.02, 91)
     f3r, u3r, _, cnt = oracle.atm_brute(x, L, NU, 2.5)
     with gpu_lib.System.create(x, L, None, precision=0, nu=NU, skin=0.1, atm_kernel=2) as s:
         _, f3 = s.forces()
