@@ -1053,12 +1053,13 @@ __device__ __forceinline__ double rsqrt_newton(double q) { return 1.0 / sqrt(q);
 // Scalar core of one triplet.  With w = 1/(abc), t5 = (abc)^(-5/2), P = (a + b - c)(a - b + c)
 // (-a + b + c) = 8 abc cos(g1) cos(g2) cos(g3) and P_a = dP/da = 2a(-a + b + c) - (a + b - c)(a - b + c):
 //   phi = nu t5 (abc + 3/8 P),  2 dphi/da = 3/4 nu t5 (P_a - bc (4 + 5/2 P w)),  likewise for b, c.
-// Returns the three edge weights pa2 = 2 dphi/da, pb2, pc2 (zero unless ok) and, with kE, phi.
+// Returns the three edge weights pa2 = 2 dphi/da, pb2, pc2 and, with kE, phi, all times the mask
+// okf (1 or 0).  abc must be positive and moderate (masked-off lanes pass a large finite c).
 template <typename T, bool kE>
 __device__ __forceinline__ void atm_weights(const T a, const T a2, const T b, const T c, const T nu,
-                                            const T nu075, const bool ok, T& pa2, T& pb2, T& pc2, T& u) {
+                                            const T nu075, const T okf, T& pa2, T& pb2, T& pc2, T& u) {
   const T ab = a * b;
-  const T q = ok ? ab * c : (T)1;
+  const T q = ab * c;
   const T t = rsqrt_newton(q);
   const T w = t * t;    // 1 / (abc)
   const T t3 = w * t;   // (abc)^(-3/2)
@@ -1070,11 +1071,11 @@ __device__ __forceinline__ void atm_weights(const T a, const T a2, const T b, co
   const T Pa = fma(a2, C, -AB), Pb = fma(b + b, B, -AC), Pc = fma(c + c, A, -BC);
   const T Pw = P * w;
   const T H4 = fma((T)2.5, Pw, (T)4);
-  const T kk = ok ? nu075 * t5 : (T)0;
+  const T kk = (nu075 * t5) * okf;
   pa2 = kk * fma(-(b * c), H4, Pa);
   pb2 = kk * fma(-(a * c), H4, Pb);
   pc2 = kk * fma(-ab, H4, Pc);
-  if (kE) u = ok ? nu * t3 * ((T)1 + (T)0.375 * Pw) : (T)0;
+  if (kE) u = (nu * t3 * fma((T)0.375, Pw, (T)1)) * okf;
 }
 
 // displacement x_j - x_i in the kernel's precision.  FP32: from the fixed-point positions of the
@@ -1229,35 +1230,50 @@ __device__ __forceinline__ bool atm_rotate(const SysDev& S, const double* __rest
     a2[h] = dj[h].w + dj[h].w;
     Wj[h] = gx[h] = gy[h] = gz[h] = (T)0;
   }
-  T uu = (T)0;
+  T uu = (T)0, cntf = (T)0;
   T dmin = (T)1e30;  // smallest |c - r_c^2| met: the guard band is checked once per base
-  unsigned cnt = 0;
+  // Lanes that take no part in a step get a large finite offset added to c: the pair then fails
+  // the cutoff and every intermediate stays finite.  offF: the full steps (lanes v < m); offH: the
+  // last step of an even m (pairs (v, v + m/2), lanes v < m/2).
   const int smax = m >> 1;
+  const bool even = (m & 1) == 0;
+  const int sfull = even ? smax - 1 : smax;
+  const T off = (T)64 * hi;
+  T offF[VL], offH[VL];
+#pragma unroll
+  for (int h = 0; h < VL; ++h) {
+    const int v = lane + 32 * h;
+    offF[h] = v < m ? (T)0 : off;
+    offH[h] = v < smax ? (T)0 : off;
+  }
   // step s with q = base + lane + s: lane v's partner is q[32 h] (neighbour (v + s) mod m)
-  auto step = [&](T4* const q, const int s, const int par) {
-    const int lim = (s + s == m) ? s : m;  // last step of an even m: only the pairs (v, v + m/2)
+  auto step = [&](T4* const q, const int par, const T (&offs)[VL]) {
 #pragma unroll
     for (int h = 0; h < VL; ++h) {
-      const int v = lane + 32 * h;
       const T4 dk = q[32 * h];
       const T ex = dk.x - dj[h].x, ey = dk.y - dj[h].y, ez = dk.z - dj[h].z;
-      const T c = fma(ez, ez, fma(ey, ey, ex * ex));
-      bool ok = v < lim && c <= hi;
+      const T c = fma(ez, ez, fma(ey, ey, ex * ex)) + offs[h];
+      T okf;
       if constexpr (kExact) {
+        bool ok = c <= hi;
         const bool band = ok && c >= lo;
         if (__any_sync(0xffffffffu, band)) {
           if (band) {
             atomicAdd(&S.ctr[CTR_GUARD], 1ull);
+            const int v = lane + 32 * h;
+            const int s = (int)(q - base) - lane;
             const int pk = (v + s < m) ? v + s : v + s - m;
             ok = exact_within(X, S.n, w.nidx[v], w.nidx[pk], S.L, S.rc3sq);
           }
         }
+        okf = ok ? (T)1 : (T)0;
       } else {
+        okf = c <= hi ? (T)1 : (T)0;
         dmin = min(dmin, abs(c - rcsq));
       }
       T pa2, pb2, pc2, u = (T)0;
-      atm_weights<T, kE>(dj[h].w, a2[h], dk.w, c, nu, nu075, ok, pa2, pb2, pc2, u);
-      cnt += ok ? 1u : 0u;
+      atm_weights<T, kE>(dj[h].w, a2[h], dk.w, c, nu, nu075, okf, pa2, pb2, pc2, u);
+      cntf += okf;
       if (kE) uu += u;
       Wj[h] += pa2;
       gx[h] = fma(pc2, ex, gx[h]);
@@ -1276,14 +1292,18 @@ __device__ __forceinline__ bool atm_rotate(const SysDev& S, const double* __rest
   // writes are distinct), steps two apart may write the same slot from different lanes
   int s = 1;
 #pragma unroll 1
-  for (; s + 1 <= smax; s += 2) {
+  for (; s + 1 <= sfull; s += 2) {
     T4* const q = base + lane + s;
-    step(q, s, 0);
-    step(q + 1, s + 1, 1);
+    step(q, 0, offF);
+    step(q + 1, 1, offF);
     __syncwarp();
   }
-  if (s <= smax) {
-    step(base + lane + s, s, 0);
+  if (s <= sfull) {
+    step(base + lane + s, 0, offF);
+    __syncwarp();
+  }
+  if (even) {
+    step(base + lane + smax, 1, offH);
     __syncwarp();
   }
   if constexpr (!kExact) {
@@ -1315,7 +1335,7 @@ __device__ __forceinline__ bool atm_rotate(const SysDev& S, const double* __rest
     }
   }
   o.u += uu;
-  o.cnt += cnt;
+  o.cnt += (unsigned)cntf;
   return true;
 }
 
