@@ -1022,562 +1022,6 @@ __global__ void __launch_bounds__(32 * kPaWarps)
   }
 }
 
-// ============================================================== rotation triplet kernel
-// One warp per base particle i.  Its half list holds the neighbours j within r_c3 that follow i in
-// the order (cell offset from i's cell, lexicographic in z, y, x; then sorted index), so that every
-// triplet is owned by exactly one member, its first one in that order (Newton 3: each triplet is
-// evaluated once).  Virtual lane v (lane + 32 h) holds neighbour v.  Step s of a cyclic rotation
-// pairs v with (v + s) mod m; steps 1 .. floor(m / 2) visit every unordered neighbour pair once.
-// The forces are kept as edge weights: with d_j = x_j - x_i, d_k = x_k - x_i, e = d_k - d_j and
-// pa2 = 2 dphi/da, pb2 = 2 dphi/db, pc2 = 2 dphi/dc (a, b, c the squared lengths of d_j, d_k, e),
-//   F_i = pa2 d_j + pb2 d_k,  F_j = -pa2 d_j + pc2 e,  F_k = -pb2 d_k - pc2 e,
-// so neighbour v accumulates one scalar W_v (its i-edge weight) and one vector G_v (its j-k edges):
-// F_v = G_v - W_v d_v and F_i = sum_v W_v d_v.  The lane of j keeps j's share in registers; k's
-// share goes to k's shared-memory slot, written by exactly one lane per step (the rotation is a
-// permutation), with a warp barrier between steps.  Per-(i, neighbour) totals are added to the
-// neighbour's force with one vector atomic; the combine kernel reads and clears them.
-constexpr int kRotMax = 64;     // neighbours in one half list (longer lists: the cell kernel)
-constexpr int kRotRow = 128;    // pair-list entries of a base prefetched into shared memory
-constexpr int kRotCand = 64;    // following neighbours of a base whose positions are prefetched
-constexpr int kRotPerWarp = 8;  // bases per warp in one work item (one software pipeline)
-
-// FP32 reciprocal square root: the hardware approximation (flush-to-zero form; the argument is a
-// product of squared distances, never subnormal) refined by one Newton step
-__device__ __forceinline__ float rsqrt_newton(float q) {
-  float t;
-  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(t) : "f"(q));
-  return t * fmaf(-0.5f * q, t * t, 1.5f);
-}
-__device__ __forceinline__ double rsqrt_newton(double q) { return 1.0 / sqrt(q); }
-
-// Scalar core of one triplet.  With w = 1/(abc), t5 = (abc)^(-5/2), P = (a + b - c)(a - b + c)
-// (-a + b + c) = 8 abc cos(g1) cos(g2) cos(g3) and P_a = dP/da = 2a(-a + b + c) - (a + b - c)(a - b + c):
-//   phi = nu t5 (abc + 3/8 P),  2 dphi/da = 3/4 nu t5 (P_a - bc (4 + 5/2 P w)),  likewise for b, c.
-// Returns the three edge weights pa2 = 2 dphi/da, pb2, pc2 and, with kE, phi, all times the mask
-// okf (1 or 0).  abc must be positive and moderate (masked-off lanes pass a large finite c).
-template <typename T, bool kE>
-__device__ __forceinline__ void atm_weights(const T a, const T a2, const T b, const T c, const T nu,
-                                            const T nu075, const T okf, T& pa2, T& pb2, T& pc2, T& u) {
-  const T ab = a * b;
-  const T q = ab * c;
-  const T t = rsqrt_newton(q);
-  const T w = t * t;    // 1 / (abc)
-  const T t3 = w * t;   // (abc)^(-3/2)
-  const T t5 = t3 * w;  // (abc)^(-5/2)
-  const T s = a + b + c;
-  const T A = fma((T)-2, c, s), B = fma((T)-2, b, s), C = fma((T)-2, a, s);
-  const T AB = A * B, AC = A * C, BC = B * C;
-  const T P = AB * C;
-  const T Pa = fma(a2, C, -AB), Pb = fma(b + b, B, -AC), Pc = fma(c + c, A, -BC);
-  const T Pw = P * w;
-  const T H4 = fma((T)2.5, Pw, (T)4);
-  const T kk = (nu075 * t5) * okf;
-  pa2 = kk * fma(-(b * c), H4, Pa);
-  pb2 = kk * fma(-(a * c), H4, Pb);
-  pc2 = kk * fma(-ab, H4, Pc);
-  if (kE) u = (nu * t3 * fma((T)0.375, Pw, (T)1)) * okf;
-}
-
-// displacement x_j - x_i in the kernel's precision.  FP32: from the fixed-point positions of the
-// last binning (box = 2^32 units; the 32-bit wrap-around difference is the minimum image), one
-// rounding to FP32 and one scaling.  FP64: cell-local coordinates plus the cell offset.
-template <typename T> struct Disp;
-template <> struct Disp<float> {
-  using Nb = int4;
-  static constexpr int kChunks = 1;  // 16-byte copies per neighbour position
-  int4 qi;
-  float scale;
-  __device__ __forceinline__ void init(const SysDev& S, const Nb& self) {
-    qi = self;
-    scale = S.f_qscale;
-  }
-  static __device__ __forceinline__ const void* src(const SysDev& S, int, int j) { return S.ipos + j; }
-  __device__ __forceinline__ void get(const SysDev&, const Nb& b, unsigned, float& dx, float& dy, float& dz) const {
-    dx = (float)(int)((unsigned)b.x - (unsigned)qi.x) * scale;
-    dy = (float)(int)((unsigned)b.y - (unsigned)qi.y) * scale;
-    dz = (float)(int)((unsigned)b.z - (unsigned)qi.z) * scale;
-  }
-};
-template <> struct Disp<double> {
-  using Nb = double4_32a;
-  static constexpr int kChunks = 2;
-  double4_32a pi;
-  __device__ __forceinline__ void init(const SysDev&, const Nb& self) { pi = self; }
-  static __device__ __forceinline__ const void* src(const SysDev& S, int buf, int j) {
-    return reinterpret_cast<const double4_32a*>(S.pos[buf]) + j;
-  }
-  __device__ __forceinline__ void get(const SysDev& S, const Nb& b, unsigned cde, double& dx, double& dy,
-                                      double& dz) const {
-    const double ox = (double)(int)(cde & 3u) - 1.0, oy = (double)(int)((cde >> 2) & 3u) - 1.0,
-                 oz = (double)(int)(cde >> 4) - 1.0;
-    dx = (b.x - pi.x) + ox * S.edge;
-    dy = (b.y - pi.y) + oy * S.edge;
-    dz = (b.z - pi.z) + oz * S.edge;
-  }
-};
-
-// asynchronous global -> shared copies (completed in commit-group order)
-__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)),
-               "l"(__cvta_generic_to_global(src))
-               : "memory");
-}
-__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(dst)), "l"(__cvta_generic_to_global(src))
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
-template <typename T> struct RotCfg { static constexpr int warps = 4; };
-
-// shared memory of one warp.  The half list is stored twice in a row (nd[v + m] = nd[v]) so that
-// the partner of lane v in step s is entry v + s without a wrap-around; partner shares go to slot
-// v + s likewise, and neighbour v's total is the sum of its slots v and v + m.  nd, sacc[0] and
-// sacc[1] lie at fixed distances, so one address register per lane serves all three.
-template <typename T>
-struct RotSmem {
-  using T4 = typename V4<T>::type;
-  T4 nd[2 * kRotMax];       // half list: d_v (x, y, z) and |d_v|^2, twice
-  T4 sacc[2][2 * kRotMax];  // partner shares (G_v, W_v) of odd and even rotation steps
-  typename Disp<T>::Nb pos[kRotCand];  // prefetched positions of the next base's following neighbours
-  typename Disp<T>::Nb self;           // and its own position
-  unsigned cand[kRotCand];             // their pair-list entries
-  unsigned row[2][kRotRow];            // prefetched pair-list rows of the next two bases
-  int nidx[kRotMax];
-  int cnt[2];
-  int ncand, pad_;
-};
-template <typename T>
-constexpr size_t rot_smem_bytes() {
-  return sizeof(RotSmem<T>) * RotCfg<T>::warps;
-}
-
-// Per-warp outputs of one base particle's rotation.
-template <typename T>
-struct RotOut {
-  T fix, fiy, fiz, u;
-  unsigned cnt;
-};
-
-constexpr unsigned kCentre = (1u << 4) | (1u << 2) | 1u;  // pair-list code of the cell offset (0, 0, 0)
-// j follows x in the order (cell offset from x's cell, lexicographic in z, y, x; sorted index)
-__device__ __forceinline__ bool follows(unsigned e, int x) {
-  const unsigned cde = e >> kNbrShift;
-  return cde > kCentre || (cde == kCentre && (int)(e & kNbrMask) > x);
-}
-
-// stage 1 of the pipeline: pair-list row and its length of base x -> shared memory
-template <typename T>
-__device__ __forceinline__ void rot_fetch_row(const SysDev& S, RotSmem<T>& w, int slot, int x, int lane) {
-  const unsigned* row = reinterpret_cast<const unsigned*>(S.nbr) + (size_t)x * S.maxnb;
-  const int lim = min(S.maxnb, kRotRow);  // maxnb is a multiple of 4: 16-byte pieces stay in the row
-  if (4 * lane < lim) cp_async16(&w.row[slot][4 * lane], row + 4 * lane);
-  if (lane == 0) cp_async4(&w.cnt[slot], S.nbr_cnt + x);
-}
-// stage 2: the following neighbours in the row (row already in shared memory), compacted, and
-// their positions.  ncand may exceed kRotCand, or the list kRotRow: the build then reads the row.
-template <typename T>
-__device__ __forceinline__ void rot_fetch_pos(const SysDev& S, RotSmem<T>& w, int slot, int buf, int x, int lane) {
-  if (lane < Disp<T>::kChunks)
-    cp_async16(reinterpret_cast<char*>(&w.self) + 16 * lane,
-               reinterpret_cast<const char*>(Disp<T>::src(S, buf, x)) + 16 * lane);
-  const unsigned lt = (1u << lane) - 1u;
-  const int c = min(w.cnt[slot], kRotRow);
-  int nc = 0;
-#pragma unroll
-  for (int u = 0; u < kRotRow / 32; ++u) {
-    const int t = lane + 32 * u;
-    const unsigned e = t < c ? w.row[slot][t] : 0u;
-    const bool cand = t < c && follows(e, x);
-    const unsigned bal = __ballot_sync(0xffffffffu, cand);
-    const int pos = nc + __popc(bal & lt);
-    if (cand && pos < kRotCand) {
-      w.cand[pos] = e;
-      const char* src = reinterpret_cast<const char*>(Disp<T>::src(S, buf, (int)(e & kNbrMask)));
-      char* dst = reinterpret_cast<char*>(&w.pos[pos]);
-#pragma unroll
-      for (int q = 0; q < Disp<T>::kChunks; ++q) cp_async16(dst + 16 * q, src + 16 * q);
-    }
-    nc += __popc(bal);
-  }
-  if (lane == 0) w.ncand = (w.cnt[slot] > kRotRow) ? kRotCand + 1 : nc;
-}
-
-// the rotation over one half list of m <= 32 VL neighbours (nd doubled, slots 0 .. 2m-1 zeroed).
-// kExact = false: cutoff decisions in FP32; returns false, having added nothing anywhere, when
-// some pair fell in the guard band around r_c^2 (the caller then repeats with kExact = true, which
-// decides those pairs in FP64 with the oracle's operation order).  On success the per-neighbour
-// force sums are added to the neighbours' accumulators and F_i, the energy and the count to o.
-template <typename T, int VL, bool kE, bool kExact>
-__device__ __forceinline__ bool atm_rotate(const SysDev& S, const double* __restrict__ X, RotSmem<T>& w, const int m,
-                                           const int lane, RotOut<T>& o) {
-  using T4 = typename V4<T>::type;
-  constexpr int kSlot = 2 * kRotMax;  // entries of nd and of each slot array; nd, sacc[0], sacc[1] are adjacent
-  const T rcsq = Par<T>::rc3sq(S), g3 = Par<T>::guard3(S), nu = Par<T>::nu(S);
-  const T nu075 = (T)0.75 * nu;
-  const T hi = rcsq + g3, lo = rcsq - g3;
-  T4* const base = w.nd;  // flat view: nd[i] = base[i], sacc[par][i] = base[kSlot (1 + par) + i]
-  T4 dj[VL];
-  T a2[VL], Wj[VL], gx[VL], gy[VL], gz[VL];
-#pragma unroll
-  for (int h = 0; h < VL; ++h) {
-    dj[h] = base[lane + 32 * h];
-    a2[h] = dj[h].w + dj[h].w;
-    Wj[h] = gx[h] = gy[h] = gz[h] = (T)0;
-  }
-  T uu = (T)0, cntf = (T)0;
-  T dmin = (T)1e30;  // smallest |c - r_c^2| met: the guard band is checked once per base
-  // Lanes that take no part in a step get a large finite offset added to c: the pair then fails
-  // the cutoff and every intermediate stays finite.  offF: the full steps (lanes v < m); offH: the
-  // last step of an even m (pairs (v, v + m/2), lanes v < m/2).
-  const int smax = m >> 1;
-  const bool even = (m & 1) == 0;
-  const int sfull = even ? smax - 1 : smax;
-  const T off = (T)64 * hi;
-  T offF[VL], offH[VL];
-#pragma unroll
-  for (int h = 0; h < VL; ++h) {
-    const int v = lane + 32 * h;
-    offF[h] = v < m ? (T)0 : off;
-    offH[h] = v < smax ? (T)0 : off;
-  }
-  // step s with q = base + lane + s: lane v's partner is q[32 h] (neighbour (v + s) mod m)
-  auto step = [&](T4* const q, const int par, const T (&offs)[VL]) {
-#pragma unroll
-    for (int h = 0; h < VL; ++h) {
-      const T4 dk = q[32 * h];
-      const T ex = dk.x - dj[h].x, ey = dk.y - dj[h].y, ez = dk.z - dj[h].z;
-      const T c = fma(ez, ez, fma(ey, ey, ex * ex)) + offs[h];
-      T okf;
-      if constexpr (kExact) {
-        bool ok = c <= hi;
-        const bool band = ok && c >= lo;
-        if (__any_sync(0xffffffffu, band)) {
-          if (band) {
-            atomicAdd(&S.ctr[CTR_GUARD], 1ull);
-            const int v = lane + 32 * h;
-            const int s = (int)(q - base) - lane;
-            const int pk = (v + s < m) ? v + s : v + s - m;
-            ok = exact_within(X, S.n, w.nidx[v], w.nidx[pk], S.L, S.rc3sq);
-          }
-        }
-        okf = ok ? (T)1 : (T)0;
-      } else {
-        okf = c <= hi ? (T)1 : (T)0;
-        dmin = min(dmin, abs(c - rcsq));
-      }
-      T pa2, pb2, pc2, u = (T)0;
-      atm_weights<T, kE>(dj[h].w, a2[h], dk.w, c, nu, nu075, okf, pa2, pb2, pc2, u);
-      cntf += okf;
-      if (kE) uu += u;
-      Wj[h] += pa2;
-      gx[h] = fma(pc2, ex, gx[h]);
-      gy[h] = fma(pc2, ey, gy[h]);
-      gz[h] = fma(pc2, ez, gz[h]);
-      T4* const sl = q + kSlot * (1 + par) + 32 * h;
-      T4 a = *sl;
-      a.x = fma(-pc2, ex, a.x);
-      a.y = fma(-pc2, ey, a.y);
-      a.z = fma(-pc2, ez, a.z);
-      a.w += pb2;
-      *sl = a;
-    }
-  };
-  // two steps per warp barrier: consecutive steps write different slot arrays (each step's slot
-  // writes are distinct), steps two apart may write the same slot from different lanes
-  int s = 1;
-#pragma unroll 1
-  for (; s + 1 <= sfull; s += 2) {
-    T4* const q = base + lane + s;
-    step(q, 0, offF);
-    step(q + 1, 1, offF);
-    __syncwarp();
-  }
-  if (s <= sfull) {
-    step(base + lane + s, 0, offF);
-    __syncwarp();
-  }
-  if (even) {
-    step(base + lane + smax, 1, offH);
-    __syncwarp();
-  }
-  if constexpr (!kExact) {
-    if (__any_sync(0xffffffffu, dmin <= g3)) return false;
-  }
-#pragma unroll
-  for (int h = 0; h < VL; ++h) {
-    const int v = lane + 32 * h;
-    if (v < m) {
-      const T4 a0 = base[kSlot + v], a1 = base[2 * kSlot + v];
-      const T4 b0 = base[kSlot + v + m], b1 = base[2 * kSlot + v + m];
-      const T W = Wj[h] + ((a0.w + a1.w) + (b0.w + b1.w));
-      const T Gx = gx[h] + ((a0.x + a1.x) + (b0.x + b1.x));
-      const T Gy = gy[h] + ((a0.y + a1.y) + (b0.y + b1.y));
-      const T Gz = gz[h] + ((a0.z + a1.z) + (b0.z + b1.z));
-      o.fix = fma(W, dj[h].x, o.fix);
-      o.fiy = fma(W, dj[h].y, o.fiy);
-      o.fiz = fma(W, dj[h].z, o.fiz);
-      const T Fx = fma(-W, dj[h].x, Gx), Fy = fma(-W, dj[h].y, Gy), Fz = fma(-W, dj[h].z, Gz);
-      const int j = w.nidx[v];
-      if constexpr (sizeof(T) == 4) {
-        atomicAdd(reinterpret_cast<float4*>(S.f3acc) + j, make_float4(Fx, Fy, Fz, 0.f));
-      } else {
-        double* qd = reinterpret_cast<double*>(S.f3acc) + 4 * (size_t)j;
-        atomicAdd(qd, Fx);
-        atomicAdd(qd + 1, Fy);
-        atomicAdd(qd + 2, Fz);
-      }
-    }
-  }
-  o.u += uu;
-  o.cnt += (unsigned)cntf;
-  return true;
-}
-
-// zero the slot arrays' entries 0 .. nz-1
-template <typename T>
-__device__ __forceinline__ void rot_zero_slots(RotSmem<T>& w, int nz, int lane) {
-  using T4 = typename V4<T>::type;
-  for (int v = lane; v < nz; v += 32) {
-    T4 z;
-    z.x = z.y = z.z = z.w = (T)0;
-    w.sacc[0][v] = z;
-    w.sacc[1][v] = z;
-  }
-}
-
-// the exact repeat, kept out of line (rare)
-template <typename T, int VL, bool kE>
-__device__ __noinline__ void atm_rotate_exact(const SysDev& S, const double* __restrict__ X, RotSmem<T>& w,
-                                              const int m, const int lane, RotOut<T>& o) {
-  __syncwarp();
-  rot_zero_slots<T>(w, 2 * m, lane);
-  __syncwarp();
-  atm_rotate<T, VL, kE, true>(S, X, w, m, lane, o);
-}
-
-template <typename T, int VL, bool kE>
-__device__ __forceinline__ void atm_rotate_any(const SysDev& S, const double* __restrict__ X, RotSmem<T>& w,
-                                               const int m, const int lane, RotOut<T>& o) {
-  if (!atm_rotate<T, VL, kE, false>(S, X, w, m, lane, o)) atm_rotate_exact<T, VL, kE>(S, X, w, m, lane, o);
-}
-
-// Warp sums of four per-lane values by a transposed butterfly (8 shuffles): afterwards lanes 0-7
-// hold the total of a, lanes 8-15 of b, 16-23 of c, 24-31 of d.
-template <typename T>
-__device__ __forceinline__ T warp_sum4(T a, T b, T c, T d, int lane) {
-  const bool h16 = (lane & 16) != 0;
-  T k0 = h16 ? c : a, k1 = h16 ? d : b;
-  const T s0 = h16 ? a : c, s1 = h16 ? b : d;
-  k0 += __shfl_xor_sync(0xffffffffu, s0, 16);
-  k1 += __shfl_xor_sync(0xffffffffu, s1, 16);
-  const bool h8 = (lane & 8) != 0;
-  T k = h8 ? k1 : k0;
-  const T sk = h8 ? k0 : k1;
-  k += __shfl_xor_sync(0xffffffffu, sk, 8);
-  k += __shfl_xor_sync(0xffffffffu, k, 4);
-  k += __shfl_xor_sync(0xffffffffu, k, 2);
-  k += __shfl_xor_sync(0xffffffffu, k, 1);
-  return k;
-}
-
-// one list entry of base x: is j a following neighbour within r_c3 (guard band decided exactly)?
-template <typename T>
-__device__ __forceinline__ bool rot_entry(const SysDev& S, const double* __restrict__ X, const Disp<T>& D,
-                                          bool cand, unsigned e, const typename Disp<T>::Nb& nb, int x, T& dx, T& dy,
-                                          T& dz) {
-  const T rcsq = Par<T>::rc3sq(S), g3 = Par<T>::guard3(S);
-  bool ok = false, band = false;
-  dx = dy = dz = (T)0;
-  if (cand) {
-    D.get(S, nb, e >> kNbrShift, dx, dy, dz);
-    const T r2 = dx * dx + dy * dy + dz * dz;
-    ok = r2 < rcsq - g3;
-    band = (r2 >= rcsq - g3) && (r2 <= rcsq + g3);
-  }
-  if (__any_sync(0xffffffffu, band)) {
-    if (band) {
-      atomicAdd(&S.ctr[CTR_GUARD], 1ull);
-      ok = exact_within(X, S.n, x, (int)(e & kNbrMask), S.L, S.rc3sq);
-    }
-  }
-  return ok;
-}
-
-template <typename T>
-__device__ __forceinline__ void rot_push(RotSmem<T>& w, int& m, bool ok, int j, T dx, T dy, T dz, unsigned lt) {
-  using T4 = typename V4<T>::type;
-  const unsigned bal = __ballot_sync(0xffffffffu, ok);
-  if (ok) {
-    const int pos = m + __popc(bal & lt);
-    if (pos < kRotMax) {
-      T4 d4;
-      d4.x = dx;
-      d4.y = dy;
-      d4.z = dz;
-      d4.w = dx * dx + dy * dy + dz * dz;
-      w.nd[pos] = d4;
-      w.nidx[pos] = j;
-    }
-  }
-  m += __popc(bal);
-}
-
-// half list of base x from its prefetched row and positions (slot); returns its length m
-template <typename T>
-__device__ __forceinline__ int atm_rot_build(const SysDev& S, RotSmem<T>& w, const int slot, const int buf,
-                                             const int x, const int lane) {
-  using T4 = typename V4<T>::type;
-  const unsigned lt = (1u << lane) - 1u;
-  const double* __restrict__ X = S.X[buf];
-  Disp<T> D;
-  D.init(S, w.self);
-  const int nc = w.ncand;
-  int m = 0;
-  if (nc <= kRotCand) {  // the prefetched candidates are all of them
-#pragma unroll
-    for (int u = 0; u < kRotCand / 32; ++u) {
-      if (32 * u >= nc) break;  // warp-uniform
-      const int t = lane + 32 * u;
-      const bool cand = t < nc;
-      const unsigned e = cand ? w.cand[t] : 0u;
-      typename Disp<T>::Nb nb;
-      if (cand) nb = w.pos[t];
-      T dx, dy, dz;
-      const bool ok = rot_entry<T>(S, X, D, cand, e, nb, x, dx, dy, dz);
-      rot_push<T>(w, m, ok, (int)(e & kNbrMask), dx, dy, dz, lt);
-    }
-  } else {  // dense systems: the whole row from global memory
-    const int cnt_list = w.cnt[slot];
-    const unsigned* row = reinterpret_cast<const unsigned*>(S.nbr) + (size_t)x * S.maxnb;
-    for (int t0 = 0; t0 < cnt_list; t0 += 32) {
-      const int t = t0 + lane;
-      const unsigned e = t < cnt_list ? __ldg(row + t) : 0u;
-      const bool cand = t < cnt_list && follows(e, x);
-      typename Disp<T>::Nb nb;
-      if (cand) nb = *reinterpret_cast<const typename Disp<T>::Nb*>(Disp<T>::src(S, buf, (int)(e & kNbrMask)));
-      T dx, dy, dz;
-      const bool ok = rot_entry<T>(S, X, D, cand, e, nb, x, dx, dy, dz);
-      rot_push<T>(w, m, ok, (int)(e & kNbrMask), dx, dy, dz, lt);
-    }
-  }
-  if (m > kRotMax) {
-    if (lane == 0) atomicOr(&S.flags[FLG_ERR], ERR_HALF_CAP);
-    m = kRotMax;
-  }
-  // the second copy (nd[v + m] = nd[v]) and, up to the last entry any lane reads (lane + 32 (VL - 1)
-  // + m / 2), harmless finite entries; slots 0 .. 2m-1 start at zero
-  __syncwarp();
-  const int nread = (m <= 32 ? 32 : 64) + (m >> 1);
-  for (int v = lane; v < nread; v += 32) {
-    if (v >= m) {
-      T4 d4;
-      if (v < 2 * m) {
-        d4 = w.nd[v - m];
-      } else {
-        d4.x = d4.y = d4.z = (T)0;
-        d4.w = (T)1;
-      }
-      w.nd[v] = d4;
-    }
-  }
-  rot_zero_slots<T>(w, 2 * m, lane);
-  __syncwarp();
-  return m;
-}
-
-// rotation and outputs of base x with its half list of length m
-template <typename T, bool kE>
-__device__ __forceinline__ void atm_rot_eval(const SysDev& S, RotSmem<T>& w, const int buf, const int x,
-                                             const int m, const int lane) {
-  const double* __restrict__ X = S.X[buf];
-  RotOut<T> o{(T)0, (T)0, (T)0, (T)0, 0u};
-  if (m >= 2) {
-    if (m <= 32)
-      atm_rotate_any<T, 1, kE>(S, X, w, m, lane, o);
-    else
-      atm_rotate_any<T, 2, kE>(S, X, w, m, lane, o);
-  }
-  // F_i, the energy and the count: warp sums
-  const unsigned ctot = __reduce_add_sync(0xffffffffu, o.cnt);
-  const T k = warp_sum4<T>(o.fix, o.fiy, o.fiz, kE ? o.u : (T)0, lane);
-  const double F0 = (double)k;
-  const double F1 = (double)__shfl_sync(0xffffffffu, k, 8);
-  const double F2 = (double)__shfl_sync(0xffffffffu, k, 16);
-  const double U = kE ? (double)__shfl_sync(0xffffffffu, k, 24) : 0.0;
-  if (lane == 0) {
-    if constexpr (sizeof(T) == 4) {
-      atomicAdd(reinterpret_cast<float4*>(S.f3acc) + x, make_float4((float)F0, (float)F1, (float)F2, 0.f));
-    } else {
-      double* q = reinterpret_cast<double*>(S.f3acc) + 4 * (size_t)x;
-      atomicAdd(q, F0);
-      atomicAdd(q + 1, F1);
-      atomicAdd(q + 2, F2);
-    }
-    if (ctot) atomicAdd(&S.ctr[CTR_TRIPLETS], (unsigned long long)ctot);
-    if (kE) {
-      atomicAdd(&S.acc[ACC_U3], U);
-      atomicAdd(&S.acc[ACC_W3], 9.0 * U);  // sum_a r_a . F_a = 9 phi (phi is homogeneous of degree -9)
-    }
-  }
-  __syncwarp();  // the next base reuses the half list and the slots
-}
-
-// Work item: bases begin + warp + W k, k < kRotPerWarp.  Per warp a two-stage software pipeline:
-// the pair-list row of base k + 2 and the neighbour positions of base k + 1 are copied into
-// shared memory (cp.async) while base k is evaluated.
-template <typename T>
-__global__ void __launch_bounds__(32 * RotCfg<T>::warps, sizeof(T) == 4 ? 5 : 3)
-    k_atm_rot(const SysDev* __restrict__ sys, const PItem* __restrict__ items) {
-  constexpr int W = RotCfg<T>::warps;
-  extern __shared__ __align__(32) unsigned char rot_raw[];
-  const PItem it = items[blockIdx.x];
-  const SysDev& S = sys[it.sys];
-  const int imode = item_mode(S, it.mode);
-  if (imode & M_SKIP) return;
-  const bool energy = (imode & M_ENERGY) != 0;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  RotSmem<T>& w = reinterpret_cast<RotSmem<T>*>(rot_raw)[warp];
-  const int n = S.n, buf = it.buf;
-  auto base = [&](int k) { return it.begin + warp + W * k; };
-  if (base(0) >= n) return;  // whole warp leaves together
-  rot_fetch_row<T>(S, w, 0, base(0), lane);
-  cp_async_commit();
-  cp_async_wait<0>();
-  __syncwarp();
-  rot_fetch_pos<T>(S, w, 0, buf, base(0), lane);
-  cp_async_commit();
-  if (1 < kRotPerWarp && base(1) < n) rot_fetch_row<T>(S, w, 1, base(1), lane);
-  cp_async_commit();
-  for (int k = 0; k < kRotPerWarp; ++k) {
-    const int x = base(k);
-    if (x >= n) break;
-    const int slot = k & 1;
-    cp_async_wait<1>();  // positions of base k (and every older group) have arrived
-    __syncwarp();
-    const int m = atm_rot_build<T>(S, w, slot, buf, x, lane);
-    // refill the pipeline before the evaluation: positions of base k + 1, row of base k + 2
-    if (k + 1 < kRotPerWarp && base(k + 1) < n) {
-      cp_async_wait<0>();
-      __syncwarp();
-      rot_fetch_pos<T>(S, w, slot ^ 1, buf, base(k + 1), lane);
-    }
-    cp_async_commit();
-    if (k + 2 < kRotPerWarp && base(k + 2) < n) rot_fetch_row<T>(S, w, slot, base(k + 2), lane);
-    cp_async_commit();
-    if (energy)
-      atm_rot_eval<T, true>(S, w, buf, x, m, lane);
-    else
-      atm_rot_eval<T, false>(S, w, buf, x, m, lane);
-  }
-  cp_async_wait<0>();
-}
-
 // ============================================================== combine + outer kicks
 template <typename T>
 __global__ void __launch_bounds__(256) k_combine(const SysDev* __restrict__ sys, const PItem* __restrict__ items) {
@@ -1784,25 +1228,6 @@ template <typename T>
 void launch_atm_pa(const Launch& L, const PItem* items, int nitems) {
   if (nitems > 0) k_atm_pa<T><<<nitems, 32 * kPaWarps, 0, L.stream>>>(L.sys, items, g_table);
 }
-// the rotation kernel's dynamic shared memory (above the 48 KB default): set once per process
-template <typename T>
-static bool rot_configure() {
-  static int done = 0;
-  if (!done) {
-    done = cudaFuncSetAttribute(k_atm_rot<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)rot_smem_bytes<T>()) == cudaSuccess ? 1 : -1;
-  }
-  return done > 0;
-}
-template <typename T>
-void launch_atm_rot(const Launch& L, const PItem* items, int nitems) {
-  static_assert(RotCfg<T>::warps * kRotPerWarp == rot_bases_per_item(sizeof(T) == 8 ? 1 : 0),
-                "items and kernel disagree");
-  if (nitems > 0 && rot_configure<T>())
-    k_atm_rot<T><<<nitems, 32 * RotCfg<T>::warps, rot_smem_bytes<T>(), L.stream>>>(L.sys, items);
-}
-template void launch_atm_rot<float>(const Launch&, const PItem*, int);
-template void launch_atm_rot<double>(const Launch&, const PItem*, int);
 template void launch_atm_pa<float>(const Launch&, const PItem*, int);
 template void launch_atm_pa<double>(const Launch&, const PItem*, int);
 

@@ -124,7 +124,7 @@ __global__ void k_scatter(const SysDev* __restrict__ sys, const PItem* __restric
   reinterpret_cast<T4*>(S.pos[it.buf])[q] = h;
   reinterpret_cast<T4*>(S.poslo)[q] = l;
   reinterpret_cast<T4*>(S.ref)[q] = h;
-  if (sizeof(T) == 4 && S.ipos) {  // fixed point: the 64-bit rounding wraps modulo 2^32 for any x
+  if (S.ipos) {  // fixed point: the 64-bit rounding wraps modulo 2^32 for any x
     int4 iq;
     iq.x = (int)(unsigned)(unsigned long long)__double2ll_rn(X[p] * S.qinv);
     iq.y = (int)(unsigned)(unsigned long long)__double2ll_rn(X[n + p] * S.qinv);
