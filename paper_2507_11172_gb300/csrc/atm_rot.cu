@@ -2,12 +2,14 @@
 // distances <= r_c" (Fig. 2 caption, Sec. 4.2.2), every triplet evaluated once (Newton 3, the
 // future-work traversal of Sec. 5).
 //
-// Ownership.  A triplet belongs to its lowest member in the order "z coordinate of the last binning in
-// fixed point, then sorted index".  Displacements come from wrapping 32-bit differences of those
-// fixed-point positions, so the order is exactly antisymmetric and transitive on every triangle of
-// particles within r_c of each other (L > 3 r_c): each triplet has exactly one owner.  The owner i
-// sees the other two in its half list {j : r_ij <= r_c3, j above i}, about half of its neighbours
-// (a half ball, so the list length varies little from particle to particle).
+// Ownership.  A triplet belongs to its lowest member in the order "cell layer along z, then z in fixed
+// point (positions of the last binning, box = 2^32 units), then sorted index".  Within a triangle of
+// particles closer than r_c the unwrapped cell layers differ by at most one (cell edge >= r_c, at least
+// three cells per side) and the fixed-point z differences are exact wrapping 32-bit integers, so the
+// order is a total order on every triangle: each triplet has exactly one owner.  The owner i sees the
+// other two in its half list {j : r_ij <= r_c3, j above i}, about half of its neighbours (a half ball,
+// so the list length varies little from particle to particle).  The pair-list build writes the half
+// lists (S.half) with exact cutoff decisions; this kernel takes them as given.
 //
 // Rotation.  One warp per base particle i.  Lane v holds half-list node v (displacement d_v = x_v - x_i
 // and a_v = |d_v|^2).  In step s, lane v pairs node v with node (v + s) mod m; steps 1 .. (m - 1) / 2
@@ -40,8 +42,9 @@
 namespace r3b {
 
 constexpr int kZrMax = 64;    // half-list capacity: two rotation groups of at most 32 nodes
-constexpr int kZrWarps = 8;   // warps per CTA
-constexpr int kZrPer = 4;     // consecutive bases per warp in one work item
+constexpr int kZrWarps = 4;   // warps per CTA
+constexpr int kZrPer = 8;     // consecutive bases per warp in one work item
+static_assert(kZrMax == kHalfCap, "half-list capacity");
 static_assert(kZrWarps * kZrPer == rot_bases_per_item(0), "work items and kernel disagree");
 
 // FP32 reciprocal square root: the hardware approximation (flush-to-zero form; the argument is a
@@ -53,15 +56,53 @@ __device__ __forceinline__ float zr_rsqrt(float q) {
 }
 __device__ __forceinline__ double zr_rsqrt(double q) { return 1.0 / sqrt(q); }
 
+// asynchronous global -> shared copies (completed in commit-group order)
+__device__ __forceinline__ unsigned zr_smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void zr_cp16(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(zr_smem_u32(dst)), "l"(__cvta_generic_to_global(src))
+               : "memory");
+}
+__device__ __forceinline__ void zr_cp4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(zr_smem_u32(dst)), "l"(__cvta_generic_to_global(src))
+               : "memory");
+}
+__device__ __forceinline__ void zr_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void zr_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 template <typename T>
 struct ZrSmem {
   using T4 = typename V4<T>::type;
-  T4 nd[kZrMax];          // half list: (d_v, |d_v|^2)
-  T4 pn[kZrMax];          // partners of the current phase, doubled (pn[t + m] = pn[t]), far dummies after
-  T4 slot[2][kZrMax];     // partner shares (G, W) of odd and even steps, in pn's index space
-  T4 tot[kZrMax];         // per-node totals across phases (lists longer than 32)
-  int nidx[kZrMax];       // sorted index of each node
-  int pidx[kZrMax];       // sorted index of each partner entry (exact repeats)
+  T4 pn[kZrMax];            // partners of the current phase, doubled (pn[t + m] = pn[t]), far dummies after;
+                            // the half list is built here: (d_v, |d_v|^2)
+  T4 slot[2][kZrMax];       // partner shares (G, W) of odd and even steps, in pn's index space
+  T4 nd[kZrMax];            // copy of the half list (lists longer than 32 nodes)
+  T4 tot[kZrMax];           // per-node totals across phases (lists longer than 32 nodes)
+  int nidx[kZrMax];         // sorted index of each node
+  int4 cq[kZrMax];          // prefetched fixed-point positions of the next base's half list
+  unsigned row[2][kZrMax];  // prefetched half lists (pair-list entries) of the next two bases
+  int4 selfq;               // fixed-point position of the prefetched base
+  int rcnt[2];              // lengths of the prefetched half lists
+  int pad_[2];
+};
+
+// Per-CTA copy of the system constants this kernel reads (shared memory: no global reloads)
+template <typename T>
+struct ZrK {
+  const unsigned* half;
+  const int* half_cnt;
+  const int4* ipos;
+  const double* X;       // FP64 positions of the evaluated buffer (exact repeats)
+  const void* pos;       // cell-local positions of the evaluated buffer (FP64 path)
+  void* f3acc;
+  unsigned long long* ctr;
+  int* flags;
+  double L, rc3sq, nu, edge;
+  T rcsq, g, fs;         // r_c3^2, guard half-width, 3/4 nu in the kernel's precision
+  float qscale;          // L / 2^32
+  int n;
 };
 template <typename T>
 constexpr size_t zr_smem_bytes() {
@@ -84,8 +125,16 @@ __device__ __forceinline__ typename V4<T>::type zr_zero() {
   f.x = f.y = f.z = f.w = (T)0;
   return f;
 }
+template <typename T>
+__device__ __forceinline__ typename V4<T>::type zr_add4(typename V4<T>::type p, typename V4<T>::type q) {
+  p.x += q.x;
+  p.y += q.y;
+  p.z += q.z;
+  p.w += q.w;
+  return p;
+}
 
-// Per-lane running sums of one base (or one phase).
+// Per-lane running sums of one phase.
 template <typename T>
 struct ZrAcc {
   T W, Gx, Gy, Gz;  // own node
@@ -93,20 +142,26 @@ struct ZrAcc {
   T dmin;           // smallest |c - r_c^2| met (FP32 decisions)
 };
 
+// partner entries of a phase: entry t of pn is node pfirst + (t mod period) (exact repeats only)
+struct ZrPart {
+  int first, period;
+};
+
 // One phase: own node J of this lane (J.w = |d_J|^2; far dummy for lanes without a node), partners in
-// w.pn / w.pidx.  Full steps s_lo .. s_hi for every lane; then, if half > 0, step `half` for lanes
-// v < half only.  Slots must be zero on entry.
+// w.pn.  Full steps s_lo .. s_hi for every lane; then, if half > 0, step `half` for lanes v < half
+// only.  Slots must be zero on entry.
 template <typename T, bool kE, bool kExact>
-__device__ __forceinline__ void zr_steps(const SysDev& S, const double* __restrict__ X, ZrSmem<T>& w,
-                                         const typename V4<T>::type J, const int jid, const int s_lo,
-                                         const int s_hi, const int half, const int lane, ZrAcc<T>& A) {
+__device__ __forceinline__ void zr_steps(const ZrK<T>& K, ZrSmem<T>& w, const typename V4<T>::type J, const int jid,
+                                         const ZrPart pp, const int s_lo, const int s_hi, const int half,
+                                         const int lane, ZrAcc<T>& A) {
   using T4 = typename V4<T>::type;
-  const T rcsq = Par<T>::rc3sq(S), g = Par<T>::guard3(S);
+  const T rcsq = K.rcsq, g = K.g;
   const T a = J.w, a2 = J.w + J.w;
-  auto step = [&](const int s, const int par, const T off) {
+  auto step = [&](const int s, const int par, const bool masked) {
     const T4 pk = w.pn[lane + s];
     const T ex = pk.x - J.x, ey = pk.y - J.y, ez = pk.z - J.z;
-    const T c = fma(ez, ez, fma(ey, ey, ex * ex)) + off;
+    T c = fma(ez, ez, fma(ey, ey, ex * ex));
+    if (masked) c += (T)1e6;  // only the last step of an even list
     const T t = c - rcsq;
     T okf;
     if constexpr (kExact) {
@@ -114,8 +169,10 @@ __device__ __forceinline__ void zr_steps(const SysDev& S, const double* __restri
       const bool band = ok && t >= -g;
       if (__any_sync(0xffffffffu, band)) {
         if (band) {
-          atomicAdd(&S.ctr[CTR_GUARD], 1ull);
-          ok = exact_within(X, S.n, jid, w.pidx[lane + s], S.L, S.rc3sq);
+          atomicAdd(&K.ctr[CTR_GUARD], 1ull);
+          const int u = lane + s;
+          const int kid = w.nidx[pp.first + (u >= pp.period ? u - pp.period : u)];
+          ok = exact_within(K.X, K.n, jid, kid, K.L, K.rc3sq);
         }
       }
       okf = ok ? (T)1 : (T)0;
@@ -163,16 +220,16 @@ __device__ __forceinline__ void zr_steps(const SysDev& S, const double* __restri
   int s = s_lo;
 #pragma unroll 1
   for (; s + 1 <= s_hi; s += 2) {
-    step(s, 0, (T)0);
-    step(s + 1, 1, (T)0);
+    step(s, 0, false);
+    step(s + 1, 1, false);
     __syncwarp();
   }
   if (s <= s_hi) {
-    step(s, 0, (T)0);
+    step(s, 0, false);
     __syncwarp();
   }
   if (half > 0) {
-    step(half, 1, lane < half ? (T)0 : (T)1e6);
+    step(half, 1, lane >= half);
     __syncwarp();
   }
 }
@@ -186,122 +243,114 @@ __device__ __forceinline__ void zr_clear_slots(ZrSmem<T>& w, int lane) {
   w.slot[1][lane + 32] = zr_zero<T>();
 }
 
-// Partner layout of a self rotation over nodes first .. first + mx - 1 (mx <= 32): doubled, then far.
+// Partner layout from w.nd: nodes first .. first + mb - 1 padded to period mp (mb <= mp <= 32),
+// doubled, then far dummies (a self rotation has mb = mp).
 template <typename T>
-__device__ __forceinline__ void zr_layout_self(ZrSmem<T>& w, int first, int mx, int lane) {
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int t = lane + 32 * h;
-    const int v = t < mx ? t : t - mx;
-    const bool real = t < 2 * mx;
-    w.pn[t] = real ? w.nd[first + v] : zr_far<T>((T)-1);
-    w.pidx[t] = real ? w.nidx[first + v] : 0;
-  }
-}
-// Partner layout of a cross rotation: nodes first .. first + mb - 1 padded to mp (mb <= mp <= 32),
-// doubled, then far.
-template <typename T>
-__device__ __forceinline__ void zr_layout_cross(ZrSmem<T>& w, int first, int mb, int mp, int lane) {
+__device__ __forceinline__ void zr_layout(ZrSmem<T>& w, int first, int mb, int mp, int lane) {
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     const int t = lane + 32 * h;
     const int v = t < mp ? t : t - mp;
     const bool real = t < 2 * mp && v < mb;
     w.pn[t] = real ? w.nd[first + v] : zr_far<T>((T)-1);
-    w.pidx[t] = real ? w.nidx[first + v] : 0;
   }
 }
 
-// Run one phase with FP32 decisions; if a pair met the guard band, discard and repeat it exactly.
-// Returns the lane's own-node sums in A (cnt, u are added to the running totals in R).
+// One phase with FP32 decisions; if a pair met the guard band, it is discarded and repeated with
+// exact decisions.  The lane's own-node sums, count and energy are left in A.
 template <typename T, bool kE>
-__device__ __forceinline__ void zr_phase_exact(const SysDev& S, const double* __restrict__ X, ZrSmem<T>& w,
-                                            const typename V4<T>::type J, const int jid, const int s_lo,
-                                            const int s_hi, const int half, const int lane, ZrAcc<T>& A) {
-  __syncwarp();
-  zr_clear_slots<T>(w, lane);
-  __syncwarp();
-  A.W = A.Gx = A.Gy = A.Gz = A.cnt = A.u = (T)0;
-  zr_steps<T, kE, true>(S, X, w, J, jid, s_lo, s_hi, half, lane, A);
-}
-template <typename T, bool kE>
-__device__ __forceinline__ void zr_phase(const SysDev& S, const double* __restrict__ X, ZrSmem<T>& w,
-                                         const typename V4<T>::type J, const int jid, const int s_lo,
-                                         const int s_hi, const int half, const int lane, ZrAcc<T>& A) {
+__device__ __forceinline__ void zr_phase(const ZrK<T>& K, ZrSmem<T>& w, const typename V4<T>::type J, const int jid,
+                                         const ZrPart pp, const int s_lo, const int s_hi, const int half,
+                                         const int lane, ZrAcc<T>& A) {
   A.W = A.Gx = A.Gy = A.Gz = A.cnt = A.u = (T)0;
   A.dmin = (T)1e30;
-  zr_steps<T, kE, false>(S, X, w, J, jid, s_lo, s_hi, half, lane, A);
-  if (__any_sync(0xffffffffu, A.dmin <= Par<T>::guard3(S))) zr_phase_exact<T, kE>(S, X, w, J, jid, s_lo, s_hi, half, lane, A);
+  zr_steps<T, kE, false>(K, w, J, jid, pp, s_lo, s_hi, half, lane, A);
+  if (__any_sync(0xffffffffu, A.dmin <= K.g)) {
+    __syncwarp();
+    zr_clear_slots<T>(w, lane);
+    __syncwarp();
+    A.W = A.Gx = A.Gy = A.Gz = A.cnt = A.u = (T)0;
+    zr_steps<T, kE, true>(K, w, J, jid, pp, s_lo, s_hi, half, lane, A);
+  }
 }
 
-// Displacement x_j - x_i in the kernel's precision.  FP32: wrapping fixed-point difference (exact
-// minimum image), one rounding to FP32, one scaling.  FP64: cell-local coordinates plus cell offset.
-__device__ __forceinline__ void zr_disp(const SysDev& S, int, const int4 qi, const int4 qj, unsigned, int, int,
-                                        float& dx, float& dy, float& dz) {
-  const float sc = S.f_qscale;
-  dx = (float)(int)((unsigned)qj.x - (unsigned)qi.x) * sc;
-  dy = (float)(int)((unsigned)qj.y - (unsigned)qi.y) * sc;
-  dz = (float)(int)((unsigned)qj.z - (unsigned)qi.z) * sc;
-}
-__device__ __forceinline__ void zr_disp(const SysDev& S, int buf, const int4, const int4, unsigned code, int i,
-                                        int j, double& dx, double& dy, double& dz) {
-  const double4_32a* P = reinterpret_cast<const double4_32a*>(S.pos[buf]);
-  const double4_32a pi = P[i], pj = P[j];
-  const double ox = (double)(int)(code & 3u) - 1.0, oy = (double)(int)((code >> 2) & 3u) - 1.0,
-               oz = (double)(int)(code >> 4) - 1.0;
-  dx = (pj.x - pi.x) + ox * S.edge;
-  dy = (pj.y - pi.y) + oy * S.edge;
-  dz = (pj.z - pi.z) + oz * S.edge;
+// ---------------------------------------------------------------- half-list nodes
+// FP32 node: displacement from the fixed-point positions (wrapping difference = exact minimum image,
+// one rounding to FP32, one scaling) and its squared length
+__device__ __forceinline__ float4 zr_qnode(const float sc, const int4 qi, const int4 qj) {
+  float4 d;
+  d.x = (float)(int)((unsigned)qj.x - (unsigned)qi.x) * sc;
+  d.y = (float)(int)((unsigned)qj.y - (unsigned)qi.y) * sc;
+  d.z = (float)(int)((unsigned)qj.z - (unsigned)qi.z) * sc;
+  d.w = fmaf(d.z, d.z, fmaf(d.y, d.y, d.x * d.x));
+  return d;
 }
 
-// Half list of base x into w.nd / w.nidx from its pair-list row; returns its length (entries beyond
-// kZrMax are counted, not stored).
+// Half list of base x read from global memory into w.pn / w.nidx (FP64 path); returns its length.
 template <typename T>
-__device__ __forceinline__ int zr_build(const SysDev& S, ZrSmem<T>& w, const int buf, const int x,
-                                        const int lane) {
-  using T4 = typename V4<T>::type;
-  const unsigned lt = (1u << lane) - 1u;
-  const unsigned* __restrict__ row = reinterpret_cast<const unsigned*>(S.nbr) + (size_t)x * S.maxnb;
-  const int cnt = S.nbr_cnt[x];
-  const int4 qi = S.ipos[x];
-  const T rcsq = Par<T>::rc3sq(S), g = Par<T>::guard3(S);
-  int m = 0;
-  for (int t0 = 0; t0 < cnt; t0 += 32) {
-    const int t = t0 + lane;
-    const bool valid = t < cnt;
-    const unsigned e = valid ? __ldg(row + t) : 0u;
-    const int j = (int)(e & kNbrMask);
-    const int4 qj = valid ? __ldg(S.ipos + j) : qi;
-    const int dzq = (int)((unsigned)qj.z - (unsigned)qi.z);
-    const bool above = valid && (dzq > 0 || (dzq == 0 && j > x));
-    T dx = (T)0, dy = (T)0, dz = (T)0;
-    if (above) zr_disp(S, buf, qi, qj, e >> kNbrShift, x, j, dx, dy, dz);
-    const T r2 = fma(dz, dz, fma(dy, dy, dx * dx));
-    bool ok = above && r2 <= rcsq - g;
-    const bool band = above && r2 > rcsq - g && r2 <= rcsq + g;
-    if (__any_sync(0xffffffffu, band)) {
-      if (band) {
-        atomicAdd(&S.ctr[CTR_GUARD], 1ull);
-        ok = exact_within(S.X[buf], S.n, x, j, S.L, S.rc3sq);
+__device__ __forceinline__ int zr_build_direct(const ZrK<T>& K, ZrSmem<T>& w, const int x, const int lane) {
+  const int m = K.half_cnt[x];
+  const unsigned* __restrict__ row = K.half + (size_t)x * kHalfCap;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int t = lane + 32 * h;
+    if (t < min(m, kZrMax)) {
+      const unsigned e = row[t];
+      const int j = (int)(e & kNbrMask);
+      typename V4<T>::type d;
+      if constexpr (sizeof(T) == 4) {
+        d = zr_qnode(K.qscale, K.ipos[x], K.ipos[j]);
+      } else {
+        const double4_32a* P = reinterpret_cast<const double4_32a*>(K.pos);
+        const double4_32a pi = P[x], pj = P[j];
+        const unsigned code = e >> kNbrShift;
+        d.x = (pj.x - pi.x) + ((double)(int)(code & 3u) - 1.0) * K.edge;
+        d.y = (pj.y - pi.y) + ((double)(int)((code >> 2) & 3u) - 1.0) * K.edge;
+        d.z = (pj.z - pi.z) + ((double)(int)(code >> 4) - 1.0) * K.edge;
+        d.w = fma(d.z, d.z, fma(d.y, d.y, d.x * d.x));
       }
+      w.pn[t] = d;
+      w.nidx[t] = j;
     }
-    const unsigned bal = __ballot_sync(0xffffffffu, ok);
-    const int pos = m + __popc(bal & lt);
-    if (ok && pos < kZrMax) {
-      T4 d4;
-      d4.x = dx;
-      d4.y = dy;
-      d4.z = dz;
-      d4.w = r2;
-      w.nd[pos] = d4;
-      w.nidx[pos] = j;
-    }
-    m += __popc(bal);
   }
   __syncwarp();
   return m;
 }
 
+// FP32 prefetch, stage 1: the half list (pair-list entries) and its length of base x
+__device__ __forceinline__ void zr_fetch_row(const ZrK<float>& K, ZrSmem<float>& w, int slot, int x, int lane) {
+  if (lane < kZrMax / 4) zr_cp16(&w.row[slot][4 * lane], K.half + (size_t)x * kHalfCap + 4 * lane);
+  if (lane == 0) zr_cp4(&w.rcnt[slot], K.half_cnt + x);
+}
+// stage 2 (half list already in shared memory): the fixed-point positions of base x and of its
+// half-list members
+__device__ __forceinline__ void zr_fetch_pos(const ZrK<float>& K, ZrSmem<float>& w, int slot, int x, int lane) {
+  if (lane == 0) zr_cp16(&w.selfq, K.ipos + x);
+  const int m = min(w.rcnt[slot], kZrMax);
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int t = lane + 32 * h;
+    if (t < m) zr_cp16(&w.cq[t], K.ipos + (w.row[slot][t] & kNbrMask));
+  }
+}
+// nodes of base x from the prefetched half list (slot) and positions; returns the list length
+__device__ __forceinline__ int zr_build_staged(const ZrK<float>& K, ZrSmem<float>& w, const int slot,
+                                               const int lane) {
+  const int m = w.rcnt[slot];
+  const int4 qi = w.selfq;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int t = lane + 32 * h;
+    if (t < min(m, kZrMax)) {
+      w.pn[t] = zr_qnode(K.qscale, qi, w.cq[t]);
+      w.nidx[t] = (int)(w.row[slot][t] & kNbrMask);
+    }
+  }
+  __syncwarp();
+  return m;
+}
+
+// ---------------------------------------------------------------- evaluation of one base
 // Warp sums of four per-lane values by a transposed butterfly (8 shuffles): afterwards lanes 0-7 hold
 // the total of a, lanes 8-15 of b, 16-23 of c, 24-31 of d.
 template <typename T>
@@ -333,82 +382,73 @@ __device__ __forceinline__ void zr_atomic_add(void* f3acc, int j, T fx, T fy, T 
   }
 }
 
-// node v's final force (scaled by 3/4 nu) to its accumulator; returns W_v d_v (unscaled) for F_i
+// node force F_v = (G_v - W_v d_v) * fs to its accumulator; W_v d_v (unscaled) into F_i
 template <typename T>
-__device__ __forceinline__ void zr_emit(const SysDev& S, const typename V4<T>::type d, int j, T W, T Gx, T Gy, T Gz,
-                                        T fs, T& fix, T& fiy, T& fiz) {
+__device__ __forceinline__ void zr_emit(const ZrK<T>& K, const typename V4<T>::type d, int j, T W, T Gx, T Gy, T Gz,
+                                        T& fix, T& fiy, T& fiz) {
   fix = fma(W, d.x, fix);
   fiy = fma(W, d.y, fiy);
   fiz = fma(W, d.z, fiz);
-  zr_atomic_add<T>(S.f3acc, j, fs * fma(-W, d.x, Gx), fs * fma(-W, d.y, Gy), fs * fma(-W, d.z, Gz));
+  zr_atomic_add<T>(K.f3acc, j, K.fs * fma(-W, d.x, Gx), K.fs * fma(-W, d.y, Gy), K.fs * fma(-W, d.z, Gz));
 }
 
-template <typename T>
-__device__ __forceinline__ typename V4<T>::type zr_add4(typename V4<T>::type p, typename V4<T>::type q) {
-  p.x += q.x;
-  p.y += q.y;
-  p.z += q.z;
-  p.w += q.w;
-  return p;
-}
-
-// All triplets owned by base x.  Adds forces to S.f3acc; returns (in lane-summed form) count and energy.
+// All triplets owned by base x, whose half list (length m) is in w.pn / w.nidx.  Adds the forces to
+// the accumulators and the count and energy (per lane) to cnt_sum, u_sum.
 template <typename T, bool kE>
-__device__ __forceinline__ void zr_base(const SysDev& S, ZrSmem<T>& w, const int buf, const int x, const int lane,
+__device__ __forceinline__ void zr_eval(const ZrK<T>& K, ZrSmem<T>& w, const int x, const int m, const int lane,
                                         T& cnt_sum, T& u_sum) {
   using T4 = typename V4<T>::type;
-  const double* __restrict__ X = S.X[buf];
-  const int m_all = zr_build<T>(S, w, buf, x, lane);
-  if (m_all > kZrMax) {
-    if (lane == 0) atomicOr(&S.flags[FLG_ERR], ERR_HALF_CAP);
+  if (m > kZrMax) {
+    if (lane == 0) atomicOr(K.flags + FLG_ERR, ERR_HALF_CAP);
     return;
   }
-  const int m = m_all;
-  const T fs = (T)0.75 * Par<T>::nu(S);
+  if (m < 2) return;
   T fix = (T)0, fiy = (T)0, fiz = (T)0;
   ZrAcc<T> A;
   if (m <= 32) {
-    if (m >= 2) {
-      zr_clear_slots<T>(w, lane);
-      zr_layout_self<T>(w, 0, m, lane);
-      __syncwarp();
-      const T4 J = lane < m ? w.nd[lane] : zr_far<T>((T)1);
-      const int jid = lane < m ? w.nidx[lane] : 0;
-      zr_phase<T, kE>(S, X, w, J, jid, 1, (m - 1) >> 1, (m & 1) ? 0 : (m >> 1), lane, A);
-      cnt_sum += A.cnt;
-      if (kE) u_sum += A.u;
-      if (lane < m) {
-        const T4 s = zr_add4<T>(zr_add4<T>(w.slot[0][lane], w.slot[1][lane]),
-                                zr_add4<T>(w.slot[0][lane + m], w.slot[1][lane + m]));
-        zr_emit<T>(S, J, jid, A.W + s.w, A.Gx + s.x, A.Gy + s.y, A.Gz + s.z, fs, fix, fiy, fiz);
-      }
+    // the list in place, doubled (pn[v + m] = pn[v]), then far dummies
+    const T4 J = lane < m ? w.pn[lane] : zr_far<T>((T)1);
+    const int jid = lane < m ? w.nidx[lane] : 0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int t = lane + 32 * h;
+      if (t >= m) w.pn[t] = t < 2 * m ? w.pn[t - m] : zr_far<T>((T)-1);
+    }
+    zr_clear_slots<T>(w, lane);
+    __syncwarp();
+    zr_phase<T, kE>(K, w, J, jid, ZrPart{0, m}, 1, (m - 1) >> 1, (m & 1) ? 0 : (m >> 1), lane, A);
+    cnt_sum += A.cnt;
+    if (kE) u_sum += A.u;
+    if (lane < m) {
+      const T4 s = zr_add4<T>(zr_add4<T>(w.slot[0][lane], w.slot[1][lane]),
+                              zr_add4<T>(w.slot[0][lane + m], w.slot[1][lane + m]));
+      zr_emit<T>(K, J, jid, A.W + s.w, A.Gx + s.x, A.Gy + s.y, A.Gz + s.z, fix, fiy, fiz);
     }
   } else {
-    // halves A = nodes 0 .. ma-1, B = nodes ma .. m-1 (mb <= ma <= 32)
+    // halves A = nodes 0 .. ma-1, B = nodes ma .. m-1 (mb <= ma <= 32): within A, within B, A x B
     const int ma = (m + 1) >> 1, mb = m - ma;
-    w.tot[lane] = zr_zero<T>();
-    w.tot[lane + 32] = zr_zero<T>();
-    // phase 1: within A; phase 2: within B; phase 3: A x B
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      w.nd[lane + 32 * h] = w.pn[lane + 32 * h];
+      w.tot[lane + 32 * h] = zr_zero<T>();
+    }
 #pragma unroll 1
     for (int ph = 0; ph < 3; ++ph) {
+      const int own_first = ph == 1 ? ma : 0, own_n = ph == 1 ? mb : ma;
+      const int par_first = ph == 0 ? 0 : ma, par_n = ph == 0 ? ma : mb, par_period = ph == 2 ? ma : par_n;
       __syncwarp();
       zr_clear_slots<T>(w, lane);
-      if (ph == 0) zr_layout_self<T>(w, 0, ma, lane);
-      else if (ph == 1) zr_layout_self<T>(w, ma, mb, lane);
-      else zr_layout_cross<T>(w, ma, mb, ma, lane);
-      __syncwarp();
-      const int own_first = ph == 1 ? ma : 0, own_n = ph == 1 ? mb : ma;
+      zr_layout<T>(w, par_first, par_n, par_period, lane);
       const T4 J = lane < own_n ? w.nd[own_first + lane] : zr_far<T>((T)1);
       const int jid = lane < own_n ? w.nidx[own_first + lane] : 0;
-      const int mx = ph == 0 ? ma : mb;
+      __syncwarp();
+      const ZrPart pp{par_first, par_period};
       if (ph < 2)
-        zr_phase<T, kE>(S, X, w, J, jid, 1, (mx - 1) >> 1, (mx & 1) ? 0 : (mx >> 1), lane, A);
+        zr_phase<T, kE>(K, w, J, jid, pp, 1, (own_n - 1) >> 1, (own_n & 1) ? 0 : (own_n >> 1), lane, A);
       else
-        zr_phase<T, kE>(S, X, w, J, jid, 0, ma - 1, 0, lane, A);
+        zr_phase<T, kE>(K, w, J, jid, pp, 0, ma - 1, 0, lane, A);
       cnt_sum += A.cnt;
       if (kE) u_sum += A.u;
-      // own-node sums and partner slots into the per-node totals
-      const int par_first = ph == 0 ? 0 : ma, par_n = ph == 0 ? ma : mb, par_period = ph == 2 ? ma : par_n;
       if (lane < own_n) {
         T4 o;
         o.x = A.Gx;
@@ -430,59 +470,121 @@ __device__ __forceinline__ void zr_base(const SysDev& S, ZrSmem<T>& w, const int
       const int v = lane + 32 * h;
       if (v < m) {
         const T4 t = w.tot[v];
-        zr_emit<T>(S, w.nd[v], w.nidx[v], t.w, t.x, t.y, t.z, fs, fix, fiy, fiz);
+        zr_emit<T>(K, w.nd[v], w.nidx[v], t.w, t.x, t.y, t.z, fix, fiy, fiz);
       }
     }
   }
   // F_i = sum_v W_v d_v (scaled): warp sum
   const T k = zr_sum4<T>(fix, fiy, fiz, (T)0, lane);
   const T Fx = k, Fy = __shfl_sync(0xffffffffu, k, 8), Fz = __shfl_sync(0xffffffffu, k, 16);
-  if (lane == 0) zr_atomic_add<T>(S.f3acc, x, fs * Fx, fs * Fy, fs * Fz);
+  if (lane == 0) zr_atomic_add<T>(K.f3acc, x, K.fs * Fx, K.fs * Fy, K.fs * Fz);
+}
+
+template <typename T>
+__device__ __forceinline__ void zr_eval_any(const ZrK<T>& K, ZrSmem<T>& w, int x, int m, int lane, bool energy, T& cnt,
+                                            T& u) {
+  if (energy)
+    zr_eval<T, true>(K, w, x, m, lane, cnt, u);
+  else
+    zr_eval<T, false>(K, w, x, m, lane, cnt, u);
   __syncwarp();  // the next base reuses the warp's shared memory
 }
 
-// Work item: 32 consecutive bases, kZrPer per warp.  Counts and energy are summed per CTA and added
-// to the system's totals with one atomic each.
+// Work item: 32 consecutive bases, kZrPer per warp.  FP32: a two-stage cp.async pipeline per warp
+// copies the half list of base k + 2 and the positions of base k + 1 into shared memory while base k
+// is evaluated.  Counts and energy are summed per CTA (the last warp to finish adds them to the
+// system's totals with one atomic each).
 template <typename T>
-__global__ void __launch_bounds__(32 * kZrWarps, sizeof(T) == 4 ? 4 : 2)
+__global__ void __launch_bounds__(32 * kZrWarps, sizeof(T) == 4 ? 7 : 4)
     k_atm_rot(const SysDev* __restrict__ sys, const PItem* __restrict__ items) {
   extern __shared__ __align__(32) unsigned char zr_raw[];
-  __shared__ double red_c[kZrWarps], red_u[kZrWarps];
+  __shared__ ZrK<T> K;
+  __shared__ unsigned long long s_cnt;
+  __shared__ double s_u;
+  __shared__ int s_done;
   const PItem it = items[blockIdx.x];
   const SysDev& S = sys[it.sys];
   const int imode = item_mode(S, it.mode);
   if (imode & M_SKIP) return;  // block-uniform
-  const bool kE = (imode & M_ENERGY) != 0;
+  const bool energy = (imode & M_ENERGY) != 0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  ZrSmem<T>& w = reinterpret_cast<ZrSmem<T>*>(zr_raw)[warp];
-  T cnt = (T)0, u = (T)0;
-  for (int k = 0; k < kZrPer; ++k) {
-    const int x = it.begin + warp * kZrPer + k;
-    if (x >= S.n) break;  // warp-uniform
-    if (kE)
-      zr_base<T, true>(S, w, it.buf, x, lane, cnt, u);
-    else
-      zr_base<T, false>(S, w, it.buf, x, lane, cnt, u);
-  }
-  // per-lane counts are exact small integers in T; sum them in FP64
-  double c = warp_sum((double)cnt);
-  double uu = kE ? warp_sum((double)u) : 0.0;
-  if (lane == 0) {
-    red_c[warp] = c;
-    red_u[warp] = uu;
+  if (threadIdx.x == 0) {
+    K.half = reinterpret_cast<const unsigned*>(S.half);
+    K.half_cnt = S.half_cnt;
+    K.ipos = S.ipos;
+    K.X = S.X[it.buf];
+    K.pos = S.pos[it.buf];
+    K.f3acc = S.f3acc;
+    K.ctr = S.ctr;
+    K.flags = S.flags;
+    K.L = S.L;
+    K.rc3sq = S.rc3sq;
+    K.nu = S.nu;
+    K.edge = S.edge;
+    K.rcsq = Par<T>::rc3sq(S);
+    K.g = Par<T>::guard3(S);
+    K.fs = (T)0.75 * Par<T>::nu(S);
+    K.qscale = S.f_qscale;
+    K.n = S.n;
+    s_cnt = 0ull;
+    s_u = 0.0;
+    s_done = 0;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double ct = 0.0, ut = 0.0;
-    for (int q = 0; q < kZrWarps; ++q) {
-      ct += red_c[q];
-      ut += red_u[q];
+  ZrSmem<T>& w = reinterpret_cast<ZrSmem<T>*>(zr_raw)[warp];
+  const int n = K.n;
+  const int x0 = it.begin + warp * kZrPer;
+  const int nb = max(0, min(kZrPer, n - x0));  // bases of this warp
+  T cnt = (T)0, u = (T)0;
+  if constexpr (sizeof(T) == 4) {
+    if (nb > 0) {
+      zr_fetch_row(K, w, 0, x0, lane);
+      zr_commit();
+      zr_wait<0>();
+      __syncwarp();
+      zr_fetch_pos(K, w, 0, x0, lane);
+      zr_commit();
+      if (nb > 1) zr_fetch_row(K, w, 1, x0 + 1, lane);
+      zr_commit();
     }
-    if (ct > 0.0) atomicAdd(&S.ctr[CTR_TRIPLETS], (unsigned long long)(ct + 0.5));
-    if (kE) {
-      const double U = S.nu * ut;
-      atomicAdd(&S.acc[ACC_U3], U);
-      atomicAdd(&S.acc[ACC_W3], 9.0 * U);  // sum_a r_a . F_a = 9 phi (phi is homogeneous of degree -9)
+    for (int k = 0; k < nb; ++k) {
+      zr_wait<1>();  // positions of base k (and every older group) have arrived
+      __syncwarp();
+      const int m = zr_build_staged(K, w, k & 1, lane);
+      if (k + 1 < nb) {  // refill: positions of base k + 1, half list of base k + 2
+        zr_wait<0>();
+        __syncwarp();
+        zr_fetch_pos(K, w, (k + 1) & 1, x0 + k + 1, lane);
+      }
+      zr_commit();
+      __syncwarp();  // every lane has read slot k & 1 before it is refilled
+      if (k + 2 < nb) zr_fetch_row(K, w, k & 1, x0 + k + 2, lane);
+      zr_commit();
+      zr_eval_any<T>(K, w, x0 + k, m, lane, energy, cnt, u);
+    }
+    zr_wait<0>();
+  } else {
+    for (int k = 0; k < nb; ++k) {
+      const int m = zr_build_direct<T>(K, w, x0 + k, lane);
+      zr_eval_any<T>(K, w, x0 + k, m, lane, energy, cnt, u);
+    }
+  }
+  // per-lane counts are exact small integers in T
+  const double c = warp_sum((double)cnt);
+  const double uu = energy ? warp_sum((double)u) : 0.0;
+  if (lane == 0) {
+    atomicAdd(&s_cnt, (unsigned long long)(c + 0.5));
+    if (energy) atomicAdd(&s_u, uu);
+    __threadfence_block();
+    if (atomicAdd(&s_done, 1) == kZrWarps - 1) {  // last warp of the CTA
+      __threadfence_block();
+      const unsigned long long ct = atomicAdd(&s_cnt, 0ull);
+      if (ct) atomicAdd(K.ctr + CTR_TRIPLETS, ct);
+      if (energy) {
+        const double U = K.nu * atomicAdd(&s_u, 0.0);
+        atomicAdd(S.acc + ACC_U3, U);
+        atomicAdd(S.acc + ACC_W3, 9.0 * U);  // sum_a r_a . F_a = 9 phi (phi is homogeneous of degree -9)
+      }
     }
   }
 }

@@ -180,6 +180,7 @@ md_status alloc_device(md_system* s) {
   size_t o_pcell = a.reserve(4 * n), o_ctmp = a.reserve(4 * n), o_rank = a.reserve(4 * n);
   size_t o_count = a.reserve(4 * (size_t)s->ncell), o_cstart = a.reserve(4 * ((size_t)s->ncell + 1));
   size_t o_nbr = a.reserve(4 * (size_t)s->maxnb * n), o_nbc = a.reserve(4 * n);
+  size_t o_half = a.reserve(4 * (size_t)kHalfCap * n), o_hc = a.reserve(4 * n);
   size_t o_part = a.reserve(tsz * 27 * 3 * n);
   size_t o_f3a = a.reserve(4 * tsz * n);
   size_t o_ipos = a.reserve(16 * n);
@@ -216,6 +217,8 @@ md_status alloc_device(md_system* s) {
   h.cell_start = (int*)(m + o_cstart);
   h.nbr = (int*)(m + o_nbr);
   h.nbr_cnt = (int*)(m + o_nbc);
+  h.half = (int*)(m + o_half);
+  h.half_cnt = (int*)(m + o_hc);
   h.partial = m + o_part;
   h.f3acc = m + o_f3a;
   h.ipos = (int4*)(m + o_ipos);
@@ -261,6 +264,8 @@ size_t arena_bytes(const md_system* s0) {
   a.reserve(4 * (size_t)tmp.ncell);
   a.reserve(4 * ((size_t)tmp.ncell + 1));
   a.reserve(4 * (size_t)tmp.maxnb * n);
+  a.reserve(4 * n);
+  a.reserve(4 * (size_t)kHalfCap * n);
   a.reserve(4 * n);
   a.reserve(tsz * 27 * 3 * n);
   a.reserve(4 * tsz * n);

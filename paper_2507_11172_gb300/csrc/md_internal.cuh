@@ -16,6 +16,7 @@ constexpr int kAtmThreads = 32 * kAtmWarps;
 constexpr int kQueue = 256;         // per-warp queue of accepted neighbour pairs (j, k)
 constexpr int kLjTeam = 8;          // lanes cooperating on one particle's pair list
 constexpr int kListWarps = 4;       // warps per CTA of the pair-list build
+constexpr int kHalfCap = 64;        // triplet half list per particle (neighbours above it within r_c3)
 
 // error bits in SysDev::flags[0]
 enum : int {
@@ -65,6 +66,7 @@ struct SysDev {
   int *cell_tmp, *rank;       // [n] binning scratch
   int *count, *cell_start;    // [ncell], [ncell + 1]
   int *nbr, *nbr_cnt;         // [n][maxnb] row-major, [n]
+  int *half, *half_cnt;       // [n][kHalfCap] triplet half list of each particle (pair-list entries), [n]
   void *partial;              // T [27][3][n] per-stencil-slot ATM partial forces
   int4 *ipos;                 // [n] FP32 mode: positions of the last binning in fixed point (box = 2^32
                               // units; x, y, z as wrapping 32-bit integers), NULL where unused

@@ -139,8 +139,12 @@ __global__ void k_scatter(const SysDev* __restrict__ sys, const PItem* __restric
 // of b tests every staged particle and ballot-compacts those within
 // (r_c2 + skin)^2 (slightly widened: the list may hold a superset) into i's row.
 // Entry = j | image code << 26, code = (dx+1) | (dy+1) << 2 | (dz+1) << 4 for the
-// cell offset from i's cell to j's cell.  The CTA also moves the permuted state of
-// b's particles back into place.
+// cell offset from i's cell to j's cell.  The same pass writes i's triplet half list
+// (S.half, S.half_cnt): the entries j with r_ij <= r_c3 (guard band around r_c3^2
+// re-decided in FP64 with the CPU definition's operation order) that lie above i in the
+// order "cell layer along z, then fixed-point z, then sorted index", which makes i the
+// owner of every triplet whose other two members are in that list.  The CTA also moves
+// the permuted state of b's particles back into place.
 template <typename T>
 __global__ void __launch_bounds__(32 * kListWarps)
     k_listbuild(const SysDev* __restrict__ sys, const CItem* __restrict__ items, int smax) {
@@ -148,6 +152,7 @@ __global__ void __launch_bounds__(32 * kListWarps)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T4* sp = reinterpret_cast<T4*>(smem_raw);
   int* sj = reinterpret_cast<int*>(sp + smax);
+  int* sqz = sj + smax;  // fixed-point z of each staged particle
   __shared__ int st_begin[28], st_cnt[27], st_cell[27];
   const CItem it = items[blockIdx.x];
   const SysDev& S = sys[it.sys];
@@ -194,6 +199,7 @@ __global__ void __launch_bounds__(32 * kListWarps)
       // image code: cell offset (dx, dy, dz) + 1 per axis in 2 bits each
       const unsigned code = (unsigned)(l % 3) | ((unsigned)((l / 3) % 3) << 2) | ((unsigned)(l / 9) << 4);
       sj[slot] = (int)((unsigned)(c0 + e) | (code << kNbrShift));
+      sqz[slot] = S.ipos[c0 + e].z;
     }
   }
   __syncthreads();
@@ -202,28 +208,54 @@ __global__ void __launch_bounds__(32 * kListWarps)
   const int i0 = S.cell_start[b];
   const double* Xa = S.X[it.buf ^ 1];
   double* X = S.X[it.buf];
+  const T rc3 = (T)S.rc3sq, g3 = (T)S.guard3;
   for (int ib = warp; ib < nbase; ib += kListWarps) {
     const int islot = st_begin[13] + ib;
     const int i = i0 + ib;
     const T4 pi = sp[islot];
-    int cnt = 0;
+    const int qzi = sqz[islot];
+    int cnt = 0, mh = 0;
     int* row = S.nbr + (size_t)i * S.maxnb;
+    int* hrow = S.half + (size_t)i * kHalfCap;
     for (int t0 = 0; t0 < nstaged; t0 += 32) {
       const int t = t0 + lane;
-      bool ok = false;
+      bool ok = false, half = false, band = false;
       if (t < nstaged && t != islot) {
         const T4 q = sp[t];
         const T dx = q.x - pi.x, dy = q.y - pi.y, dz = q.z - pi.z;
-        ok = dx * dx + dy * dy + dz * dz <= rl;
+        const T r2 = dx * dx + dy * dy + dz * dz;
+        ok = r2 <= rl;
+        if (ok) {
+          // above i: the upper cell layer, or the same layer with larger fixed-point z (ties: index)
+          const unsigned e = (unsigned)sj[t];
+          const unsigned lay = e >> (kNbrShift + 4);
+          const int dqz = (int)((unsigned)sqz[t] - (unsigned)qzi);
+          const bool above = lay == 2u || (lay == 1u && (dqz > 0 || (dqz == 0 && (int)(e & kNbrMask) > i)));
+          if (above) {
+            half = r2 <= rc3 - g3;
+            band = !half && r2 <= rc3 + g3;
+          }
+        }
+      }
+      if (__any_sync(0xffffffffu, band)) {
+        if (band) {
+          atomicAdd(&S.ctr[CTR_GUARD], 1ull);
+          half = exact_within(Xa, n, i, (int)((unsigned)sj[t] & kNbrMask), S.L, S.rc3sq);
+        }
       }
       const unsigned bal = __ballot_sync(0xffffffffu, ok);
       const int pos = cnt + __popc(bal & lt);
       if (ok && pos < S.maxnb) row[pos] = sj[t];
       cnt += __popc(bal);
+      const unsigned balh = __ballot_sync(0xffffffffu, half);
+      const int hpos = mh + __popc(balh & lt);
+      if (half && hpos < kHalfCap) hrow[hpos] = sj[t];
+      mh += __popc(balh);
     }
     if (lane == 0) {
       if (cnt > S.maxnb) atomicOr(&S.flags[FLG_ERR], ERR_NBR_CAP);
       S.nbr_cnt[i] = min(cnt, S.maxnb);
+      S.half_cnt[i] = mh;  // more than kHalfCap: the triplet kernel reports ERR_HALF_CAP
     }
   }
   // every particle of b: permuted state back into place
@@ -296,14 +328,14 @@ void launch_scatter(const Launch& L, const PItem* items, int nitems, int block) 
 template <typename T>
 void launch_listbuild(const Launch& L, const CItem* items, int nitems, int smax) {
   if (nitems <= 0) return;
-  const int bytes = (int)(smax * (sizeof(typename V4<T>::type) + sizeof(int)));
+  const int bytes = (int)(smax * (sizeof(typename V4<T>::type) + 2 * sizeof(int)));
   k_listbuild<T><<<nitems, 32 * kListWarps, bytes, L.stream>>>(L.sys, items, smax);
 }
 // the kernel's dynamic shared-memory limit is process-wide: only ever raised
 static int g_list_smem_attr[2] = {0, 0};
 
 int listbuild_configure(int smax, int precision) {
-  const int bytes = (int)(smax * ((precision ? sizeof(double4_32a) : sizeof(float4)) + sizeof(int)));
+  const int bytes = (int)(smax * ((precision ? sizeof(double4_32a) : sizeof(float4)) + 2 * sizeof(int)));
   const int p = precision ? 1 : 0;
   if (bytes <= g_list_smem_attr[p]) return bytes;
   cudaError_t e = precision
