@@ -349,7 +349,7 @@ PItem* pitems_for(md_system* s, int tag, int mode, int buf) {
   auto it = s->pitems.find(key);
   if (it != s->pitems.end()) return it->second;
   std::vector<PItem> v;
-  const int per = (tag == T_LJ)      ? kBlock / kLjTeam
+  const int per = (tag == T_LJ)      ? kLjPer
                   : (tag == T_ATMPA)  ? kPaPerBlock
                   : (tag == T_ATMROT) ? rot_bases_per_item(s->precision)
                                       : kBlock;
@@ -378,7 +378,7 @@ CItem* citems_for(md_system* s, int mode, int buf) {
 // all item variants a call can use, created before any graph capture
 md_status prepare_items(md_system* s) {
   s->nblocks = (int)((s->n + kBlock - 1) / kBlock);
-  const int per_lj = kBlock / kLjTeam;
+  const int per_lj = kLjPer;
   s->nblocks_lj = (int)((s->n + per_lj - 1) / per_lj);
   s->nblocks_pa = (int)((s->n + kPaPerBlock - 1) / kPaPerBlock);
   s->nblocks_rot = (int)((s->n + rot_bases_per_item(s->precision) - 1) / rot_bases_per_item(s->precision));
@@ -486,7 +486,7 @@ struct Plan {
   }
   template <typename T>
   void lj(int kind, int buf, bool energy) {
-    launch_lj<T>(L, pitems_for(s, T_LJ, kind | (energy ? M_ENERGY : 0), buf), s->nblocks_lj, kBlock);
+    launch_lj<T>(L, pitems_for(s, T_LJ, kind | (energy ? M_ENERGY : 0), buf), s->nblocks_lj, kLjPer);
   }
   template <typename T>
   void atm(int buf, bool energy, int ev) {
@@ -1262,7 +1262,7 @@ void enqueue_cycle(md_batch* b, const std::vector<TickItems>& ticks, bool with_s
     chk("scatter", t);
     launch_listbuild<T>(L, b->d_citems + it.list, it.nlist, b->smax_list);
     chk("listbuild", t);
-    launch_lj<T>(L, b->d_pitems + it.lj, it.nlj, kBlock);
+    launch_lj<T>(L, b->d_pitems + it.lj, it.nlj, kLjPer);
     chk("lj", t);
     if (b->variant == 2)
       launch_atm_rot<T>(L, b->d_pitems + it.atm, it.natm);
@@ -1377,7 +1377,7 @@ md_status batch_build(md_batch* b) {
       for (int j = 0; j < ns; ++j) {
         const Request& r = b->req[b->resident[j]];
         const int tt = t % r.k;
-        for (int q = 0; q < (int)r.s->n; q += kBlock / kLjTeam) pit.push_back(PItem{j, q, tab(KT_LJ), tt & 1});
+        for (int q = 0; q < (int)r.s->n; q += kLjPer) pit.push_back(PItem{j, q, tab(KT_LJ), tt & 1});
       }
       ti.nlj = (int)(pit.size() - ti.lj);
       if (b->variant >= 1) {

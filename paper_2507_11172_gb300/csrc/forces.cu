@@ -101,27 +101,11 @@ __device__ __forceinline__ void store_pos(const SysDev& S, int buf, int i, const
 }
 
 // ============================================================== LJ pair kernel
-// A team of kLjTeam lanes shares one particle i: lane t of the team walks list
-// entries t, t + kLjTeam, ... (unrolled so several gathers are in flight), sums
-// its share in a compensated (hi, lo) accumulator, and the team combines the
-// shares with error-free TwoSum steps.  The team's first lane then applies the
-// velocity-Verlet kick/drift of Algorithm 2 for i.
-template <typename T>
-__device__ __forceinline__ void team_sum(CompF& c) {
-#pragma unroll
-  for (int o = kLjTeam / 2; o > 0; o >>= 1) {
-    const float oh = __shfl_xor_sync(0xffffffffu, c.hi, o);
-    const float ol = __shfl_xor_sync(0xffffffffu, c.lo, o);
-    float s, e;
-    two_sum(c.hi, oh, s, e);
-    c.hi = s;
-    c.lo = c.lo + (ol + e);
-  }
-}
-__device__ __forceinline__ void team_sum_d(double& v) {
-#pragma unroll
-  for (int o = kLjTeam / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-}
+// One thread per particle i.  The thread walks i's pair-list row four entries at a time (one 16-byte
+// row load, prefetched a group ahead, then four position gathers in flight), adds the plain sum of
+// every eight pair forces to a compensated (hi, lo) accumulator with an error-free TwoSum, and then
+// applies the velocity-Verlet kick/drift of Algorithm 2 for i in FP64 (every lane of the warp busy).
+// The offset of a neighbour's cell (entry code, one of 27) comes from a shared-memory table.
 
 // read-only cached load of a 4-vector (the position buffer read by a kernel is never written by it)
 __device__ __forceinline__ float4 ldg4(const float4* p) { return __ldg(p); }
@@ -136,10 +120,14 @@ template <> __device__ __forceinline__ float recip_fast<float>(float x) {
 }
 template <> __device__ __forceinline__ double recip_fast<double>(double x) { return 1.0 / x; }
 
+constexpr int kLjCodes = 43;  // entry codes (dx+1) | (dy+1) << 2 | (dz+1) << 4 span 0 .. 42
+constexpr unsigned kCentreCode = 1u | (1u << 2) | (1u << 4);
+
 template <typename T>
-__global__ void __launch_bounds__(256, 3) k_lj(const SysDev* __restrict__ sys, const PItem* __restrict__ items) {
+__global__ void __launch_bounds__(kLjPer, 14) k_lj(const SysDev* __restrict__ sys, const PItem* __restrict__ items) {
   using T4 = typename V4<T>::type;
-  constexpr int kBatch = 4;
+  constexpr int kGroup = 4;
+  __shared__ T4 s_off[kLjCodes];
   __shared__ double red[32];
   const PItem it = items[blockIdx.x];
   const SysDev& S = sys[it.sys];
@@ -147,162 +135,143 @@ __global__ void __launch_bounds__(256, 3) k_lj(const SysDev* __restrict__ sys, c
   if (mode & M_SKIP) return;  // block-uniform: a block belongs to one system
   const int kind = mode & M_KIND_MASK;
   const bool energy = (mode & M_ENERGY) != 0;
+  if (threadIdx.x < kLjCodes) {
+    const unsigned c = threadIdx.x;
+    const T e = Par<T>::edge(S);
+    T4 o;
+    o.x = fma((T)(c & 3u), e, -e);
+    o.y = fma((T)((c >> 2) & 3u), e, -e);
+    o.z = fma((T)((c >> 4) & 3u), e, -e);
+    o.w = (T)0;
+    s_off[threadIdx.x] = o;
+  }
+  __syncthreads();
   const int n = S.n;
-  const int tl = threadIdx.x % kLjTeam;
-  const int i = it.begin + threadIdx.x / kLjTeam;
+  const int i = it.begin + threadIdx.x;
   const bool active = i < n;
   const T4* __restrict__ P = reinterpret_cast<const T4*>(S.pos[it.buf]);
   const double* __restrict__ X = S.X[it.buf];
-  T fx = 0, fy = 0, fz = 0, uu_t = 0, ww_t = 0;  // plain partial sums of <= maxnb / kLjTeam terms
+  Acc3<T> f;
+  T px = 0, py = 0, pz = 0;  // plain sum of the previous group
+  unsigned band = 0;         // some pair fell in the guard band around r_c2^2
+  T uu_t = 0, ww_t = 0;      // energy and virial partials (FP32 sums are ample for the totals' tolerance)
   if (active) {
     const T4 pi = P[i];
-    const T edge = Par<T>::edge(S);
     const T rcsq = Par<T>::rc2sq(S);
     const T g2 = Par<T>::guard2(S);
     const T sig2 = Par<T>::sig2(S);
     const T eps24 = Par<T>::eps24(S), eps4 = Par<T>::eps4(S);
     const int cnt = S.nbr_cnt[i];
-    const int* __restrict__ row = S.nbr + (size_t)i * S.maxnb;
-    for (int t0 = tl; t0 < cnt; t0 += kLjTeam * kBatch) {
-      unsigned e[kBatch];
-      T4 pj[kBatch];
+    const int4* __restrict__ row4 = reinterpret_cast<const int4*>(S.nbr + (size_t)i * S.maxnb);
+    int4 en = __ldg(row4);  // entries of the next group (prefetched one group ahead)
+    for (int t0 = 0; t0 < cnt; t0 += kGroup) {
+      const int4 ea = en;
+      if (t0 + kGroup < cnt) en = __ldg(row4 + (t0 >> 2) + 1);
+      const unsigned e[kGroup] = {(unsigned)ea.x, (unsigned)ea.y, (unsigned)ea.z, (unsigned)ea.w};
+      T4 pj[kGroup];
 #pragma unroll
-      for (int u = 0; u < kBatch; ++u) {
-        const int t = t0 + u * kLjTeam;
-        e[u] = (t < cnt) ? (unsigned)__ldg(row + t) : (unsigned)i;  // padding entry: i itself
-      }
+      for (int u = 0; u < kGroup; ++u) pj[u] = ldg4(P + ((t0 + u < cnt) ? (int)(e[u] & kNbrMask) : i));
+      T sx = 0, sy = 0, sz = 0;
 #pragma unroll
-      for (int u = 0; u < kBatch; ++u) pj[u] = ldg4(P + (e[u] & kNbrMask));
-#pragma unroll
-      for (int u = 0; u < kBatch; ++u) {
-        const unsigned c = e[u] >> kNbrShift;
-        const T sx = fma((T)(c & 3u), edge, -edge);
-        const T sy = fma((T)((c >> 2) & 3u), edge, -edge);
-        const T sz = fma((T)(c >> 4), edge, -edge);
-        const T dx = (pj[u].x - pi.x) + sx;
-        const T dy = (pj[u].y - pi.y) + sy;
-        const T dz = (pj[u].z - pi.z) + sz;
-        const T r2 = dx * dx + dy * dy + dz * dz;
-        bool in = (r2 <= rcsq - g2) && (t0 + u * kLjTeam < cnt);
-        if ((r2 < rcsq + g2) && (r2 > rcsq - g2) && (t0 + u * kLjTeam < cnt)) {  // guard band: exact FP64
-          atomicAdd(&S.ctr[CTR_GUARD], 1ull);
-          in = exact_within(X, n, i, (int)(e[u] & kNbrMask), S.L, S.rc2sq);
-        }
-        const T r2s = in ? r2 : (T)1;
-        const T ir2 = recip_fast<T>(r2s);
+      for (int u = 0; u < kGroup; ++u) {
+        const bool valid = t0 + u < cnt;
+        const T4 o = s_off[valid ? (e[u] >> kNbrShift) : kCentreCode];
+        const T dx = (pj[u].x - pi.x) + o.x;
+        const T dy = (pj[u].y - pi.y) + o.y;
+        const T dz = (pj[u].z - pi.z) + o.z;
+        const T r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+        const bool in = valid && r2 <= rcsq - g2;
+        band |= (valid && r2 > rcsq - g2 && r2 < rcsq + g2) ? 1u : 0u;  // decided after the loop, exactly
+        const T ir2 = recip_fast<T>(in ? r2 : (T)1);
         const T sr2 = sig2 * ir2;
         const T sr6 = sr2 * sr2 * sr2;
         const T sr12 = sr6 * sr6;
         const T g = in ? eps24 * (sr12 + sr12 - sr6) * ir2 : (T)0;  // F_i = -g d
-        fx = fma(-g, dx, fx);
-        fy = fma(-g, dy, fy);
-        fz = fma(-g, dz, fz);
+        sx = fma(-g, dx, sx);
+        sy = fma(-g, dy, sy);
+        sz = fma(-g, dz, sz);
         if (energy) {
           uu_t += in ? eps4 * (sr12 - sr6) : (T)0;
-          ww_t += g * r2;
+          ww_t = fma(g, r2, ww_t);
+        }
+      }
+      // groups of (at most 8 terms: two groups of four) are summed plainly, then added exactly
+      if ((t0 & 4) || t0 + kGroup >= cnt) {
+        f.add(sx + px, sy + py, sz + pz);
+        px = py = pz = (T)0;
+      } else {
+        px = sx;
+        py = sy;
+        pz = sz;
+      }
+    }
+    if (band) {
+      // Rare: the pairs whose r^2 fell in the guard band (left out above) are decided in FP64 with the
+      // CPU definition's operation order, and the ones inside the cutoff are added.
+      for (int t = 0; t < cnt; ++t) {
+        const unsigned e = (unsigned)S.nbr[(size_t)i * S.maxnb + t];
+        const int j = (int)(e & kNbrMask);
+        const T4 pj = P[j];
+        const T4 o = s_off[e >> kNbrShift];
+        const T dx = (pj.x - pi.x) + o.x, dy = (pj.y - pi.y) + o.y, dz = (pj.z - pi.z) + o.z;
+        const T r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+        if (!(r2 > rcsq - g2 && r2 < rcsq + g2)) continue;
+        atomicAdd(&S.ctr[CTR_GUARD], 1ull);
+        if (!exact_within(X, n, i, j, S.L, S.rc2sq)) continue;
+        const T ir2 = recip_fast<T>(r2);
+        const T sr2 = sig2 * ir2;
+        const T sr6 = sr2 * sr2 * sr2;
+        const T sr12 = sr6 * sr6;
+        const T g = eps24 * (sr12 + sr12 - sr6) * ir2;
+        f.add(-g * dx, -g * dy, -g * dz);
+        if (energy) {
+          uu_t += eps4 * (sr12 - sr6);
+          ww_t = fma(g, r2, ww_t);
         }
       }
     }
   }
-  Acc3<T> f;
-  AccS<T> u, w;
-  f.add(fx, fy, fz);
-  if (energy) {
-    u.add(uu_t);
-    w.add(ww_t);
-  }
-  // combine the team's shares (all lanes take part in the shuffles); the (hi, lo) results
-  // are parked in shared memory and converted to FP64 by the full-warp epilogue below.
-  // On GB300 an FP64 instruction costs 64 FP32 issue slots, so the FP64 work runs on
-  // full warps: warp 0 updates the block's 32 particles with one lane each.
-  constexpr int kPer = 256 / kLjTeam;
-  __shared__ T sFh[3][kPer], sFl[3][kPer], sEh[2][kPer], sEl[2][kPer];
-  const int team = threadIdx.x / kLjTeam;
-  if constexpr (sizeof(T) == 4) {
+  bool bad = false;
+  if (active) {
+    double Fq[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) team_sum<T>(f.c[a]);
-    if (energy) {
-      team_sum<T>(u.c);
-      team_sum<T>(w.c);
+    for (int a = 0; a < 3; ++a) {
+      Fq[a] = f.get(a);
+      S.f2[a * n + i] = Fq[a];
+      bad |= !finite_bits(Fq[a]);
     }
-    if (tl == 0) {
+    if (kind == LJ_MID) {
+      // closing half kick of this inner step + opening half kick of the next, then the drift
+      const double c = S.dt_in * S.inv_mass;
+      double xn[3], rel[3];
+      double* Xo = S.X[it.buf ^ 1];
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        sFh[a][team] = f.c[a].hi;
-        sFl[a][team] = f.c[a].lo;
+        const double vv = fma(c, Fq[a], S.v[a * n + i]);
+        S.v[a * n + i] = vv;
+        xn[a] = fma(S.dt_in, vv, X[a * n + i]);
+        Xo[a * n + i] = xn[a];
+        bad |= !finite_bits(vv);
       }
-      sEh[0][team] = active && energy ? u.c.hi : 0.f;
-      sEl[0][team] = active && energy ? u.c.lo : 0.f;
-      sEh[1][team] = active && energy ? w.c.hi : 0.f;
-      sEl[1][team] = active && energy ? w.c.lo : 0.f;
-    }
-  } else {
-    double Fd[3] = {f.get(0), f.get(1), f.get(2)};
-    double ud = energy ? u.get() : 0.0, wd = energy ? w.get() : 0.0;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) team_sum_d(Fd[a]);
-    if (energy) {
-      team_sum_d(ud);
-      team_sum_d(wd);
-    }
-    if (tl == 0) {
+      cell_rel(S, S.pcell[i], xn, rel);
+      store_pos<T>(S, it.buf ^ 1, i, rel, true);
+    } else if (kind == LJ_LAST) {
+      const double c = 0.5 * S.dt_in * S.inv_mass;
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        sFh[a][team] = Fd[a];
-        sFl[a][team] = 0.0;
+        const double vv = fma(c, Fq[a], S.v[a * n + i]);
+        S.v[a * n + i] = vv;
+        bad |= !finite_bits(vv);
       }
-      sEh[0][team] = active ? ud : 0.0;
-      sEl[0][team] = 0.0;
-      sEh[1][team] = active ? wd : 0.0;
-      sEl[1][team] = 0.0;
     }
   }
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    const int q = it.begin + threadIdx.x;
-    if (q < n) {
-      double Fq[3];
-#pragma unroll
-      for (int a = 0; a < 3; ++a) Fq[a] = (double)sFh[a][threadIdx.x] + (double)sFl[a][threadIdx.x];
-      bool bad = false;
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        S.f2[a * n + q] = Fq[a];
-        bad |= !finite_bits(Fq[a]);
-      }
-      if (kind == LJ_MID) {
-        // closing half kick of this inner step + opening half kick of the next, then the drift
-        const double c = S.dt_in * S.inv_mass;
-        double xn[3], rel[3];
-        double* Xo = S.X[it.buf ^ 1];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          const double vv = fma(c, Fq[a], S.v[a * n + q]);
-          S.v[a * n + q] = vv;
-          xn[a] = fma(S.dt_in, vv, X[a * n + q]);
-          Xo[a * n + q] = xn[a];
-          bad |= !finite_bits(vv);
-        }
-        cell_rel(S, S.pcell[q], xn, rel);
-        store_pos<T>(S, it.buf ^ 1, q, rel, true);
-      } else if (kind == LJ_LAST) {
-        const double c = 0.5 * S.dt_in * S.inv_mass;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          const double vv = fma(c, Fq[a], S.v[a * n + q]);
-          S.v[a * n + q] = vv;
-          bad |= !finite_bits(vv);
-        }
-      }
-      if (bad) atomicOr(&S.flags[FLG_ERR], ERR_NONFINITE);
-    }
-    if (energy) {  // every pair appears in both members' lists: halve
-      const double us = warp_sum(0.5 * ((double)sEh[0][threadIdx.x] + (double)sEl[0][threadIdx.x]));
-      const double ws = warp_sum(0.5 * ((double)sEh[1][threadIdx.x] + (double)sEl[1][threadIdx.x]));
-      if (threadIdx.x == 0) {
-        atomicAdd(&S.acc[ACC_U2], us);
-        atomicAdd(&S.acc[ACC_W2], ws);
-      }
+  if (bad) atomicOr(&S.flags[FLG_ERR], ERR_NONFINITE);
+  if (energy) {  // every pair appears in both members' lists: halve
+    const double us = block_sum(active ? 0.5 * (double)uu_t : 0.0, red);
+    const double ws = block_sum(active ? 0.5 * (double)ww_t : 0.0, red);
+    if (threadIdx.x == 0) {
+      atomicAdd(&S.acc[ACC_U2], us);
+      atomicAdd(&S.acc[ACC_W2], ws);
     }
   }
 }

@@ -14,7 +14,7 @@ constexpr int kPairTable = kMaxHalf * (kMaxHalf - 1) / 2;  // (j, k) pairs, k-ma
 constexpr int kAtmWarps = 8;
 constexpr int kAtmThreads = 32 * kAtmWarps;
 constexpr int kQueue = 256;         // per-warp queue of accepted neighbour pairs (j, k)
-constexpr int kLjTeam = 8;          // lanes cooperating on one particle's pair list
+constexpr int kLjPer = 64;          // particles (one thread each) per CTA of the LJ kernel
 constexpr int kListWarps = 4;       // warps per CTA of the pair-list build
 constexpr int kHalfCap = 64;        // triplet half list per particle (neighbours above it within r_c3)
 

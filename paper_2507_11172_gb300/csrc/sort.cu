@@ -208,55 +208,74 @@ __global__ void __launch_bounds__(32 * kListWarps)
   const int i0 = S.cell_start[b];
   const double* Xa = S.X[it.buf ^ 1];
   double* X = S.X[it.buf];
+  // staged slot of a list entry: its index plus the offset of its stencil cell in the staging
+  __shared__ int st_delta[27];
+  if (threadIdx.x < 27) st_delta[threadIdx.x] = st_begin[threadIdx.x] - S.cell_start[st_cell[threadIdx.x]];
+  __syncthreads();
   const T rc3 = (T)S.rc3sq, g3 = (T)S.guard3;
   for (int ib = warp; ib < nbase; ib += kListWarps) {
     const int islot = st_begin[13] + ib;
     const int i = i0 + ib;
     const T4 pi = sp[islot];
-    const int qzi = sqz[islot];
-    int cnt = 0, mh = 0;
+    int cnt = 0;
     int* row = S.nbr + (size_t)i * S.maxnb;
-    int* hrow = S.half + (size_t)i * kHalfCap;
+    // pass 1: every staged particle within the list radius
     for (int t0 = 0; t0 < nstaged; t0 += 32) {
       const int t = t0 + lane;
-      bool ok = false, half = false, band = false;
+      bool ok = false;
       if (t < nstaged && t != islot) {
         const T4 q = sp[t];
         const T dx = q.x - pi.x, dy = q.y - pi.y, dz = q.z - pi.z;
-        const T r2 = dx * dx + dy * dy + dz * dz;
-        ok = r2 <= rl;
-        if (ok) {
-          // above i: the upper cell layer, or the same layer with larger fixed-point z (ties: index)
-          const unsigned e = (unsigned)sj[t];
-          const unsigned lay = e >> (kNbrShift + 4);
-          const int dqz = (int)((unsigned)sqz[t] - (unsigned)qzi);
-          const bool above = lay == 2u || (lay == 1u && (dqz > 0 || (dqz == 0 && (int)(e & kNbrMask) > i)));
-          if (above) {
-            half = r2 <= rc3 - g3;
-            band = !half && r2 <= rc3 + g3;
-          }
-        }
-      }
-      if (__any_sync(0xffffffffu, band)) {
-        if (band) {
-          atomicAdd(&S.ctr[CTR_GUARD], 1ull);
-          half = exact_within(Xa, n, i, (int)((unsigned)sj[t] & kNbrMask), S.L, S.rc3sq);
-        }
+        ok = dx * dx + dy * dy + dz * dz <= rl;
       }
       const unsigned bal = __ballot_sync(0xffffffffu, ok);
       const int pos = cnt + __popc(bal & lt);
       if (ok && pos < S.maxnb) row[pos] = sj[t];
       cnt += __popc(bal);
-      const unsigned balh = __ballot_sync(0xffffffffu, half);
-      const int hpos = mh + __popc(balh & lt);
-      if (half && hpos < kHalfCap) hrow[hpos] = sj[t];
-      mh += __popc(balh);
     }
     if (lane == 0) {
       if (cnt > S.maxnb) atomicOr(&S.flags[FLG_ERR], ERR_NBR_CAP);
       S.nbr_cnt[i] = min(cnt, S.maxnb);
-      S.half_cnt[i] = mh;  // more than kHalfCap: the triplet kernel reports ERR_HALF_CAP
     }
+    cnt = min(cnt, S.maxnb);
+    __syncwarp();  // the row written above is read back below by other lanes
+    // pass 2: the triplet half list among the list entries
+    const int qzi = sqz[islot];
+    int* hrow = S.half + (size_t)i * kHalfCap;
+    int mh = 0;
+    for (int t0 = 0; t0 < cnt; t0 += 32) {
+      const int t = t0 + lane;
+      bool half = false, band = false;
+      unsigned e = 0u;
+      if (t < cnt) {
+        e = (unsigned)row[t];
+        const unsigned code = e >> kNbrShift;
+        const int l = (int)(code & 3u) + 3 * (int)((code >> 2) & 3u) + 9 * (int)(code >> 4);
+        const int slot = (int)(e & kNbrMask) + st_delta[l];
+        // above i: the upper cell layer, or the same layer with larger fixed-point z (ties: index)
+        const unsigned lay = code >> 4;
+        const int dqz = (int)((unsigned)sqz[slot] - (unsigned)qzi);
+        const bool above = lay == 2u || (lay == 1u && (dqz > 0 || (dqz == 0 && (int)(e & kNbrMask) > i)));
+        if (above) {
+          const T4 q = sp[slot];
+          const T dx = q.x - pi.x, dy = q.y - pi.y, dz = q.z - pi.z;
+          const T r2 = dx * dx + dy * dy + dz * dz;
+          half = r2 <= rc3 - g3;
+          band = !half && r2 <= rc3 + g3;
+        }
+      }
+      if (__any_sync(0xffffffffu, band)) {
+        if (band) {
+          atomicAdd(&S.ctr[CTR_GUARD], 1ull);
+          half = exact_within(Xa, n, i, (int)(e & kNbrMask), S.L, S.rc3sq);
+        }
+      }
+      const unsigned balh = __ballot_sync(0xffffffffu, half);
+      const int hpos = mh + __popc(balh & lt);
+      if (half && hpos < kHalfCap) hrow[hpos] = (int)e;
+      mh += __popc(balh);
+    }
+    if (lane == 0) S.half_cnt[i] = mh;  // more than kHalfCap: the triplet kernel reports ERR_HALF_CAP
   }
   // every particle of b: permuted state back into place
   for (int ib = threadIdx.x; ib < st_cnt[13]; ib += blockDim.x) {
