@@ -242,7 +242,7 @@ def run_ours(args):
         "profiled_pass_ms_per_step": q32["ms"] / K,
         "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved_tflops / FP32_PEAK_TFLOPS, "traffic": None,
-                     "kernel": ("k_atm_pa<float>" if q32["kernel"] == 1 else "k_atm<float>"),
+                     "kernel": {0: "k_atm<float>", 1: "k_atm_pa<float>", 2: "k_atm_rot<float>"}.get(q32["kernel"]),
                      "note": f"{ATM_FLOPS_PER_TRIPLET} flop per interacting triplet; peak = 152 SM x 128 "
                              "FP32 lanes x 2 x 2.07 GHz"},
         "clocks": clk,

@@ -78,8 +78,18 @@ struct ZrSmem {
   T4 pn[kZrMax];            // partners of the current phase, doubled (pn[t + m] = pn[t]), far dummies after;
                             // the half list is built here: (d_v, |d_v|^2)
   T4 slot[2][kZrMax];       // partner shares (G, W) of odd and even steps, in pn's index space
-  T4 nd[kZrMax];            // copy of the half list (lists longer than 32 nodes)
-  T4 tot[kZrMax];           // per-node totals across phases (lists longer than 32 nodes)
+  union {
+    struct {
+      T4 nd[kZrMax];        // copy of the half list (lists longer than 32 nodes)
+      T4 tot[kZrMax];       // per-node totals across phases (lists longer than 32 nodes)
+    };
+    struct {                // lists of at most 32 nodes, FP32: partner pairs of consecutive steps,
+      T px[kZrMax][2];      // (pn[t].x, pn[t + 1].x), likewise y, z and |d|^2
+      T py[kZrMax][2];
+      T pz[kZrMax][2];
+      T pw[kZrMax][2];
+    };
+  };
   int nidx[kZrMax];         // sorted index of each node
   int4 cq[kZrMax];          // prefetched fixed-point positions of the next base's half list
   unsigned row[2][kZrMax];  // prefetched half lists (pair-list entries) of the next two bases
@@ -274,6 +284,128 @@ __device__ __forceinline__ void zr_phase(const ZrK<T>& K, ZrSmem<T>& w, const ty
   }
 }
 
+// ---------------------------------------------------------------- paired steps (FP32, m <= 32)
+// The rotation over m <= 32 nodes (node v on lane v) with two consecutive steps s, s + 1 evaluated
+// together in the two halves of packed FP32x2 instructions (Blackwell FFMA2/FADD2/FMUL2).  Partner
+// data of both steps comes from pair arrays in shared memory (px[t] = (pn[t].x, pn[t + 1].x), ...).
+// The partner shares do not go through shared memory: they travel with the partners.  In iteration
+// k (steps 2k+1, 2k+2) lane v holds the running shares of nodes v + 2k + 1 (first half) and
+// v + 2k + 2 (second half); those nodes are the partners of lane v - 2 in iteration k + 1, so the
+// shares move two lanes down after each iteration (shuffles on the ring of m lanes), and after the
+// last one they are delivered to the nodes' own lanes.  Steps 1 .. floor(m / 2); for even m the last
+// one pairs v with v + m / 2 on lanes v < m / 2 only.  Returns false, with nothing accumulated, if
+// some pair fell in the guard band around r_c^2 (the caller repeats with exact decisions).
+struct ZrOut32 {
+  float W, Gx, Gy, Gz, cnt, u;
+};
+__device__ __forceinline__ float2 f2s(float x) { return make_float2(x, x); }
+
+template <bool kE>
+__device__ __forceinline__ bool zr_self_f2(const ZrK<float>& K, ZrSmem<float>& w, const float4 J, const int m,
+                                           const int lane, ZrOut32& o) {
+  const float rcsq = K.rcsq, g = K.g;
+  const int T = m >> 1;                 // steps
+  const int K2 = (T + 1) >> 1;          // iterations (pairs of steps)
+  const bool real = lane < m;
+  const bool even = (m & 1) == 0;
+  const float2 jx = f2s(J.x), jy = f2s(J.y), jz = f2s(J.z), ja = f2s(J.w), ja2 = f2s(J.w + J.w);
+  const float2 nrc = f2s(-rcsq), m2 = f2s(-2.f), h25 = f2s(2.5f), c4 = f2s(4.f);
+  float2 W = f2s(0.f), Gx = W, Gy = W, Gz = W, cnt = W, uu = W;
+  float2 tW = W, tx = W, ty = W, tz = W;  // travelling shares of this lane's two partners
+  float dmin = 1e30f;
+  const int pass = real ? (lane + 2 < m ? lane + 2 : lane + 2 - m) : lane;
+  auto iter = [&](const int s1, const float2 off) {
+    const int t = lane + s1;
+    const float2 px = *reinterpret_cast<const float2*>(w.px[t]);
+    const float2 py = *reinterpret_cast<const float2*>(w.py[t]);
+    const float2 pz = *reinterpret_cast<const float2*>(w.pz[t]);
+    const float2 b = *reinterpret_cast<const float2*>(w.pw[t]);
+    const float2 ex = __fadd2_rn(px, make_float2(-jx.x, -jx.y));
+    const float2 ey = __fadd2_rn(py, make_float2(-jy.x, -jy.y));
+    const float2 ez = __fadd2_rn(pz, make_float2(-jz.x, -jz.y));
+    float2 c = __ffma2_rn(ez, ez, __ffma2_rn(ey, ey, __fmul2_rn(ex, ex)));
+    c = __fadd2_rn(c, off);
+    const float2 tt = __fadd2_rn(c, nrc);
+    dmin = fminf(dmin, fminf(fabsf(tt.x), fabsf(tt.y)));
+    const float2 okf = make_float2(tt.x <= g ? 1.f : 0.f, tt.y <= g ? 1.f : 0.f);
+    const float2 ab = __fmul2_rn(ja, b);
+    const float2 q = __fmul2_rn(ab, c);
+    float2 u;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(u.x) : "f"(q.x));
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(u.y) : "f"(q.y));
+    // one Newton-Raphson step: u (1.5 - 0.5 q u^2)
+    u = __fmul2_rn(u, __ffma2_rn(__fmul2_rn(f2s(-0.5f), q), __fmul2_rn(u, u), f2s(1.5f)));
+    const float2 ww = __fmul2_rn(u, u);
+    const float2 t3 = __fmul2_rn(ww, u);
+    const float2 t5 = __fmul2_rn(t3, ww);
+    const float2 sum = __fadd2_rn(__fadd2_rn(ja, b), c);
+    const float2 Aa = __ffma2_rn(m2, c, sum);   // a + b - c
+    const float2 Bb = __ffma2_rn(m2, b, sum);   // a - b + c
+    const float2 Cc = __ffma2_rn(m2, ja, sum);  // -a + b + c
+    const float2 AB = __fmul2_rn(Aa, Bb), AC = __fmul2_rn(Aa, Cc), BC = __fmul2_rn(Bb, Cc);
+    const float2 P = __fmul2_rn(AB, Cc);
+    const float2 Pa = __ffma2_rn(ja2, Cc, make_float2(-AB.x, -AB.y));
+    const float2 Pb = __ffma2_rn(__fadd2_rn(b, b), Bb, make_float2(-AC.x, -AC.y));
+    const float2 Pc = __ffma2_rn(__fadd2_rn(c, c), Aa, make_float2(-BC.x, -BC.y));
+    const float2 Pw = __fmul2_rn(P, ww);
+    const float2 H = __ffma2_rn(h25, Pw, c4);
+    const float2 nH = make_float2(-H.x, -H.y);
+    const float2 kk = __fmul2_rn(t5, okf);
+    const float2 pa2 = __fmul2_rn(kk, __ffma2_rn(__fmul2_rn(b, c), nH, Pa));
+    const float2 pb2 = __fmul2_rn(kk, __ffma2_rn(__fmul2_rn(ja, c), nH, Pb));
+    const float2 pc2 = __fmul2_rn(kk, __ffma2_rn(ab, nH, Pc));
+    cnt = __fadd2_rn(cnt, okf);
+    if constexpr (kE) uu = __ffma2_rn(__fmul2_rn(t3, okf), __ffma2_rn(f2s(0.375f), Pw, f2s(1.f)), uu);
+    W = __fadd2_rn(W, pa2);
+    Gx = __ffma2_rn(pc2, ex, Gx);
+    Gy = __ffma2_rn(pc2, ey, Gy);
+    Gz = __ffma2_rn(pc2, ez, Gz);
+    const float2 npc = make_float2(-pc2.x, -pc2.y);
+    tW = __fadd2_rn(tW, pb2);
+    tx = __ffma2_rn(npc, ex, tx);
+    ty = __ffma2_rn(npc, ey, ty);
+    tz = __ffma2_rn(npc, ez, tz);
+  };
+  auto shift = [&](float2& v, int src) {
+    v.x = __shfl_sync(0xffffffffu, v.x, src);
+    v.y = __shfl_sync(0xffffffffu, v.y, src);
+  };
+  const float2 zero2 = f2s(0.f), big = f2s(1e6f);
+  const float2 offr = real ? zero2 : big;
+  int k = 0;
+#pragma unroll 1
+  for (; k < K2 - 1; ++k) {  // full iterations: both steps on every lane with a node
+    iter(2 * k + 1, offr);
+    shift(tW, pass);
+    shift(tx, pass);
+    shift(ty, pass);
+    shift(tz, pass);
+  }
+  // last iteration: s1 = 2k + 1 <= T; s2 = s1 + 1 exists iff s2 <= T; the step T is the half step
+  // (lanes v < m / 2) when m is even
+  const int s1 = 2 * k + 1, s2 = s1 + 1;
+  const bool half_ok = lane < (m >> 1);
+  const bool v1 = real && (!(even && s1 == T) || half_ok);
+  const bool v2 = real && s2 <= T && (!(even && s2 == T) || half_ok);
+  iter(s1, make_float2(v1 ? 0.f : 1e6f, v2 ? 0.f : 1e6f));
+  if (__any_sync(0xffffffffu, dmin <= g)) return false;
+  // deliver the travelling shares to their nodes' lanes: node u's first-half share sits on lane
+  // u - s1, its second-half share on lane u - s2 (mod m)
+  const int d1 = real ? (lane - s1 >= 0 ? lane - s1 : lane - s1 + m) : lane;
+  const int d2 = real ? (lane - s2 >= 0 ? lane - s2 : lane - s2 + m) : lane;
+  const float rW = __shfl_sync(0xffffffffu, tW.x, d1) + __shfl_sync(0xffffffffu, tW.y, d2);
+  const float rx = __shfl_sync(0xffffffffu, tx.x, d1) + __shfl_sync(0xffffffffu, tx.y, d2);
+  const float ry = __shfl_sync(0xffffffffu, ty.x, d1) + __shfl_sync(0xffffffffu, ty.y, d2);
+  const float rz = __shfl_sync(0xffffffffu, tz.x, d1) + __shfl_sync(0xffffffffu, tz.y, d2);
+  o.W = (W.x + W.y) + rW;
+  o.Gx = (Gx.x + Gx.y) + rx;
+  o.Gy = (Gy.x + Gy.y) + ry;
+  o.Gz = (Gz.x + Gz.y) + rz;
+  o.cnt = cnt.x + cnt.y;
+  o.u = uu.x + uu.y;
+  return true;
+}
+
 // ---------------------------------------------------------------- half-list nodes
 // FP32 node: displacement from the fixed-point positions (wrapping difference = exact minimum image,
 // one rounding to FP32, one scaling) and its squared length
@@ -414,15 +546,43 @@ __device__ __forceinline__ void zr_eval(const ZrK<T>& K, ZrSmem<T>& w, const int
       const int t = lane + 32 * h;
       if (t >= m) w.pn[t] = t < 2 * m ? w.pn[t - m] : zr_far<T>((T)-1);
     }
-    zr_clear_slots<T>(w, lane);
-    __syncwarp();
-    zr_phase<T, kE>(K, w, J, jid, ZrPart{0, m}, 1, (m - 1) >> 1, (m & 1) ? 0 : (m >> 1), lane, A);
-    cnt_sum += A.cnt;
-    if (kE) u_sum += A.u;
-    if (lane < m) {
-      const T4 s = zr_add4<T>(zr_add4<T>(w.slot[0][lane], w.slot[1][lane]),
-                              zr_add4<T>(w.slot[0][lane + m], w.slot[1][lane + m]));
-      zr_emit<T>(K, J, jid, A.W + s.w, A.Gx + s.x, A.Gy + s.y, A.Gz + s.z, fix, fiy, fiz);
+    bool done = false;
+    if constexpr (sizeof(T) == 4) {
+      // pair arrays of consecutive entries for the packed two-step rotation
+      __syncwarp();
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int t = lane + 32 * h;
+        const T4 p0 = w.pn[t], p1 = t + 1 < kZrMax ? w.pn[t + 1] : zr_far<T>((T)-1);
+        w.px[t][0] = p0.x;
+        w.px[t][1] = p1.x;
+        w.py[t][0] = p0.y;
+        w.py[t][1] = p1.y;
+        w.pz[t][0] = p0.z;
+        w.pz[t][1] = p1.z;
+        w.pw[t][0] = p0.w;
+        w.pw[t][1] = p1.w;
+      }
+      __syncwarp();
+      ZrOut32 r;
+      if (zr_self_f2<kE>(K, w, J, m, lane, r)) {
+        done = true;
+        cnt_sum += r.cnt;
+        if (kE) u_sum += r.u;
+        if (lane < m) zr_emit<T>(K, J, jid, r.W, r.Gx, r.Gy, r.Gz, fix, fiy, fiz);
+      }
+    }
+    if (!done) {  // FP64 path, or a pair in the guard band: shared-memory rotation (exact repeat if needed)
+      zr_clear_slots<T>(w, lane);
+      __syncwarp();
+      zr_phase<T, kE>(K, w, J, jid, ZrPart{0, m}, 1, (m - 1) >> 1, (m & 1) ? 0 : (m >> 1), lane, A);
+      cnt_sum += A.cnt;
+      if (kE) u_sum += A.u;
+      if (lane < m) {
+        const T4 s = zr_add4<T>(zr_add4<T>(w.slot[0][lane], w.slot[1][lane]),
+                                zr_add4<T>(w.slot[0][lane + m], w.slot[1][lane + m]));
+        zr_emit<T>(K, J, jid, A.W + s.w, A.Gx + s.x, A.Gy + s.y, A.Gz + s.z, fix, fiy, fiz);
+      }
     }
   } else {
     // halves A = nodes 0 .. ma-1, B = nodes ma .. m-1 (mb <= ma <= 32): within A, within B, A x B
@@ -569,11 +729,11 @@ __global__ void __launch_bounds__(32 * kZrWarps, sizeof(T) == 4 ? 7 : 4)
       zr_eval_any<T>(K, w, x0 + k, m, lane, energy, cnt, u);
     }
   }
-  // per-lane counts are exact small integers in T
-  const double c = warp_sum((double)cnt);
-  const double uu = energy ? warp_sum((double)u) : 0.0;
+  // per-lane counts are exact small integers in T (integer warp reduction: no FP64 instructions)
+  const unsigned c = __reduce_add_sync(0xffffffffu, (unsigned)cnt);
+  const double uu = energy ? (double)warp_sum_t<T>(u) : 0.0;
   if (lane == 0) {
-    atomicAdd(&s_cnt, (unsigned long long)(c + 0.5));
+    atomicAdd(&s_cnt, (unsigned long long)c);
     if (energy) atomicAdd(&s_u, uu);
     __threadfence_block();
     if (atomicAdd(&s_done, 1) == kZrWarps - 1) {  // last warp of the CTA

@@ -82,7 +82,7 @@ struct md_system {
   std::map<std::tuple<int, int>, CItem*> citems;        // (mode, buf)
   SItem* sitem = nullptr;
   std::vector<void*> item_allocs;
-  int nblocks = 0, nblocks_lj = 0;
+  int nblocks = 0;
   // execution
   cudaStream_t stream = nullptr;
   bool own_stream = false;
@@ -113,7 +113,7 @@ struct md_system {
 
 namespace {
 
-enum KTag { T_BIN = 1, T_SCATTER, T_LIST, T_LJ, T_COMB, T_START, T_KIN, T_ATMPA, T_ATMROT };
+enum KTag { T_BIN = 1, T_SCATTER, T_LIST, T_LJ, T_COMB, T_START, T_KIN, T_ATMPA, T_ATMROT, T_KICK };
 
 void free_items(md_system* s) {
   for (void* p : s->item_allocs) cudaFree(p);
@@ -184,6 +184,7 @@ md_status alloc_device(md_system* s) {
   size_t o_part = a.reserve(tsz * 27 * 3 * n);
   size_t o_f3a = a.reserve(4 * tsz * n);
   size_t o_ipos = a.reserve(16 * n);
+  size_t o_ccen = a.reserve(8 * (size_t)s->nc);
   size_t o_acc = a.reserve(8 * ACC_N), o_ctr = a.reserve(8 * CTR_N), o_flg = a.reserve(4 * FLG_N);
   size_t o_sx = a.reserve(24 * n), o_sv = a.reserve(24 * n), o_sf2 = a.reserve(24 * n), o_sf3 = a.reserve(24 * n);
   size_t o_sid = a.reserve(4 * n), o_scell = a.reserve(4 * n);
@@ -222,6 +223,13 @@ md_status alloc_device(md_system* s) {
   h.partial = m + o_part;
   h.f3acc = m + o_f3a;
   h.ipos = (int4*)(m + o_ipos);
+  {
+    std::vector<double> cen(s->nc);
+    for (int c = 0; c < s->nc; ++c) cen[c] = (c + 0.5) * s->edge;
+    CK(cudaMemcpyAsync(m + o_ccen, cen.data(), 8 * cen.size(), cudaMemcpyHostToDevice, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    h.ccen = (const double*)(m + o_ccen);
+  }
   h.acc = (double*)(m + o_acc);
   h.ctr = (unsigned long long*)(m + o_ctr);
   h.flags = (int*)(m + o_flg);
@@ -270,6 +278,7 @@ size_t arena_bytes(const md_system* s0) {
   a.reserve(tsz * 27 * 3 * n);
   a.reserve(4 * tsz * n);
   a.reserve(16 * n);
+  a.reserve(8 * (size_t)tmp.nc);
   a.reserve(8 * ACC_N);
   a.reserve(8 * CTR_N);
   a.reserve(4 * FLG_N);
@@ -353,7 +362,7 @@ PItem* pitems_for(md_system* s, int tag, int mode, int buf) {
                   : (tag == T_ATMPA)  ? kPaPerBlock
                   : (tag == T_ATMROT) ? rot_bases_per_item(s->precision)
                                       : kBlock;
-  const int nb = (tag == T_LJ)       ? s->nblocks_lj
+  const int nb = (tag == T_LJ)       ? (s->n + kLjPer - 1) / kLjPer
                  : (tag == T_ATMPA)  ? s->nblocks_pa
                  : (tag == T_ATMROT) ? s->nblocks_rot
                                      : s->nblocks;
@@ -378,8 +387,6 @@ CItem* citems_for(md_system* s, int mode, int buf) {
 // all item variants a call can use, created before any graph capture
 md_status prepare_items(md_system* s) {
   s->nblocks = (int)((s->n + kBlock - 1) / kBlock);
-  const int per_lj = kLjPer;
-  s->nblocks_lj = (int)((s->n + per_lj - 1) / per_lj);
   s->nblocks_pa = (int)((s->n + kPaPerBlock - 1) / kPaPerBlock);
   s->nblocks_rot = (int)((s->n + rot_bases_per_item(s->precision) - 1) / rot_bases_per_item(s->precision));
   for (int b = 0; b < 2; ++b) {
@@ -391,6 +398,8 @@ md_status prepare_items(md_system* s) {
       pitems_for(s, T_LJ, LJ_INIT | E, b);
       pitems_for(s, T_LJ, LJ_MID | E, b);
       pitems_for(s, T_LJ, LJ_LAST | E, b);
+      pitems_for(s, T_KICK, LJ_MID, b);
+      pitems_for(s, T_KICK, LJ_LAST, b);
       pitems_for(s, T_COMB, CB_INIT | E, b);
       pitems_for(s, T_COMB, CB_LAST | E, b);
       pitems_for(s, T_COMB, CB_CONT | E, b);
@@ -486,7 +495,8 @@ struct Plan {
   }
   template <typename T>
   void lj(int kind, int buf, bool energy) {
-    launch_lj<T>(L, pitems_for(s, T_LJ, kind | (energy ? M_ENERGY : 0), buf), s->nblocks_lj, kLjPer);
+    launch_lj<T>(L, pitems_for(s, T_LJ, kind | (energy ? M_ENERGY : 0), buf), (s->n + kLjPer - 1) / kLjPer);
+    if (kind != LJ_INIT) launch_kick<T>(L, pitems_for(s, T_KICK, kind, buf), s->nblocks);
   }
   template <typename T>
   void atm(int buf, bool energy, int ev) {
@@ -1167,8 +1177,8 @@ struct Request {
 };
 
 struct TickItems {
-  size_t bin = 0, scan = 0, list = 0, lj = 0, atm = 0, comb = 0;  // offsets (items) in the pools
-  int nbin = 0, nscan = 0, nlist = 0, nlj = 0, natm = 0, ncomb = 0;
+  size_t bin = 0, scan = 0, list = 0, lj = 0, kick = 0, atm = 0, comb = 0;  // offsets (items) in the pools
+  int nbin = 0, nscan = 0, nlist = 0, nlj = 0, nkick = 0, natm = 0, ncomb = 0;
 };
 
 }  // namespace
@@ -1262,8 +1272,10 @@ void enqueue_cycle(md_batch* b, const std::vector<TickItems>& ticks, bool with_s
     chk("scatter", t);
     launch_listbuild<T>(L, b->d_citems + it.list, it.nlist, b->smax_list);
     chk("listbuild", t);
-    launch_lj<T>(L, b->d_pitems + it.lj, it.nlj, kLjPer);
+    launch_lj<T>(L, b->d_pitems + it.lj, it.nlj);
     chk("lj", t);
+    launch_kick<T>(L, b->d_pitems + it.kick, it.nkick);
+    chk("kick", t);
     if (b->variant == 2)
       launch_atm_rot<T>(L, b->d_pitems + it.atm, it.natm);
     else if (b->variant == 1)
@@ -1380,6 +1392,13 @@ md_status batch_build(md_batch* b) {
         for (int q = 0; q < (int)r.s->n; q += kLjPer) pit.push_back(PItem{j, q, tab(KT_LJ), tt & 1});
       }
       ti.nlj = (int)(pit.size() - ti.lj);
+      ti.kick = pit.size();
+      for (int j = 0; j < ns; ++j) {
+        const Request& r = b->req[b->resident[j]];
+        const int tt = t % r.k;
+        for (int q = 0; q < (int)r.s->n; q += kBlock) pit.push_back(PItem{j, q, tab(KT_LJ), tt & 1});
+      }
+      ti.nkick = (int)(pit.size() - ti.kick);
       if (b->variant >= 1) {
         const int per = (b->variant == 1) ? kPaPerBlock : rot_bases_per_item(b->precision);
         ti.atm = pit.size();

@@ -71,17 +71,20 @@ __device__ __forceinline__ bool finite_bits(double x) {
   return ((unsigned long long)__double_as_longlong(x) & 0x7ff0000000000000ull) != 0x7ff0000000000000ull;
 }
 
-// cell-local coordinate of an FP64 position relative to the centre of cell
-// `cell`, folded to the nearest image (|rel| <= L/2)
+// cell-local coordinate of an FP64 position relative to the centre of cell `cell` (its cell at the
+// last binning).  Positions are folded into [0, L) only at a binning, together with the cell
+// assignment, so between two binnings x - centre stays within about half a cell edge plus the
+// displacement: no periodic fold is needed here.  One FP64 subtraction per axis (the centres come
+// from a table; on GB300 every FP64 instruction is costly).
 __device__ __forceinline__ void cell_rel(const SysDev& S, int cell, const double x[3], double rel[3]) {
-  int cc[3] = {cell % S.nc, (cell / S.nc) % S.nc, cell / (S.nc * S.nc)};
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    double r = x[a] - (cc[a] + 0.5) * S.edge;
-    if (r > S.half_L) r -= S.L;
-    if (r < -S.half_L) r += S.L;
-    rel[a] = r;
-  }
+  const int nc = S.nc;
+  const int cz = cell / (nc * nc);
+  const int r = cell - cz * nc * nc;
+  const int cy = r / nc;
+  const int cx = r - cy * nc;
+  rel[0] = x[0] - S.ccen[cx];
+  rel[1] = x[1] - S.ccen[cy];
+  rel[2] = x[2] - S.ccen[cz];
 }
 
 template <typename T>
@@ -101,11 +104,13 @@ __device__ __forceinline__ void store_pos(const SysDev& S, int buf, int i, const
 }
 
 // ============================================================== LJ pair kernel
-// One thread per particle i.  The thread walks i's pair-list row four entries at a time (one 16-byte
-// row load, prefetched a group ahead, then four position gathers in flight), adds the plain sum of
-// every eight pair forces to a compensated (hi, lo) accumulator with an error-free TwoSum, and then
-// applies the velocity-Verlet kick/drift of Algorithm 2 for i in FP64 (every lane of the warp busy).
-// The offset of a neighbour's cell (entry code, one of 27) comes from a shared-memory table.
+// One thread per particle i (F_i only: every pair is evaluated from both sides, no scatter).  The
+// thread walks i's pair-list row four entries at a time with a software pipeline: the row entries
+// of group g + 2 and the neighbour positions of group g + 1 are loaded while group g is evaluated.
+// The offset of a neighbour's cell (entry code, one of 27) comes from a shared-memory table; list
+// padding uses code 63, whose offset is far outside every cutoff.  The plain sum of every eight pair
+// forces is added to a compensated (hi, lo) accumulator with an error-free TwoSum.  The
+// velocity-Verlet kick/drift of Algorithm 2 follows in k_kick.
 
 // read-only cached load of a 4-vector (the position buffer read by a kernel is never written by it)
 __device__ __forceinline__ float4 ldg4(const float4* p) { return __ldg(p); }
@@ -120,22 +125,19 @@ template <> __device__ __forceinline__ float recip_fast<float>(float x) {
 }
 template <> __device__ __forceinline__ double recip_fast<double>(double x) { return 1.0 / x; }
 
-constexpr int kLjCodes = 43;  // entry codes (dx+1) | (dy+1) << 2 | (dz+1) << 4 span 0 .. 42
-constexpr unsigned kCentreCode = 1u | (1u << 2) | (1u << 4);
+constexpr unsigned kPadCode = 63u;  // code of a padding entry (offset far outside every cutoff)
 
 template <typename T>
 __global__ void __launch_bounds__(kLjPer, 14) k_lj(const SysDev* __restrict__ sys, const PItem* __restrict__ items) {
   using T4 = typename V4<T>::type;
-  constexpr int kGroup = 4;
-  __shared__ T4 s_off[kLjCodes];
-  __shared__ double red[32];
+  __shared__ T4 s_off[64];
+  __shared__ T red_u[kLjPer / 32], red_w[kLjPer / 32];
   const PItem it = items[blockIdx.x];
   const SysDev& S = sys[it.sys];
   const int mode = item_mode(S, it.mode);
   if (mode & M_SKIP) return;  // block-uniform: a block belongs to one system
-  const int kind = mode & M_KIND_MASK;
   const bool energy = (mode & M_ENERGY) != 0;
-  if (threadIdx.x < kLjCodes) {
+  if (threadIdx.x < 64) {
     const unsigned c = threadIdx.x;
     const T e = Par<T>::edge(S);
     T4 o;
@@ -143,6 +145,7 @@ __global__ void __launch_bounds__(kLjPer, 14) k_lj(const SysDev* __restrict__ sy
     o.y = fma((T)((c >> 2) & 3u), e, -e);
     o.z = fma((T)((c >> 4) & 3u), e, -e);
     o.w = (T)0;
+    if (c == kPadCode) o.x = o.y = o.z = (T)1e3;
     s_off[threadIdx.x] = o;
   }
   __syncthreads();
@@ -152,51 +155,64 @@ __global__ void __launch_bounds__(kLjPer, 14) k_lj(const SysDev* __restrict__ sy
   const T4* __restrict__ P = reinterpret_cast<const T4*>(S.pos[it.buf]);
   const double* __restrict__ X = S.X[it.buf];
   Acc3<T> f;
-  T px = 0, py = 0, pz = 0;  // plain sum of the previous group
-  unsigned band = 0;         // some pair fell in the guard band around r_c2^2
-  T uu_t = 0, ww_t = 0;      // energy and virial partials (FP32 sums are ample for the totals' tolerance)
+  T uu = 0, ww = 0;  // energy and virial partials (FP32 path: FP32 sums are ample for the totals' tolerance)
   if (active) {
     const T4 pi = P[i];
-    const T rcsq = Par<T>::rc2sq(S);
-    const T g2 = Par<T>::guard2(S);
+    const T rcsq = Par<T>::rc2sq(S), g2 = Par<T>::guard2(S);
+    const T lo = rcsq - g2;
     const T sig2 = Par<T>::sig2(S);
     const T eps24 = Par<T>::eps24(S), eps4 = Par<T>::eps4(S);
     const int cnt = S.nbr_cnt[i];
     const int4* __restrict__ row4 = reinterpret_cast<const int4*>(S.nbr + (size_t)i * S.maxnb);
-    int4 en = __ldg(row4);  // entries of the next group (prefetched one group ahead)
-    for (int t0 = 0; t0 < cnt; t0 += kGroup) {
-      const int4 ea = en;
-      if (t0 + kGroup < cnt) en = __ldg(row4 + (t0 >> 2) + 1);
-      const unsigned e[kGroup] = {(unsigned)ea.x, (unsigned)ea.y, (unsigned)ea.z, (unsigned)ea.w};
-      T4 pj[kGroup];
-#pragma unroll
-      for (int u = 0; u < kGroup; ++u) pj[u] = ldg4(P + ((t0 + u < cnt) ? (int)(e[u] & kNbrMask) : i));
+    const int4 pad = make_int4((int)(kPadCode << kNbrShift), (int)(kPadCode << kNbrShift),
+                               (int)(kPadCode << kNbrShift), (int)(kPadCode << kNbrShift));
+    // entries of a group, padded beyond the row's length
+    auto entries = [&](int t0) {
+      int4 e = t0 < cnt ? __ldg(row4 + (t0 >> 2)) : pad;
+      if (t0 + 1 >= cnt) e.y = pad.y;
+      if (t0 + 2 >= cnt) e.z = pad.z;
+      if (t0 + 3 >= cnt) e.w = pad.w;
+      return e;
+    };
+    auto gather = [&](const int4 e, T4* pj) {
+      pj[0] = ldg4(P + ((unsigned)e.x & kNbrMask));
+      pj[1] = ldg4(P + ((unsigned)e.y & kNbrMask));
+      pj[2] = ldg4(P + ((unsigned)e.z & kNbrMask));
+      pj[3] = ldg4(P + ((unsigned)e.w & kNbrMask));
+    };
+    int4 ea = entries(0), eb = entries(4);
+    T4 pa[4], pb[4];
+    gather(ea, pa);
+    T bmin = (T)1e30;        // smallest |r^2 - r_c^2| met: the guard band is checked once at the end
+    T px = 0, py = 0, pz = 0;  // plain sum of the previous group
+    for (int t0 = 0; t0 < cnt; t0 += 4) {
+      gather(eb, pb);  // positions of the next group
+      const int4 ec = entries(t0 + 8);
+      const unsigned e[4] = {(unsigned)ea.x, (unsigned)ea.y, (unsigned)ea.z, (unsigned)ea.w};
       T sx = 0, sy = 0, sz = 0;
 #pragma unroll
-      for (int u = 0; u < kGroup; ++u) {
-        const bool valid = t0 + u < cnt;
-        const T4 o = s_off[valid ? (e[u] >> kNbrShift) : kCentreCode];
-        const T dx = (pj[u].x - pi.x) + o.x;
-        const T dy = (pj[u].y - pi.y) + o.y;
-        const T dz = (pj[u].z - pi.z) + o.z;
+      for (int u = 0; u < 4; ++u) {
+        const T4 o = s_off[e[u] >> kNbrShift];
+        const T dx = (pa[u].x - pi.x) + o.x;
+        const T dy = (pa[u].y - pi.y) + o.y;
+        const T dz = (pa[u].z - pi.z) + o.z;
         const T r2 = fma(dz, dz, fma(dy, dy, dx * dx));
-        const bool in = valid && r2 <= rcsq - g2;
-        band |= (valid && r2 > rcsq - g2 && r2 < rcsq + g2) ? 1u : 0u;  // decided after the loop, exactly
-        const T ir2 = recip_fast<T>(in ? r2 : (T)1);
+        bmin = fmin(bmin, fabs(r2 - rcsq));
+        const T ir2 = recip_fast<T>(r2);
         const T sr2 = sig2 * ir2;
         const T sr6 = sr2 * sr2 * sr2;
         const T sr12 = sr6 * sr6;
-        const T g = in ? eps24 * (sr12 + sr12 - sr6) * ir2 : (T)0;  // F_i = -g d
+        const T g = r2 <= lo ? eps24 * (sr12 + sr12 - sr6) * ir2 : (T)0;  // F_i = -g d
         sx = fma(-g, dx, sx);
         sy = fma(-g, dy, sy);
         sz = fma(-g, dz, sz);
         if (energy) {
-          uu_t += in ? eps4 * (sr12 - sr6) : (T)0;
-          ww_t = fma(g, r2, ww_t);
+          uu += r2 <= lo ? eps4 * (sr12 - sr6) : (T)0;
+          ww = fma(g, r2, ww);
         }
       }
-      // groups of (at most 8 terms: two groups of four) are summed plainly, then added exactly
-      if ((t0 & 4) || t0 + kGroup >= cnt) {
+      // every eight terms (two groups) are summed plainly, then added exactly
+      if ((t0 & 4) || t0 + 4 >= cnt) {
         f.add(sx + px, sy + py, sz + pz);
         px = py = pz = (T)0;
       } else {
@@ -204,10 +220,14 @@ __global__ void __launch_bounds__(kLjPer, 14) k_lj(const SysDev* __restrict__ sy
         py = sy;
         pz = sz;
       }
+      ea = eb;
+      eb = ec;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) pa[u] = pb[u];
     }
-    if (band) {
-      // Rare: the pairs whose r^2 fell in the guard band (left out above) are decided in FP64 with the
-      // CPU definition's operation order, and the ones inside the cutoff are added.
+    if (bmin < g2) {
+      // Rare: pairs whose r^2 fell in the guard band around r_c2^2 (left out above) are decided in
+      // FP64 with the CPU definition's operation order; the ones inside the cutoff are added.
       for (int t = 0; t < cnt; ++t) {
         const unsigned e = (unsigned)S.nbr[(size_t)i * S.maxnb + t];
         const int j = (int)(e & kNbrMask);
@@ -215,7 +235,7 @@ __global__ void __launch_bounds__(kLjPer, 14) k_lj(const SysDev* __restrict__ sy
         const T4 o = s_off[e >> kNbrShift];
         const T dx = (pj.x - pi.x) + o.x, dy = (pj.y - pi.y) + o.y, dz = (pj.z - pi.z) + o.z;
         const T r2 = fma(dz, dz, fma(dy, dy, dx * dx));
-        if (!(r2 > rcsq - g2 && r2 < rcsq + g2)) continue;
+        if (!(r2 > lo && r2 < rcsq + g2)) continue;
         atomicAdd(&S.ctr[CTR_GUARD], 1ull);
         if (!exact_within(X, n, i, j, S.L, S.rc2sq)) continue;
         const T ir2 = recip_fast<T>(r2);
@@ -225,55 +245,82 @@ __global__ void __launch_bounds__(kLjPer, 14) k_lj(const SysDev* __restrict__ sy
         const T g = eps24 * (sr12 + sr12 - sr6) * ir2;
         f.add(-g * dx, -g * dy, -g * dz);
         if (energy) {
-          uu_t += eps4 * (sr12 - sr6);
-          ww_t = fma(g, r2, ww_t);
+          uu += eps4 * (sr12 - sr6);
+          ww = fma(g, r2, ww);
         }
       }
     }
-  }
-  bool bad = false;
-  if (active) {
-    double Fq[3];
+    bool bad = false;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      Fq[a] = f.get(a);
-      S.f2[a * n + i] = Fq[a];
-      bad |= !finite_bits(Fq[a]);
+      const double F = f.get(a);
+      S.f2[a * n + i] = F;
+      bad |= !finite_bits(F);
     }
-    if (kind == LJ_MID) {
-      // closing half kick of this inner step + opening half kick of the next, then the drift
-      const double c = S.dt_in * S.inv_mass;
-      double xn[3], rel[3];
-      double* Xo = S.X[it.buf ^ 1];
+    if (bad) atomicOr(&S.flags[FLG_ERR], ERR_NONFINITE);
+  }
+  if (energy) {  // every pair appears in both members' lists: halve
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const T us = warp_sum_t<T>(uu), ws = warp_sum_t<T>(ww);
+    if (lane == 0) {
+      red_u[warp] = us;
+      red_w[warp] = ws;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double ut = 0.0, wt = 0.0;
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const double vv = fma(c, Fq[a], S.v[a * n + i]);
-        S.v[a * n + i] = vv;
-        xn[a] = fma(S.dt_in, vv, X[a * n + i]);
-        Xo[a * n + i] = xn[a];
-        bad |= !finite_bits(vv);
+      for (int q = 0; q < kLjPer / 32; ++q) {
+        ut += (double)red_u[q];
+        wt += (double)red_w[q];
       }
-      cell_rel(S, S.pcell[i], xn, rel);
-      store_pos<T>(S, it.buf ^ 1, i, rel, true);
-    } else if (kind == LJ_LAST) {
-      const double c = 0.5 * S.dt_in * S.inv_mass;
+      atomicAdd(&S.acc[ACC_U2], 0.5 * ut);
+      atomicAdd(&S.acc[ACC_W2], 0.5 * wt);
+    }
+  }
+}
+
+// Velocity-Verlet kick/drift of Algorithm 2 after an LJ evaluation, one thread per particle (FP64):
+//   LJ_MID:  v += dt F2 / m (closing half kick of this inner step + opening half kick of the next),
+//            x += dt v, cell-local FP32 coordinates of the new positions, displacement check;
+//   LJ_LAST: v += dt/2 F2 / m (closing half kick before the three-body evaluation).
+template <typename T>
+__global__ void __launch_bounds__(256) k_kick(const SysDev* __restrict__ sys, const PItem* __restrict__ items) {
+  const PItem it = items[blockIdx.x];
+  const SysDev& S = sys[it.sys];
+  const int mode = item_mode(S, it.mode);
+  if (mode & M_SKIP) return;
+  const int kind = mode & M_KIND_MASK;
+  if (kind != LJ_MID && kind != LJ_LAST) return;
+  const int n = S.n;
+  const int i = it.begin + threadIdx.x;
+  if (i >= n) return;
+  bool bad = false;
+  if (kind == LJ_MID) {
+    const double c = S.dt_in * S.inv_mass;
+    const double* __restrict__ X = S.X[it.buf];
+    double* Xo = S.X[it.buf ^ 1];
+    double xn[3], rel[3];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const double vv = fma(c, Fq[a], S.v[a * n + i]);
-        S.v[a * n + i] = vv;
-        bad |= !finite_bits(vv);
-      }
+    for (int a = 0; a < 3; ++a) {
+      const double vv = fma(c, S.f2[a * n + i], S.v[a * n + i]);
+      S.v[a * n + i] = vv;
+      xn[a] = fma(S.dt_in, vv, X[a * n + i]);
+      Xo[a * n + i] = xn[a];
+      bad |= !finite_bits(vv);
+    }
+    cell_rel(S, S.pcell[i], xn, rel);
+    store_pos<T>(S, it.buf ^ 1, i, rel, true);
+  } else {
+    const double c = 0.5 * S.dt_in * S.inv_mass;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const double vv = fma(c, S.f2[a * n + i], S.v[a * n + i]);
+      S.v[a * n + i] = vv;
+      bad |= !finite_bits(vv);
     }
   }
   if (bad) atomicOr(&S.flags[FLG_ERR], ERR_NONFINITE);
-  if (energy) {  // every pair appears in both members' lists: halve
-    const double us = block_sum(active ? 0.5 * (double)uu_t : 0.0, red);
-    const double ws = block_sum(active ? 0.5 * (double)ww_t : 0.0, red);
-    if (threadIdx.x == 0) {
-      atomicAdd(&S.acc[ACC_U2], us);
-      atomicAdd(&S.acc[ACC_W2], ws);
-    }
-  }
 }
 
 // ============================================================== ATM triplet kernel
@@ -1175,8 +1222,8 @@ int atm_configure(int smax, int precision, int* smem_bytes) {
 
 // ---------------------------------------------------------------- launchers
 template <typename T>
-void launch_lj(const Launch& L, const PItem* items, int nitems, int block) {
-  if (nitems > 0) k_lj<T><<<nitems, block, 0, L.stream>>>(L.sys, items);
+void launch_lj(const Launch& L, const PItem* items, int nitems) {
+  if (nitems > 0) k_lj<T><<<nitems, kLjPer, 0, L.stream>>>(L.sys, items);
 }
 template <typename T>
 void launch_atm(const Launch& L, const CItem* items, int nitems, int grid, int smax) {
@@ -1201,6 +1248,13 @@ template void launch_atm_pa<float>(const Launch&, const PItem*, int);
 template void launch_atm_pa<double>(const Launch&, const PItem*, int);
 
 template <typename T>
+void launch_kick(const Launch& L, const PItem* items, int nitems) {
+  if (nitems > 0) k_kick<T><<<nitems, 256, 0, L.stream>>>(L.sys, items);
+}
+template void launch_kick<float>(const Launch&, const PItem*, int);
+template void launch_kick<double>(const Launch&, const PItem*, int);
+
+template <typename T>
 void launch_combine(const Launch& L, const PItem* items, int nitems, int block) {
   if (nitems > 0) k_combine<T><<<nitems, block, 0, L.stream>>>(L.sys, items);
 }
@@ -1212,8 +1266,8 @@ void launch_kinetic(const Launch& L, const PItem* items, int nitems, int block) 
   if (nitems > 0) k_kinetic<<<nitems, block, 0, L.stream>>>(L.sys, items);
 }
 
-template void launch_lj<float>(const Launch&, const PItem*, int, int);
-template void launch_lj<double>(const Launch&, const PItem*, int, int);
+template void launch_lj<float>(const Launch&, const PItem*, int);
+template void launch_lj<double>(const Launch&, const PItem*, int);
 template void launch_combine<float>(const Launch&, const PItem*, int, int);
 template void launch_combine<double>(const Launch&, const PItem*, int, int);
 template void launch_start<float>(const Launch&, const PItem*, int, int);

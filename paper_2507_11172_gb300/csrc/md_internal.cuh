@@ -14,7 +14,6 @@ constexpr int kPairTable = kMaxHalf * (kMaxHalf - 1) / 2;  // (j, k) pairs, k-ma
 constexpr int kAtmWarps = 8;
 constexpr int kAtmThreads = 32 * kAtmWarps;
 constexpr int kQueue = 256;         // per-warp queue of accepted neighbour pairs (j, k)
-constexpr int kLjPer = 64;          // particles (one thread each) per CTA of the LJ kernel
 constexpr int kListWarps = 4;       // warps per CTA of the pair-list build
 constexpr int kHalfCap = 64;        // triplet half list per particle (neighbours above it within r_c3)
 
@@ -68,8 +67,9 @@ struct SysDev {
   int *nbr, *nbr_cnt;         // [n][maxnb] row-major, [n]
   int *half, *half_cnt;       // [n][kHalfCap] triplet half list of each particle (pair-list entries), [n]
   void *partial;              // T [27][3][n] per-stencil-slot ATM partial forces
-  int4 *ipos;                 // [n] FP32 mode: positions of the last binning in fixed point (box = 2^32
-                              // units; x, y, z as wrapping 32-bit integers), NULL where unused
+  int4 *ipos;                 // [n] positions of the last binning in fixed point (box = 2^32 units;
+                              // x, y, z as wrapping 32-bit integers), NULL where unused
+  const double *ccen;         // [nc] cell centres along one axis: (c + 0.5) * edge
   void *f3acc;                // [n] float4 (FP32) or double [n][4]: rotation-kernel ATM force sums,
                               // zero between evaluations (the combine kernel clears what it reads)
   double *acc;                // [ACC_N]
@@ -255,6 +255,78 @@ __device__ __forceinline__ double block_sum(double v, double* smem32) {
   return r;
 }
 
+// ---------------------------------------------------------------- 27-cell stencil staging
+// Stencil of cell b (called by one full warp): for l = 0..26 (offset (l % 3 - 1, l / 3 % 3 - 1,
+// l / 9 - 1)) the particle count, first sorted index and the exclusive prefix of counts (staging
+// offset, st_begin[27] = total), and per pair-list entry code (dx+1) | (dy+1) << 2 | (dz+1) << 4 the
+// difference "staged slot - sorted index" of that cell.
+__device__ __forceinline__ void stencil_table(const SysDev& S, int b, int* st_begin, int* st_cnt, int* st_c0,
+                                              int* s_delta) {
+  const int lane = threadIdx.x & 31, nc = S.nc;
+  int cnt = 0, c0 = 0;
+  if (lane < 27) {
+    const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
+    const int bx = b % nc, by = (b / nc) % nc, bz = b / (nc * nc);
+    const int c = (((bz + dz + nc) % nc) * nc + (by + dy + nc) % nc) * nc + (bx + dx + nc) % nc;
+    c0 = S.cell_start[c];
+    cnt = S.cell_start[c + 1] - c0;
+  }
+  int incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (lane < 27) {
+    st_begin[lane] = incl - cnt;
+    st_cnt[lane] = cnt;
+    st_c0[lane] = c0;
+    const unsigned code = (unsigned)(lane % 3) | ((unsigned)((lane / 3) % 3) << 2) | ((unsigned)(lane / 9) << 4);
+    s_delta[code] = (incl - cnt) - c0;
+  }
+  if (lane == 26) st_begin[27] = incl;
+}
+// stencil cell of a staged slot (binary search over the staging offsets)
+__device__ __forceinline__ int stencil_cell_of(const int* st_begin, int slot) {
+  int lo = 0;
+#pragma unroll
+  for (int w = 16; w > 0; w >>= 1)
+    if (lo + w < 27 && st_begin[lo + w] <= slot) lo += w;
+  return lo;
+}
+// Positions of the 27 cells into sp[0 .. nstaged) relative to b's centre (cell-local coordinates of
+// buffer buf plus the cell offset); every thread of the CTA takes slots threadIdx.x + k blockDim.x,
+// loads first, so that all loads of a thread are in flight together.
+template <typename T>
+__device__ __forceinline__ void stage_cells(const SysDev& S, int buf, const int* st_begin, const int* st_c0,
+                                            int nstaged, typename V4<T>::type* sp) {
+  using T4 = typename V4<T>::type;
+  constexpr int kU = 4;
+  const T edge = Par<T>::edge(S);
+  const T4* __restrict__ P = reinterpret_cast<const T4*>(S.pos[buf]);
+  for (int s0 = threadIdx.x; s0 < nstaged; s0 += kU * blockDim.x) {
+    T4 h[kU];
+    int ls[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int slot = s0 + u * blockDim.x;
+      ls[u] = slot < nstaged ? stencil_cell_of(st_begin, slot) : 0;
+      if (slot < nstaged) h[u] = P[st_c0[ls[u]] + slot - st_begin[ls[u]]];
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int slot = s0 + u * blockDim.x;
+      if (slot < nstaged) {
+        const int l = ls[u];
+        h[u].x += (T)(l % 3 - 1) * edge;
+        h[u].y += (T)((l / 3) % 3 - 1) * edge;
+        h[u].z += (T)(l / 9 - 1) * edge;
+        sp[slot] = h[u];
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------------- launchers
 struct Launch {
   cudaStream_t stream;
@@ -270,7 +342,9 @@ template <typename T> void launch_scatter(const Launch& L, const PItem* items, i
 template <typename T> void launch_listbuild(const Launch& L, const CItem* items, int nitems, int smax);
 int listbuild_configure(int smax, int precision);
 // forces.cu
-template <typename T> void launch_lj(const Launch& L, const PItem* items, int nitems, int block);
+// LJ pair forces: items of kLjPer particles (one thread each)
+constexpr int kLjPer = 64;
+template <typename T> void launch_lj(const Launch& L, const PItem* items, int nitems);
 template <typename T> void launch_atm(const Launch& L, const CItem* items, int nitems, int grid, int smax);
 // staged-particle capacity of an ATM CTA: the particles within r_c of a base cell (edge >= r_c)
 // occupy at most the volume of about 21 cells (16 cells plus margin is sized for the typical mean
@@ -288,6 +362,8 @@ constexpr int rot_bases_per_item(int) { return 32; }
 template <typename T>
 void launch_atm_table(const Launch& L, const CItem* items, int nitems, int grid, int smax, const uint16_t* table);
 template <typename T> void launch_combine(const Launch& L, const PItem* items, int nitems, int block);
+// FP64 kick/drift after an LJ evaluation: items of 256 particles with the LJ kind as mode
+template <typename T> void launch_kick(const Launch& L, const PItem* items, int nitems);
 template <typename T> void launch_start(const Launch& L, const PItem* items, int nitems, int block);
 void launch_kinetic(const Launch& L, const PItem* items, int nitems, int block);
 void launch_nonfinite_check(const Launch& L, const PItem* items, int nitems, int block);
