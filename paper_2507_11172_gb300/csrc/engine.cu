@@ -353,6 +353,12 @@ I* upload_items(md_system* s, const std::vector<I>& v) {
   return d;
 }
 
+// number of items of an SM-interleaved particle launch of nb blocks (a multiple of the SM count)
+int padded_blocks(int nb) {
+  const int nsm = std::max(1, device_sm_count());
+  return nsm * ((nb + nsm - 1) / nsm);
+}
+
 PItem* pitems_for(md_system* s, int tag, int mode, int buf) {
   auto key = std::make_tuple(tag, mode, buf);
   auto it = s->pitems.find(key);
@@ -366,7 +372,20 @@ PItem* pitems_for(md_system* s, int tag, int mode, int buf) {
                  : (tag == T_ATMPA)  ? s->nblocks_pa
                  : (tag == T_ATMROT) ? s->nblocks_rot
                                      : s->nblocks;
-  for (int b = 0; b < nb; ++b) v.push_back(PItem{0, b * per, mode, buf});
+  if (tag == T_LJ || tag == T_ATMROT || tag == T_KICK) {
+    // Gather kernels: the block scheduler hands consecutive blocks to different SMs, so blocks
+    // b, b + nsm, b + 2 nsm, ... tend to share an SM.  Giving those blocks adjacent particle ranges
+    // keeps each SM's neighbour gathers within one region of the box (L1 reuse); the order of the
+    // items changes nothing else.
+    const int nsm = std::max(1, device_sm_count());
+    const int per_sm = (nb + nsm - 1) / nsm;
+    for (int b = 0; b < nsm * per_sm; ++b) {  // padded_blocks(nb) items; those past n do nothing
+      const int r = (b % nsm) * per_sm + b / nsm;
+      v.push_back(PItem{0, r * per, mode, buf});
+    }
+  } else {
+    for (int b = 0; b < nb; ++b) v.push_back(PItem{0, b * per, mode, buf});
+  }
   PItem* d = upload_items(s, v);
   s->pitems[key] = d;
   return d;
@@ -495,14 +514,15 @@ struct Plan {
   }
   template <typename T>
   void lj(int kind, int buf, bool energy) {
-    launch_lj<T>(L, pitems_for(s, T_LJ, kind | (energy ? M_ENERGY : 0), buf), (s->n + kLjPer - 1) / kLjPer);
-    if (kind != LJ_INIT) launch_kick<T>(L, pitems_for(s, T_KICK, kind, buf), s->nblocks);
+    launch_lj<T>(L, pitems_for(s, T_LJ, kind | (energy ? M_ENERGY : 0), buf),
+                 padded_blocks((s->n + kLjPer - 1) / kLjPer));
+    if (kind != LJ_INIT) launch_kick<T>(L, pitems_for(s, T_KICK, kind, buf), padded_blocks(s->nblocks));
   }
   template <typename T>
   void atm(int buf, bool energy, int ev) {
     if (ev >= 0) cudaEventRecord(s->events[2 * ev], L.stream);
     if (s->atm_variant == 2)
-      launch_atm_rot<T>(L, pitems_for(s, T_ATMROT, energy ? M_ENERGY : 0, buf), s->nblocks_rot);
+      launch_atm_rot<T>(L, pitems_for(s, T_ATMROT, energy ? M_ENERGY : 0, buf), padded_blocks(s->nblocks_rot));
     else if (s->atm_variant == 1)
       launch_atm_pa<T>(L, pitems_for(s, T_ATMPA, energy ? M_ENERGY : 0, buf), s->nblocks_pa);
     else
