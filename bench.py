@@ -246,7 +246,9 @@ def run_ours(args):
                      "note": f"{ATM_FLOPS_PER_TRIPLET} flop per interacting triplet; peak = 152 SM x 128 "
                              "FP32 lanes x 2 x 2.07 GHz"},
         "clocks": clk,
-        "gpu_launches": K * (w.k_inner + 7),
+        # per outer step: 2 LJ-phase launches (forces, kick/drift) per inner step, the sort (4), the
+        # triplet kernel and the combine; plus the opening kick of each call
+        "gpu_launches": K * (2 * w.k_inner + 6 + 1),
         "e2e": e2e,
     }
     if peaks:

@@ -190,6 +190,24 @@ def test_dense_cluster_grows_cell_capacity(gpu_lib, kernel):
     assert force_err(f2, f2r) <= 1e-5 and force_err(f3, f3r) <= 1e-5
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_half_lists_of_33_to_64_nodes(gpu_lib, prec):
+    """At density 1.15 a particle has about 75 neighbours within r_c = 2.5, so most half lists
+    (the neighbours above it) hold 33 to 64 nodes: the rotation kernel splits them into two
+    halves (rotations within each half and across the halves).  Forces, energy and the exact
+    triplet count must match the oracle, and the rotation kernel must stay selected."""
+    x, L = md_inputs.fcc_jitter(1000, 1.15, 0.05, 93)
+    f3r, u3r, _, cnt = oracle.atm_brute(x, L, NU, 2.5)
+    with gpu_lib.System.create(x, L, None, precision=prec, nu=NU, skin=0.1, atm_kernel=2) as s:
+        _, f3 = s.forces()
+        _, _, u3, _ = s.energy()
+        st = s.stats()
+    assert st["atm_kernel"] == 2
+    assert st["triplets_last"] == cnt
+    assert force_err(f3, f3r) <= TOL[prec]
+    assert abs(u3 - u3r) <= (1e-6 if prec == 0 else 1e-12) * abs(u3r)
+
+
 def test_long_half_lists_fall_back_to_the_cell_kernel(gpu_lib):
     """At density 1.7 some of 1500 particles have more than 64 neighbours within r_c = 2.5 on
     their side, more than the rotation kernel's half list holds: the call is replayed with the
