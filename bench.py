@@ -213,6 +213,22 @@ def run_ours(args):
             r3.md_destroy_system(h)
         del ctypes
 
+    # observables (Sec. 4.2.2): RDF pair counts over the pair list of the final positions (100 bins
+    # up to r_c2), timed through the C ABI call (synchronous)
+    obs_line = None
+    if rank == 0:
+        h = r3.md_create_system(w.x, w.L, w.v, 1.0, r3.MD_FP32, stream.cuda_stream)
+        try:
+            r3.md_set_potentials(h, 1.0, 1.0, w.rc2, w.nu, w.rc3)
+            r3.md_get_rdf(h, 100, w.rc2)
+            t0 = time.perf_counter()
+            for _ in range(5):
+                cnt = r3.md_get_rdf(h, 100, w.rc2)
+            rdf_ms = (time.perf_counter() - t0) / 5 * 1e3
+            obs_line = {"rdf_call_ms": rdf_ms, "rdf_pairs_below_rc": int(cnt.sum()), "rdf_bins": 100}
+        finally:
+            r3.md_destroy_system(h)
+
     peaks = {}
     if os.path.exists(PEAKS_FILE):
         peaks = json.load(open(PEAKS_FILE))
@@ -250,6 +266,7 @@ def run_ours(args):
         # triplet kernel and the combine; plus the opening kick of each call
         "gpu_launches": K * (2 * w.k_inner + 6 + 1),
         "e2e": e2e,
+        "observables": obs_line,
     }
     if peaks:
         line["measured_peaks"] = {"hbm_gbs": peaks.get("hbm_gbs"), "bf16_tflops": peaks.get("bf16_tflops")}

@@ -114,6 +114,17 @@ md_status md_get_forces(md_system *s, double *f2, double *f3);
  * NULL. */
 md_status md_get_energy(md_system *s, double *e_kin, double *u2, double *u3, double *virial);
 
+/* Radial distribution function pair counts at the current positions (the RDF of
+ * Sec. 4.2.2, before normalisation): counts[b] = number of unordered pairs {i, j}
+ * with b * dr <= r_ij < (b + 1) * dr, dr = r_max / nbins, r_ij the minimum-image
+ * distance computed in IEEE double as sqrt((dx*dx + dy*dy) + dz*dz) (the integer
+ * counts equal a plain CPU histogram of the positions md_get_state returns).
+ * 1 <= nbins <= 8192; 0 < r_max <= r_c2 + skin (the pair-list radius), else
+ * MD_ERR_ARG.  counts: host array of nbins, caller-owned.  g(r) for bin b is
+ * counts[b] / (n / 2 * (n / L^3) * 4/3 pi ((b+1)^3 - b^3) dr^3).  Evaluates the
+ * forces first if they are not cached (the counts then refer to the same positions). */
+md_status md_get_rdf(md_system *s, int nbins, double r_max, uint64_t *counts);
+
 /* Copy positions (folded into [0, L)) and velocities out / in, caller order,
  * n x 3 each; either may be NULL.  md_set_state invalidates cached forces. */
 md_status md_get_state(md_system *s, double *pos, double *vel);
@@ -130,11 +141,11 @@ md_status md_set_profiling(md_system *s, int profile);
  *      Newton-3 scatter of the three forces;
  *   1  one warp per particle, neighbours from the pair list, only the force on that
  *      particle per evaluation (each triplet evaluated from each member, no scatter);
- *   2  one warp per particle and its half list (neighbours that follow it in cell-offset,
- *      then index, order), every neighbour pair visited once by a cyclic rotation across
- *      the lanes, each triplet evaluated once (Newton 3) with its forces kept as edge
- *      weights; per-neighbour sums added with vector atomics (summation order varies
- *      from run to run at the FP32 rounding level);
+ *   2  one warp per particle and its half list (its neighbours within r_c3 above it in the
+ *      order: cell layer along z, fixed-point z, sorted index), every neighbour pair visited
+ *      once by a cyclic rotation across the lanes, each triplet evaluated once (Newton 3)
+ *      with its forces kept as edge weights; per-neighbour sums added with vector atomics
+ *      (summation order varies from run to run at the FP32 rounding level);
  *      1 and 2 need r_c3 <= r_c2 + skin, else 0 is used;
  *  -1  (default) time the allowed kernels on the system's first evaluation and keep the
  *      fastest.  A batch uses its members' common choice, else 2 where allowed, else 0. */

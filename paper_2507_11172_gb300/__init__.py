@@ -54,6 +54,7 @@ SIGNATURES = {
     "md_respa_step": (_I, [_P, _I, _I, _D]),
     "md_get_forces": (_I, [_P, _P, _P]),
     "md_get_energy": (_I, [_P, _P, _P, _P, _P]),
+    "md_get_rdf": (_I, [_P, _I, _D, _P]),
     "md_get_state": (_I, [_P, _P, _P]),
     "md_set_state": (_I, [_P, _P, _P]),
     "md_get_stats": (_I, [_P, ctypes.POINTER(md_stats)]),
@@ -164,6 +165,12 @@ def md_get_energy(h):
     _check(load().md_get_energy(h, ctypes.byref(ek), ctypes.byref(u2), ctypes.byref(u3), ctypes.byref(w)),
            "md_get_energy")
     return ek.value, u2.value, u3.value, w.value
+
+
+def md_get_rdf(h, nbins: int, r_max: float) -> np.ndarray:
+    counts = np.zeros(int(nbins), dtype=np.uint64)
+    _check(load().md_get_rdf(h, int(nbins), float(r_max), _ptr(counts)), "md_get_rdf")
+    return counts
 
 
 def md_get_state(h, pos_out=None, vel_out=None):
@@ -292,6 +299,9 @@ class System:
 
     def state(self):
         return md_get_state(self.handle)
+
+    def rdf(self, nbins, r_max):
+        return md_get_rdf(self.handle, nbins, r_max)
 
     def set_state(self, pos=None, vel=None):
         md_set_state(self.handle, pos, vel)

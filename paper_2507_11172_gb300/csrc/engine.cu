@@ -1086,6 +1086,32 @@ md_status md_get_energy(md_system* s, double* e_kin, double* u2, double* u3, dou
   return MD_OK;
 }
 
+md_status md_get_rdf(md_system* s, int nbins, double r_max, uint64_t* counts) {
+  if (!s || !counts || nbins < 1 || nbins > kRdfMaxBins || !(r_max > 0) || !isfinite(r_max)) return MD_ERR_ARG;
+  if (s->batch) return MD_ERR_STATE;
+  if (r_max > s->rc2 + s->skin) return MD_ERR_ARG;  // the pair list holds every pair within r_c2 + skin
+  md_status st = ensure_forces(s);  // positions of the last binning, with their pair list
+  if (st != MD_OK) return st;
+  unsigned long long* d = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&d), 8 * (size_t)nbins, s->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return MD_ERR_OOM;
+  }
+  const double dr = r_max / nbins;
+  Launch L{s->stream, s->d_sys};
+  e = cudaMemsetAsync(d, 0, 8 * (size_t)nbins, s->stream);
+  if (e == cudaSuccess) {
+    launch_rdf(L, pitems_for(s, T_BIN, 0, s->cur), s->nblocks, nbins, dr, d);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(counts, d, 8 * (size_t)nbins, cudaMemcpyDeviceToHost, s->stream);
+  cudaFreeAsync(d, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "md_get_rdf");
+  return MD_OK;
+}
+
 md_status md_get_state(md_system* s, double* pos, double* vel) {
   if (!s) return MD_ERR_ARG;
   if (s->batch) return MD_ERR_STATE;

@@ -362,6 +362,9 @@ constexpr int rot_bases_per_item(int) { return 32; }
 template <typename T>
 void launch_atm_table(const Launch& L, const CItem* items, int nitems, int grid, int smax, const uint16_t* table);
 template <typename T> void launch_combine(const Launch& L, const PItem* items, int nitems, int block);
+// RDF pair counts (observables.cu): items of 256 particles, nbins <= kRdfMaxBins shared counters
+constexpr int kRdfMaxBins = 8192;
+void launch_rdf(const Launch& L, const PItem* items, int nitems, int nbins, double dr, unsigned long long* counts);
 // FP64 kick/drift after an LJ evaluation: items of 256 particles with the LJ kind as mode
 template <typename T> void launch_kick(const Launch& L, const PItem* items, int nitems);
 template <typename T> void launch_start(const Launch& L, const PItem* items, int nitems, int block);
