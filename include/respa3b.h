@@ -189,6 +189,19 @@ md_status md_batch_latency(md_batch *b, uint64_t ticket, double *ms, int *count)
 md_status md_batch_pending(md_batch *b, int *queued, int *resident);
 md_status md_batch_destroy(md_batch *b);
 
+/* ---------------- all-triplet (DirectSum) ATM forces ----------------
+ * The reference method of the paper's energy studies (Sec. 4.1, "DirectSum"):
+ * every unordered triplet of n distinct particles, open boundaries (no periodic
+ * images), no cutoff.  pos: host, n x 3 (caller order); f3: host n x 3 output;
+ * u3: host output or NULL.  precision: MD_FP32 (FP32 triplet arithmetic, the
+ * per-particle sums compensated, combined in FP64) or MD_FP64.  cuda_stream:
+ * cudaStream_t or NULL.  Every triplet is evaluated from each of its three
+ * members (3 C(n, 3) evaluations, no scatter).  Capacity: all particles' positions
+ * fit in one CTA's shared memory (n <= 14464 FP32, 7232 FP64), else
+ * MD_ERR_CAPACITY.  Allocates and frees its device buffers; synchronous. */
+md_status md_atm_direct(const double *pos, int64_t n, double atm_nu, int precision, double *f3, double *u3,
+                        void *cuda_stream);
+
 /* ---------------- allocation-free ATM forces ----------------
  * No counterpart in the paper: an entry point for callers that cannot
  * allocate device memory (code living inside another framework's memory

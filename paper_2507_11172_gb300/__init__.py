@@ -71,6 +71,7 @@ SIGNATURES = {
     "md_batch_latency": (_I, [_P, ctypes.c_uint64, _P, ctypes.POINTER(_I)]),
     "md_batch_pending": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "md_batch_destroy": (_I, [_P]),
+    "md_atm_direct": (_I, [_P, _I64, _D, _I, _P, _P, _P]),
     "md_atm_forces_noalloc": (_I, [_P, _I64, _D, _D, _D, _P, ctypes.POINTER(_D), _U64P, _P]),
 }
 
@@ -251,6 +252,17 @@ def md_batch_pending(b):
 def md_batch_destroy(b):
     if b:
         _check(load().md_batch_destroy(b), "md_batch_destroy")
+
+
+def md_atm_direct(pos, nu: float, precision: int = MD_FP32, stream=None):
+    """All-triplet ATM forces (open boundaries, no cutoff): returns (f3 (n, 3), u3)."""
+    n = int(np.asarray(pos).shape[0])
+    x = _arr(pos, n)
+    f = np.zeros((n, 3), dtype=np.float64)
+    u = _D()
+    _check(load().md_atm_direct(_ptr(x), n, float(nu), int(precision), _ptr(f), ctypes.byref(u),
+                                stream if stream else None), "md_atm_direct")
+    return f, u.value
 
 
 def md_atm_forces_noalloc(d_pos_ptr: int, n: int, box_L: float, nu: float, rc_triplet: float, d_f3_ptr: int,

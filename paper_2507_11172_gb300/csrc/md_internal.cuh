@@ -362,6 +362,10 @@ constexpr int rot_bases_per_item(int) { return 32; }
 template <typename T>
 void launch_atm_table(const Launch& L, const CItem* items, int nitems, int grid, int smax, const uint16_t* table);
 template <typename T> void launch_combine(const Launch& L, const PItem* items, int nitems, int block);
+// all-triplet ATM forces, open boundaries (direct.cu): X, F host-order AoS device arrays, U[n]
+int direct_max_n(int precision);
+cudaError_t launch_atm_direct(const double* X, int n, double nu, int precision, double* F, double* U,
+                              cudaStream_t s);
 // RDF pair counts (observables.cu): items of 256 particles, nbins <= kRdfMaxBins shared counters
 constexpr int kRdfMaxBins = 8192;
 void launch_rdf(const Launch& L, const PItem* items, int nitems, int nbins, double dr, unsigned long long* counts);
