@@ -92,3 +92,81 @@ def rvite(e_tot: np.ndarray, e_kin: np.ndarray) -> float:
     """Relative variation in true energy (Eq. 4): mean |e(i) - mean(e)| / mean(K)."""
     e_tot = np.asarray(e_tot, dtype=np.float64)
     return float(np.mean(np.abs(e_tot - e_tot.mean())) / np.mean(e_kin))
+
+
+# ---------------------------------------------------------------------------------------------
+# Distance classes for the three-body force (the outlook of Sec. 5, after Nakano et al. and
+# Grubmueller et al., Sec. 3): an intermediate triplet cutoff r_a < r_c splits the ATM triplets
+# into a near class (all three pair distances <= r_a) and a far class (the other triplets with all
+# three distances <= r_c).  r-RESPA with three levels (Sec. 2.3.1: "an arbitrary number of
+# separations ... nested loop"): the LJ force every iteration of step dt, the near triplets with the
+# step-size factor s_near (every s_near iterations), the far triplets with s = k_inner.
+
+@dataclass
+class State3:
+    x: np.ndarray
+    v: np.ndarray
+    L: float
+    mass: float = 1.0
+    f2: Optional[np.ndarray] = None
+    f3n: Optional[np.ndarray] = None
+    f3f: Optional[np.ndarray] = None
+    u2: float = 0.0
+    u3n: float = 0.0
+    u3f: float = 0.0
+    energies: list = field(default_factory=list)  # (e_kin, u2, u3n + u3f) at each full step
+
+
+def class_forces(L: float, nu: float, r_a: float, rc3: float):
+    """Near and far ATM force fields x -> (F, U, W): near = every triplet within r_a (the triplet
+    cutoff r_a), far = the triplets within r_c minus the near ones."""
+    def near(x):
+        f, u, w, _ = atm_brute(x, L, nu, r_a)
+        return f, u, w
+
+    def far(x):
+        fa, ua, wa, _ = atm_brute(x, L, nu, rc3)
+        fn, un, wn, _ = atm_brute(x, L, nu, r_a)
+        return fa - fn, ua - un, wa - wn
+    return near, far
+
+
+def run3(state: State3, n_outer: int, k_inner: int, s_near: int, dt_outer: float, f2b: ForceFn,
+         f3near: ForceFn, f3far: ForceFn, periodic: bool = True, record: bool = False) -> State3:
+    """n_outer outer steps of k_inner iterations (dt = dt_outer / k_inner), written as one loop in
+    the manner of Algorithm 2: the far kick dt k_inner / (2m) F3far opens and closes every block of
+    k_inner iterations, the near kick dt s_near / (2m) F3near every block of s_near iterations, and
+    every iteration is a velocity-Verlet step with F2.  s_near must divide k_inner."""
+    if n_outer < 0 or k_inner < 1 or s_near < 1 or k_inner % s_near or not dt_outer > 0:
+        raise ValueError("n_outer >= 0, s_near | k_inner and dt_outer > 0 required")
+    dt = dt_outer / k_inner
+    m = state.mass
+    x, v = state.x, state.v
+    if state.f2 is None:
+        state.f2, state.u2, _ = f2b(x)
+    if state.f3n is None:
+        state.f3n, state.u3n, _ = f3near(x)
+    if state.f3f is None:
+        state.f3f, state.u3f, _ = f3far(x)
+    f2, f3n, f3f = state.f2, state.f3n, state.f3f
+    for i in range(n_outer * k_inner):
+        if i % k_inner == 0:
+            v = v + (dt * k_inner / (2.0 * m)) * f3f
+        if i % s_near == 0:
+            v = v + (dt * s_near / (2.0 * m)) * f3n
+        x_new = x + dt * v + (dt * dt / (2.0 * m)) * f2
+        if periodic:
+            x_new = wrap(x_new, state.L)
+        f2_new, state.u2, _ = f2b(x_new)
+        v = v + (dt / (2.0 * m)) * (f2 + f2_new)
+        x, f2 = x_new, f2_new
+        if (i + 1) % s_near == 0:
+            f3n, state.u3n, _ = f3near(x)
+            v = v + (dt * s_near / (2.0 * m)) * f3n
+        if (i + 1) % k_inner == 0:
+            f3f, state.u3f, _ = f3far(x)
+            v = v + (dt * k_inner / (2.0 * m)) * f3f
+            if record:
+                state.energies.append((kinetic(v, m), state.u2, state.u3n + state.u3f))
+    state.x, state.v, state.f2, state.f3n, state.f3f = x, v, f2, f3n, f3f
+    return state

@@ -1,0 +1,77 @@
+"""Energy-conservation sweep of the method (Sec. 4.2.1, toy scenario): relative variation in true
+energy, RVITE (Eq. 4), over the step-size factor s and the ATM strength nu.
+
+Scenario (Sec. 4.2): 675 particles in a periodic 10 x 10 x 10 box, eps = sigma = m = 1,
+dt = 0.001 (the paper's inner step), 24 000 iterations, s = 1 .. 12, nu in [0.05, 1.0].  The paper
+does not state the cutoff or the initial state: this sweep uses r_c2 = r_c3 = 2.5, an FCC lattice with
+0.05 sigma jitter and Maxwell velocities at T* = 1.0, equilibrated for 2 000 Stormer-Verlet
+iterations (s = 1) before the measured run.  The total energy e(i) = E_kin + U2 + U3 is read at
+every full step (iterations divisible by s; Sec. 4.1) and RVITE = mean_i |e(i) - mean(e)| / mean(E_kin).
+
+Everything runs through the C ABI (md_respa_step with k_inner = s, dt_outer = s dt; md_get_energy).
+
+    python -m paper_2507_11172_gb300.sweeps [--iters 24000] [--nus 0.05,0.25,0.5,0.75,1.0] [--s 1,2,...]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+from . import MD_FP32, MD_FP64, System
+
+
+def toy_state(n: int = 675, L: float = 10.0, temperature: float = 1.0, seed: int = 2507):
+    """FCC sites of the box (4 nc^3 >= n, seeded vacancies), 0.05 sigma jitter, Maxwell velocities."""
+    import md_inputs
+    x, Lx = md_inputs.fcc_jitter(n, n / L ** 3, 0.05, seed)
+    v = md_inputs.maxwell(n, temperature, seed + 1)
+    return x, Lx, v
+
+
+def rvite(e_tot, e_kin) -> float:
+    """Eq. 4: (1 / (K J)) sum_i |e(i) - mean(e)|, K the mean kinetic energy, J the number of full steps."""
+    e_tot = np.asarray(e_tot, dtype=np.float64)
+    return float(np.mean(np.abs(e_tot - e_tot.mean())) / np.mean(e_kin))
+
+
+def run_point(x, L, v, nu: float, s: int, iters: int, dt: float = 0.001, equil: int = 2000,
+              precision: int = MD_FP32, rc: float = 2.5):
+    """One (nu, s) point: returns (RVITE, energies (J, 3) = (E_kin, U2, U3) at the full steps, seconds)."""
+    with System.create(x, L, v, precision=precision, nu=nu, rc_pair=rc, rc_triplet=rc) as sysm:
+        for _ in range(equil // 100):  # equilibration in calls of 100 Stormer-Verlet iterations
+            sysm.step(100, 1, dt)
+        e = []
+        t0 = time.perf_counter()
+        for _ in range(iters // s):
+            sysm.step(1, s, s * dt)
+            ek, u2, u3, _ = sysm.energy()
+            e.append((ek, u2, u3))
+        dt_wall = time.perf_counter() - t0
+    e = np.asarray(e)
+    return rvite(e.sum(1), e[:, 0]), e, dt_wall
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--iters", type=int, default=24000)
+    ap.add_argument("--nus", default="0.05,0.25,0.5,0.75,1.0")
+    ap.add_argument("--s", default=",".join(str(k) for k in range(1, 13)))
+    ap.add_argument("--fp64", action="store_true")
+    args = ap.parse_args(argv)
+    x, L, v = toy_state()
+    out = []
+    for nu in [float(a) for a in args.nus.split(",")]:
+        for s in [int(a) for a in args.s.split(",")]:
+            r, e, wall = run_point(x, L, v, nu, s, args.iters, precision=MD_FP64 if args.fp64 else MD_FP32)
+            out.append({"nu": nu, "s": s, "rvite": r, "full_steps": len(e), "seconds": wall,
+                        "e_mean": float(e.sum(1).mean()),
+                        "max_dev_rel": float(np.abs(e.sum(1) - e.sum(1).mean()).max() / abs(e.sum(1).mean()))})
+            print(json.dumps(out[-1]), flush=True)
+    return out
+
+
+if __name__ == "__main__":
+    main()
