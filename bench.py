@@ -229,6 +229,8 @@ def run_ours(args):
         finally:
             r3.md_destroy_system(h)
 
+    classes_line = run_classes(r3, w, stream, flush, K) if rank == 0 else None
+
     peaks = {}
     if os.path.exists(PEAKS_FILE):
         peaks = json.load(open(PEAKS_FILE))
@@ -267,6 +269,7 @@ def run_ours(args):
         "gpu_launches": K * (2 * w.k_inner + 6 + 1),
         "e2e": e2e,
         "observables": obs_line,
+        "distance_classes": classes_line,
     }
     if peaks:
         line["measured_peaks"] = {"hbm_gbs": peaks.get("hbm_gbs"), "bf16_tflops": peaks.get("bf16_tflops")}
@@ -279,6 +282,48 @@ def run_ours(args):
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_classes(r3, w, stream, flush, steps, r_a=1.5, s_near=2):
+    """Distance classes of the three-body force on the same workload (FP32): near triplets (all three
+    distances <= r_a) every s_near inner steps, far triplets every outer step (k = 10).  Timed like
+    the main line (graph replay, L2 flushed, CUDA events per outer step), beside Algorithm 2 with
+    k = s_near, which evaluates every triplet as often as the near class."""
+    import torch
+
+    def timed(r_a_, k, n_outer):
+        h = r3.md_create_system(w.x, w.L, w.v, 1.0, r3.MD_FP32, stream.cuda_stream)
+        try:
+            r3.md_set_potentials(h, 1.0, 1.0, w.rc2, w.nu, w.rc3)
+            if r_a_ > 0:
+                r3.md_set_distance_classes(h, r_a_, s_near)
+            dt = w.dt_outer * k / w.k_inner  # same inner step dt_outer / k_inner
+            with torch.cuda.stream(stream):
+                for _ in range(4):
+                    r3.md_respa_step(h, n_outer, k, dt)
+                ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                      for _ in range(steps)]
+                torch.cuda.synchronize()
+                s0 = r3.md_get_stats(h)
+                for e0, e1 in ev:
+                    flush.fill_(1.0)
+                    e0.record(stream)
+                    r3.md_respa_step(h, n_outer, k, dt)
+                    e1.record(stream)
+                torch.cuda.synchronize()
+                st = r3.md_get_stats(h)
+            return sum(e0.elapsed_time(e1) for e0, e1 in ev) / steps, st, s0
+        finally:
+            r3.md_destroy_system(h)
+
+    ms_c, st_c, _ = timed(r_a, w.k_inner, 1)
+    ms_2, _, _ = timed(0.0, s_near, w.k_inner // s_near)
+    return {"r_a": r_a, "s_near": s_near, "k_inner": w.k_inner,
+            "ms_per_outer_step": ms_c, "near_triplets_per_eval": st_c["near_triplets_last"],
+            "triplets_per_eval": st_c["triplets_last"],
+            "alg2_k_eq_s_near_ms_per_same_time": ms_2,
+            "note": "ms for k_inner inner steps of dt_outer / k_inner: classes (near every s_near, far every "
+                    "k_inner) vs Algorithm 2 with every triplet every s_near inner steps"}
 
 
 def _skin_for(L, rc2=2.5, rc3=2.5):

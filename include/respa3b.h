@@ -73,6 +73,7 @@ typedef struct {
   int32_t cells_per_side;      /* binning grid */
   int32_t atm_kernel;          /* triplet kernel in use: 0 cell, 1 per-particle, 2 rotation, -1 not chosen yet */
   int32_t reserved_;
+  uint64_t near_triplets_last; /* distance classes: near-class triplets found by the last near evaluation */
 } md_stats;
 
 /* Create a system of n >= 3 particles in a periodic cube of side box_L.
@@ -129,6 +130,26 @@ md_status md_get_rdf(md_system *s, int nbins, double r_max, uint64_t *counts);
  * n x 3 each; either may be NULL.  md_set_state invalidates cached forces. */
 md_status md_get_state(md_system *s, double *pos, double *vel);
 md_status md_set_state(md_system *s, const double *pos, const double *vel);
+
+/* Distance classes for the three-body force (the multiple-time-stepping outlook of Sec. 5, after the
+ * intermediate-cutoff splitting of Nakano et al. cited in Sec. 3): an intermediate cutoff r_a splits
+ * the ATM triplets into a near class (all three pair distances <= r_a) and a far class (the other
+ * triplets with all three distances <= r_c3).  md_respa_step then integrates three levels in one
+ * loop, in the manner of Algorithm 2: LJ every inner step dt, the near class with step-size factor
+ * s_near (kicks s_near dt / 2 F3near / m around every block of s_near inner steps), the far class
+ * with the outer step (kicks dt_outer / 2 (F3 - F3near) / m).  k_inner must be a multiple of s_near
+ * (MD_ERR_ARG otherwise); s_near = k_inner, or r_a below every pair distance, is Algorithm 2 again.
+ * Requires 0 < r_a <= min(r_c2, r_c3) and r_c3 <= r_c2 + skin (the rotation triplet kernel, the only
+ * one with a near-class mode); single systems only (md_batch_submit rejects them, MD_ERR_ARG).
+ * r_a <= 0 turns the classes off.  Reallocates the handle's device memory (state kept) and
+ * invalidates the cached forces.  Triplet half lists longer than 64 give MD_ERR_CAPACITY (no
+ * fallback kernel).  The near-class lists are rebuilt from the current positions before every near
+ * evaluation between two binnings (exact cutoff decisions, as for r_c3). */
+md_status md_set_distance_classes(md_system *s, double r_a, int s_near);
+
+/* Cached near-class ATM forces F3near (n x 3, caller order) at the current positions; md_get_forces'
+ * f3 is the whole ATM force (near + far).  MD_ERR_STATE if the classes are off. */
+md_status md_get_near_forces(md_system *s, double *f3near);
 
 /* Counters (see md_stats).  profile = 1 launches a call's kernels one by one
  * (instead of replaying a captured CUDA graph) with CUDA events recorded on

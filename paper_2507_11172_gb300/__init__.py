@@ -36,7 +36,8 @@ class md_stats(ctypes.Structure):
                 ("atm_evals", ctypes.c_uint64), ("lj_evals", ctypes.c_uint64), ("outer_steps", ctypes.c_uint64),
                 ("replays", ctypes.c_uint64), ("guard_rechecks", ctypes.c_uint64), ("atm_ms_total", ctypes.c_double),
                 ("atm_timed", ctypes.c_uint64), ("max_cell_count", ctypes.c_int32),
-                ("cells_per_side", ctypes.c_int32), ("atm_kernel", ctypes.c_int32), ("reserved_", ctypes.c_int32)]
+                ("cells_per_side", ctypes.c_int32), ("atm_kernel", ctypes.c_int32), ("reserved_", ctypes.c_int32),
+                ("near_triplets_last", ctypes.c_uint64)]
 
 
 _lib = None
@@ -60,6 +61,8 @@ SIGNATURES = {
     "md_get_stats": (_I, [_P, ctypes.POINTER(md_stats)]),
     "md_set_profiling": (_I, [_P, _I]),
     "md_set_atm_kernel": (_I, [_P, _I]),
+    "md_set_distance_classes": (_I, [_P, _D, _I]),
+    "md_get_near_forces": (_I, [_P, _P]),
     "md_get_info": (_I, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_D), ctypes.POINTER(_I)]),
     "md_destroy_system": (_I, [_P]),
     "md_status_string": (ctypes.c_char_p, [_I]),
@@ -203,6 +206,17 @@ def md_set_atm_kernel(h, variant: int):
     _check(load().md_set_atm_kernel(h, int(variant)), "md_set_atm_kernel")
 
 
+def md_set_distance_classes(h, r_a: float, s_near: int):
+    _check(load().md_set_distance_classes(h, float(r_a), int(s_near)), "md_set_distance_classes")
+
+
+def md_get_near_forces(h, out=None):
+    n = md_get_info(h)[0]
+    f = np.empty((n, 3)) if out is None else out
+    _check(load().md_get_near_forces(h, _ptr(f)), "md_get_near_forces")
+    return f
+
+
 def md_destroy_system(h):
     if h:
         _check(load().md_destroy_system(h), "md_destroy_system")
@@ -311,6 +325,12 @@ class System:
 
     def state(self):
         return md_get_state(self.handle)
+
+    def set_distance_classes(self, r_a, s_near):
+        md_set_distance_classes(self.handle, r_a, s_near)
+
+    def near_forces(self):
+        return md_get_near_forces(self.handle)
 
     def rdf(self, nbins, r_max):
         return md_get_rdf(self.handle, nbins, r_max)

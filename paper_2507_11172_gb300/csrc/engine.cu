@@ -66,6 +66,9 @@ struct md_system {
   double L = 0, mass = 1.0;
   int precision = MD_FP32;
   double eps = 1.0, sigma = 1.0, rc2 = 2.5, nu = 0.0, rc3 = 2.5, skin = 0.3;
+  // distance classes of the three-body force (r_a = 0: off, plain Algorithm 2)
+  double r_a = 0.0;
+  int s_near = 0;
   // grid and capacities
   int nc = 0, ncell = 0, cap_cell = 0, maxnb = 0;
   double edge = 0;
@@ -75,7 +78,7 @@ struct md_system {
   SysDev h{};              // host copy of the device descriptor
   SysDev* d_sys = nullptr;  // device copy (inside mem)
   // snapshot for replay
-  double *snap_x = nullptr, *snap_v = nullptr, *snap_f2 = nullptr, *snap_f3 = nullptr;
+  double *snap_x = nullptr, *snap_v = nullptr, *snap_f2 = nullptr, *snap_f3 = nullptr, *snap_f3n = nullptr;
   int *snap_id = nullptr, *snap_cell = nullptr;
   // work items
   std::map<std::tuple<int, int, int>, PItem*> pitems;  // (kernel tag, mode, buf) -> device array
@@ -188,6 +191,15 @@ md_status alloc_device(md_system* s) {
   size_t o_acc = a.reserve(8 * ACC_N), o_ctr = a.reserve(8 * CTR_N), o_flg = a.reserve(4 * FLG_N);
   size_t o_sx = a.reserve(24 * n), o_sv = a.reserve(24 * n), o_sf2 = a.reserve(24 * n), o_sf3 = a.reserve(24 * n);
   size_t o_sid = a.reserve(4 * n), o_scell = a.reserve(4 * n);
+  const bool classes = s->r_a > 0;
+  size_t o_halfa = 0, o_hca = 0, o_f3n = 0, o_f3na = 0, o_sf3n = 0;
+  if (classes) {
+    o_halfa = a.reserve(4 * (size_t)kHalfCap * n);
+    o_hca = a.reserve(4 * n);
+    o_f3n = a.reserve(24 * n);
+    o_f3na = a.reserve(4 * tsz * n);
+    o_sf3n = a.reserve(24 * n);
+  }
   char* m = nullptr;
   cudaError_t e = cudaMalloc(&m, a.used);
   if (e != cudaSuccess) {
@@ -223,6 +235,13 @@ md_status alloc_device(md_system* s) {
   h.partial = m + o_part;
   h.f3acc = m + o_f3a;
   h.ipos = (int4*)(m + o_ipos);
+  if (classes) {
+    h.half_a = (int*)(m + o_halfa);
+    h.half_a_cnt = (int*)(m + o_hca);
+    h.f3n = (double*)(m + o_f3n);
+    h.f3nacc = m + o_f3na;
+  }
+  s->snap_f3n = classes ? (double*)(m + o_sf3n) : nullptr;
   {
     std::vector<double> cen(s->nc);
     for (int c = 0; c < s->nc; ++c) cen[c] = (c + 0.5) * s->edge;
@@ -285,6 +304,13 @@ size_t arena_bytes(const md_system* s0) {
   for (int i = 0; i < 4; ++i) a.reserve(24 * n);
   a.reserve(4 * n);
   a.reserve(4 * n);
+  if (s0->r_a > 0) {  // distance classes
+    a.reserve(4 * (size_t)kHalfCap * n);
+    a.reserve(4 * n);
+    a.reserve(24 * n);
+    a.reserve(4 * tsz * n);
+    a.reserve(24 * n);
+  }
   // work-item arrays (about 30 particle-block variants and 4 cell variants)
   return a.used + 30 * sizeof(PItem) * (n / 32 + 2) + 4 * sizeof(CItem) * (size_t)tmp.ncell;
 }
@@ -318,6 +344,11 @@ md_status upload_desc(md_system* s, double dt_in, double dt_out) {
   h.guard3 = gfac * std::max(1.0, h.rc3sq);
   h.dt_in = dt_in;
   h.dt_out = dt_out;
+  h.rasq = s->r_a * s->r_a;
+  h.guarda = gfac * std::max(1.0, h.rasq);
+  h.dt_near = s->s_near * dt_in;
+  h.f_rasq = (float)h.rasq;
+  h.f_guarda = (float)h.guarda;
   h.mass = s->mass;
   h.inv_mass = 1.0 / s->mass;
   h.maxnb = s->maxnb;
@@ -432,6 +463,11 @@ md_status prepare_items(md_system* s) {
       pitems_for(s, T_ATMROT, E, b);
       citems_for(s, E, b);
     }
+    if (s->r_a > 0) {  // distance classes
+      pitems_for(s, T_KICK, LJ_MID | M_NEAR, b);
+      pitems_for(s, T_ATMROT, M_NEAR, b);
+      citems_for(s, M_NEAR, b);
+    }
   }
   pitems_for(s, T_KIN, 0, 0);
   if (!s->sitem) {
@@ -512,18 +548,32 @@ struct Plan {
     launch_scatter<T>(L, pitems_for(s, T_SCATTER, 0, buf), s->nblocks, kBlock);
     launch_listbuild<T>(L, citems_for(s, 0, buf), s->ncell, 27 * s->cap_cell);
   }
+  // half lists at r_a of the current positions (distance classes, between two binnings)
   template <typename T>
-  void lj(int kind, int buf, bool energy) {
+  void near_lists(int buf) {
+    launch_listbuild<T>(L, citems_for(s, M_NEAR, buf), s->ncell, 27 * s->cap_cell);
+  }
+  // LJ forces and the velocity-Verlet kick/drift; with near = true (distance classes, LJ_MID) the
+  // near-class triplets are evaluated between the two and their kicks join the LJ kick
+  template <typename T>
+  void lj(int kind, int buf, bool energy, bool near = false) {
     launch_lj<T>(L, pitems_for(s, T_LJ, kind | (energy ? M_ENERGY : 0), buf),
                  padded_blocks((s->n + kLjPer - 1) / kLjPer));
-    if (kind != LJ_INIT) launch_kick<T>(L, pitems_for(s, T_KICK, kind, buf), padded_blocks(s->nblocks));
+    if (near) atm_near<T>(buf);
+    if (kind != LJ_INIT)
+      launch_kick<T>(L, pitems_for(s, T_KICK, kind | (near ? M_NEAR : 0), buf), padded_blocks(s->nblocks));
+  }
+  template <typename T>
+  void atm_near(int buf) {
+    launch_atm_rot<T>(L, pitems_for(s, T_ATMROT, M_NEAR, buf), padded_blocks(s->nblocks_rot));
   }
   template <typename T>
   void atm(int buf, bool energy, int ev) {
     if (ev >= 0) cudaEventRecord(s->events[2 * ev], L.stream);
-    if (s->atm_variant == 2)
+    if (s->atm_variant == 2) {
       launch_atm_rot<T>(L, pitems_for(s, T_ATMROT, energy ? M_ENERGY : 0, buf), padded_blocks(s->nblocks_rot));
-    else if (s->atm_variant == 1)
+      if (s->r_a > 0) atm_near<T>(buf);  // distance classes: the near class of the same configuration
+    } else if (s->atm_variant == 1)
       launch_atm_pa<T>(L, pitems_for(s, T_ATMPA, energy ? M_ENERGY : 0, buf), s->nblocks_pa);
     else
       launch_atm<T>(L, citems_for(s, energy ? M_ENERGY : 0, buf), s->ncell, s->atm_grid,
@@ -565,9 +615,14 @@ void enqueue_steps(Plan& P, int n_outer, int k, int cur, bool safe, bool profile
     if (last) P.zero_energy();
     for (int t = 0; t < k; ++t) {
       const int b = t & 1;
-      if (t == k - 1 || safe) P.sort<T>(b);  // binning + pair list at the outer boundary
+      // distance classes: iteration t closes a block of s_near inner steps
+      const bool near = P.s->r_a > 0 && t < k - 1 && (t + 1) % P.s->s_near == 0;
+      if (t == k - 1 || safe)
+        P.sort<T>(b);  // binning + pair list at the outer boundary
+      else if (near)
+        P.near_lists<T>(b);
       if (t < k - 1)
-        P.lj<T>(LJ_MID, b, false);
+        P.lj<T>(LJ_MID, b, false, near);
       else
         P.lj<T>(LJ_LAST, b, last);
     }
@@ -600,6 +655,7 @@ md_status snapshot(md_system* s, bool save) {
     CK(cp(s->snap_v, s->h.v, 24 * n));
     CK(cp(s->snap_f2, s->h.f2, 24 * n));
     CK(cp(s->snap_f3, s->h.f3, 24 * n));
+    if (s->snap_f3n) CK(cp(s->snap_f3n, s->h.f3n, 24 * n));
     CK(cp(s->snap_id, s->h.id, 4 * n));
     CK(cp(s->snap_cell, s->h.pcell, 4 * n));
   } else {
@@ -607,6 +663,7 @@ md_status snapshot(md_system* s, bool save) {
     CK(cp(s->h.v, s->snap_v, 24 * n));
     CK(cp(s->h.f2, s->snap_f2, 24 * n));
     CK(cp(s->h.f3, s->snap_f3, 24 * n));
+    if (s->snap_f3n) CK(cp(s->h.f3n, s->snap_f3n, 24 * n));
     CK(cp(s->h.id, s->snap_id, 4 * n));
     CK(cp(s->h.pcell, s->snap_cell, 4 * n));
   }
@@ -705,6 +762,14 @@ bool variant_allowed(const md_system* s, int v) {
 // each allowed variant is launched a few times on the same configuration with CUDA events
 // around each launch; the faster one is kept for the system.
 md_status tune_atm(md_system* s) {
+  if (s->r_a > 0) {  // distance classes run on the rotation kernel only
+    if (!variant_allowed(s, 2)) {
+      g_last_error = "distance classes need the rotation triplet kernel (r_c3 <= r_c2 + skin)";
+      return MD_ERR_ARG;
+    }
+    s->atm_variant = 2;
+    return MD_OK;
+  }
   const int req = s->atm_variant_req;
   if (req >= 0) {
     s->atm_variant = variant_allowed(s, req) ? req : 0;
@@ -755,6 +820,10 @@ md_status tune_atm(md_system* s) {
 
 // one respa_step call with snapshot / replay
 md_status do_call(md_system* s, int n_outer, int k, double dt_outer) {
+  if (s->r_a > 0 && ((n_outer > 0 && k % s->s_near != 0) || s->r_a > s->rc2 || s->r_a > s->rc3)) {
+    g_last_error = "distance classes: k_inner must be a multiple of s_near and r_a <= min(r_c2, r_c3)";
+    return MD_ERR_ARG;
+  }
   if (s->atm_variant < 0) {
     md_status st = tune_atm(s);
     if (st != MD_OK) return st;
@@ -771,6 +840,7 @@ md_status do_call(md_system* s, int n_outer, int k, double dt_outer) {
     st = snapshot(s, true);
     if (st != MD_OK) return st;
     const unsigned long long trip0 = s->h_ctr[CTR_TRIPLETS];  // device counter as of the last call
+    const unsigned long long near0 = s->h_ctr[CTR_NEAR];
     st = run_plan(s, n_outer, k, init, safe);
     if (st != MD_OK) return st;
     st = finish_call(s, n_outer);
@@ -781,6 +851,15 @@ md_status do_call(md_system* s, int n_outer, int k, double dt_outer) {
     // the rotation and per-particle kernels hold shorter half lists than the cell kernel
     const bool half_bad = (err & ERR_HALF_CAP) != 0 && s->atm_variant != 0;
     s->stats.max_cell_count = s->h_flags[FLG_MAXCELL];
+    if (half_bad && s->r_a > 0) {  // no fallback kernel for distance classes
+      s->cur = cur0;
+      snapshot(s, false);
+      s->forces_valid = false;
+      s->energy_valid = false;
+      cudaStreamSynchronize(s->stream);
+      g_last_error = "distance classes: a triplet half list exceeds 64 neighbours";
+      return MD_ERR_CAPACITY;
+    }
     if (!(skin_bad || cap_bad || half_bad) || (err & ERR_NONFINITE)) {
       md_status fs = status_from_flags(s);
       if (fs != MD_OK) {
@@ -795,6 +874,10 @@ md_status do_call(md_system* s, int n_outer, int k, double dt_outer) {
       unsigned long long trip1 = s->h_ctr[CTR_TRIPLETS];
       int evals = n_outer + (init ? 1 : 0);
       if (evals > 0) s->stats.triplets_last = (trip1 - trip0) / (unsigned long long)evals;
+      if (s->r_a > 0) {  // near-class evaluations: every s_near inner steps, plus initial
+        const int nevals = n_outer * (k / s->s_near) + (init ? 1 : 0);
+        if (nevals > 0) s->stats.near_triplets_last = (s->h_ctr[CTR_NEAR] - near0) / (unsigned long long)nevals;
+      }
       s->stats.triplets_total += trip1 - trip0;
       s->stats.atm_evals += evals;
       s->stats.lj_evals += (uint64_t)n_outer * k + (init ? 1 : 0);
@@ -1045,6 +1128,24 @@ md_status md_set_skin(md_system* s, double skin) {
   if (s->deferred) return MD_OK;
   if (s->batch) return MD_ERR_STATE;
   return rebuild(s, true);
+}
+
+md_status md_set_distance_classes(md_system* s, double r_a, int s_near) {
+  if (!s || !isfinite(r_a)) return MD_ERR_ARG;
+  if (s->batch) return MD_ERR_STATE;
+  if (r_a > 0 && (s_near < 1 || r_a > s->rc2 || r_a > s->rc3)) return MD_ERR_ARG;
+  s->r_a = r_a > 0 ? r_a : 0.0;
+  s->s_near = r_a > 0 ? s_near : 0;
+  if (s->deferred) return MD_OK;
+  return rebuild(s, true);
+}
+
+md_status md_get_near_forces(md_system* s, double* f3near) {
+  if (!s || !f3near) return MD_ERR_ARG;
+  if (s->batch || !(s->r_a > 0)) return MD_ERR_STATE;
+  md_status st = ensure_forces(s);
+  if (st != MD_OK) return st;
+  return fetch_sorted(s, s->h.f3n, f3near, false);
 }
 
 md_status md_respa_step(md_system* s, int n_outer, int k_inner, double dt_outer) {
@@ -1738,6 +1839,7 @@ md_status md_batch_submit(md_batch* b, md_system* s, int n_outer, int k_inner, d
   if (s->batch) return MD_ERR_STATE;
   for (auto& kv : b->req)
     if (kv.second.s == s && (kv.second.state == RQ_QUEUED || kv.second.state == RQ_RESIDENT)) return MD_ERR_STATE;
+  if (s->r_a > 0) return MD_ERR_ARG;  // distance classes run on single systems only
   if (b->precision < 0) b->precision = s->precision;
   if (s->precision != b->precision) return MD_ERR_ARG;
   Request r;

@@ -103,6 +103,31 @@ __device__ __forceinline__ void store_pos(const SysDev& S, int buf, int i, const
   }
 }
 
+// distance classes: near-class evaluations between two binnings read the fixed-point positions, so
+// every drift refreshes them
+__device__ __forceinline__ void store_fixed(const SysDev& S, int i, const double xn[3]) {
+  if (S.f3n) S.ipos[i] = make_int4(to_fixed(xn[0], S.qinv), to_fixed(xn[1], S.qinv), to_fixed(xn[2], S.qinv), 0);
+}
+
+// near-class force of particle p from the rotation kernel's sums (read and cleared)
+template <typename T>
+__device__ __forceinline__ void take_near(const SysDev& S, int p, double f[3]) {
+  if (sizeof(T) == 4) {
+    float4* a4 = reinterpret_cast<float4*>(S.f3nacc) + p;
+    const float4 a = *a4;
+    f[0] = (double)a.x;
+    f[1] = (double)a.y;
+    f[2] = (double)a.z;
+    *a4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  } else {
+    double* a = reinterpret_cast<double*>(S.f3nacc) + 4 * (size_t)p;
+    f[0] = a[0];
+    f[1] = a[1];
+    f[2] = a[2];
+    a[0] = a[1] = a[2] = 0.0;
+  }
+}
+
 // ============================================================== LJ pair kernel
 // One thread per particle i (F_i only: every pair is evaluated from both sides, no scatter).  The
 // thread walks i's pair-list row four entries at a time with a software pipeline: the row entries
@@ -284,6 +309,8 @@ __global__ void __launch_bounds__(kLjPer, 14) k_lj(const SysDev* __restrict__ sy
 //   LJ_MID:  v += dt F2 / m (closing half kick of this inner step + opening half kick of the next),
 //            x += dt v, cell-local FP32 coordinates of the new positions, displacement check;
 //   LJ_LAST: v += dt/2 F2 / m (closing half kick before the three-body evaluation).
+// M_NEAR (distance classes, LJ_MID only): the step closes a block of s_near inner steps, so the
+// near-class kicks s_near dt/2 F3near / m closing this block and opening the next are added too.
 template <typename T>
 __global__ void __launch_bounds__(256) k_kick(const SysDev* __restrict__ sys, const PItem* __restrict__ items) {
   const PItem it = items[blockIdx.x];
@@ -300,10 +327,12 @@ __global__ void __launch_bounds__(256) k_kick(const SysDev* __restrict__ sys, co
     const double c = S.dt_in * S.inv_mass;
     const double* __restrict__ X = S.X[it.buf];
     double* Xo = S.X[it.buf ^ 1];
-    double xn[3], rel[3];
+    double xn[3], rel[3], fn[3] = {0.0, 0.0, 0.0};
+    if (mode & M_NEAR) take_near<T>(S, i, fn);
+    const double cn = S.dt_near * S.inv_mass;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const double vv = fma(c, S.f2[a * n + i], S.v[a * n + i]);
+      const double vv = fma(cn, fn[a], fma(c, S.f2[a * n + i], S.v[a * n + i]));
       S.v[a * n + i] = vv;
       xn[a] = fma(S.dt_in, vv, X[a * n + i]);
       Xo[a * n + i] = xn[a];
@@ -311,6 +340,7 @@ __global__ void __launch_bounds__(256) k_kick(const SysDev* __restrict__ sys, co
     }
     cell_rel(S, S.pcell[i], xn, rel);
     store_pos<T>(S, it.buf ^ 1, i, rel, true);
+    store_fixed(S, i, xn);
   } else {
     const double c = 0.5 * S.dt_in * S.inv_mass;
 #pragma unroll
@@ -1101,11 +1131,27 @@ __global__ void __launch_bounds__(256) k_combine(const SysDev* __restrict__ sys,
       S.f3[a * n + p] = F[a];
       bad |= !isfinite(F[a]);
     }
+    // distance classes: F holds near + far; the near part comes from the second evaluation
+    const bool classes = S.f3n != nullptr;
+    double Fn[3] = {0.0, 0.0, 0.0};
+    if (classes) {
+      take_near<T>(S, p, Fn);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        S.f3n[a * n + p] = Fn[a];
+        bad |= !isfinite(Fn[a]);
+      }
+    }
     if (kind != CB_INIT) {
       const double h = 0.5 * S.dt_out * S.inv_mass;
-      double vv[3];
+      const double hn = 0.5 * S.dt_near * S.inv_mass;
+      double kk[3], vv[3];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) vv[a] = S.v[a * n + p] + h * F[a];  // closing outer kick
+      for (int a = 0; a < 3; ++a) {
+        // far class every outer step, near class every s_near inner steps
+        kk[a] = classes ? h * (F[a] - Fn[a]) + hn * Fn[a] : h * F[a];
+        vv[a] = S.v[a * n + p] + kk[a];  // closing kicks
+      }
       if (energy) ek = 0.5 * S.mass * (vv[0] * vv[0] + vv[1] * vv[1] + vv[2] * vv[2]);
       if (kind == CB_CONT) {
         const double* X = S.X[it.buf];
@@ -1113,12 +1159,13 @@ __global__ void __launch_bounds__(256) k_combine(const SysDev* __restrict__ sys,
         double xn[3], rel[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-          vv[a] += h * F[a] + 0.5 * S.dt_in * S.inv_mass * S.f2[a * n + p];  // opening kicks of the next step
+          vv[a] += kk[a] + 0.5 * S.dt_in * S.inv_mass * S.f2[a * n + p];  // opening kicks of the next step
           xn[a] = X[a * n + p] + S.dt_in * vv[a];
           Xo[a * n + p] = xn[a];
         }
         cell_rel(S, cell, xn, rel);
         store_pos<T>(S, 0, p, rel, true);
+        store_fixed(S, p, xn);
       }
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
@@ -1148,8 +1195,12 @@ __global__ void __launch_bounds__(256) k_start(const SysDev* __restrict__ sys, c
   bool bad = false;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    double vv = S.v[a * n + p] + 0.5 * S.dt_out * S.inv_mass * S.f3[a * n + p] +
-                0.5 * S.dt_in * S.inv_mass * S.f2[a * n + p];
+    const double f3 = S.f3[a * n + p];
+    // distance classes: far part (f3 - f3n) with the outer step, near part with s_near dt
+    const double k3 = S.f3n ? 0.5 * S.dt_out * S.inv_mass * (f3 - S.f3n[a * n + p]) +
+                                  0.5 * S.dt_near * S.inv_mass * S.f3n[a * n + p]
+                            : 0.5 * S.dt_out * S.inv_mass * f3;
+    double vv = S.v[a * n + p] + k3 + 0.5 * S.dt_in * S.inv_mass * S.f2[a * n + p];
     S.v[a * n + p] = vv;
     xn[a] = X[a * n + p] + S.dt_in * vv;
     Xo[a * n + p] = xn[a];
@@ -1157,6 +1208,7 @@ __global__ void __launch_bounds__(256) k_start(const SysDev* __restrict__ sys, c
   }
   cell_rel(S, S.pcell[p], xn, rel);
   store_pos<T>(S, 0, p, rel, true);
+  store_fixed(S, p, xn);
   if (bad) atomicOr(&S.flags[FLG_ERR], ERR_NONFINITE);
 }
 

@@ -29,7 +29,7 @@ enum : int {
 // accumulator slots in SysDev::acc (double)
 enum : int { ACC_U2 = 0, ACC_W2 = 1, ACC_U3 = 2, ACC_W3 = 3, ACC_EK = 4, ACC_N = 8 };
 // counter slots in SysDev::ctr (unsigned long long)
-enum : int { CTR_TRIPLETS = 0, CTR_GUARD = 1, CTR_N = 4 };
+enum : int { CTR_TRIPLETS = 0, CTR_GUARD = 1, CTR_NEAR = 2, CTR_N = 4 };  // CTR_NEAR: near-class triplets
 // flag slots in SysDev::flags (int)
 enum : int { FLG_ERR = 0, FLG_SKIN = 1, FLG_MAXCELL = 2, FLG_N = 4 };
 
@@ -53,6 +53,14 @@ struct SysDev {
   float f_rc3sq, f_guard3, f_nu, f_reach2, f_half_skin_sq, f_qscale;  // f_qscale = L / 2^32
   int precision;  // 0 = FP32 forces, 1 = FP64
   int pad_;
+  // distance classes of the three-body force (all NULL / zero when off): near = triplets whose three
+  // pair distances are <= r_a, integrated every s_near inner steps; far = the rest within r_c3
+  double rasq, guarda;        // r_a^2 and the half-width of its FP64 re-decision band
+  double dt_near;             // s_near * dt_in
+  float f_rasq, f_guarda;
+  int *half_a, *half_a_cnt;   // [n][kHalfCap], [n]: half lists at r_a (same order and ownership)
+  double *f3n;                // [3][n] cached near-class force (f3 holds near + far)
+  void *f3nacc;               // like f3acc, for the near-class evaluation
   // state in cell-sorted order, double SoA [3][n] (x block, y block, z block)
   double *X[2];       // positions, ping-pong by inner-step parity
   double *v, *f2, *f3;
@@ -111,6 +119,8 @@ enum : int {
   M_F3READY = 1 << 9,   // combine: f3 already holds complete forces (per-particle triplet kernel)
   M_SKIP = 1 << 10,     // batch: this member does nothing in this launch
   M_F3ACC = 1 << 11,    // combine: read (and clear) the rotation kernel's per-particle sums
+  M_NEAR = 1 << 12,     // distance classes: near-class triplet evaluation (rotation kernel), half lists
+                        // at r_a only (pair-list build), near-class kick after an LJ step (k_kick)
   M_TABLE = 1 << 30,    // batch: the low bits index SysDev::mode_tab, which holds the real mode
   M_TABLE_MASK = 0xffff,
   M_KIND_MASK = 0xff,
@@ -149,6 +159,8 @@ template <> struct Par<float> {
   static __device__ __forceinline__ float nu(const SysDev& S) { return S.f_nu; }
   static __device__ __forceinline__ float reach2(const SysDev& S) { return S.f_reach2; }
   static __device__ __forceinline__ float half_skin_sq(const SysDev& S) { return S.f_half_skin_sq; }
+  static __device__ __forceinline__ float rasq(const SysDev& S) { return S.f_rasq; }
+  static __device__ __forceinline__ float guarda(const SysDev& S) { return S.f_guarda; }
 };
 template <> struct Par<double> {
   static __device__ __forceinline__ double edge(const SysDev& S) { return S.edge; }
@@ -167,6 +179,8 @@ template <> struct Par<double> {
     return r * r;
   }
   static __device__ __forceinline__ double half_skin_sq(const SysDev& S) { return S.half_skin_sq; }
+  static __device__ __forceinline__ double rasq(const SysDev& S) { return S.rasq; }
+  static __device__ __forceinline__ double guarda(const SysDev& S) { return S.guarda; }
 };
 
 template <typename T> struct V4;
@@ -190,6 +204,11 @@ __device__ __forceinline__ int cell_coord(double x, double inv_edge, int nc) {
 // r2 = (dx*dx + dy*dy) + dz*dz; counts iff r2 <= rcsq.  The _rn intrinsics
 // forbid fused multiply-add contraction, so the result is bit-identical to a
 // plain IEEE evaluation.
+// fixed-point coordinate (2^32 units per box side): the 64-bit rounding wraps modulo 2^32 for any x
+__device__ __forceinline__ int to_fixed(double x, double qinv) {
+  return (int)(unsigned)(unsigned long long)__double2ll_rn(x * qinv);
+}
+
 __device__ __forceinline__ bool exact_within(const double* __restrict__ X, int n, int i, int j, double L,
                                              double rcsq) {
   double r2 = 0.0;
