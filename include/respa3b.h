@@ -139,12 +139,11 @@ md_status md_set_state(md_system *s, const double *pos, const double *vel);
  * s_near (kicks s_near dt / 2 F3near / m around every block of s_near inner steps), the far class
  * with the outer step (kicks dt_outer / 2 (F3 - F3near) / m).  k_inner must be a multiple of s_near
  * (MD_ERR_ARG otherwise); s_near = k_inner, or r_a below every pair distance, is Algorithm 2 again.
- * Requires 0 < r_a <= min(r_c2, r_c3) and r_c3 <= r_c2 + skin (the rotation triplet kernel, the only
- * one with a near-class mode); single systems only (md_batch_submit rejects them, MD_ERR_ARG).
- * r_a <= 0 turns the classes off.  Reallocates the handle's device memory (state kept) and
- * invalidates the cached forces.  Triplet half lists longer than 64 give MD_ERR_CAPACITY (no
- * fallback kernel).  The near-class lists are rebuilt from the current positions before every near
- * evaluation between two binnings (exact cutoff decisions, as for r_c3). */
+ * Requires 0 < r_a <= min(r_c2, r_c3); single systems only (md_batch_submit rejects them,
+ * MD_ERR_ARG).  r_a <= 0 turns the classes off.  Reallocates the handle's device memory (state kept)
+ * and invalidates the cached forces.  At every binning each particle keeps as near-class candidates
+ * its neighbours above it (the triplet ownership order) within r_a + skin; more than 64 give
+ * MD_ERR_CAPACITY.  Every near evaluation re-decides r_a exactly at the current positions. */
 md_status md_set_distance_classes(md_system *s, double r_a, int s_near);
 
 /* Cached near-class ATM forces F3near (n x 3, caller order) at the current positions; md_get_forces'

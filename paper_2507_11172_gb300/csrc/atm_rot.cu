@@ -3,7 +3,7 @@
 // future-work traversal of Sec. 5).
 //
 // Ownership.  A triplet belongs to its lowest member in the order "cell layer along z, then z in fixed
-// point (positions of the evaluated configuration, box = 2^32 units), then sorted index".  Within a triangle of
+// point (positions of the last binning, box = 2^32 units), then sorted index".  Within a triangle of
 // particles closer than r_c the unwrapped cell layers differ by at most one (cell edge >= r_c, at least
 // three cells per side) and the fixed-point z differences are exact wrapping 32-bit integers, so the
 // order is a total order on every triangle: each triplet has exactly one owner.  The owner i sees the
@@ -37,10 +37,6 @@
 // around r_c^2 is re-decided in FP64 from the FP64 positions with the CPU definition's operation
 // order (exact_within).  Pair tests inside the rotation run in FP32 first; a phase that met the band
 // is discarded and repeated with exact decisions.
-//
-// Distance classes (M_NEAR).  The near-class evaluation runs the same kernel on the half lists cut at
-// r_a (S.half_a) with r_a as the cutoff of every pair test: it finds exactly the triplets whose three
-// distances are <= r_a, and adds their forces to a second set of sums (S.f3nacc).
 #include "md_internal.cuh"
 
 namespace r3b {
@@ -670,25 +666,23 @@ __global__ void __launch_bounds__(32 * kZrWarps, sizeof(T) == 4 ? 7 : 4)
   const SysDev& S = sys[it.sys];
   const int imode = item_mode(S, it.mode);
   if (imode & M_SKIP) return;  // block-uniform
-  // near class (distance classes): the half lists, cutoff and sums at r_a; energy only with all triplets
-  const bool nearc = (imode & M_NEAR) != 0;
-  const bool energy = (imode & M_ENERGY) != 0 && !nearc;
+  const bool energy = (imode & M_ENERGY) != 0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    K.half = reinterpret_cast<const unsigned*>(nearc ? S.half_a : S.half);
-    K.half_cnt = nearc ? S.half_a_cnt : S.half_cnt;
+    K.half = reinterpret_cast<const unsigned*>(S.half);
+    K.half_cnt = S.half_cnt;
     K.ipos = S.ipos;
     K.X = S.X[it.buf];
     K.pos = S.pos[it.buf];
-    K.f3acc = nearc ? S.f3nacc : S.f3acc;
+    K.f3acc = S.f3acc;
     K.ctr = S.ctr;
     K.flags = S.flags;
     K.L = S.L;
-    K.rc3sq = nearc ? S.rasq : S.rc3sq;
+    K.rc3sq = S.rc3sq;
     K.nu = S.nu;
     K.edge = S.edge;
-    K.rcsq = nearc ? Par<T>::rasq(S) : Par<T>::rc3sq(S);
-    K.g = nearc ? Par<T>::guarda(S) : Par<T>::guard3(S);
+    K.rcsq = Par<T>::rc3sq(S);
+    K.g = Par<T>::guard3(S);
     K.fs = (T)0.75 * Par<T>::nu(S);
     K.qscale = S.f_qscale;
     K.n = S.n;
@@ -745,7 +739,7 @@ __global__ void __launch_bounds__(32 * kZrWarps, sizeof(T) == 4 ? 7 : 4)
     if (atomicAdd(&s_done, 1) == kZrWarps - 1) {  // last warp of the CTA
       __threadfence_block();
       const unsigned long long ct = atomicAdd(&s_cnt, 0ull);
-      if (ct) atomicAdd(K.ctr + (nearc ? CTR_NEAR : CTR_TRIPLETS), ct);
+      if (ct) atomicAdd(K.ctr + CTR_TRIPLETS, ct);
       if (energy) {
         const double U = K.nu * atomicAdd(&s_u, 0.0);
         atomicAdd(S.acc + ACC_U3, U);

@@ -116,7 +116,7 @@ struct md_system {
 
 namespace {
 
-enum KTag { T_BIN = 1, T_SCATTER, T_LIST, T_LJ, T_COMB, T_START, T_KIN, T_ATMPA, T_ATMROT, T_KICK };
+enum KTag { T_BIN = 1, T_SCATTER, T_LIST, T_LJ, T_COMB, T_START, T_KIN, T_ATMPA, T_ATMROT, T_KICK, T_NEARL, T_ATMNEAR };
 
 void free_items(md_system* s) {
   for (void* p : s->item_allocs) cudaFree(p);
@@ -349,6 +349,7 @@ md_status upload_desc(md_system* s, double dt_in, double dt_out) {
   h.dt_near = s->s_near * dt_in;
   h.f_rasq = (float)h.rasq;
   h.f_guarda = (float)h.guarda;
+  h.f_nearcand = (float)((s->r_a + s->skin) * (s->r_a + s->skin) * (1.0 + 1e-4));
   h.mass = s->mass;
   h.inv_mass = 1.0 / s->mass;
   h.maxnb = s->maxnb;
@@ -398,12 +399,16 @@ PItem* pitems_for(md_system* s, int tag, int mode, int buf) {
   const int per = (tag == T_LJ)      ? kLjPer
                   : (tag == T_ATMPA)  ? kPaPerBlock
                   : (tag == T_ATMROT) ? rot_bases_per_item(s->precision)
+                  : (tag == T_NEARL)  ? kNearWarps
+                  : (tag == T_ATMNEAR) ? kNearThreads
                                       : kBlock;
   const int nb = (tag == T_LJ)       ? (s->n + kLjPer - 1) / kLjPer
                  : (tag == T_ATMPA)  ? s->nblocks_pa
                  : (tag == T_ATMROT) ? s->nblocks_rot
+                 : (tag == T_NEARL)  ? (int)((s->n + kNearWarps - 1) / kNearWarps)
+                 : (tag == T_ATMNEAR) ? (int)((s->n + kNearThreads - 1) / kNearThreads)
                                      : s->nblocks;
-  if (tag == T_LJ || tag == T_ATMROT || tag == T_KICK) {
+  if (tag == T_LJ || tag == T_ATMROT || tag == T_KICK || tag == T_NEARL || tag == T_ATMNEAR) {
     // Gather kernels: the block scheduler hands consecutive blocks to different SMs, so blocks
     // b, b + nsm, b + 2 nsm, ... tend to share an SM.  Giving those blocks adjacent particle ranges
     // keeps each SM's neighbour gathers within one region of the box (L1 reuse); the order of the
@@ -465,8 +470,8 @@ md_status prepare_items(md_system* s) {
     }
     if (s->r_a > 0) {  // distance classes
       pitems_for(s, T_KICK, LJ_MID | M_NEAR, b);
-      pitems_for(s, T_ATMROT, M_NEAR, b);
-      citems_for(s, M_NEAR, b);
+      pitems_for(s, T_NEARL, 0, b);
+      pitems_for(s, T_ATMNEAR, 0, b);
     }
   }
   pitems_for(s, T_KIN, 0, 0);
@@ -547,11 +552,8 @@ struct Plan {
     launch_scan(L, s->sitem, 1);
     launch_scatter<T>(L, pitems_for(s, T_SCATTER, 0, buf), s->nblocks, kBlock);
     launch_listbuild<T>(L, citems_for(s, 0, buf), s->ncell, 27 * s->cap_cell);
-  }
-  // half lists at r_a of the current positions (distance classes, between two binnings)
-  template <typename T>
-  void near_lists(int buf) {
-    launch_listbuild<T>(L, citems_for(s, M_NEAR, buf), s->ncell, 27 * s->cap_cell);
+    if (s->r_a > 0)  // distance classes: near-class candidates, ranked by this binning
+      launch_near_lists(L, pitems_for(s, T_NEARL, 0, buf), padded_blocks((int)((s->n + kNearWarps - 1) / kNearWarps)));
   }
   // LJ forces and the velocity-Verlet kick/drift; with near = true (distance classes, LJ_MID) the
   // near-class triplets are evaluated between the two and their kicks join the LJ kick
@@ -563,22 +565,28 @@ struct Plan {
     if (kind != LJ_INIT)
       launch_kick<T>(L, pitems_for(s, T_KICK, kind | (near ? M_NEAR : 0), buf), padded_blocks(s->nblocks));
   }
+  // distance classes: the near-class triplets at the current positions
   template <typename T>
   void atm_near(int buf) {
-    launch_atm_rot<T>(L, pitems_for(s, T_ATMROT, M_NEAR, buf), padded_blocks(s->nblocks_rot));
+    launch_atm_near<T>(L, pitems_for(s, T_ATMNEAR, 0, buf), padded_blocks((int)((s->n + kNearThreads - 1) / kNearThreads)));
   }
+  // every triplet within r_c3, with the chosen kernel
   template <typename T>
-  void atm(int buf, bool energy, int ev) {
-    if (ev >= 0) cudaEventRecord(s->events[2 * ev], L.stream);
-    if (s->atm_variant == 2) {
+  void atm_all(int buf, bool energy) {
+    if (s->atm_variant == 2)
       launch_atm_rot<T>(L, pitems_for(s, T_ATMROT, energy ? M_ENERGY : 0, buf), padded_blocks(s->nblocks_rot));
-      if (s->r_a > 0) atm_near<T>(buf);  // distance classes: the near class of the same configuration
-    } else if (s->atm_variant == 1)
+    else if (s->atm_variant == 1)
       launch_atm_pa<T>(L, pitems_for(s, T_ATMPA, energy ? M_ENERGY : 0, buf), s->nblocks_pa);
     else
       launch_atm<T>(L, citems_for(s, energy ? M_ENERGY : 0, buf), s->ncell, s->atm_grid,
                     atm_stage_capacity(s->cap_cell));
+  }
+  template <typename T>
+  void atm(int buf, bool energy, int ev) {
+    if (ev >= 0) cudaEventRecord(s->events[2 * ev], L.stream);
+    atm_all<T>(buf, energy);
     if (ev >= 0) cudaEventRecord(s->events[2 * ev + 1], L.stream);
+    if (s->r_a > 0) atm_near<T>(buf);  // distance classes: the near class of the same configuration
   }
   template <typename T>
   void combine(int kind, int buf, bool energy) {
@@ -617,10 +625,7 @@ void enqueue_steps(Plan& P, int n_outer, int k, int cur, bool safe, bool profile
       const int b = t & 1;
       // distance classes: iteration t closes a block of s_near inner steps
       const bool near = P.s->r_a > 0 && t < k - 1 && (t + 1) % P.s->s_near == 0;
-      if (t == k - 1 || safe)
-        P.sort<T>(b);  // binning + pair list at the outer boundary
-      else if (near)
-        P.near_lists<T>(b);
+      if (t == k - 1 || safe) P.sort<T>(b);  // binning + pair list at the outer boundary
       if (t < k - 1)
         P.lj<T>(LJ_MID, b, false, near);
       else
@@ -748,6 +753,10 @@ md_status finish_call(md_system* s, int n_outer) {
 md_status status_from_flags(md_system* s) {
   int err = s->h_flags[FLG_ERR];
   if (err & ERR_NONFINITE) return MD_ERR_NONFINITE;
+  if (err & ERR_NEAR_CAP) {
+    g_last_error = "distance classes: more than 64 near-class candidates (neighbours above within r_a + skin)";
+    return MD_ERR_CAPACITY;
+  }
   if (err & (ERR_CELL_CAP | ERR_NBR_CAP | ERR_HALF_CAP)) return MD_ERR_CAPACITY;
   if (err & ERR_TIMEOUT) return MD_ERR_DEVICE_TIMEOUT;
   return MD_OK;
@@ -762,14 +771,6 @@ bool variant_allowed(const md_system* s, int v) {
 // each allowed variant is launched a few times on the same configuration with CUDA events
 // around each launch; the faster one is kept for the system.
 md_status tune_atm(md_system* s) {
-  if (s->r_a > 0) {  // distance classes run on the rotation kernel only
-    if (!variant_allowed(s, 2)) {
-      g_last_error = "distance classes need the rotation triplet kernel (r_c3 <= r_c2 + skin)";
-      return MD_ERR_ARG;
-    }
-    s->atm_variant = 2;
-    return MD_OK;
-  }
   const int req = s->atm_variant_req;
   if (req >= 0) {
     s->atm_variant = variant_allowed(s, req) ? req : 0;
@@ -795,7 +796,7 @@ md_status tune_atm(md_system* s) {
     float tot = 0.f;
     for (int r = 0; r < 4; ++r) {
       CK(cudaEventRecord(s->events[0], s->stream));
-      if (s->precision) P.atm<double>(s->cur, false, -1); else P.atm<float>(s->cur, false, -1);
+      if (s->precision) P.atm_all<double>(s->cur, false); else P.atm_all<float>(s->cur, false);
       CK(cudaEventRecord(s->events[1], s->stream));
       CK(cudaEventSynchronize(s->events[1]));
       float ms = 0.f;
@@ -851,15 +852,6 @@ md_status do_call(md_system* s, int n_outer, int k, double dt_outer) {
     // the rotation and per-particle kernels hold shorter half lists than the cell kernel
     const bool half_bad = (err & ERR_HALF_CAP) != 0 && s->atm_variant != 0;
     s->stats.max_cell_count = s->h_flags[FLG_MAXCELL];
-    if (half_bad && s->r_a > 0) {  // no fallback kernel for distance classes
-      s->cur = cur0;
-      snapshot(s, false);
-      s->forces_valid = false;
-      s->energy_valid = false;
-      cudaStreamSynchronize(s->stream);
-      g_last_error = "distance classes: a triplet half list exceeds 64 neighbours";
-      return MD_ERR_CAPACITY;
-    }
     if (!(skin_bad || cap_bad || half_bad) || (err & ERR_NONFINITE)) {
       md_status fs = status_from_flags(s);
       if (fs != MD_OK) {

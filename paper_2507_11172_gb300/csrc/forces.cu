@@ -103,12 +103,6 @@ __device__ __forceinline__ void store_pos(const SysDev& S, int buf, int i, const
   }
 }
 
-// distance classes: near-class evaluations between two binnings read the fixed-point positions, so
-// every drift refreshes them
-__device__ __forceinline__ void store_fixed(const SysDev& S, int i, const double xn[3]) {
-  if (S.f3n) S.ipos[i] = make_int4(to_fixed(xn[0], S.qinv), to_fixed(xn[1], S.qinv), to_fixed(xn[2], S.qinv), 0);
-}
-
 // near-class force of particle p from the rotation kernel's sums (read and cleared)
 template <typename T>
 __device__ __forceinline__ void take_near(const SysDev& S, int p, double f[3]) {
@@ -340,7 +334,6 @@ __global__ void __launch_bounds__(256) k_kick(const SysDev* __restrict__ sys, co
     }
     cell_rel(S, S.pcell[i], xn, rel);
     store_pos<T>(S, it.buf ^ 1, i, rel, true);
-    store_fixed(S, i, xn);
   } else {
     const double c = 0.5 * S.dt_in * S.inv_mass;
 #pragma unroll
@@ -1165,7 +1158,6 @@ __global__ void __launch_bounds__(256) k_combine(const SysDev* __restrict__ sys,
         }
         cell_rel(S, cell, xn, rel);
         store_pos<T>(S, 0, p, rel, true);
-        store_fixed(S, p, xn);
       }
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
@@ -1208,7 +1200,6 @@ __global__ void __launch_bounds__(256) k_start(const SysDev* __restrict__ sys, c
   }
   cell_rel(S, S.pcell[p], xn, rel);
   store_pos<T>(S, 0, p, rel, true);
-  store_fixed(S, p, xn);
   if (bad) atomicOr(&S.flags[FLG_ERR], ERR_NONFINITE);
 }
 

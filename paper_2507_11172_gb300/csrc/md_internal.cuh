@@ -15,6 +15,8 @@ constexpr int kAtmWarps = 8;
 constexpr int kAtmThreads = 32 * kAtmWarps;
 constexpr int kQueue = 256;         // per-warp queue of accepted neighbour pairs (j, k)
 constexpr int kListWarps = 4;       // warps per CTA of the pair-list build
+constexpr int kNearWarps = 8;       // particles (one warp each) per CTA of the near-class candidate lists
+constexpr int kNearThreads = 128;   // owners (one thread each) per CTA of the near-class triplet kernel
 constexpr int kHalfCap = 64;        // triplet half list per particle (neighbours above it within r_c3)
 
 // error bits in SysDev::flags[0]
@@ -24,6 +26,7 @@ enum : int {
   ERR_HALF_CAP = 4,   // an ATM half list overflowed kMaxHalf
   ERR_NONFINITE = 8,  // NaN / Inf in positions, velocities or forces
   ERR_TIMEOUT = 16,   // a bounded wait gave up
+  ERR_NEAR_CAP = 32,  // distance classes: a near-class candidate list overflowed kHalfCap
 };
 
 // accumulator slots in SysDev::acc (double)
@@ -58,7 +61,10 @@ struct SysDev {
   double rasq, guarda;        // r_a^2 and the half-width of its FP64 re-decision band
   double dt_near;             // s_near * dt_in
   float f_rasq, f_guarda;
-  int *half_a, *half_a_cnt;   // [n][kHalfCap], [n]: half lists at r_a (same order and ownership)
+  float f_nearcand;           // (r_a + skin)^2 widened by 1e-4: candidate test of k_near_lists
+  int pad2_;
+  int *half_a, *half_a_cnt;   // [n][kHalfCap], [n]: near-class candidates of each particle (neighbours
+                              // above it within r_a + skin at the last binning), from k_near_lists
   double *f3n;                // [3][n] cached near-class force (f3 holds near + far)
   void *f3nacc;               // like f3acc, for the near-class evaluation
   // state in cell-sorted order, double SoA [3][n] (x block, y block, z block)
@@ -119,8 +125,7 @@ enum : int {
   M_F3READY = 1 << 9,   // combine: f3 already holds complete forces (per-particle triplet kernel)
   M_SKIP = 1 << 10,     // batch: this member does nothing in this launch
   M_F3ACC = 1 << 11,    // combine: read (and clear) the rotation kernel's per-particle sums
-  M_NEAR = 1 << 12,     // distance classes: near-class triplet evaluation (rotation kernel), half lists
-                        // at r_a only (pair-list build), near-class kick after an LJ step (k_kick)
+  M_NEAR = 1 << 12,     // distance classes: near-class kick after an LJ step (k_kick)
   M_TABLE = 1 << 30,    // batch: the low bits index SysDev::mode_tab, which holds the real mode
   M_TABLE_MASK = 0xffff,
   M_KIND_MASK = 0xff,
@@ -359,6 +364,8 @@ void launch_stamp(cudaStream_t s, unsigned long long* out);
 void launch_scan(const Launch& L, const SItem* items, int nitems);
 template <typename T> void launch_scatter(const Launch& L, const PItem* items, int nitems, int block);
 template <typename T> void launch_listbuild(const Launch& L, const CItem* items, int nitems, int smax);
+void launch_near_lists(const Launch& L, const PItem* items, int nitems);
+template <typename T> void launch_atm_near(const Launch& L, const PItem* items, int nitems);
 int listbuild_configure(int smax, int precision);
 // forces.cu
 // LJ pair forces: items of kLjPer particles (one thread each)

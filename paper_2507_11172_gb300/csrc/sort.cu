@@ -136,11 +136,8 @@ __global__ void k_scatter(const SysDev* __restrict__ sys, const PItem* __restric
 // (S.half, S.half_cnt): the entries j with r_ij <= r_c3 (guard band around r_c3^2
 // re-decided in FP64 with the CPU definition's operation order) that lie above i in the
 // order "cell layer along z, then fixed-point z, then sorted index", which makes i the
-// owner of every triplet whose other two members are in that list.  With distance classes
-// on, the pass also writes the half lists at r_a (S.half_a): the same entries, cut at r_a.
-// The CTA also moves the permuted state of b's particles back into place.
-// M_NEAR (between two binnings): only the half lists at r_a, from the existing pair-list rows
-// and the current positions (buffer it.buf, fixed point updated by the kick), with no sort.
+// owner of every triplet whose other two members are in that list.  The CTA also moves
+// the permuted state of b's particles back into place.
 template <typename T>
 __global__ void __launch_bounds__(32 * kListWarps)
     k_listbuild(const SysDev* __restrict__ sys, const CItem* __restrict__ items, int smax) {
@@ -152,9 +149,7 @@ __global__ void __launch_bounds__(32 * kListWarps)
   __shared__ int st_begin[28], st_cnt[27], st_cell[27];
   const CItem it = items[blockIdx.x];
   const SysDev& S = sys[it.sys];
-  const int imode = item_mode(S, it.mode);
-  if (imode & M_SKIP) return;
-  const bool near_only = (imode & M_NEAR) != 0;
+  if (item_mode(S, it.mode) & M_SKIP) return;
   const int b = it.cell, nc = S.nc, n = S.n;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
@@ -206,14 +201,11 @@ __global__ void __launch_bounds__(32 * kListWarps)
   const int i0 = S.cell_start[b];
   const double* Xa = S.X[it.buf ^ 1];
   double* X = S.X[it.buf];
-  const double* Xe = near_only ? X : Xa;  // FP64 positions in the sorted order (exact re-decisions)
   // staged slot of a list entry: its index plus the offset of its stencil cell in the staging
   __shared__ int st_delta[27];
   if (threadIdx.x < 27) st_delta[threadIdx.x] = st_begin[threadIdx.x] - S.cell_start[st_cell[threadIdx.x]];
   __syncthreads();
   const T rc3 = (T)S.rc3sq, g3 = (T)S.guard3;
-  const T ra = (T)S.rasq, ga = (T)S.guarda;
-  const bool want_all = !near_only, want_near = S.half_a != nullptr;
   for (int ib = warp; ib < nbase; ib += kListWarps) {
     const int islot = st_begin[13] + ib;
     const int i = i0 + ib;
@@ -221,7 +213,7 @@ __global__ void __launch_bounds__(32 * kListWarps)
     int cnt = 0;
     int* row = S.nbr + (size_t)i * S.maxnb;
     // pass 1: every staged particle within the list radius
-    for (int t0 = 0; t0 < (near_only ? 0 : nstaged); t0 += 32) {
+    for (int t0 = 0; t0 < nstaged; t0 += 32) {
       const int t = t0 + lane;
       bool ok = false;
       if (t < nstaged && t != islot) {
@@ -234,9 +226,7 @@ __global__ void __launch_bounds__(32 * kListWarps)
       if (ok && pos < S.maxnb) row[pos] = sj[t];
       cnt += __popc(bal);
     }
-    if (near_only) {
-      cnt = S.nbr_cnt[i];
-    } else if (lane == 0) {
+    if (lane == 0) {
       if (cnt > S.maxnb) atomicOr(&S.flags[FLG_ERR], ERR_NBR_CAP);
       S.nbr_cnt[i] = min(cnt, S.maxnb);
     }
@@ -245,11 +235,10 @@ __global__ void __launch_bounds__(32 * kListWarps)
     // pass 2: the triplet half list among the list entries
     const int qzi = sqz[islot];
     int* hrow = S.half + (size_t)i * kHalfCap;
-    int* arow = want_near ? S.half_a + (size_t)i * kHalfCap : nullptr;
-    int mh = 0, ma = 0;
+    int mh = 0;
     for (int t0 = 0; t0 < cnt; t0 += 32) {
       const int t = t0 + lane;
-      bool half = false, band = false, nearh = false, banda = false;
+      bool half = false, band = false;
       unsigned e = 0u;
       if (t < cnt) {
         e = (unsigned)row[t];
@@ -264,47 +253,23 @@ __global__ void __launch_bounds__(32 * kListWarps)
           const T4 q = sp[slot];
           const T dx = q.x - pi.x, dy = q.y - pi.y, dz = q.z - pi.z;
           const T r2 = dx * dx + dy * dy + dz * dz;
-          if (want_all) {
-            half = r2 <= rc3 - g3;
-            band = !half && r2 <= rc3 + g3;
-          }
-          if (want_near) {
-            nearh = r2 <= ra - ga;
-            banda = !nearh && r2 <= ra + ga;
-          }
+          half = r2 <= rc3 - g3;
+          band = !half && r2 <= rc3 + g3;
         }
       }
-      if (want_all) {
-        if (__any_sync(0xffffffffu, band)) {
-          if (band) {
-            atomicAdd(&S.ctr[CTR_GUARD], 1ull);
-            half = exact_within(Xe, n, i, (int)(e & kNbrMask), S.L, S.rc3sq);
-          }
+      if (__any_sync(0xffffffffu, band)) {
+        if (band) {
+          atomicAdd(&S.ctr[CTR_GUARD], 1ull);
+          half = exact_within(Xa, n, i, (int)(e & kNbrMask), S.L, S.rc3sq);
         }
-        const unsigned balh = __ballot_sync(0xffffffffu, half);
-        const int hpos = mh + __popc(balh & lt);
-        if (half && hpos < kHalfCap) hrow[hpos] = (int)e;
-        mh += __popc(balh);
       }
-      if (want_near) {
-        if (__any_sync(0xffffffffu, banda)) {
-          if (banda) {
-            atomicAdd(&S.ctr[CTR_GUARD], 1ull);
-            nearh = exact_within(Xe, n, i, (int)(e & kNbrMask), S.L, S.rasq);
-          }
-        }
-        const unsigned bala = __ballot_sync(0xffffffffu, nearh);
-        const int apos = ma + __popc(bala & lt);
-        if (nearh && apos < kHalfCap) arow[apos] = (int)e;
-        ma += __popc(bala);
-      }
+      const unsigned balh = __ballot_sync(0xffffffffu, half);
+      const int hpos = mh + __popc(balh & lt);
+      if (half && hpos < kHalfCap) hrow[hpos] = (int)e;
+      mh += __popc(balh);
     }
-    if (lane == 0) {  // more than kHalfCap: the triplet kernel reports ERR_HALF_CAP
-      if (want_all) S.half_cnt[i] = mh;
-      if (want_near) S.half_a_cnt[i] = ma;
-    }
+    if (lane == 0) S.half_cnt[i] = mh;  // more than kHalfCap: the triplet kernel reports ERR_HALF_CAP
   }
-  if (near_only) return;  // nothing was permuted
   // every particle of b: permuted state back into place
   for (int ib = threadIdx.x; ib < st_cnt[13]; ib += blockDim.x) {
     const int i = i0 + ib;

@@ -1,5 +1,6 @@
 """Energy-conservation sweep of the method (Sec. 4.2.1, toy scenario): relative variation in true
-energy, RVITE (Eq. 4), over the step-size factor s and the ATM strength nu.
+energy, RVITE (Eq. 4), over the step-size factor s and the ATM strength nu, and the histogram of the
+relative deviation of the total energy from the Stormer-Verlet run (s = 1) at the same times.
 
 Scenario (Sec. 4.2): 675 particles in a periodic 10 x 10 x 10 box, eps = sigma = m = 1,
 dt = 0.001 (the paper's inner step), 24 000 iterations, s = 1 .. 12, nu in [0.05, 1.0].  The paper
@@ -37,6 +38,18 @@ def rvite(e_tot, e_kin) -> float:
     return float(np.mean(np.abs(e_tot - e_tot.mean())) / np.mean(e_kin))
 
 
+def deviation_histogram(e_s, e_1, s: int, bins: int = 50):
+    """Sec. 4.2.1: relative deviation of the total energy of a run with step-size factor s from the
+    Stormer-Verlet run (s = 1) at the same times, (E_s(j) - E_1(j s)) / |E_1(j s)|, as a histogram of
+    `bins` equal bins over its range.  e_s[j] is the energy after j + 1 full steps of s iterations,
+    e_1[k] after k + 1 iterations.  Returns (counts, edges)."""
+    e_1 = np.asarray(e_1, dtype=np.float64)[s - 1::s]
+    e_s = np.asarray(e_s, dtype=np.float64)
+    m = min(len(e_1), len(e_s))
+    dev = (e_s[:m] - e_1[:m]) / np.abs(e_1[:m])
+    return np.histogram(dev, bins=bins)
+
+
 def run_point(x, L, v, nu: float, s: int, iters: int, dt: float = 0.001, equil: int = 2000,
               precision: int = MD_FP32, rc: float = 2.5):
     """One (nu, s) point: returns (RVITE, energies (J, 3) = (E_kin, U2, U3) at the full steps, seconds)."""
@@ -64,11 +77,18 @@ def main(argv=None):
     x, L, v = toy_state()
     out = []
     for nu in [float(a) for a in args.nus.split(",")]:
+        e_sv = None  # the Stormer-Verlet (s = 1) energies of this nu, for the deviation histogram
         for s in [int(a) for a in args.s.split(",")]:
             r, e, wall = run_point(x, L, v, nu, s, args.iters, precision=MD_FP64 if args.fp64 else MD_FP32)
-            out.append({"nu": nu, "s": s, "rvite": r, "full_steps": len(e), "seconds": wall,
-                        "e_mean": float(e.sum(1).mean()),
-                        "max_dev_rel": float(np.abs(e.sum(1) - e.sum(1).mean()).max() / abs(e.sum(1).mean()))})
+            point = {"nu": nu, "s": s, "rvite": r, "full_steps": len(e), "seconds": wall,
+                     "e_mean": float(e.sum(1).mean()),
+                     "max_dev_rel": float(np.abs(e.sum(1) - e.sum(1).mean()).max() / abs(e.sum(1).mean()))}
+            if s == 1:
+                e_sv = e.sum(1)
+            elif e_sv is not None:
+                counts, edges = deviation_histogram(e.sum(1), e_sv, s)
+                point["dev_hist"] = {"lo": float(edges[0]), "hi": float(edges[-1]), "counts": counts.tolist()}
+            out.append(point)
             print(json.dumps(out[-1]), flush=True)
     return out
 

@@ -24,8 +24,8 @@ def cfg1():
     return md_inputs.small_fcc_1k()
 
 
-def make(r3, w, prec, r_a, s_near, skin=None):
-    s = r3.System.create(w.x, w.L, w.v, precision=prec, nu=NU, skin=skin)
+def make(r3, w, prec, r_a, s_near, skin=None, kernel=-1):
+    s = r3.System.create(w.x, w.L, w.v, precision=prec, nu=NU, skin=skin, atm_kernel=kernel)
     s.set_distance_classes(r_a, s_near)
     return s
 
@@ -47,10 +47,22 @@ def test_class_forces_and_counts_at_x0(gpu_lib, cfg1, prec, r_a):
         _, f3 = s.forces()
         f3n = s.near_forces()
         st = s.stats()
-    assert st["atm_kernel"] == 2
     assert st["triplets_last"] == cnt and st["near_triplets_last"] == cntn
     assert force_err(f3, f3r) <= TOL[prec]
     assert force_err(f3n, f3nr) <= TOL[prec]
+
+
+@pytest.mark.parametrize("kernel", [0, 1, 2])
+def test_every_triplet_kernel_with_classes(gpu_lib, cfg1, kernel):
+    """The whole ATM force comes from any of the three triplet kernels; the near class from its own."""
+    st = oracle_run3(cfg1, 2, 4, 2, 0.008, 1.8)
+    with make(gpu_lib, cfg1, 1, 1.8, 2, kernel=kernel) as s:
+        s.step(2, 4, 0.008)
+        x, v = s.state()
+        assert s.stats()["atm_kernel"] == kernel
+    d = x - st.x
+    d -= cfg1.L * np.rint(d / cfg1.L)
+    assert np.abs(d).max() < 1e-10 and np.abs(v - st.v).max() < 1e-9
 
 
 @pytest.mark.parametrize("prec", [0, 1])
