@@ -524,6 +524,13 @@ md_status rebuild(md_system* s, bool keep_state) {
   if (st != MD_OK) return st;
   st = upload_desc(s, 0.0, 0.0);
   if (st != MD_OK) return st;
+  if (!keep_state || x.empty()) {  // fresh arena: zero state in the caller's order
+    std::vector<int> ident(n);
+    for (size_t i = 0; i < n; ++i) ident[i] = (int)i;
+    s->cur = 0;
+    CK(cudaMemcpyAsync(s->h.id, ident.data(), 4 * n, cudaMemcpyHostToDevice, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+  }
   if (keep_state && !x.empty()) {
     s->cur = 0;
     CK(cudaMemcpyAsync(s->h.X[0], x.data(), 24 * n, cudaMemcpyHostToDevice, s->stream));
@@ -912,71 +919,44 @@ md_status do_call(md_system* s, int n_outer, int k, double dt_outer) {
   return MD_ERR_CAPACITY;
 }
 
-void aos_to_soa(const double* a, std::vector<double>& s, size_t n) {
-  s.resize(3 * n);
-  for (size_t i = 0; i < n; ++i)
-    for (int c = 0; c < 3; ++c) s[c * n + i] = a[3 * i + c];
-}
 
+// caller-order AoS copy (out_aos, host) of a sorted SoA device array; the permutation runs on the
+// device (staged in snap_x, free between calls), the host only receives the result
 md_status fetch_sorted(md_system* s, const double* dsrc, double* out_aos, bool wrap) {
   const size_t n = (size_t)s->n;
-  std::vector<double> soa(3 * n);
-  std::vector<int> id(n);
-  CK(cudaMemcpyAsync(soa.data(), dsrc, 24 * n, cudaMemcpyDeviceToHost, s->stream));
-  CK(cudaMemcpyAsync(id.data(), s->h.id, 4 * n, cudaMemcpyDeviceToHost, s->stream));
+  Launch L{s->stream, s->d_sys};
+  CK(cudaMemsetAsync(s->h.flags + FLG_STATE, 0, 4, s->stream));
+  launch_take_state(L, (int)n, dsrc, s->snap_x, wrap ? 1 : 0);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(out_aos, s->snap_x, 24 * n, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaMemcpyAsync(s->h_flags + FLG_STATE, s->h.flags + FLG_STATE, 4, cudaMemcpyDeviceToHost, s->stream));
   CK(cudaStreamSynchronize(s->stream));
-  for (size_t q = 0; q < n; ++q) {
-    size_t o = (size_t)id[q];
-    if (o >= n) return MD_ERR_STATE;
-    for (int c = 0; c < 3; ++c) {
-      double x = soa[c * n + q];
-      if (wrap) {
-        x -= s->L * floor(x / s->L);
-        if (x >= s->L) x -= s->L;
-      }
-      out_aos[3 * o + c] = x;
-    }
-  }
-  return MD_OK;
+  return s->h_flags[FLG_STATE] ? MD_ERR_STATE : MD_OK;
 }
 
+// new positions and/or velocities in caller order (host AoS): copied straight into device staging
+// (the force arrays: set_state invalidates them), checked and placed into the sorted layout by a
+// kernel writing the free buffers, committed only if every value was finite
 md_status set_state_impl(md_system* s, const double* pos, const double* vel) {
   const size_t n = (size_t)s->n;
   if (!pos && !vel) return MD_OK;
-  std::vector<double> soa;
-  // bring the device state into caller order first (ids = identity afterwards)
-  std::vector<double> xcur(3 * n), vcur(3 * n);
-  md_status st = fetch_sorted(s, s->h.X[s->cur], xcur.data(), true);
-  if (st != MD_OK) return st;
-  st = fetch_sorted(s, s->h.v, vcur.data(), false);
-  if (st != MD_OK) return st;
-  if (pos) {
-    for (size_t i = 0; i < 3 * n; ++i)
-      if (!isfinite(pos[i])) return MD_ERR_NONFINITE;
-    memcpy(xcur.data(), pos, 24 * n);
-  }
-  if (vel) {
-    for (size_t i = 0; i < 3 * n; ++i)
-      if (!isfinite(vel[i])) return MD_ERR_NONFINITE;
-    memcpy(vcur.data(), vel, 24 * n);
-  }
-  for (size_t i = 0; i < 3 * n; ++i) {
-    double x = xcur[i] - s->L * floor(xcur[i] / s->L);
-    if (x >= s->L) x -= s->L;
-    xcur[i] = x;
-  }
-  std::vector<int> id(n);
-  for (size_t i = 0; i < n; ++i) id[i] = (int)i;
-  aos_to_soa(xcur.data(), soa, n);
-  std::vector<double> vs;
-  aos_to_soa(vcur.data(), vs, n);
-  s->cur = 0;
-  CK(cudaMemcpyAsync(s->h.X[0], soa.data(), 24 * n, cudaMemcpyHostToDevice, s->stream));
-  CK(cudaMemcpyAsync(s->h.v, vs.data(), 24 * n, cudaMemcpyHostToDevice, s->stream));
-  CK(cudaMemcpyAsync(s->h.id, id.data(), 4 * n, cudaMemcpyHostToDevice, s->stream));
-  CK(cudaStreamSynchronize(s->stream));
+  const bool full = pos && vel;
+  Launch L{s->stream, s->d_sys};
   s->forces_valid = false;
   s->energy_valid = false;
+  CK(cudaMemsetAsync(s->h.flags + FLG_STATE, 0, 4, s->stream));
+  if (pos) CK(cudaMemcpyAsync(s->h.f2, pos, 24 * n, cudaMemcpyHostToDevice, s->stream));
+  if (vel) CK(cudaMemcpyAsync(s->h.f3, vel, 24 * n, cudaMemcpyHostToDevice, s->stream));
+  launch_put_state(L, (int)n, pos ? s->h.f2 : nullptr, vel ? s->h.f3 : nullptr, s->cur, full ? 1 : 0);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(s->h_flags + FLG_STATE, s->h.flags + FLG_STATE, 4, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));  // the caller may reuse its buffers after return
+  const int f = s->h_flags[FLG_STATE];
+  if (f & 2) return MD_ERR_STATE;
+  if (f & 1) return MD_ERR_NONFINITE;
+  s->cur ^= 1;
+  CK(cudaMemcpyAsync(s->h.v, s->h.v_alt, 24 * n, cudaMemcpyDeviceToDevice, s->stream));
+  if (full) CK(cudaMemcpyAsync(s->h.id, s->h.id_alt, 4 * n, cudaMemcpyDeviceToDevice, s->stream));
   return MD_OK;
 }
 

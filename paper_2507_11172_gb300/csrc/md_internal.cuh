@@ -34,7 +34,7 @@ enum : int { ACC_U2 = 0, ACC_W2 = 1, ACC_U3 = 2, ACC_W3 = 3, ACC_EK = 4, ACC_N =
 // counter slots in SysDev::ctr (unsigned long long)
 enum : int { CTR_TRIPLETS = 0, CTR_GUARD = 1, CTR_NEAR = 2, CTR_N = 4 };  // CTR_NEAR: near-class triplets
 // flag slots in SysDev::flags (int)
-enum : int { FLG_ERR = 0, FLG_SKIN = 1, FLG_MAXCELL = 2, FLG_N = 4 };
+enum : int { FLG_ERR = 0, FLG_SKIN = 1, FLG_MAXCELL = 2, FLG_STATE = 3, FLG_N = 4 };  // FLG_STATE: state transfer
 
 // Device-resident description of one system.  Kernels read it from global
 // memory at run time (never from constant memory) so graphs stay valid when
@@ -361,6 +361,9 @@ struct Launch {
 void launch_bin_count(const Launch& L, const PItem* items, int nitems, int block);
 void launch_snapshot(const Launch& L, const PItem* items, int nitems, int restore);
 void launch_stamp(cudaStream_t s, unsigned long long* out);
+// state.cu (one system, sys[0])
+void launch_put_state(const Launch& L, int n, const double* pos, const double* vel, int cur, int full);
+void launch_take_state(const Launch& L, int n, const double* src, double* out, int fold);
 void launch_scan(const Launch& L, const SItem* items, int nitems);
 template <typename T> void launch_scatter(const Launch& L, const PItem* items, int nitems, int block);
 template <typename T> void launch_listbuild(const Launch& L, const CItem* items, int nitems, int smax);

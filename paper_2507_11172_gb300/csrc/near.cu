@@ -86,13 +86,18 @@ __device__ __forceinline__ void near_red(void* acc, int j, T fx, T fy, T fz) {
   }
 }
 
+// FP64 re-decision of r_pq <= r_a (out of line: rare, and it keeps the FP64 registers out of the loops)
+__device__ __noinline__ bool near_exact(const SysDev& S, const double* X, int p, int q) {
+  atomicAdd(&S.ctr[CTR_GUARD], 1ull);
+  return exact_within(X, S.n, p, q, S.L, S.rasq);
+}
+
 // r^2 <= r_a^2 in the kernel's precision, re-decided in FP64 inside the guard band
 template <typename T>
 __device__ __forceinline__ bool near_within(const SysDev& S, const double* X, T r2, T ra, T ga, int p, int q) {
   if (r2 <= ra - ga) return true;
   if (r2 > ra + ga) return false;
-  atomicAdd(&S.ctr[CTR_GUARD], 1ull);
-  return exact_within(X, S.n, p, q, S.L, S.rasq);
+  return near_exact(S, X, p, q);
 }
 
 // one near triplet (i, a, b): a = |d_a|^2, b = |d_b|^2, c = |e|^2, e = d_b - d_a; adds F_i and F_a to
@@ -125,7 +130,7 @@ __device__ __forceinline__ void near_triplet(T fs, T aa, T bb, T cc, T ax, T ay,
 
 // near nodes of a thread kept in shared memory (strided by thread); owners with more use the
 // global-memory path
-template <typename T> __host__ __device__ constexpr int near_slots() { return sizeof(T) == 4 ? 16 : 8; }
+template <typename T> __host__ __device__ constexpr int near_slots() { return sizeof(T) == 4 ? 12 : 8; }
 
 template <typename T>
 __global__ void __launch_bounds__(kNearThreads) k_atm_near(const SysDev* __restrict__ sys, const PItem* __restrict__ items) {

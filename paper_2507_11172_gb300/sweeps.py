@@ -9,9 +9,15 @@ does not state the cutoff or the initial state: this sweep uses r_c2 = r_c3 = 2.
 iterations (s = 1) before the measured run.  The total energy e(i) = E_kin + U2 + U3 is read at
 every full step (iterations divisible by s; Sec. 4.1) and RVITE = mean_i |e(i) - mean(e)| / mean(E_kin).
 
+Aluminium scenario (--scenario aluminium; Sec. 4.3, Table 1): 4995 particles in a 20 x 20 x 20 box,
+dt = 0.00304, nu = 0.3095, T* = 1.1, 24 000 iterations.  The paper runs it with open boundaries and
+states no cutoff; here it is periodic with r_c2 = r_c3 = 2.5 and starts from the same kind of jittered
+FCC state (no equilibrated aluminium configuration is available).
+
 Everything runs through the C ABI (md_respa_step with k_inner = s, dt_outer = s dt; md_get_energy).
 
-    python -m paper_2507_11172_gb300.sweeps [--iters 24000] [--nus 0.05,0.25,0.5,0.75,1.0] [--s 1,2,...]
+    python -m paper_2507_11172_gb300.sweeps [--scenario toy|aluminium] [--iters 24000]
+        [--nus 0.05,0.25,0.5,0.75,1.0] [--s 1,2,...]
 """
 from __future__ import annotations
 
@@ -30,6 +36,13 @@ def toy_state(n: int = 675, L: float = 10.0, temperature: float = 1.0, seed: int
     x, Lx = md_inputs.fcc_jitter(n, n / L ** 3, 0.05, seed)
     v = md_inputs.maxwell(n, temperature, seed + 1)
     return x, Lx, v
+
+
+# (n, box side, T*, dt, default nu values) of the two scenarios of Sec. 4.2-4.3
+SCENARIOS = {
+    "toy": (675, 10.0, 1.0, 0.001, "0.05,0.25,0.5,0.75,1.0"),
+    "aluminium": (4995, 20.0, 1.1, 0.00304, "0.3095"),
+}
 
 
 def rvite(e_tot, e_kin) -> float:
@@ -69,18 +82,20 @@ def run_point(x, L, v, nu: float, s: int, iters: int, dt: float = 0.001, equil: 
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--scenario", default="toy", choices=sorted(SCENARIOS))
     ap.add_argument("--iters", type=int, default=24000)
-    ap.add_argument("--nus", default="0.05,0.25,0.5,0.75,1.0")
+    ap.add_argument("--nus", default=None)
     ap.add_argument("--s", default=",".join(str(k) for k in range(1, 13)))
     ap.add_argument("--fp64", action="store_true")
     args = ap.parse_args(argv)
-    x, L, v = toy_state()
+    n, box, temp, dt, nus = SCENARIOS[args.scenario]
+    x, L, v = toy_state(n, box, temp)
     out = []
-    for nu in [float(a) for a in args.nus.split(",")]:
+    for nu in [float(a) for a in (args.nus or nus).split(",")]:
         e_sv = None  # the Stormer-Verlet (s = 1) energies of this nu, for the deviation histogram
         for s in [int(a) for a in args.s.split(",")]:
-            r, e, wall = run_point(x, L, v, nu, s, args.iters, precision=MD_FP64 if args.fp64 else MD_FP32)
-            point = {"nu": nu, "s": s, "rvite": r, "full_steps": len(e), "seconds": wall,
+            r, e, wall = run_point(x, L, v, nu, s, args.iters, dt=dt, precision=MD_FP64 if args.fp64 else MD_FP32)
+            point = {"scenario": args.scenario, "nu": nu, "s": s, "rvite": r, "full_steps": len(e), "seconds": wall,
                      "e_mean": float(e.sum(1).mean()),
                      "max_dev_rel": float(np.abs(e.sum(1) - e.sum(1).mean()).max() / abs(e.sum(1).mean()))}
             if s == 1:
