@@ -396,13 +396,13 @@ PItem* pitems_for(md_system* s, int tag, int mode, int buf) {
   auto it = s->pitems.find(key);
   if (it != s->pitems.end()) return it->second;
   std::vector<PItem> v;
-  const int per = (tag == T_LJ)      ? kLjPer
+  const int per = (tag == T_LJ)      ? kLjParticles
                   : (tag == T_ATMPA)  ? kPaPerBlock
                   : (tag == T_ATMROT) ? rot_bases_per_item(s->precision)
                   : (tag == T_NEARL)  ? kNearWarps
                   : (tag == T_ATMNEAR) ? kNearThreads
                                       : kBlock;
-  const int nb = (tag == T_LJ)       ? (s->n + kLjPer - 1) / kLjPer
+  const int nb = (tag == T_LJ)       ? (s->n + kLjParticles - 1) / kLjParticles
                  : (tag == T_ATMPA)  ? s->nblocks_pa
                  : (tag == T_ATMROT) ? s->nblocks_rot
                  : (tag == T_NEARL)  ? (int)((s->n + kNearWarps - 1) / kNearWarps)
@@ -567,7 +567,7 @@ struct Plan {
   template <typename T>
   void lj(int kind, int buf, bool energy, bool near = false) {
     launch_lj<T>(L, pitems_for(s, T_LJ, kind | (energy ? M_ENERGY : 0), buf),
-                 padded_blocks((s->n + kLjPer - 1) / kLjPer));
+                 padded_blocks((s->n + kLjParticles - 1) / kLjParticles));
     if (near) atm_near<T>(buf);
     if (kind != LJ_INIT)
       launch_kick<T>(L, pitems_for(s, T_KICK, kind | (near ? M_NEAR : 0), buf), padded_blocks(s->nblocks));
@@ -1508,7 +1508,7 @@ md_status batch_build(md_batch* b) {
       for (int j = 0; j < ns; ++j) {
         const Request& r = b->req[b->resident[j]];
         const int tt = t % r.k;
-        for (int q = 0; q < (int)r.s->n; q += kLjPer) pit.push_back(PItem{j, q, tab(KT_LJ), tt & 1});
+        for (int q = 0; q < (int)r.s->n; q += kLjParticles) pit.push_back(PItem{j, q, tab(KT_LJ), tt & 1});
       }
       ti.nlj = (int)(pit.size() - ti.lj);
       ti.kick = pit.size();

@@ -123,9 +123,12 @@ __device__ __forceinline__ void take_near(const SysDev& S, int p, double f[3]) {
 }
 
 // ============================================================== LJ pair kernel
-// One thread per particle i (F_i only: every pair is evaluated from both sides, no scatter).  The
-// thread walks i's pair-list row four entries at a time with a software pipeline: the row entries
-// of group g + 2 and the neighbour positions of group g + 1 are loaded while group g is evaluated.
+// A team of kLjTeam adjacent threads per particle i (F_i only: every pair is evaluated from both
+// sides, no scatter).  Thread h of the team walks the groups h, h + kLjTeam, ... of four consecutive
+// entries of i's pair-list row with a software pipeline: the row entries of its group after next and
+// the neighbour positions of its next group are loaded while its current group is evaluated; a team's
+// partial forces are added in FP64 at the end.  On GB300 one thread per particle is fastest (teams of
+// 2 and 4 measured 3 % and 1 % slower per outer step on the 100k workload).
 // The offset of a neighbour's cell (entry code, one of 27) comes from a shared-memory table; list
 // padding uses code 63, whose offset is far outside every cutoff.  The plain sum of every eight pair
 // forces is added to a compensated (hi, lo) accumulator with an error-free TwoSum.  The
@@ -169,7 +172,8 @@ __global__ void __launch_bounds__(kLjPer, 14) k_lj(const SysDev* __restrict__ sy
   }
   __syncthreads();
   const int n = S.n;
-  const int i = it.begin + threadIdx.x;
+  const int h = threadIdx.x % kLjTeam;  // this thread's share of the row
+  const int i = it.begin + threadIdx.x / kLjTeam;
   const bool active = i < n;
   const T4* __restrict__ P = reinterpret_cast<const T4*>(S.pos[it.buf]);
   const double* __restrict__ X = S.X[it.buf];
@@ -199,14 +203,16 @@ __global__ void __launch_bounds__(kLjPer, 14) k_lj(const SysDev* __restrict__ sy
       pj[2] = ldg4(P + ((unsigned)e.z & kNbrMask));
       pj[3] = ldg4(P + ((unsigned)e.w & kNbrMask));
     };
-    int4 ea = entries(0), eb = entries(4);
+    constexpr int kStride = 4 * kLjTeam;
+    int4 ea = entries(4 * h), eb = entries(4 * h + kStride);
     T4 pa[4], pb[4];
     gather(ea, pa);
     T bmin = (T)1e30;        // smallest |r^2 - r_c^2| met: the guard band is checked once at the end
     T px = 0, py = 0, pz = 0;  // plain sum of the previous group
-    for (int t0 = 0; t0 < cnt; t0 += 4) {
+    bool odd = false;          // a group's plain sum is waiting in (px, py, pz)
+    for (int t0 = 4 * h; t0 < cnt; t0 += kStride) {
       gather(eb, pb);  // positions of the next group
-      const int4 ec = entries(t0 + 8);
+      const int4 ec = entries(t0 + 2 * kStride);
       const unsigned e[4] = {(unsigned)ea.x, (unsigned)ea.y, (unsigned)ea.z, (unsigned)ea.w};
       T sx = 0, sy = 0, sz = 0;
 #pragma unroll
@@ -231,13 +237,15 @@ __global__ void __launch_bounds__(kLjPer, 14) k_lj(const SysDev* __restrict__ sy
         }
       }
       // every eight terms (two groups) are summed plainly, then added exactly
-      if ((t0 & 4) || t0 + 4 >= cnt) {
+      if (odd || t0 + kStride >= cnt) {
         f.add(sx + px, sy + py, sz + pz);
         px = py = pz = (T)0;
+        odd = false;
       } else {
         px = sx;
         py = sy;
         pz = sz;
+        odd = true;
       }
       ea = eb;
       eb = ec;
@@ -248,6 +256,7 @@ __global__ void __launch_bounds__(kLjPer, 14) k_lj(const SysDev* __restrict__ sy
       // Rare: pairs whose r^2 fell in the guard band around r_c2^2 (left out above) are decided in
       // FP64 with the CPU definition's operation order; the ones inside the cutoff are added.
       for (int t = 0; t < cnt; ++t) {
+        if ((t >> 2) % kLjTeam != h) continue;  // this thread's groups only
         const unsigned e = (unsigned)S.nbr[(size_t)i * S.maxnb + t];
         const int j = (int)(e & kNbrMask);
         const T4 pj = P[j];
@@ -269,14 +278,25 @@ __global__ void __launch_bounds__(kLjPer, 14) k_lj(const SysDev* __restrict__ sy
         }
       }
     }
-    bool bad = false;
+  }
+  {
+    // the team's partial forces, added in FP64 (every thread of the warp takes part in the shuffles)
+    double F[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const double F = f.get(a);
-      S.f2[a * n + i] = F;
-      bad |= !finite_bits(F);
+      F[a] = active ? f.get(a) : 0.0;
+#pragma unroll
+      for (int o = 1; o < kLjTeam; o <<= 1) F[a] += __shfl_xor_sync(0xffffffffu, F[a], o);
     }
-    if (bad) atomicOr(&S.flags[FLG_ERR], ERR_NONFINITE);
+    if (active && h == 0) {
+      bool bad = false;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        S.f2[a * n + i] = F[a];
+        bad |= !finite_bits(F[a]);
+      }
+      if (bad) atomicOr(&S.flags[FLG_ERR], ERR_NONFINITE);
+    }
   }
   if (energy) {  // every pair appears in both members' lists: halve
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

@@ -371,8 +371,14 @@ void launch_near_lists(const Launch& L, const PItem* items, int nitems);
 template <typename T> void launch_atm_near(const Launch& L, const PItem* items, int nitems);
 int listbuild_configure(int smax, int precision);
 // forces.cu
-// LJ pair forces: items of kLjPer particles (one thread each)
+// LJ pair forces: blocks of kLjPer threads, teams of kLjTeam threads per particle, so items of
+// kLjParticles particles
 constexpr int kLjPer = 64;
+#ifndef R3B_LJ_TEAM
+#define R3B_LJ_TEAM 1
+#endif
+constexpr int kLjTeam = R3B_LJ_TEAM;  // a power of two dividing 32
+constexpr int kLjParticles = kLjPer / kLjTeam;
 template <typename T> void launch_lj(const Launch& L, const PItem* items, int nitems);
 template <typename T> void launch_atm(const Launch& L, const CItem* items, int nitems, int grid, int smax);
 // staged-particle capacity of an ATM CTA: the particles within r_c of a base cell (edge >= r_c)
