@@ -38,6 +38,9 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # counted from atm_triplet: d_jk 3, c 5, ab/q 2, rsqrt 1 + Newton 4, w/t3/t5 3, s/A/B/C 8,
 # AB/AC/BC/P 4, Pa/Pb/Pc 9, G 3, ia/ib/ic 5, nu*t5 1, pa2/pb2/pc2 12, F_i 9, F_j 9, F_k 3,
 # accumulation of F_i (3) and scatter of F_j, F_k (6)
+# DRAM bytes (read + write) of one launch of the rotation kernel on the 100k workload, from an ncu
+# capture of the current kernel (dram__bytes_read.sum + dram__bytes_write.sum; cold caches)
+ATM_ROT_TRAFFIC_BYTES = 29.425408e6 + 256.0
 ATM_FLOPS_PER_TRIPLET = 3 + 5 + 2 + 5 + 3 + 8 + 4 + 9 + 3 + 5 + 1 + 12 + 9 + 9 + 3 + 3 + 6
 
 
@@ -260,7 +263,8 @@ def run_ours(args):
         "atm_kernel_ms": atm_ms,
         "profiled_pass_ms_per_step": q32["ms"] / K,
         "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved_tflops / FP32_PEAK_TFLOPS, "traffic": None,
+                     "frac": achieved_tflops / FP32_PEAK_TFLOPS,
+                     "traffic": ATM_ROT_TRAFFIC_BYTES if q32["kernel"] == 2 else None,
                      "kernel": {0: "k_atm<float>", 1: "k_atm_pa<float>", 2: "k_atm_rot<float>"}.get(q32["kernel"]),
                      "note": f"{ATM_FLOPS_PER_TRIPLET} flop per interacting triplet; peak = 152 SM x 128 "
                              "FP32 lanes x 2 x 2.07 GHz"},
