@@ -361,7 +361,7 @@ def _skin_for(L, rc2=2.5, rc3=2.5):
     return max(0.02, min(0.3, L / 3.0 - rc2 - 0.02))
 
 
-def run_ensemble(r3, n_replicas=256, n_outer=20, seed=None):
+def run_ensemble(r3, n_replicas=256, n_outer=20, seed=None, atm_kernel=2):
     """256 independent replicas, N log-uniform in [500, 20000], rho U[0.6, 0.9], T U[0.8, 1.5],
     k in {4, 8, 16}, dt = 0.002, 20 outer steps each, FP32, all in one batch."""
     import md_inputs
@@ -376,7 +376,7 @@ def run_ensemble(r3, n_replicas=256, n_outer=20, seed=None):
             h = r3.md_create_system(w.x, w.L, w.v, 1.0, r3.MD_FP32)
             r3.md_set_skin(h, _skin_for(w.L))
             r3.md_set_potentials(h, 1.0, 1.0, 2.5, 0.073, 2.5)
-            r3.md_set_atm_kernel(h, 1)
+            r3.md_set_atm_kernel(h, atm_kernel)
             r3.md_respa_step(h, 0, w.k_inner, w.dt_outer)  # initial forces outside the timed region
             hs.append(h)
             tickets.append(r3.md_batch_submit(b, h, n_outer, w.k_inner, w.dt_outer))
@@ -402,7 +402,7 @@ def run_ensemble(r3, n_replicas=256, n_outer=20, seed=None):
             r3.md_destroy_system(h)
 
 
-def run_serving(r3, seconds=3.0, rate=50.0, n_outer=100, k=10, seed=None):
+def run_serving(r3, seconds=3.0, rate=50.0, n_outer=100, k=10, seed=None, atm_kernel=2):
     """Poisson arrivals (rate per second) of replicas with N log-uniform in [1e3, 2e5] and rho
     U[0.7, 0.9]; each asks for n_outer outer steps at k inner steps; admitted by a device-memory
     budget (80 % of free HBM), state resident, batched continuously; arrivals stop after
@@ -429,7 +429,7 @@ def run_serving(r3, seconds=3.0, rate=50.0, n_outer=100, k=10, seed=None):
                 h = r3.md_create_system(w.x, w.L, w.v, 1.0, r3.MD_FP32 | r3.MD_DEFERRED)
                 r3.md_set_skin(h, _skin_for(w.L))
                 r3.md_set_potentials(h, 1.0, 1.0, 2.5, 0.073, 2.5)
-                r3.md_set_atm_kernel(h, 1)
+                r3.md_set_atm_kernel(h, atm_kernel)
                 t = r3.md_batch_submit(b, h, n_outer, k, 0.002 * k)
                 live[t] = (h, arrivals[nxt])
                 nxt += 1
