@@ -116,7 +116,7 @@ struct md_system {
 
 namespace {
 
-enum KTag { T_BIN = 1, T_SCATTER, T_LIST, T_LJ, T_COMB, T_START, T_KIN, T_ATMPA, T_ATMROT, T_KICK, T_NEARL, T_ATMNEAR };
+enum KTag { T_BIN = 1, T_SCATTER, T_LIST, T_LJ, T_COMB, T_START, T_KIN, T_ATMPA, T_ATMROT, T_KICK, T_ATMNEAR };
 
 void free_items(md_system* s) {
   for (void* p : s->item_allocs) cudaFree(p);
@@ -399,16 +399,14 @@ PItem* pitems_for(md_system* s, int tag, int mode, int buf) {
   const int per = (tag == T_LJ)      ? kLjParticles
                   : (tag == T_ATMPA)  ? kPaPerBlock
                   : (tag == T_ATMROT) ? rot_bases_per_item(s->precision)
-                  : (tag == T_NEARL)  ? kNearWarps
                   : (tag == T_ATMNEAR) ? kNearThreads
                                       : kBlock;
   const int nb = (tag == T_LJ)       ? (s->n + kLjParticles - 1) / kLjParticles
                  : (tag == T_ATMPA)  ? s->nblocks_pa
                  : (tag == T_ATMROT) ? s->nblocks_rot
-                 : (tag == T_NEARL)  ? (int)((s->n + kNearWarps - 1) / kNearWarps)
                  : (tag == T_ATMNEAR) ? (int)((s->n + kNearThreads - 1) / kNearThreads)
                                      : s->nblocks;
-  if (tag == T_LJ || tag == T_ATMROT || tag == T_KICK || tag == T_NEARL || tag == T_ATMNEAR) {
+  if (tag == T_LJ || tag == T_ATMROT || tag == T_KICK || tag == T_ATMNEAR) {
     // Gather kernels: the block scheduler hands consecutive blocks to different SMs, so blocks
     // b, b + nsm, b + 2 nsm, ... tend to share an SM.  Giving those blocks adjacent particle ranges
     // keeps each SM's neighbour gathers within one region of the box (L1 reuse); the order of the
@@ -470,7 +468,6 @@ md_status prepare_items(md_system* s) {
     }
     if (s->r_a > 0) {  // distance classes
       pitems_for(s, T_KICK, LJ_MID | M_NEAR, b);
-      pitems_for(s, T_NEARL, 0, b);
       pitems_for(s, T_ATMNEAR, 0, b);
     }
   }
@@ -559,8 +556,6 @@ struct Plan {
     launch_scan(L, s->sitem, 1);
     launch_scatter<T>(L, pitems_for(s, T_SCATTER, 0, buf), s->nblocks, kBlock);
     launch_listbuild<T>(L, citems_for(s, 0, buf), s->ncell, 27 * s->cap_cell);
-    if (s->r_a > 0)  // distance classes: near-class candidates, ranked by this binning
-      launch_near_lists(L, pitems_for(s, T_NEARL, 0, buf), padded_blocks((int)((s->n + kNearWarps - 1) / kNearWarps)));
   }
   // LJ forces and the velocity-Verlet kick/drift; with near = true (distance classes, LJ_MID) the
   // near-class triplets are evaluated between the two and their kicks join the LJ kick

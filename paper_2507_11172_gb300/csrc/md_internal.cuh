@@ -15,7 +15,6 @@ constexpr int kAtmWarps = 8;
 constexpr int kAtmThreads = 32 * kAtmWarps;
 constexpr int kQueue = 256;         // per-warp queue of accepted neighbour pairs (j, k)
 constexpr int kListWarps = 4;       // warps per CTA of the pair-list build
-constexpr int kNearWarps = 8;       // particles (one warp each) per CTA of the near-class candidate lists
 constexpr int kNearThreads = 128;   // owners (one thread each) per CTA of the near-class triplet kernel
 constexpr int kHalfCap = 64;        // triplet half list per particle (neighbours above it within r_c3)
 
@@ -61,10 +60,10 @@ struct SysDev {
   double rasq, guarda;        // r_a^2 and the half-width of its FP64 re-decision band
   double dt_near;             // s_near * dt_in
   float f_rasq, f_guarda;
-  float f_nearcand;           // (r_a + skin)^2 widened by 1e-4: candidate test of k_near_lists
+  float f_nearcand;           // (r_a + skin)^2 widened by 1e-4: near-class candidate test
   int pad2_;
   int *half_a, *half_a_cnt;   // [n][kHalfCap], [n]: near-class candidates of each particle (neighbours
-                              // above it within r_a + skin at the last binning), from k_near_lists
+                              // above it within r_a + skin at the last binning), from k_listbuild
   double *f3n;                // [3][n] cached near-class force (f3 holds near + far)
   void *f3nacc;               // like f3acc, for the near-class evaluation
   // state in cell-sorted order, double SoA [3][n] (x block, y block, z block)
@@ -367,7 +366,6 @@ void launch_take_state(const Launch& L, int n, const double* src, double* out, i
 void launch_scan(const Launch& L, const SItem* items, int nitems);
 template <typename T> void launch_scatter(const Launch& L, const PItem* items, int nitems, int block);
 template <typename T> void launch_listbuild(const Launch& L, const CItem* items, int nitems, int smax);
-void launch_near_lists(const Launch& L, const PItem* items, int nitems);
 template <typename T> void launch_atm_near(const Launch& L, const PItem* items, int nitems);
 int listbuild_configure(int smax, int precision);
 // forces.cu

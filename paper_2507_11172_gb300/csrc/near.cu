@@ -2,7 +2,7 @@
 // outlook of Sec. 5; intermediate cutoff r_a after Nakano et al., Sec. 3): every triplet whose three
 // pair distances are <= r_a, evaluated once, forces added to S.f3nacc.
 //
-// Candidates.  Right after every binning, k_near_lists cuts each particle's pair-list row to its
+// Candidates.  At every binning the pair-list build (k_listbuild, pass 2) keeps each particle's
 // candidates: the neighbours ranked above it (cell layer along z, fixed-point z of the binning, sorted
 // index: the ownership order of the triplet half lists) within (r_a + skin) of it.  A binning happens at
 // least once per outer step and whenever a particle has moved more than skin / 2, so every pair that is
@@ -23,48 +23,6 @@
 #include "md_internal.cuh"
 
 namespace r3b {
-
-// candidate half lists at (r_a + skin) from the pair-list rows, one warp per particle (right after a
-// binning: fixed-point positions and pair list are those of the binning).  The test is a superset test
-// (FP32 from the fixed-point positions, widened by 1e-4 relative), so no exact re-decision is needed.
-__global__ void __launch_bounds__(32 * kNearWarps) k_near_lists(const SysDev* __restrict__ sys, const PItem* __restrict__ items) {
-  const PItem it = items[blockIdx.x];
-  const SysDev& S = sys[it.sys];
-  const int lane = threadIdx.x & 31;
-  const int i = it.begin + (threadIdx.x >> 5);
-  if (i >= S.n) return;  // warp-uniform
-  const unsigned lt = (1u << lane) - 1u;
-  const int cnt = min(S.nbr_cnt[i], S.maxnb);
-  const int* __restrict__ row = S.nbr + (size_t)i * S.maxnb;
-  int* arow = S.half_a + (size_t)i * kHalfCap;
-  const int4 qi = S.ipos[i];
-  const float sc = S.f_qscale, reach = S.f_nearcand;
-  int ma = 0;
-  for (int t0 = 0; t0 < cnt; t0 += 32) {
-    const int t = t0 + lane;
-    bool cand = false;
-    unsigned e = 0u;
-    if (t < cnt) {
-      e = (unsigned)row[t];
-      const int j = (int)(e & kNbrMask);
-      const int4 qj = S.ipos[j];
-      const unsigned lay = (e >> kNbrShift) >> 4;  // z cell offset + 1
-      const int dqz = (int)((unsigned)qj.z - (unsigned)qi.z);
-      const bool above = lay == 2u || (lay == 1u && (dqz > 0 || (dqz == 0 && j > i)));
-      if (above) {
-        const float dx = (float)(int)((unsigned)qj.x - (unsigned)qi.x) * sc;
-        const float dy = (float)(int)((unsigned)qj.y - (unsigned)qi.y) * sc;
-        const float dz = (float)dqz * sc;
-        cand = fmaf(dz, dz, fmaf(dy, dy, dx * dx)) <= reach;
-      }
-    }
-    const unsigned bal = __ballot_sync(0xffffffffu, cand);
-    const int pos = ma + __popc(bal & lt);
-    if (cand && pos < kHalfCap) arow[pos] = (int)e;
-    ma += __popc(bal);
-  }
-  if (lane == 0) S.half_a_cnt[i] = ma;  // more than kHalfCap: k_atm_near reports ERR_NEAR_CAP
-}
 
 // FP32 reciprocal square root: hardware approximation refined by one Newton-Raphson step
 __device__ __forceinline__ float nr_rsqrt(float q) {
@@ -249,9 +207,6 @@ __global__ void __launch_bounds__(kNearThreads) k_atm_near(const SysDev* __restr
   if (threadIdx.x == 0 && s_cnt) atomicAdd(&S.ctr[CTR_NEAR], (unsigned long long)s_cnt);
 }
 
-void launch_near_lists(const Launch& L, const PItem* items, int nitems) {
-  if (nitems > 0) k_near_lists<<<nitems, 32 * kNearWarps, 0, L.stream>>>(L.sys, items);
-}
 template <typename T>
 void launch_atm_near(const Launch& L, const PItem* items, int nitems) {
   if (nitems > 0) k_atm_near<T><<<nitems, kNearThreads, 0, L.stream>>>(L.sys, items);

@@ -136,8 +136,10 @@ __global__ void k_scatter(const SysDev* __restrict__ sys, const PItem* __restric
 // (S.half, S.half_cnt): the entries j with r_ij <= r_c3 (guard band around r_c3^2
 // re-decided in FP64 with the CPU definition's operation order) that lie above i in the
 // order "cell layer along z, then fixed-point z, then sorted index", which makes i the
-// owner of every triplet whose other two members are in that list.  The CTA also moves
-// the permuted state of b's particles back into place.
+// owner of every triplet whose other two members are in that list.  With distance classes on, the
+// same pass keeps the near-class candidates (S.half_a): the entries above i within r_a + skin (a
+// superset test, widened by 1e-4).  The CTA also moves the permuted state of b's particles back into
+// place.
 template <typename T>
 __global__ void __launch_bounds__(32 * kListWarps)
     k_listbuild(const SysDev* __restrict__ sys, const CItem* __restrict__ items, int smax) {
@@ -235,10 +237,10 @@ __global__ void __launch_bounds__(32 * kListWarps)
     // pass 2: the triplet half list among the list entries
     const int qzi = sqz[islot];
     int* hrow = S.half + (size_t)i * kHalfCap;
-    int mh = 0;
+    int mh = 0, ma = 0;
     for (int t0 = 0; t0 < cnt; t0 += 32) {
       const int t = t0 + lane;
-      bool half = false, band = false;
+      bool half = false, band = false, cand = false;
       unsigned e = 0u;
       if (t < cnt) {
         e = (unsigned)row[t];
@@ -255,6 +257,7 @@ __global__ void __launch_bounds__(32 * kListWarps)
           const T r2 = dx * dx + dy * dy + dz * dz;
           half = r2 <= rc3 - g3;
           band = !half && r2 <= rc3 + g3;
+          cand = r2 <= (T)S.f_nearcand;  // distance classes: near-class candidate (superset test)
         }
       }
       if (__any_sync(0xffffffffu, band)) {
@@ -267,8 +270,17 @@ __global__ void __launch_bounds__(32 * kListWarps)
       const int hpos = mh + __popc(balh & lt);
       if (half && hpos < kHalfCap) hrow[hpos] = (int)e;
       mh += __popc(balh);
+      if (S.half_a) {
+        const unsigned bala = __ballot_sync(0xffffffffu, cand);
+        const int apos = ma + __popc(bala & lt);
+        if (cand && apos < kHalfCap) S.half_a[(size_t)i * kHalfCap + apos] = (int)e;
+        ma += __popc(bala);
+      }
     }
-    if (lane == 0) S.half_cnt[i] = mh;  // more than kHalfCap: the triplet kernel reports ERR_HALF_CAP
+    if (lane == 0) {  // more than kHalfCap: the triplet kernels report ERR_HALF_CAP / ERR_NEAR_CAP
+      S.half_cnt[i] = mh;
+      if (S.half_a) S.half_a_cnt[i] = ma;
+    }
   }
   // every particle of b: permuted state back into place
   for (int ib = threadIdx.x; ib < st_cnt[13]; ib += blockDim.x) {
