@@ -44,7 +44,44 @@ ATM_ROT_TRAFFIC_BYTES = 29.425408e6 + 256.0
 ATM_FLOPS_PER_TRIPLET = 3 + 5 + 2 + 5 + 3 + 8 + 4 + 9 + 3 + 5 + 1 + 12 + 9 + 9 + 3 + 3 + 6
 
 
+def _nvml_sampler():
+    """Read-only NVML queries through ctypes (SM clock, its maximum, clock-event reasons) for the GPU
+    of this rank; None where the library is unavailable."""
+    import ctypes
+    try:
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            return None
+        h = ctypes.c_void_p()
+        if lib.nvmlDeviceGetHandleByIndex_v2(int(os.environ.get("LOCAL_RANK", "0")), ctypes.byref(h)) != 0:
+            return None
+        reasons_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+    except (OSError, AttributeError):
+        return None
+    mx = ctypes.c_uint(0)
+    lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx))  # NVML_CLOCK_SM
+
+    def sample():
+        c, r = ctypes.c_uint(0), ctypes.c_ulonglong(0)
+        if lib.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(c)) != 0 or reasons_fn(h, ctypes.byref(r)) != 0:
+            return None
+        bits = (0x8, 0x40, 0x20, 0x4)  # hw_slowdown, hw_thermal_slowdown, sw_thermal_slowdown, sw_power_cap
+        flags = ["Active" if r.value & b else "Not Active" for b in bits]
+        return ", ".join([str(c.value), str(mx.value), "", hex(r.value)] + flags)
+    return sample
+
+
 def sample_clocks(stop, out):
+    """Clock samples while the timed region runs: NVML every 10 ms, else nvidia-smi in a loop."""
+    nv = _nvml_sampler()
+    if nv is not None:
+        while not stop.is_set():
+            line = nv()
+            if line:
+                out.append(line)
+            stop.wait(0.01)
+        return
     cmd = ["nvidia-smi", "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
            "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
            "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
