@@ -306,9 +306,10 @@ def run_ours(args):
                      "note": f"{ATM_FLOPS_PER_TRIPLET} flop per interacting triplet; peak = 152 SM x 128 "
                              "FP32 lanes x 2 x 2.07 GHz"},
         "clocks": clk,
-        # per outer step: 2 LJ-phase launches (forces, kick/drift) per inner step, the sort (4), the
-        # triplet kernel and the combine; plus the opening kick of each call
-        "gpu_launches": K * (2 * w.k_inner + 6 + 1),
+        # per outer step: 2 LJ-phase launches (forces, kick/drift) per inner step, the sort (bin, scan,
+        # cell order (2), scatter, listbuild), the triplet kernel and the combine; plus the opening
+        # kick of each call
+        "gpu_launches": K * (2 * w.k_inner + 8 + 1),
         "e2e": e2e,
         "observables": obs_line,
         "distance_classes": classes_line,

@@ -181,6 +181,7 @@ md_status alloc_device(md_system* s) {
   size_t o_id = a.reserve(4 * n), o_ida = a.reserve(4 * n);
   size_t o_p0 = a.reserve(t4 * n), o_p1 = a.reserve(t4 * n), o_plo = a.reserve(t4 * n), o_ref = a.reserve(t4 * n);
   size_t o_pcell = a.reserve(4 * n), o_ctmp = a.reserve(4 * n), o_rank = a.reserve(4 * n);
+  size_t o_skey = a.reserve(4 * n), o_memb = a.reserve(4 * n);
   size_t o_count = a.reserve(4 * (size_t)s->ncell), o_cstart = a.reserve(4 * ((size_t)s->ncell + 1));
   size_t o_nbr = a.reserve(4 * (size_t)s->maxnb * n), o_nbc = a.reserve(4 * n);
   size_t o_half = a.reserve(4 * (size_t)kHalfCap * n), o_hc = a.reserve(4 * n);
@@ -226,6 +227,8 @@ md_status alloc_device(md_system* s) {
   h.pcell = (int*)(m + o_pcell);
   h.cell_tmp = (int*)(m + o_ctmp);
   h.rank = (int*)(m + o_rank);
+  h.skey = (int*)(m + o_skey);
+  h.members = (int*)(m + o_memb);
   h.count = (int*)(m + o_count);
   h.cell_start = (int*)(m + o_cstart);
   h.nbr = (int*)(m + o_nbr);
@@ -287,7 +290,7 @@ size_t arena_bytes(const md_system* s0) {
   a.reserve(4 * n);
   a.reserve(4 * n);
   for (int i = 0; i < 4; ++i) a.reserve(t4 * n);
-  for (int i = 0; i < 3; ++i) a.reserve(4 * n);
+  for (int i = 0; i < 5; ++i) a.reserve(4 * n);
   a.reserve(4 * (size_t)tmp.ncell);
   a.reserve(4 * ((size_t)tmp.ncell + 1));
   a.reserve(4 * (size_t)tmp.maxnb * n);
@@ -554,6 +557,7 @@ struct Plan {
   void sort(int buf) {
     launch_bin_count(L, pitems_for(s, T_BIN, 0, buf), s->nblocks, kBlock);
     launch_scan(L, s->sitem, 1);
+    launch_cell_order(L, pitems_for(s, T_BIN, 0, buf), s->nblocks, kBlock, citems_for(s, 0, buf), s->ncell);
     launch_scatter<T>(L, pitems_for(s, T_SCATTER, 0, buf), s->nblocks, kBlock);
     launch_listbuild<T>(L, citems_for(s, 0, buf), s->ncell, 27 * s->cap_cell);
   }
@@ -1382,6 +1386,8 @@ void enqueue_cycle(md_batch* b, const std::vector<TickItems>& ticks, bool with_s
     chk("bin_count", t);
     launch_scan(L, b->d_sitems + it.scan, it.nscan);
     chk("scan", t);
+    launch_cell_order(L, b->d_pitems + it.bin, it.nbin, kBlock, b->d_citems + it.list, it.nlist);
+    chk("cell_order", t);
     launch_scatter<T>(L, b->d_pitems + it.bin, it.nbin, kBlock);
     chk("scatter", t);
     launch_listbuild<T>(L, b->d_citems + it.list, it.nlist, b->smax_list);

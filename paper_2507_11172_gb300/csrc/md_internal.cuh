@@ -76,6 +76,7 @@ struct SysDev {
   void *ref;          // T4 [n]: pos at the sort (displacement check)
   int *pcell;         // [n] cell of the last sort
   int *cell_tmp, *rank;       // [n] binning scratch
+  int *skey, *members;        // [n] binning scratch for the order within a cell (NULL: arrival order)
   int *count, *cell_start;    // [ncell], [ncell + 1]
   int *nbr, *nbr_cnt;         // [n][maxnb] row-major, [n]
   int *half, *half_cnt;       // [n][kHalfCap] triplet half list of each particle (pair-list entries), [n]
@@ -358,6 +359,8 @@ struct Launch {
 
 // sort.cu
 void launch_bin_count(const Launch& L, const PItem* items, int nitems, int block);
+void launch_cell_order(const Launch& L, const PItem* pitems, int npitems, int block, const CItem* citems,
+                       int ncitems);
 void launch_snapshot(const Launch& L, const PItem* items, int nitems, int restore);
 void launch_stamp(cudaStream_t s, unsigned long long* out);
 // state.cu (one system, sys[0])

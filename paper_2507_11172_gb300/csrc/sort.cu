@@ -1,7 +1,8 @@
 // Cell-binning counting sort and Verlet pair-list build (linked cells, Sec. 2.2 / Sec. 4.1).
 //
 // Per sort: bin_count (wrap into [0, L), cell id, atomic rank within the
-// cell) -> scan (exclusive prefix over cells, resets counts) -> scatter
+// cell, Morton key within the cell) -> scan (exclusive prefix over cells,
+// resets counts) -> cell order (rank within the cell by key) -> scatter
 // (permute positions, velocities, ids into cell order; write the cell-local
 // coordinates used by the force kernels) -> listbuild (pair list with skin,
 // copies the permuted state back into place).
@@ -27,6 +28,55 @@ __global__ void k_bin_count(const SysDev* __restrict__ sys, const PItem* __restr
   int cell = (c[2] * S.nc + c[1]) * S.nc + c[0];
   S.cell_tmp[p] = cell;
   S.rank[p] = atomicAdd(&S.count[cell], 1);
+  if (S.skey) {  // position within the cell on an 8 x 8 x 8 grid, bits interleaved (Morton order)
+    unsigned key = 0u;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const double f = (X[a * n + p] - c[a] * S.edge) * S.inv_edge * 8.0;
+      const unsigned q = (unsigned)min(7, max(0, (int)f));
+#pragma unroll
+      for (int bit = 0; bit < 3; ++bit) key |= ((q >> bit) & 1u) << (3 * bit + a);
+    }
+    S.skey[p] = (int)key;
+  }
+}
+
+// Order within each cell: every particle's slot in its cell's segment is replaced by its rank by
+// (Morton key of its position within the cell, index), so that consecutive particles of a cell lie
+// close together (their neighbour sets overlap: gathers of consecutive threads share cache lines) and
+// the order no longer depends on the arrival order of the binning's atomics.
+// Step 1 (per particle): the members of each cell, in arrival order.
+__global__ void k_cell_members(const SysDev* __restrict__ sys, const PItem* __restrict__ items) {
+  const PItem it = items[blockIdx.x];
+  const SysDev& S = sys[it.sys];
+  if (item_mode(S, it.mode) & M_SKIP) return;
+  const int p = it.begin + threadIdx.x;
+  if (p >= S.n) return;
+  S.members[S.cell_start[S.cell_tmp[p]] + S.rank[p]] = p;
+}
+// Step 2 (one warp per cell): rank of each member by (key, index) among its cell's members.
+__global__ void k_cell_rank(const SysDev* __restrict__ sys, const CItem* __restrict__ items, int nitems) {
+  const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (w >= nitems) return;  // warp-uniform
+  const CItem it = items[w];
+  const SysDev& S = sys[it.sys];
+  if (item_mode(S, it.mode) & M_SKIP) return;  // warp-uniform
+  const int lane = threadIdx.x & 31;
+  const int b = S.cell_start[it.cell], cnt = S.cell_start[it.cell + 1] - b;
+  for (int a0 = 0; a0 < cnt; a0 += 32) {
+    const int a = a0 + lane;
+    if (a < cnt) {
+      const int pa = S.members[b + a];
+      const int ka = S.skey[pa];
+      int r = 0;
+      for (int q = 0; q < cnt; ++q) {
+        const int pq = S.members[b + q];
+        const int kq = S.skey[pq];
+        r += (kq < ka || (kq == ka && pq < pa)) ? 1 : 0;
+      }
+      S.rank[pa] = r;
+    }
+  }
 }
 
 // One 1024-thread CTA per system: exclusive scan of count[] into
@@ -339,6 +389,12 @@ void launch_snapshot(const Launch& L, const PItem* items, int nitems, int restor
 }
 void launch_stamp(cudaStream_t s, unsigned long long* out) { k_stamp<<<1, 1, 0, s>>>(out); }
 
+void launch_cell_order(const Launch& L, const PItem* pitems, int npitems, int block, const CItem* citems,
+                       int ncitems) {
+  if (npitems <= 0 || ncitems <= 0) return;
+  k_cell_members<<<npitems, block, 0, L.stream>>>(L.sys, pitems);
+  k_cell_rank<<<(ncitems + 7) / 8, 256, 0, L.stream>>>(L.sys, citems, ncitems);
+}
 void launch_bin_count(const Launch& L, const PItem* items, int nitems, int block) {
   if (nitems > 0) k_bin_count<<<nitems, block, 0, L.stream>>>(L.sys, items);
 }
