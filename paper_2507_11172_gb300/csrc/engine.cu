@@ -566,7 +566,7 @@ struct Plan {
   template <typename T>
   void lj(int kind, int buf, bool energy, bool near = false) {
     launch_lj<T>(L, pitems_for(s, T_LJ, kind | (energy ? M_ENERGY : 0), buf),
-                 padded_blocks((s->n + kLjParticles - 1) / kLjParticles));
+                 padded_blocks((s->n + kLjParticles - 1) / kLjParticles), energy);
     if (near) atm_near<T>(buf);
     if (kind != LJ_INIT)
       launch_kick<T>(L, pitems_for(s, T_KICK, kind | (near ? M_NEAR : 0), buf), padded_blocks(s->nblocks));
@@ -1392,7 +1392,7 @@ void enqueue_cycle(md_batch* b, const std::vector<TickItems>& ticks, bool with_s
     chk("scatter", t);
     launch_listbuild<T>(L, b->d_citems + it.list, it.nlist, b->smax_list);
     chk("listbuild", t);
-    launch_lj<T>(L, b->d_pitems + it.lj, it.nlj);
+    launch_lj<T>(L, b->d_pitems + it.lj, it.nlj, true);  // members' modes decide the energy
     chk("lj", t);
     launch_kick<T>(L, b->d_pitems + it.kick, it.nkick);
     chk("kick", t);

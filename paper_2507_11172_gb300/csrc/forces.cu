@@ -149,7 +149,8 @@ template <> __device__ __forceinline__ double recip_fast<double>(double x) { ret
 
 constexpr unsigned kPadCode = 63u;  // code of a padding entry (offset far outside every cutoff)
 
-template <typename T>
+// kE = false: a launch whose items never ask for energies (compiled without the energy terms)
+template <typename T, bool kE>
 __global__ void __launch_bounds__(kLjPer, 14) k_lj(const SysDev* __restrict__ sys, const PItem* __restrict__ items) {
   using T4 = typename V4<T>::type;
   __shared__ T4 s_off[64];
@@ -158,7 +159,7 @@ __global__ void __launch_bounds__(kLjPer, 14) k_lj(const SysDev* __restrict__ sy
   const SysDev& S = sys[it.sys];
   const int mode = item_mode(S, it.mode);
   if (mode & M_SKIP) return;  // block-uniform: a block belongs to one system
-  const bool energy = (mode & M_ENERGY) != 0;
+  const bool energy = kE && (mode & M_ENERGY) != 0;
   if (threadIdx.x < 64) {
     const unsigned c = threadIdx.x;
     const T e = Par<T>::edge(S);
@@ -1285,8 +1286,12 @@ int atm_configure(int smax, int precision, int* smem_bytes) {
 
 // ---------------------------------------------------------------- launchers
 template <typename T>
-void launch_lj(const Launch& L, const PItem* items, int nitems) {
-  if (nitems > 0) k_lj<T><<<nitems, kLjPer, 0, L.stream>>>(L.sys, items);
+void launch_lj(const Launch& L, const PItem* items, int nitems, bool energy) {
+  if (nitems <= 0) return;
+  if (energy)
+    k_lj<T, true><<<nitems, kLjPer, 0, L.stream>>>(L.sys, items);
+  else
+    k_lj<T, false><<<nitems, kLjPer, 0, L.stream>>>(L.sys, items);
 }
 template <typename T>
 void launch_atm(const Launch& L, const CItem* items, int nitems, int grid, int smax) {
@@ -1329,8 +1334,8 @@ void launch_kinetic(const Launch& L, const PItem* items, int nitems, int block) 
   if (nitems > 0) k_kinetic<<<nitems, block, 0, L.stream>>>(L.sys, items);
 }
 
-template void launch_lj<float>(const Launch&, const PItem*, int);
-template void launch_lj<double>(const Launch&, const PItem*, int);
+template void launch_lj<float>(const Launch&, const PItem*, int, bool);
+template void launch_lj<double>(const Launch&, const PItem*, int, bool);
 template void launch_combine<float>(const Launch&, const PItem*, int, int);
 template void launch_combine<double>(const Launch&, const PItem*, int, int);
 template void launch_start<float>(const Launch&, const PItem*, int, int);

@@ -380,7 +380,7 @@ constexpr int kLjPer = 64;
 #endif
 constexpr int kLjTeam = R3B_LJ_TEAM;  // a power of two dividing 32
 constexpr int kLjParticles = kLjPer / kLjTeam;
-template <typename T> void launch_lj(const Launch& L, const PItem* items, int nitems);
+template <typename T> void launch_lj(const Launch& L, const PItem* items, int nitems, bool energy);
 template <typename T> void launch_atm(const Launch& L, const CItem* items, int nitems, int grid, int smax);
 // staged-particle capacity of an ATM CTA: the particles within r_c of a base cell (edge >= r_c)
 // occupy at most the volume of about 21 cells (16 cells plus margin is sized for the typical mean
