@@ -205,3 +205,18 @@ def test_100k_class_forces_after_steps(gpu_lib, cfg2, prec, tol):
     assert force_err(f3n[sub], rn) <= tol
     assert force_err(f3[sub], ra) <= tol
     assert np.abs(v.sum(0) - cfg2.v.sum(0)).max() < (1e-3 if prec == 0 else 1e-9)
+
+
+def test_too_many_near_candidates_is_a_capacity_error(gpu_lib):
+    """At density 1.7 a particle has about 55 neighbours above it within r_a + skin = 2.6: more than
+    the 64 candidate slots for many particles.  The call reports MD_ERR_CAPACITY (no fallback for the
+    near class) and leaves the state as it was."""
+    x, L = md_inputs.fcc_jitter(1500, 1.7, 0.02, 91)
+    with gpu_lib.System.create(x, L, None, precision=0, nu=NU, skin=0.1) as s:
+        s.set_distance_classes(2.5, 2)
+        x0, v0 = s.state()
+        with pytest.raises(gpu_lib.MDError) as e:
+            s.step(1, 4, 0.002)
+        assert e.value.status == -8
+        x1, v1 = s.state()
+    assert np.array_equal(x0, x1) and np.array_equal(v0, v1)
