@@ -78,18 +78,8 @@ struct ZrSmem {
   T4 pn[kZrMax];            // partners of the current phase, doubled (pn[t + m] = pn[t]), far dummies after;
                             // the half list is built here: (d_v, |d_v|^2)
   T4 slot[2][kZrMax];       // partner shares (G, W) of odd and even steps, in pn's index space
-  union {
-    struct {
-      T4 nd[kZrMax];        // copy of the half list (lists longer than 32 nodes)
-      T4 tot[kZrMax];       // per-node totals across phases (lists longer than 32 nodes)
-    };
-    struct {                // lists of at most 32 nodes, FP32: partner pairs of consecutive steps,
-      T px[kZrMax][2];      // (pn[t].x, pn[t + 1].x), likewise y, z and |d|^2
-      T py[kZrMax][2];
-      T pz[kZrMax][2];
-      T pw[kZrMax][2];
-    };
-  };
+  T4 nd[kZrMax];            // copy of the half list (lists longer than 32 nodes)
+  T4 tot[kZrMax];           // per-node totals across phases (lists longer than 32 nodes)
   int nidx[kZrMax];         // sorted index of each node
   int4 cq[kZrMax];          // prefetched fixed-point positions of the next base's half list
   unsigned row[2][kZrMax];  // prefetched half lists (pair-list entries) of the next two bases
@@ -287,7 +277,7 @@ __device__ __forceinline__ void zr_phase(const ZrK<T>& K, ZrSmem<T>& w, const ty
 // ---------------------------------------------------------------- paired steps (FP32, m <= 32)
 // The rotation over m <= 32 nodes (node v on lane v) with two consecutive steps s, s + 1 evaluated
 // together in the two halves of packed FP32x2 instructions (Blackwell FFMA2/FADD2/FMUL2).  Partner
-// data of both steps comes from pair arrays in shared memory (px[t] = (pn[t].x, pn[t + 1].x), ...).
+// data of both steps comes from the doubled list in shared memory (pn[t] and pn[t + 1]).
 // The partner shares do not go through shared memory: they travel with the partners.  In iteration
 // k (steps 2k+1, 2k+2) lane v holds the running shares of nodes v + 2k + 1 (first half) and
 // v + 2k + 2 (second half); those nodes are the partners of lane v - 2 in iteration k + 1, so the
@@ -316,10 +306,9 @@ __device__ __forceinline__ bool zr_self_f2(const ZrK<float>& K, ZrSmem<float>& w
   const int pass = real ? (lane + 2 < m ? lane + 2 : lane + 2 - m) : lane;
   auto iter = [&](const int s1, const float2 off) {
     const int t = lane + s1;
-    const float2 px = *reinterpret_cast<const float2*>(w.px[t]);
-    const float2 py = *reinterpret_cast<const float2*>(w.py[t]);
-    const float2 pz = *reinterpret_cast<const float2*>(w.pz[t]);
-    const float2 b = *reinterpret_cast<const float2*>(w.pw[t]);
+    const float4 p0 = w.pn[t], p1 = w.pn[t + 1];  // partners of steps s1 and s1 + 1 (t + 1 < 2m + 32)
+    const float2 px = make_float2(p0.x, p1.x), py = make_float2(p0.y, p1.y), pz = make_float2(p0.z, p1.z);
+    const float2 b = make_float2(p0.w, p1.w);
     const float2 ex = __fadd2_rn(px, make_float2(-jx.x, -jx.y));
     const float2 ey = __fadd2_rn(py, make_float2(-jy.x, -jy.y));
     const float2 ez = __fadd2_rn(pz, make_float2(-jz.x, -jz.y));
@@ -548,22 +537,7 @@ __device__ __forceinline__ void zr_eval(const ZrK<T>& K, ZrSmem<T>& w, const int
     }
     bool done = false;
     if constexpr (sizeof(T) == 4) {
-      // pair arrays of consecutive entries for the packed two-step rotation
-      __syncwarp();
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int t = lane + 32 * h;
-        const T4 p0 = w.pn[t], p1 = t + 1 < kZrMax ? w.pn[t + 1] : zr_far<T>((T)-1);
-        w.px[t][0] = p0.x;
-        w.px[t][1] = p1.x;
-        w.py[t][0] = p0.y;
-        w.py[t][1] = p1.y;
-        w.pz[t][0] = p0.z;
-        w.pz[t][1] = p1.z;
-        w.pw[t][0] = p0.w;
-        w.pw[t][1] = p1.w;
-      }
-      __syncwarp();
+      __syncwarp();  // the doubled list is read by other lanes
       ZrOut32 r;
       if (zr_self_f2<kE>(K, w, J, m, lane, r)) {
         done = true;
