@@ -270,6 +270,7 @@ def run_ours(args):
             r3.md_destroy_system(h)
 
     classes_line = run_classes(r3, w, stream, flush, K) if rank == 0 else None
+    large_line = run_large(r3, stream, flush) if (rank == 0 and args.large) else None
     direct_line = run_direct(r3, stream) if rank == 0 else None
 
     peaks = {}
@@ -314,6 +315,7 @@ def run_ours(args):
         "observables": obs_line,
         "distance_classes": classes_line,
         "direct_sum": direct_line,
+        "large_2m": large_line,
     }
     if peaks:
         line["measured_peaks"] = {"hbm_gbs": peaks.get("hbm_gbs"), "bf16_tflops": peaks.get("bf16_tflops")}
@@ -326,6 +328,42 @@ def run_ours(args):
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_large(r3, stream, flush, steps=50):
+    """Large single system (2,000,000 particles, random-sequential-addition start at density 0.75,
+    T* = 1.2, FP32 forces, k = 10, dt_outer = 0.02) with triplet cutoffs 2.0 and 2.5: whole outer steps
+    through the graph-replayed path, CUDA events, L2 flushed before each step."""
+    import torch
+    import md_inputs
+    out = {}
+    w = md_inputs.rsa_2m(2.5)
+    for rc3 in (2.0, 2.5):
+        h = r3.md_create_system(w.x, w.L, w.v, 1.0, r3.MD_FP32, stream.cuda_stream)
+        try:
+            r3.md_set_potentials(h, 1.0, 1.0, w.rc2, w.nu, rc3)
+            with torch.cuda.stream(stream):
+                r3.md_respa_step(h, 0, w.k_inner, w.dt_outer)
+                for _ in range(3):
+                    r3.md_respa_step(h, 1, w.k_inner, w.dt_outer)
+                s0 = r3.md_get_stats(h)
+                ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                      for _ in range(steps)]
+                for e0, e1 in ev:
+                    flush.fill_(1.0)
+                    e0.record(stream)
+                    r3.md_respa_step(h, 1, w.k_inner, w.dt_outer)
+                    e1.record(stream)
+                torch.cuda.synchronize()
+                s1 = r3.md_get_stats(h)
+            ms = sum(e0.elapsed_time(e1) for e0, e1 in ev) / steps
+            trip = (s1["triplets_total"] - s0["triplets_total"]) / steps
+            out[f"rc3_{rc3}"] = {"ms_per_outer_step": ms, "triplets_per_eval": trip,
+                                 "triplets_per_s": trip / (ms / 1e3), "rrespa_steps_per_s": 1e3 / ms,
+                                 "atm_kernel": s1["atm_kernel"], "replays": s1["replays"] - s0["replays"]}
+        finally:
+            r3.md_destroy_system(h)
+    return out
 
 
 def run_direct(r3, stream, n=4995, calls=2):
@@ -570,6 +608,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=100_000,
                     help="particles in the oracle's timed per-particle pass (100000 = one full evaluation)")
     ap.add_argument("--no-batch", action="store_true", help="skip the ensemble and serving runs")
+    ap.add_argument("--large", action="store_true",
+                    help="also time the 2,000,000-particle system (its input takes about a minute to generate)")
     ap.add_argument("--serve-seconds", type=float, default=3.0, help="arrival window of the serving run")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -34,6 +34,7 @@ md_status cuda_fail(cudaError_t e, const char* what) {
   } while (0)
 
 constexpr int kBlock = 256;
+constexpr int kSafeCalls = 4;  // initial run of calls started in safe mode after a skin replay
 
 int device_sm_count() {
   static int sms = 0;
@@ -84,6 +85,7 @@ struct md_system {
   std::map<std::tuple<int, int, int>, PItem*> pitems;  // (kernel tag, mode, buf) -> device array
   std::map<std::tuple<int, int>, CItem*> citems;        // (mode, buf)
   SItem* sitem = nullptr;
+  SItem* sitem_cond = nullptr;
   std::vector<void*> item_allocs;
   int nblocks = 0;
   // execution
@@ -109,6 +111,9 @@ struct md_system {
   double e_kin = 0, u2 = 0, u3 = 0, w2 = 0, w3 = 0;
   // batch membership
   md_batch* batch = nullptr;
+  // calls since the last skin replay that started in safe mode (0: start with the normal plan), and the
+  // length of such a run before the normal plan is tried again
+  int safe_calls = 0, safe_span = 4;
   // deferred allocation: state kept on the host until first use
   bool deferred = false;
   std::vector<double> host_x, host_v;
@@ -124,6 +129,7 @@ void free_items(md_system* s) {
   s->pitems.clear();
   s->citems.clear();
   s->sitem = nullptr;
+  s->sitem_cond = nullptr;
 }
 
 void clear_graphs(md_system* s) {
@@ -448,6 +454,9 @@ md_status prepare_items(md_system* s) {
   for (int b = 0; b < 2; ++b) {
     pitems_for(s, T_BIN, 0, b);
     pitems_for(s, T_SCATTER, 0, b);
+    pitems_for(s, T_BIN, M_COND, b);
+    pitems_for(s, T_SCATTER, M_COND, b);
+    citems_for(s, M_COND, b);
     pitems_for(s, T_START, 0, b);
     for (int e = 0; e < 2; ++e) {
       int E = e ? M_ENERGY : 0;
@@ -479,12 +488,16 @@ md_status prepare_items(md_system* s) {
     std::vector<SItem> v{SItem{0, 0}};
     s->sitem = upload_items(s, v);
   }
+  if (!s->sitem_cond) {
+    std::vector<SItem> v{SItem{0, M_COND}};
+    s->sitem_cond = upload_items(s, v);
+  }
   CK(cudaStreamSynchronize(s->stream));
   for (auto& kv : s->pitems)
     if (!kv.second) return MD_ERR_OOM;
   for (auto& kv : s->citems)
     if (!kv.second) return MD_ERR_OOM;
-  if (!s->sitem) return MD_ERR_OOM;
+  if (!s->sitem || !s->sitem_cond) return MD_ERR_OOM;
   return MD_OK;
 }
 
@@ -553,13 +566,17 @@ md_status rebuild(md_system* s, bool keep_state) {
 struct Plan {
   md_system* s;
   Launch L;
+  // binning, pair list and half lists; cond: only if the last drifts moved a particle more than
+  // skin / 2 since the previous binning (decided on the device, adaptive binning)
   template <typename T>
-  void sort(int buf) {
-    launch_bin_count(L, pitems_for(s, T_BIN, 0, buf), s->nblocks, kBlock);
-    launch_scan(L, s->sitem, 1);
-    launch_cell_order(L, pitems_for(s, T_BIN, 0, buf), s->nblocks, kBlock, citems_for(s, 0, buf), s->ncell);
-    launch_scatter<T>(L, pitems_for(s, T_SCATTER, 0, buf), s->nblocks, kBlock);
-    launch_listbuild<T>(L, citems_for(s, 0, buf), s->ncell, 27 * s->cap_cell);
+  void sort(int buf, bool cond = false) {
+    const int c = cond ? M_COND : 0;
+    if (cond) launch_sort_decide(L);
+    launch_bin_count(L, pitems_for(s, T_BIN, c, buf), s->nblocks, kBlock);
+    launch_scan(L, cond ? s->sitem_cond : s->sitem, 1);
+    launch_cell_order(L, pitems_for(s, T_BIN, c, buf), s->nblocks, kBlock, citems_for(s, c, buf), s->ncell);
+    launch_scatter<T>(L, pitems_for(s, T_SCATTER, c, buf), s->nblocks, kBlock);
+    launch_listbuild<T>(L, citems_for(s, c, buf), s->ncell, 27 * s->cap_cell);
   }
   // LJ forces and the velocity-Verlet kick/drift; with near = true (distance classes, LJ_MID) the
   // near-class triplets are evaluated between the two and their kicks join the LJ kick
@@ -631,7 +648,12 @@ void enqueue_steps(Plan& P, int n_outer, int k, int cur, bool safe, bool profile
       const int b = t & 1;
       // distance classes: iteration t closes a block of s_near inner steps
       const bool near = P.s->r_a > 0 && t < k - 1 && (t + 1) % P.s->s_near == 0;
-      if (t == k - 1 || safe) P.sort<T>(b);  // binning + pair list at the outer boundary
+      // binning + pair list at the outer boundary; in safe mode (after a skin replay) also before any
+      // inner step whose positions have moved more than skin / 2 since the last binning
+      if (t == k - 1)
+        P.sort<T>(b);
+      else if (safe)
+        P.sort<T>(b, true);
       if (t < k - 1)
         P.lj<T>(LJ_MID, b, false, near);
       else
@@ -837,7 +859,10 @@ md_status do_call(md_system* s, int n_outer, int k, double dt_outer) {
   }
   const double dt_in = dt_outer / k;
   for (int attempt = 0; attempt < 6; ++attempt) {
-    const bool safe = attempt > 0 && s->h_flags[FLG_SKIN] && !(s->h_flags[FLG_ERR] & (ERR_CELL_CAP | ERR_NBR_CAP));
+    // after a skin replay the next calls start with a binning on every inner step (a first attempt that
+    // would be replayed anyway costs a whole call); every kSafeCalls-th call tries the normal plan again
+    const bool safe = attempt > 0 ? (s->h_flags[FLG_SKIN] && !(s->h_flags[FLG_ERR] & (ERR_CELL_CAP | ERR_NBR_CAP)))
+                                  : s->safe_calls > 0;
     md_status st = upload_desc(s, dt_in, dt_outer);
     if (st != MD_OK) return st;
     st = clear_flags(s);
@@ -869,6 +894,8 @@ md_status do_call(md_system* s, int n_outer, int k, double dt_outer) {
         return fs;
       }
       // success
+      if (safe && n_outer > 0) s->safe_calls = (s->safe_calls + 1) % s->safe_span;
+      if (!safe && n_outer > 0) s->safe_span = kSafeCalls;  // the normal plan works again
       unsigned long long trip1 = s->h_ctr[CTR_TRIPLETS];
       int evals = n_outer + (init ? 1 : 0);
       if (evals > 0) s->stats.triplets_last = (trip1 - trip0) / (unsigned long long)evals;
@@ -908,6 +935,9 @@ md_status do_call(md_system* s, int n_outer, int k, double dt_outer) {
       s->forces_valid = false;  // the failed attempt re-sorted: rebuild the lists from the snapshot
     } else {
       s->stats.replays += 1;
+      // back off: each failed return to the normal plan doubles the run of safe calls (up to 64)
+      if (s->safe_calls == 0 && s->stats.replays > 1) s->safe_span = std::min(2 * s->safe_span, 64);
+      s->safe_calls = 1;
     }
     // a replay must recompute the cached forces only if they were not valid before
     if (init) s->forces_valid = false;

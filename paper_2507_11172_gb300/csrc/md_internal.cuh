@@ -33,7 +33,8 @@ enum : int { ACC_U2 = 0, ACC_W2 = 1, ACC_U3 = 2, ACC_W3 = 3, ACC_EK = 4, ACC_N =
 // counter slots in SysDev::ctr (unsigned long long)
 enum : int { CTR_TRIPLETS = 0, CTR_GUARD = 1, CTR_NEAR = 2, CTR_N = 4 };  // CTR_NEAR: near-class triplets
 // flag slots in SysDev::flags (int)
-enum : int { FLG_ERR = 0, FLG_SKIN = 1, FLG_MAXCELL = 2, FLG_STATE = 3, FLG_N = 4 };  // FLG_STATE: state transfer
+// FLG_STATE: state transfer; FLG_DOSORT: adaptive binning, a binning is due before the next LJ evaluation
+enum : int { FLG_ERR = 0, FLG_SKIN = 1, FLG_MAXCELL = 2, FLG_STATE = 3, FLG_DOSORT = 4, FLG_N = 8 };
 
 // Device-resident description of one system.  Kernels read it from global
 // memory at run time (never from constant memory) so graphs stay valid when
@@ -126,6 +127,7 @@ enum : int {
   M_SKIP = 1 << 10,     // batch: this member does nothing in this launch
   M_F3ACC = 1 << 11,    // combine: read (and clear) the rotation kernel's per-particle sums
   M_NEAR = 1 << 12,     // distance classes: near-class kick after an LJ step (k_kick)
+  M_COND = 1 << 13,     // binning kernels: run only if flags[FLG_DOSORT] is set (adaptive binning)
   M_TABLE = 1 << 30,    // batch: the low bits index SysDev::mode_tab, which holds the real mode
   M_TABLE_MASK = 0xffff,
   M_KIND_MASK = 0xff,
@@ -144,6 +146,11 @@ enum : int {  // combine kinds
 // mode of a work item: its own, or the member's table entry for batched launches
 __device__ __forceinline__ int item_mode(const SysDev& S, int imode) {
   return (imode & M_TABLE) ? S.mode_tab[imode & M_TABLE_MASK] : imode;
+}
+// binning kernels: nothing to do for a skipped member, or for a conditional binning that is not due
+__device__ __forceinline__ bool sort_idle(const SysDev& S, int imode) {
+  const int m = item_mode(S, imode);
+  return (m & M_SKIP) || ((m & M_COND) && S.flags[FLG_DOSORT] == 0);
 }
 
 // ---------------------------------------------------------------- helpers
@@ -363,6 +370,7 @@ void launch_cell_order(const Launch& L, const PItem* pitems, int npitems, int bl
                        int ncitems);
 void launch_snapshot(const Launch& L, const PItem* items, int nitems, int restore);
 void launch_stamp(cudaStream_t s, unsigned long long* out);
+void launch_sort_decide(const Launch& L);
 // state.cu (one system, sys[0])
 void launch_put_state(const Launch& L, int n, const double* pos, const double* vel, int cur, int full);
 void launch_take_state(const Launch& L, int n, const double* src, double* out, int fold);

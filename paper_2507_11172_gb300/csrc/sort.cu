@@ -13,7 +13,7 @@ namespace r3b {
 __global__ void k_bin_count(const SysDev* __restrict__ sys, const PItem* __restrict__ items) {
   const PItem it = items[blockIdx.x];
   const SysDev& S = sys[it.sys];
-  if (item_mode(S, it.mode) & M_SKIP) return;
+  if (sort_idle(S, it.mode)) return;
   int p = it.begin + threadIdx.x;
   if (p >= S.n) return;
   double* X = S.X[it.buf];
@@ -49,7 +49,7 @@ __global__ void k_bin_count(const SysDev* __restrict__ sys, const PItem* __restr
 __global__ void k_cell_members(const SysDev* __restrict__ sys, const PItem* __restrict__ items) {
   const PItem it = items[blockIdx.x];
   const SysDev& S = sys[it.sys];
-  if (item_mode(S, it.mode) & M_SKIP) return;
+  if (sort_idle(S, it.mode)) return;
   const int p = it.begin + threadIdx.x;
   if (p >= S.n) return;
   S.members[S.cell_start[S.cell_tmp[p]] + S.rank[p]] = p;
@@ -60,7 +60,7 @@ __global__ void k_cell_rank(const SysDev* __restrict__ sys, const CItem* __restr
   if (w >= nitems) return;  // warp-uniform
   const CItem it = items[w];
   const SysDev& S = sys[it.sys];
-  if (item_mode(S, it.mode) & M_SKIP) return;  // warp-uniform
+  if (sort_idle(S, it.mode)) return;  // warp-uniform
   const int lane = threadIdx.x & 31;
   const int b = S.cell_start[it.cell], cnt = S.cell_start[it.cell + 1] - b;
   for (int a0 = 0; a0 < cnt; a0 += 32) {
@@ -83,7 +83,7 @@ __global__ void k_cell_rank(const SysDev* __restrict__ sys, const CItem* __restr
 // cell_start[], count[] reset to zero, largest occupancy checked.
 __global__ void __launch_bounds__(1024) k_scan(const SysDev* __restrict__ sys, const SItem* __restrict__ items) {
   const SysDev& S = sys[items[blockIdx.x].sys];
-  if (item_mode(S, items[blockIdx.x].mode) & M_SKIP) return;
+  if (sort_idle(S, items[blockIdx.x].mode)) return;
   __shared__ int wsum[32];
   __shared__ int wmax[32];
   const int ncell = S.ncell;
@@ -145,7 +145,7 @@ __global__ void k_scatter(const SysDev* __restrict__ sys, const PItem* __restric
   using T4 = typename V4<T>::type;
   const PItem it = items[blockIdx.x];
   const SysDev& S = sys[it.sys];
-  if (item_mode(S, it.mode) & M_SKIP) return;
+  if (sort_idle(S, it.mode)) return;
   int p = it.begin + threadIdx.x;
   if (p >= S.n) return;
   const int n = S.n;
@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(32 * kListWarps)
   __shared__ int st_begin[28], st_cnt[27], st_cell[27];
   const CItem it = items[blockIdx.x];
   const SysDev& S = sys[it.sys];
-  if (item_mode(S, it.mode) & M_SKIP) return;
+  if (sort_idle(S, it.mode)) return;
   const int b = it.cell, nc = S.nc, n = S.n;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
@@ -383,6 +383,16 @@ __global__ void k_stamp(unsigned long long* out) {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   *out = t;
 }
+
+// Adaptive binning: a binning is due before the next LJ evaluation if some particle has moved more than
+// skin / 2 since the last one (flag set by the drifts); the decision is taken once, for every kernel of
+// the binning, and the drift flag starts over.
+__global__ void k_sort_decide(const SysDev* __restrict__ sys) {
+  const SysDev& S = sys[0];
+  S.flags[FLG_DOSORT] = S.flags[FLG_SKIN] != 0 ? 1 : 0;
+  S.flags[FLG_SKIN] = 0;
+}
+void launch_sort_decide(const Launch& L) { k_sort_decide<<<1, 1, 0, L.stream>>>(L.sys); }
 
 void launch_snapshot(const Launch& L, const PItem* items, int nitems, int restore) {
   if (nitems > 0) k_snapshot<<<nitems, 256, 0, L.stream>>>(L.sys, items, restore);

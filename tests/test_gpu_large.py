@@ -68,3 +68,32 @@ def test_100k_forces_after_steps(gpu_lib, cfg2, subset, prec, tol):
     r2f, _ = oracle.lj_particles(x, cfg2.L, subset, 1.0, 1.0, 2.5)
     assert force_err(f3[subset], r3f, np.sqrt((r3f ** 2).sum(1).mean())) <= tol
     assert force_err(f2[subset], r2f, np.sqrt((r2f ** 2).sum(1).mean())) <= tol
+
+
+@pytest.fixture(scope="module")
+def cfg3():
+    return md_inputs.rsa_2m(2.5)
+
+
+@pytest.mark.parametrize("rc3", [2.0, 2.5])
+def test_2m_rsa_subset_forces_at_x0_and_after_steps(gpu_lib, cfg3, rc3):
+    """2,000,000 particles, random-sequential-addition start at density 0.75, T* = 1.2, FP32 path, triplet
+    cutoff 2.0 and 2.5: the forces of a seeded 300-particle subset equal the oracle's per-particle pass
+    at x0 and, after 2 outer steps (k = 10, dt_outer = 0.02), at the GPU's own positions; total momentum
+    is conserved."""
+    u = md_inputs.uniform(md_inputs.config_seed(3), 9, 0, 600)
+    sub = np.unique((u * cfg3.n).astype(np.int64))[:300]
+    with gpu_lib.System.create(cfg3.x, cfg3.L, cfg3.v, precision=0, nu=NU, rc_triplet=rc3) as s:
+        f2, f3 = s.forces()
+        r3f, _, _ = oracle.atm_particles(cfg3.x, cfg3.L, sub, NU, rc3)
+        r2f, _ = oracle.lj_particles(cfg3.x, cfg3.L, sub, 1.0, 1.0, 2.5)
+        assert force_err(f3[sub], r3f, np.sqrt((r3f ** 2).sum(1).mean())) <= 1e-5
+        assert force_err(f2[sub], r2f, np.sqrt((r2f ** 2).sum(1).mean())) <= 1e-5
+        s.step(2, 10, 0.02)
+        x, v = s.state()
+        f2, f3 = s.forces()
+    r3f, _, _ = oracle.atm_particles(x, cfg3.L, sub, NU, rc3)
+    r2f, _ = oracle.lj_particles(x, cfg3.L, sub, 1.0, 1.0, 2.5)
+    assert force_err(f3[sub], r3f, np.sqrt((r3f ** 2).sum(1).mean())) <= 1e-5
+    assert force_err(f2[sub], r2f, np.sqrt((r2f ** 2).sum(1).mean())) <= 1e-5
+    assert np.abs(v.sum(0) - cfg3.v.sum(0)).max() < 1e-2
