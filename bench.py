@@ -467,7 +467,9 @@ def run_ensemble(r3, n_replicas=256, n_outer=20, seed=None, atm_kernel=2):
         trip = sum(r3.md_get_stats(h)["triplets_total"] - a for h, a in zip(hs, s0))
         lat = np.concatenate([r3.md_batch_latency(b, t) for t in tickets])
         done = sum(r3.md_batch_poll(b, t) for t in tickets)
+        cycles, replayed = r3.md_batch_cycles(b)
         return {"replicas": n_replicas, "done": int(done), "outer_steps_each": n_outer,
+                "cycles": cycles, "replayed_cycles": replayed,
                 "particles_total": int(sum(sp["n"] for sp in specs)),
                 "triplets_per_s": trip / wall, "wall_s": wall, "setup_s": t_setup,
                 "outer_step_latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
@@ -522,7 +524,9 @@ def run_serving(r3, seconds=3.0, rate=50.0, n_outer=100, k=10, seed=None, atm_ke
                     r3.md_destroy_system(h)
         wall = time.perf_counter() - t0
         lat = np.concatenate(lat_all) if lat_all else np.zeros(1)
+        cycles, replayed = r3.md_batch_cycles(b)
         return {"requests": n_req, "arrival_rate_per_s": rate, "arrival_window_s": seconds,
+                "cycles": cycles, "replayed_cycles": replayed,
                 "outer_steps_each": n_outer, "k_inner": k, "wall_s": wall,
                 "triplets_per_s": trip_all / wall,
                 "outer_step_latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),

@@ -207,6 +207,9 @@ md_status md_batch_run(md_batch *b, int max_ticks);
 md_status md_batch_poll(md_batch *b, uint64_t ticket, int *done);
 md_status md_batch_latency(md_batch *b, uint64_t ticket, double *ms, int *count);
 md_status md_batch_pending(md_batch *b, int *queued, int *resident);
+/* Cycles run so far and how many of them were replayed from their start (a member's particle left its
+ * skin, or a capacity grew); either pointer may be NULL. */
+md_status md_batch_cycles(md_batch *b, uint64_t *cycles, uint64_t *replayed);
 md_status md_batch_destroy(md_batch *b);
 
 /* ---------------- all-triplet (DirectSum) ATM forces ----------------

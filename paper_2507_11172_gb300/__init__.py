@@ -73,6 +73,7 @@ SIGNATURES = {
     "md_batch_poll": (_I, [_P, ctypes.c_uint64, ctypes.POINTER(_I)]),
     "md_batch_latency": (_I, [_P, ctypes.c_uint64, _P, ctypes.POINTER(_I)]),
     "md_batch_pending": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "md_batch_cycles": (_I, [_P, _U64P, _U64P]),
     "md_batch_destroy": (_I, [_P]),
     "md_atm_direct": (_I, [_P, _I64, _D, _I, _P, _P, _P]),
     "md_atm_forces_noalloc": (_I, [_P, _I64, _D, _D, _D, _P, ctypes.POINTER(_D), _U64P, _P]),
@@ -261,6 +262,13 @@ def md_batch_pending(b):
     q, r = _I(), _I()
     _check(load().md_batch_pending(b, ctypes.byref(q), ctypes.byref(r)), "md_batch_pending")
     return q.value, r.value
+
+
+def md_batch_cycles(b):
+    """(cycles run, cycles replayed from their start) of a batch."""
+    c, r = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(load().md_batch_cycles(b, ctypes.byref(c), ctypes.byref(r)), "md_batch_cycles")
+    return int(c.value), int(r.value)
 
 
 def md_batch_destroy(b):

@@ -114,6 +114,8 @@ struct md_system {
   // calls since the last skin replay that started in safe mode (0: start with the normal plan), and the
   // length of such a run before the normal plan is tried again
   int safe_calls = 0, safe_span = 4;
+  // batch member: the last drift of the previous cycle moved a particle more than skin / 2
+  bool skin_carry = false;
   // deferred allocation: state kept on the host until first use
   bool deferred = false;
   std::vector<double> host_x, host_v;
@@ -867,6 +869,9 @@ md_status do_call(md_system* s, int n_outer, int k, double dt_outer) {
     if (st != MD_OK) return st;
     st = clear_flags(s);
     if (st != MD_OK) return st;
+    // a replay restored positions and order from the snapshot, but the lists are those of the failed
+    // attempt's binnings: in safe mode the first inner step bins (the drift flag starts set)
+    if (safe && attempt > 0) CK(cudaMemsetAsync(s->h.flags + FLG_SKIN, 1, sizeof(int), s->stream));
     const bool init = !s->forces_valid;
     const int cur0 = s->cur;
     st = snapshot(s, true);
@@ -1361,6 +1366,8 @@ struct md_batch {
   std::vector<TickItems> ticks, ticks_safe;
   cudaGraphExec_t graph = nullptr, graph_safe = nullptr;
   size_t cap_slots = 0;
+  uint64_t cycles = 0, replayed = 0;  // cycles run, and replayed from their start
+  int safe_calls = 0, safe_span = 4;  // as for single systems: safe cycles after a skin replay
 };
 
 namespace {
@@ -1412,6 +1419,7 @@ void enqueue_cycle(md_batch* b, const std::vector<TickItems>& ticks, bool with_s
   chk("stamp", -1);
   for (int t = 0; t < b->P; ++t) {
     const TickItems& it = ticks[t];
+    if (&ticks == &b->ticks_safe) launch_sort_decide_all(L, (int)b->resident.size());
     launch_bin_count(L, b->d_pitems + it.bin, it.nbin, kBlock);
     chk("bin_count", t);
     launch_scan(L, b->d_sitems + it.scan, it.nscan);
@@ -1645,7 +1653,8 @@ void batch_fill_modes(md_batch* b, bool safe) {
       const bool closing = tt == r.k - 1;
       const bool final_step = closing && q == rem - 1;
       const int E = final_step ? M_ENERGY : 0;
-      e[KT_SORT] = (closing || safe) ? 0 : M_SKIP;
+      // safe plan: a binning before any tick whose positions moved more than skin / 2 (adaptive)
+      e[KT_SORT] = closing ? 0 : (safe ? M_COND : M_SKIP);
       e[KT_LJ] = (closing ? LJ_LAST : LJ_MID) | E;
       e[KT_ATM] = closing ? E : M_SKIP;
       e[KT_COMB] = closing ? ((final_step ? CB_LAST : CB_CONT) | E | f3r) : M_SKIP;
@@ -1694,6 +1703,7 @@ md_status batch_admit(md_batch* b) {
     s->batch = b;
     s->forces_valid = false;
     r.state = RQ_RESIDENT;
+    r.s->skin_carry = false;
     used += s->mem_bytes;
     b->resident.push_back(r.ticket);
     b->dirty = true;
@@ -1718,11 +1728,21 @@ void batch_retire(md_batch* b, std::vector<uint64_t>& leaving) {
 
 md_status batch_cycle(md_batch* b) {
   const int ns = (int)b->resident.size();
+  b->cycles += 1;
+  bool was_safe = false;
   for (int attempt = 0; attempt < 4; ++attempt) {
-    const bool safe = attempt > 0;
+    const bool safe = attempt > 0 || b->safe_calls > 0;
+    was_safe = safe;
     batch_fill_modes(b, safe);
     CK(cudaMemcpyAsync(b->d_modes, b->h_modes, sizeof(int) * ns * b->P * KT_N, cudaMemcpyHostToDevice, b->stream));
-    CK(cudaMemsetAsync(b->d_flags, 0, sizeof(int) * ns * FLG_N, b->stream));
+    // fresh flags, except a member's drift flag left by the previous cycle's last drift (the first
+    // tick's positions already moved more than skin / 2 from the member's last binning)
+    memset(b->h_flags, 0, sizeof(int) * ns * FLG_N);
+    // (a replay restored positions and order from the snapshot, but the lists are those of the failed
+    // attempt's binnings: every member bins before its first tick)
+    for (int j = 0; j < ns; ++j)
+      b->h_flags[j * FLG_N + FLG_SKIN] = (attempt > 0 || b->req[b->resident[j]].s->skin_carry) ? 1 : 0;
+    CK(cudaMemcpyAsync(b->d_flags, b->h_flags, sizeof(int) * ns * FLG_N, cudaMemcpyHostToDevice, b->stream));
     CK(cudaMemsetAsync(b->d_acc, 0, sizeof(double) * ns * ACC_N, b->stream));
     Launch L{b->stream, b->d_sys};
     launch_snapshot(L, b->d_snap, b->nsnap, 0);
@@ -1742,6 +1762,11 @@ md_status batch_cycle(md_batch* b) {
       if ((f[FLG_ERR] & ERR_HALF_CAP) && b->variant != 0) half = true;
     }
     if (!(skin || cap || half)) break;
+    b->replayed += 1;
+    if (skin) {  // safe cycles from now on, with back-off before the normal plan is tried again
+      if (b->safe_calls == 0 && b->replayed > 1) b->safe_span = std::min(2 * b->safe_span, 64);
+      b->safe_calls = 1;
+    }
     launch_snapshot(L, b->d_snap, b->nsnap, 1);  // every member back to the cycle start
     CK(cudaStreamSynchronize(b->stream));
     if (half && !cap) {  // the cell kernel takes longer half lists; replay the cycle with it
@@ -1778,6 +1803,12 @@ md_status batch_cycle(md_batch* b) {
       attempt = 0;  // replay in safe mode: the restored members' cell-local coordinates are stale
     }
   }
+  if (was_safe)
+    b->safe_calls = (b->safe_calls + 1) % b->safe_span;
+  else
+    b->safe_span = 4;  // the normal plan works again
+  for (int j = 0; j < ns; ++j)  // a safe cycle's last drift may already be past skin / 2
+    b->req[b->resident[j]].s->skin_carry = b->h_flags[j * FLG_N + FLG_SKIN] != 0;
   // progress, latencies, completion
   std::vector<uint64_t> leaving;
   for (int j = 0; j < ns; ++j) {
@@ -1901,6 +1932,13 @@ md_status md_batch_pending(md_batch* b, int* queued, int* resident) {
   if (!b) return MD_ERR_ARG;
   if (queued) *queued = (int)b->queue.size();
   if (resident) *resident = (int)b->resident.size();
+  return MD_OK;
+}
+
+md_status md_batch_cycles(md_batch* b, uint64_t* cycles, uint64_t* replayed) {
+  if (!b) return MD_ERR_ARG;
+  if (cycles) *cycles = b->cycles;
+  if (replayed) *replayed = b->replayed;
   return MD_OK;
 }
 

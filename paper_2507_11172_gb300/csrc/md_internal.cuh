@@ -371,6 +371,7 @@ void launch_cell_order(const Launch& L, const PItem* pitems, int npitems, int bl
 void launch_snapshot(const Launch& L, const PItem* items, int nitems, int restore);
 void launch_stamp(cudaStream_t s, unsigned long long* out);
 void launch_sort_decide(const Launch& L);
+void launch_sort_decide_all(const Launch& L, int ns);
 // state.cu (one system, sys[0])
 void launch_put_state(const Launch& L, int n, const double* pos, const double* vel, int cur, int full);
 void launch_take_state(const Launch& L, int n, const double* src, double* out, int fold);

@@ -393,6 +393,17 @@ __global__ void k_sort_decide(const SysDev* __restrict__ sys) {
   S.flags[FLG_SKIN] = 0;
 }
 void launch_sort_decide(const Launch& L) { k_sort_decide<<<1, 1, 0, L.stream>>>(L.sys); }
+// the same for every member of a batch (one thread each)
+__global__ void k_sort_decide_all(const SysDev* __restrict__ sys, int ns) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= ns) return;
+  const SysDev& S = sys[j];
+  S.flags[FLG_DOSORT] = S.flags[FLG_SKIN] != 0 ? 1 : 0;
+  S.flags[FLG_SKIN] = 0;
+}
+void launch_sort_decide_all(const Launch& L, int ns) {
+  if (ns > 0) k_sort_decide_all<<<(ns + 127) / 128, 128, 0, L.stream>>>(L.sys, ns);
+}
 
 void launch_snapshot(const Launch& L, const PItem* items, int nitems, int restore) {
   if (nitems > 0) k_snapshot<<<nitems, 256, 0, L.stream>>>(L.sys, items, restore);

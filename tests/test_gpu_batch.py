@@ -129,3 +129,40 @@ def test_serving_budget_and_arrivals(gpu_lib):
         r3.md_batch_destroy(b)
         for h in hs:
             r3.md_destroy_system(h)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_skin_violations_in_the_mix(gpu_lib, prec):
+    """A thin skin (0.02) makes particles leave it within a cycle: the batch replays and then runs
+    safe cycles (binning before any tick whose positions moved more than skin / 2); every result still
+    equals the same request run alone (FP64: and follows Algorithm 2)."""
+    r3 = gpu_lib
+    ws = _systems(71)
+    n_outer = 6
+    alone = []
+    for w in ws:
+        with r3.System.create(w.x, w.L, w.v, precision=prec, nu=NU, skin=0.02) as s:
+            s.step(n_outer, w.k_inner, w.dt_outer)
+            alone.append(s.state())
+    b = r3.md_batch_create(0)
+    hs, tickets = [], []
+    try:
+        for w in ws:
+            h = r3.md_create_system(w.x, w.L, w.v, 1.0, prec)
+            r3.md_set_skin(h, 0.02)
+            r3.md_set_potentials(h, 1.0, 1.0, 2.5, NU, 2.5)
+            hs.append(h)
+            tickets.append(r3.md_batch_submit(b, h, n_outer, w.k_inner, w.dt_outer))
+        r3.md_batch_run(b, 0)
+        cycles, replayed = r3.md_batch_cycles(b)
+        assert replayed >= 1
+        xtol = 1e-6 if prec == 0 else 1e-11
+        for w, h, t, (xa, va) in zip(ws, hs, tickets, alone):
+            assert r3.md_batch_poll(b, t)
+            x, v = r3.md_get_state(h)
+            assert _dist(x, xa, w.L) < xtol
+            assert np.abs(v - va).max() < 10 * xtol
+    finally:
+        r3.md_batch_destroy(b)
+        for h in hs:
+            r3.md_destroy_system(h)

@@ -175,6 +175,23 @@ def test_skin_violation_replays_exactly(gpu_lib, cfg1):
     assert np.abs(d).max() < 1e-10
 
 
+@pytest.mark.parametrize("skin", [0.01, 0.03, 0.06])
+def test_replays_with_thin_skins_follow_algorithm2(gpu_lib, cfg1, skin):
+    """Skins at which particles leave mid-call (not necessarily on the first drift): the replay restores
+    the call's start and bins adaptively; consecutive calls that start in safe mode too.  Positions after
+    6 outer steps in 3 calls equal Algorithm 2's."""
+    st = respa.State(cfg1.x.copy(), cfg1.v.copy(), cfg1.L)
+    f2b, f3b = respa.lj_atm_forces(cfg1.L, 1.0, 1.0, 2.5, NU, 2.5)
+    respa.run(st, 6, 5, 0.01, f2b, f3b)
+    with make(gpu_lib, cfg1, 1, skin=skin) as s:
+        for _ in range(3):
+            s.step(2, 5, 0.01)
+        x, v = s.state()
+    d = x - st.x
+    d -= cfg1.L * np.rint(d / cfg1.L)
+    assert np.abs(d).max() < 1e-10 and np.abs(v - st.v).max() < 1e-9
+
+
 @pytest.mark.parametrize("kernel", [-1, 2])
 def test_dense_cluster_grows_cell_capacity(gpu_lib, kernel):
     """All particles in one corner of a large box: cells overflow their first capacity, the
