@@ -196,7 +196,7 @@ def run_ours(args):
                                         trip=s1["triplets_total"] - s0["triplets_total"],
                                         atm_ms=(s1["atm_ms_total"] - s0["atm_ms_total"]),
                                         atm_n=s1["atm_timed"] - s0["atm_timed"], clocks=clock_summary(samples),
-                                        kernel=s1["atm_kernel"])
+                                        kernel=s1["atm_kernel"], per=s1["atm_bases_per_warp"])
             return out
         finally:
             r3.md_destroy_system(h)
@@ -304,6 +304,7 @@ def run_ours(args):
                      "frac": achieved_tflops / FP32_PEAK_TFLOPS,
                      "traffic": ATM_ROT_TRAFFIC_BYTES if q32["kernel"] == 2 else None,
                      "kernel": {0: "k_atm<float>", 1: "k_atm_pa<float>", 2: "k_atm_rot<float>"}.get(q32["kernel"]),
+                     "bases_per_warp": q32["per"] if q32["kernel"] == 2 else None,
                      "note": f"{ATM_FLOPS_PER_TRIPLET} flop per interacting triplet; peak = 152 SM x 128 "
                              "FP32 lanes x 2 x 2.07 GHz"},
         "clocks": clk,

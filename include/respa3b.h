@@ -72,7 +72,7 @@ typedef struct {
   int32_t max_cell_count;      /* largest cell occupancy seen at the last binning */
   int32_t cells_per_side;      /* binning grid */
   int32_t atm_kernel;          /* triplet kernel in use: 0 cell, 1 per-particle, 2 rotation, -1 not chosen yet */
-  int32_t reserved_;
+  int32_t atm_bases_per_warp;  /* rotation kernel: consecutive bases per warp in a work item (autotuned) */
   uint64_t near_triplets_last; /* distance classes: near-class triplets found by the last near evaluation */
 } md_stats;
 
@@ -167,8 +167,8 @@ md_status md_set_profiling(md_system *s, int profile);
  *      with its forces kept as edge weights; per-neighbour sums added with vector atomics
  *      (summation order varies from run to run at the FP32 rounding level);
  *      1 and 2 need r_c3 <= r_c2 + skin, else 0 is used;
- *  -1  (default) time the allowed kernels on the system's first evaluation and keep the
- *      fastest.  A batch uses its members' common choice, else 2 where allowed, else 0. */
+ *  -1  (default) time the allowed kernels (the rotation kernel with 4, 8 and 16 bases per warp in
+ *      a work item) on the system's first evaluation and keep the fastest.  A batch uses its members' common choice, else 2 where allowed, else 0. */
 md_status md_set_atm_kernel(md_system *s, int variant);
 
 /* Number of particles, box side and precision of a handle. */

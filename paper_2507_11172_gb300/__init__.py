@@ -36,7 +36,7 @@ class md_stats(ctypes.Structure):
                 ("atm_evals", ctypes.c_uint64), ("lj_evals", ctypes.c_uint64), ("outer_steps", ctypes.c_uint64),
                 ("replays", ctypes.c_uint64), ("guard_rechecks", ctypes.c_uint64), ("atm_ms_total", ctypes.c_double),
                 ("atm_timed", ctypes.c_uint64), ("max_cell_count", ctypes.c_int32),
-                ("cells_per_side", ctypes.c_int32), ("atm_kernel", ctypes.c_int32), ("reserved_", ctypes.c_int32),
+                ("cells_per_side", ctypes.c_int32), ("atm_kernel", ctypes.c_int32), ("atm_bases_per_warp", ctypes.c_int32),
                 ("near_triplets_last", ctypes.c_uint64)]
 
 

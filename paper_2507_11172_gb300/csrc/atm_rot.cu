@@ -43,9 +43,9 @@ namespace r3b {
 
 constexpr int kZrMax = 64;    // half-list capacity: two rotation groups of at most 32 nodes
 constexpr int kZrWarps = 4;   // warps per CTA
-constexpr int kZrPer = 8;     // consecutive bases per warp in one work item
+constexpr int kZrPer = 8;     // default number of consecutive bases per warp in one work item
 static_assert(kZrMax == kHalfCap, "half-list capacity");
-static_assert(kZrWarps * kZrPer == rot_bases_per_item(0), "work items and kernel disagree");
+static_assert(kZrWarps * kZrPer == rot_bases_per_item(0) && kZrWarps == kRotWarps, "work items and kernel disagree");
 
 // FP32 reciprocal square root: the hardware approximation (flush-to-zero form; the argument is a
 // product of three squared distances, never subnormal) refined by one Newton-Raphson step
@@ -624,13 +624,14 @@ __device__ __forceinline__ void zr_eval_any(const ZrK<T>& K, ZrSmem<T>& w, int x
   __syncwarp();  // the next base reuses the warp's shared memory
 }
 
-// Work item: 32 consecutive bases, kZrPer per warp.  FP32: a two-stage cp.async pipeline per warp
+// Work item: 4 per consecutive bases, per of them for each warp (the autotuner picks per; 8 by
+// default, kZrPer).  FP32: a two-stage cp.async pipeline per warp
 // copies the half list of base k + 2 and the positions of base k + 1 into shared memory while base k
 // is evaluated.  Counts and energy are summed per CTA (the last warp to finish adds them to the
 // system's totals with one atomic each).
 template <typename T>
 __global__ void __launch_bounds__(32 * kZrWarps, sizeof(T) == 4 ? 7 : 4)
-    k_atm_rot(const SysDev* __restrict__ sys, const PItem* __restrict__ items) {
+    k_atm_rot(const SysDev* __restrict__ sys, const PItem* __restrict__ items, const int per) {
   extern __shared__ __align__(32) unsigned char zr_raw[];
   __shared__ ZrK<T> K;
   __shared__ unsigned long long s_cnt;
@@ -667,8 +668,8 @@ __global__ void __launch_bounds__(32 * kZrWarps, sizeof(T) == 4 ? 7 : 4)
   __syncthreads();
   ZrSmem<T>& w = reinterpret_cast<ZrSmem<T>*>(zr_raw)[warp];
   const int n = K.n;
-  const int x0 = it.begin + warp * kZrPer;
-  const int nb = max(0, min(kZrPer, n - x0));  // bases of this warp
+  const int x0 = it.begin + warp * per;
+  const int nb = max(0, min(per, n - x0));  // bases of this warp
   T cnt = (T)0, u = (T)0;
   if constexpr (sizeof(T) == 4) {
     if (nb > 0) {
@@ -736,11 +737,11 @@ static bool zr_configure() {
 }
 
 template <typename T>
-void launch_atm_rot(const Launch& L, const PItem* items, int nitems) {
+void launch_atm_rot(const Launch& L, const PItem* items, int nitems, int per) {
   if (nitems > 0 && zr_configure<T>())
-    k_atm_rot<T><<<nitems, 32 * kZrWarps, zr_smem_bytes<T>(), L.stream>>>(L.sys, items);
+    k_atm_rot<T><<<nitems, 32 * kZrWarps, zr_smem_bytes<T>(), L.stream>>>(L.sys, items, per);
 }
-template void launch_atm_rot<float>(const Launch&, const PItem*, int);
-template void launch_atm_rot<double>(const Launch&, const PItem*, int);
+template void launch_atm_rot<float>(const Launch&, const PItem*, int, int);
+template void launch_atm_rot<double>(const Launch&, const PItem*, int, int);
 
 }  // namespace r3b

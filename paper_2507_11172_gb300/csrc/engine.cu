@@ -99,6 +99,7 @@ struct md_system {
   int atm_variant_req = -1;   // requested by md_set_atm_kernel (-1 = autotune)
   int nblocks_pa = 0;
   int nblocks_rot = 0;
+  int rot_per = rot_bases_per_item(0) / kRotWarps;  // rotation kernel: bases per warp in a work item
   std::map<std::tuple<int, int, int, int, int>, cudaGraphExec_t> graphs;  // (n_outer, k, cur, safe, profile)
   // host mirrors
   int* h_flags = nullptr;       // pinned [FLG_N]
@@ -409,7 +410,7 @@ PItem* pitems_for(md_system* s, int tag, int mode, int buf) {
   std::vector<PItem> v;
   const int per = (tag == T_LJ)      ? kLjParticles
                   : (tag == T_ATMPA)  ? kPaPerBlock
-                  : (tag == T_ATMROT) ? rot_bases_per_item(s->precision)
+                  : (tag == T_ATMROT) ? kRotWarps * s->rot_per
                   : (tag == T_ATMNEAR) ? kNearThreads
                                       : kBlock;
   const int nb = (tag == T_LJ)       ? (s->n + kLjParticles - 1) / kLjParticles
@@ -452,7 +453,7 @@ CItem* citems_for(md_system* s, int mode, int buf) {
 md_status prepare_items(md_system* s) {
   s->nblocks = (int)((s->n + kBlock - 1) / kBlock);
   s->nblocks_pa = (int)((s->n + kPaPerBlock - 1) / kPaPerBlock);
-  s->nblocks_rot = (int)((s->n + rot_bases_per_item(s->precision) - 1) / rot_bases_per_item(s->precision));
+  s->nblocks_rot = (int)((s->n + kRotWarps * s->rot_per - 1) / (kRotWarps * s->rot_per));
   for (int b = 0; b < 2; ++b) {
     pitems_for(s, T_BIN, 0, b);
     pitems_for(s, T_SCATTER, 0, b);
@@ -599,7 +600,8 @@ struct Plan {
   template <typename T>
   void atm_all(int buf, bool energy) {
     if (s->atm_variant == 2)
-      launch_atm_rot<T>(L, pitems_for(s, T_ATMROT, energy ? M_ENERGY : 0, buf), padded_blocks(s->nblocks_rot));
+      launch_atm_rot<T>(L, pitems_for(s, T_ATMROT, energy ? M_ENERGY : 0, buf), padded_blocks(s->nblocks_rot),
+                        s->rot_per);
     else if (s->atm_variant == 1)
       launch_atm_pa<T>(L, pitems_for(s, T_ATMPA, energy ? M_ENERGY : 0, buf), s->nblocks_pa);
     else
@@ -797,9 +799,30 @@ bool variant_allowed(const md_system* s, int v) {
   return v == 0 || ((v == 1 || v == 2) && s->rc3 <= s->rc2 + s->skin);
 }
 
+// rotation kernel work items of kRotWarps x per bases (the items of the previous shape are dropped
+// from the cache; their memory is released with the other items)
+md_status set_rot_per(md_system* s, int per) {
+  if (per == s->rot_per) return MD_OK;
+  s->rot_per = per;
+  s->nblocks_rot = (int)((s->n + kRotWarps * per - 1) / (kRotWarps * per));
+  for (auto it = s->pitems.begin(); it != s->pitems.end();) {
+    if (std::get<0>(it->first) == T_ATMROT)
+      it = s->pitems.erase(it);
+    else
+      ++it;
+  }
+  for (int b = 0; b < 2; ++b)
+    for (int e = 0; e < 2; ++e)
+      if (!pitems_for(s, T_ATMROT, e ? M_ENERGY : 0, b)) return MD_ERR_OOM;
+  CK(cudaStreamSynchronize(s->stream));
+  clear_graphs(s);
+  return MD_OK;
+}
+
 // Autotuner for the triplet kernel: after one initial evaluation (binning, pair list, forces)
-// each allowed variant is launched a few times on the same configuration with CUDA events
-// around each launch; the faster one is kept for the system.
+// each allowed variant, and for the rotation kernel each work-item shape (4, 8 or 16 bases per warp),
+// is launched a few times on the same configuration with CUDA events around each launch; the fastest
+// is kept for the system.
 md_status tune_atm(md_system* s) {
   const int req = s->atm_variant_req;
   if (req >= 0) {
@@ -819,10 +842,17 @@ md_status tune_atm(md_system* s) {
   st = run_plan(s, 0, 1, true, false);  // binning + pair list at the current positions
   if (st != MD_OK) return st;
   float best = 1e30f;
-  int bestv = 0;
-  for (int v = 0; v < 3; ++v) {
+  int bestv = 0, bestper = s->rot_per;
+  // candidates: (variant, bases per warp of the rotation kernel's work items)
+  const int cand[][2] = {{0, 0}, {1, 0}, {2, 4}, {2, 8}, {2, 16}};
+  for (const auto& c : cand) {
+    const int v = c[0];
     if (!variant_allowed(s, v)) continue;
     s->atm_variant = v;
+    if (v == 2) {
+      st = set_rot_per(s, c[1]);
+      if (st != MD_OK) return st;
+    }
     float tot = 0.f;
     for (int r = 0; r < 4; ++r) {
       CK(cudaEventRecord(s->events[0], s->stream));
@@ -836,9 +866,12 @@ md_status tune_atm(md_system* s) {
     if (tot < best) {
       best = tot;
       bestv = v;
+      if (v == 2) bestper = c[1];
     }
   }
   s->atm_variant = bestv;
+  st = set_rot_per(s, bestper);
+  if (st != MD_OK) return st;
   s->profile = prof;
   // the rotation kernel's trial launches left sums that no combine cleared
   CK(cudaMemsetAsync(s->h.f3acc, 0, (size_t)(s->precision ? 32 : 16) * (size_t)s->n, s->stream));
@@ -1260,6 +1293,7 @@ md_status md_set_state(md_system* s, const double* pos, const double* vel) {
 md_status md_get_stats(md_system* s, md_stats* out) {
   if (!s || !out) return MD_ERR_ARG;
   s->stats.atm_kernel = s->atm_variant;
+  s->stats.atm_bases_per_warp = s->rot_per;
   *out = s->stats;
   return MD_OK;
 }
@@ -1435,7 +1469,7 @@ void enqueue_cycle(md_batch* b, const std::vector<TickItems>& ticks, bool with_s
     launch_kick<T>(L, b->d_pitems + it.kick, it.nkick);
     chk("kick", t);
     if (b->variant == 2)
-      launch_atm_rot<T>(L, b->d_pitems + it.atm, it.natm);
+      launch_atm_rot<T>(L, b->d_pitems + it.atm, it.natm, rot_bases_per_item(b->precision) / kRotWarps);
     else if (b->variant == 1)
       launch_atm_pa<T>(L, b->d_pitems + it.atm, it.natm);
     else

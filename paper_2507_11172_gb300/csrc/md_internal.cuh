@@ -401,8 +401,10 @@ int atm_configure(int smax, int precision, int* smem_bytes);
 // per-particle ATM variant: items of 4 particles (one warp each)
 template <typename T> void launch_atm_pa(const Launch& L, const PItem* items, int nitems);
 constexpr int kPaPerBlock = 4;
-// rotation variant: items of rot_bases_per_item(precision) particles (4 warps of 8 particles each)
-template <typename T> void launch_atm_rot(const Launch& L, const PItem* items, int nitems);
+// rotation variant: items of kRotWarps x per particles (per consecutive particles per warp; the
+// autotuner picks per, rot_bases_per_item is the default item)
+constexpr int kRotWarps = 4;
+template <typename T> void launch_atm_rot(const Launch& L, const PItem* items, int nitems, int per);
 constexpr int rot_bases_per_item(int) { return 32; }
 template <typename T>
 void launch_atm_table(const Launch& L, const CItem* items, int nitems, int grid, int smax, const uint16_t* table);

@@ -315,3 +315,16 @@ def test_both_triplet_kernels_match_oracle(gpu_lib, cfg1, cfg1_ref, variant, pre
     frms = np.sqrt((r3f ** 2).sum(1).mean())
     err = np.linalg.norm(f3b[sel] - r3f, axis=1) / np.maximum(np.linalg.norm(r3f, axis=1), frms)
     assert err.max() <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_autotuned_rotation_shape_matches_oracle(gpu_lib, cfg1, cfg1_ref, prec):
+    """Whatever kernel and work-item shape the autotuner keeps, forces and the triplet count equal the
+    oracle's, before and after a call."""
+    with make(gpu_lib, cfg1, prec) as s:
+        _, f3 = s.forces()
+        st = s.stats()
+        assert st["triplets_last"] == cfg1_ref["cnt"]
+        assert force_err(f3, cfg1_ref["f3"]) <= TOL[prec]
+        s.step(1, 5, 0.01)
+        assert s.stats()["atm_kernel"] in (0, 1, 2)
