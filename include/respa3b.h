@@ -11,7 +11,9 @@
  *     truncation, no shift;
  *   - integrator: the single-loop r-RESPA of Algorithm 2 (Sec. 4.1), with the
  *     step-size factor s = k_inner and the paper's dt = dt_outer / k_inner;
- *   - Newton's third law (Sec. 2.2): each pair and triplet is evaluated once.
+ *   - Newton's third law (Sec. 2.2; the paper's outlook in Sec. 5): the default triplet
+ *     kernel evaluates each triplet once and gives all three members their forces;
+ *     LJ pairs are evaluated from both members (no scatter), as a GPU trade-off.
  *
  * Units are reduced LJ units (Sec. 4.2, Table 1): the caller chooses eps,
  * sigma, nu and the mass; k_B = 1.  The box is a periodic cube of side L
