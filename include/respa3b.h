@@ -96,10 +96,13 @@ md_status md_set_potentials(md_system *s, double lj_eps, double lj_sigma, double
                             double rc_triplet);
 
 /* Verlet-list skin for the pair list (default 0.3 sigma, thinner for boxes below
- * 3 (r_c2 + 0.3) at creation).  The pair list is
- * rebuilt at every outer step; if any particle moves more than skin/2 within
- * one, the call is replayed from its start with a rebuild on every inner
- * step, so results never depend on the skin. */
+ * 3 (r_c2 + 0.3) at creation).  The pair list is rebuilt at every outer step; if
+ * any particle moves more than skin/2 within one, the call is replayed from its
+ * start with a rebuild before every inner step at which some particle has moved
+ * more than skin/2 since the last rebuild (decided on the device), so results
+ * never depend on the skin.  The next calls start that way too; the plain plan is
+ * retried after 4 calls, then after 8, 16, ... (up to 64) while replays recur
+ * (md_stats.replays counts them).  Batches do the same per cycle. */
 md_status md_set_skin(md_system *s, double skin);
 
 /* Advance n_outer >= 0 outer steps of k_inner >= 1 inner steps each:
@@ -129,7 +132,10 @@ md_status md_get_energy(md_system *s, double *e_kin, double *u2, double *u3, dou
 md_status md_get_rdf(md_system *s, int nbins, double r_max, uint64_t *counts);
 
 /* Copy positions (folded into [0, L)) and velocities out / in, caller order,
- * n x 3 each; either may be NULL.  md_set_state invalidates cached forces. */
+ * n x 3 each; either may be NULL.  md_set_state invalidates cached forces; it
+ * returns MD_ERR_NONFINITE, with nothing changed, if an input value is NaN/Inf.
+ * Both copy straight between the caller's buffers and the device (pinned caller
+ * memory moves by DMA) and permute to and from the sorted layout on the device. */
 md_status md_get_state(md_system *s, double *pos, double *vel);
 md_status md_set_state(md_system *s, const double *pos, const double *vel);
 
