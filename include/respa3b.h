@@ -176,7 +176,8 @@ md_status md_set_profiling(md_system *s, int profile);
  *      (summation order varies from run to run at the FP32 rounding level);
  *      1 and 2 need r_c3 <= r_c2 + skin, else 0 is used;
  *  -1  (default) time the allowed kernels (the rotation kernel with 4, 8 and 16 bases per warp in
- *      a work item) on the system's first evaluation and keep the fastest.  A batch uses its members' common choice, else 2 where allowed, else 0. */
+ *      a work item) on the system's first evaluation and keep the fastest.  A batch uses its
+ *      members' common choice, else 2 where allowed, else 0. */
 md_status md_set_atm_kernel(md_system *s, int variant);
 
 /* Number of particles, box side and precision of a handle. */
