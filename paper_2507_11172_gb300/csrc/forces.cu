@@ -151,7 +151,7 @@ constexpr unsigned kPadCode = 63u;  // code of a padding entry (offset far outsi
 
 // kE = false: a launch whose items never ask for energies (compiled without the energy terms)
 template <typename T, bool kE>
-__global__ void __launch_bounds__(kLjPer, 14) k_lj(const SysDev* __restrict__ sys, const PItem* __restrict__ items) {
+__global__ void __launch_bounds__(kLjPer, 896 / kLjPer) k_lj(const SysDev* __restrict__ sys, const PItem* __restrict__ items) {
   using T4 = typename V4<T>::type;
   __shared__ T4 s_off[64];
   __shared__ T red_u[kLjPer / 32], red_w[kLjPer / 32];
@@ -160,8 +160,7 @@ __global__ void __launch_bounds__(kLjPer, 14) k_lj(const SysDev* __restrict__ sy
   const int mode = item_mode(S, it.mode);
   if (mode & M_SKIP) return;  // block-uniform: a block belongs to one system
   const bool energy = kE && (mode & M_ENERGY) != 0;
-  if (threadIdx.x < 64) {
-    const unsigned c = threadIdx.x;
+  for (unsigned c = threadIdx.x; c < 64u; c += blockDim.x) {
     const T e = Par<T>::edge(S);
     T4 o;
     o.x = fma((T)(c & 3u), e, -e);
@@ -169,7 +168,7 @@ __global__ void __launch_bounds__(kLjPer, 14) k_lj(const SysDev* __restrict__ sy
     o.z = fma((T)((c >> 4) & 3u), e, -e);
     o.w = (T)0;
     if (c == kPadCode) o.x = o.y = o.z = (T)1e3;
-    s_off[threadIdx.x] = o;
+    s_off[c] = o;
   }
   __syncthreads();
   const int n = S.n;

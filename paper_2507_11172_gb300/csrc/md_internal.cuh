@@ -383,7 +383,10 @@ int listbuild_configure(int smax, int precision);
 // forces.cu
 // LJ pair forces: blocks of kLjPer threads, teams of kLjTeam threads per particle, so items of
 // kLjParticles particles
-constexpr int kLjPer = 64;
+#ifndef R3B_LJ_PER
+#define R3B_LJ_PER 64
+#endif
+constexpr int kLjPer = R3B_LJ_PER;  // threads per block
 #ifndef R3B_LJ_TEAM
 #define R3B_LJ_TEAM 1
 #endif
