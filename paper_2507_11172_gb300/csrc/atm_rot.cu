@@ -41,6 +41,9 @@
 
 namespace r3b {
 
+#ifndef R3B_ROT_MINB
+#define R3B_ROT_MINB 5  // FP32: CTAs per SM the register allocation is sized for (5-8 measured: 5, without spills, fastest)
+#endif
 constexpr int kZrMax = 64;    // half-list capacity: two rotation groups of at most 32 nodes
 constexpr int kZrWarps = 4;   // warps per CTA
 constexpr int kZrPer = 8;     // default number of consecutive bases per warp in one work item
@@ -630,7 +633,7 @@ __device__ __forceinline__ void zr_eval_any(const ZrK<T>& K, ZrSmem<T>& w, int x
 // is evaluated.  Counts and energy are summed per CTA (the last warp to finish adds them to the
 // system's totals with one atomic each).
 template <typename T>
-__global__ void __launch_bounds__(32 * kZrWarps, sizeof(T) == 4 ? 7 : 4)
+__global__ void __launch_bounds__(32 * kZrWarps, sizeof(T) == 4 ? R3B_ROT_MINB : 4)
     k_atm_rot(const SysDev* __restrict__ sys, const PItem* __restrict__ items, const int per) {
   extern __shared__ __align__(32) unsigned char zr_raw[];
   __shared__ ZrK<T> K;
