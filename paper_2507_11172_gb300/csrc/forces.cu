@@ -151,7 +151,10 @@ constexpr unsigned kPadCode = 63u;  // code of a padding entry (offset far outsi
 
 // kE = false: a launch whose items never ask for energies (compiled without the energy terms)
 template <typename T, bool kE>
-__global__ void __launch_bounds__(kLjPer, 896 / kLjPer) k_lj(const SysDev* __restrict__ sys, const PItem* __restrict__ items) {
+#ifndef R3B_LJ_THREADS_PER_SM
+#define R3B_LJ_THREADS_PER_SM 896  // resident LJ threads per SM the register allocation is sized for
+#endif
+__global__ void __launch_bounds__(kLjPer, R3B_LJ_THREADS_PER_SM / kLjPer) k_lj(const SysDev* __restrict__ sys, const PItem* __restrict__ items) {
   using T4 = typename V4<T>::type;
   __shared__ T4 s_off[64];
   __shared__ T red_u[kLjPer / 32], red_w[kLjPer / 32];
