@@ -40,7 +40,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # accumulation of F_i (3) and scatter of F_j, F_k (6)
 # DRAM bytes (read + write) of one launch of the rotation kernel on the 100k workload, from an ncu
 # capture of the current kernel (dram__bytes_read.sum + dram__bytes_write.sum; cold caches)
-ATM_ROT_TRAFFIC_BYTES = 29.425408e6 + 256.0
+ATM_ROT_TRAFFIC_BYTES = 29.475840e6 + 0.0
 ATM_FLOPS_PER_TRIPLET = 3 + 5 + 2 + 5 + 3 + 8 + 4 + 9 + 3 + 5 + 1 + 12 + 9 + 9 + 3 + 3 + 6
 
 
