@@ -14,7 +14,10 @@ constexpr int kPairTable = kMaxHalf * (kMaxHalf - 1) / 2;  // (j, k) pairs, k-ma
 constexpr int kAtmWarps = 8;
 constexpr int kAtmThreads = 32 * kAtmWarps;
 constexpr int kQueue = 256;         // per-warp queue of accepted neighbour pairs (j, k)
-constexpr int kListWarps = 4;       // warps per CTA of the pair-list build
+#ifndef R3B_LIST_WARPS
+#define R3B_LIST_WARPS 4
+#endif
+constexpr int kListWarps = R3B_LIST_WARPS;  // warps per CTA of the pair-list build
 constexpr int kNearThreads = 128;   // owners (one thread each) per CTA of the near-class triplet kernel
 constexpr int kHalfCap = 64;        // triplet half list per particle (neighbours above it within r_c3)
 
