@@ -894,8 +894,8 @@ md_status do_call(md_system* s, int n_outer, int k, double dt_outer) {
   }
   const double dt_in = dt_outer / k;
   for (int attempt = 0; attempt < 6; ++attempt) {
-    // after a skin replay the next calls start with a binning on every inner step (a first attempt that
-    // would be replayed anyway costs a whole call); every kSafeCalls-th call tries the normal plan again
+    // after a skin replay the next calls start in safe mode (adaptive binning; a first attempt that
+    // would be replayed anyway costs a whole call); after safe_span calls the normal plan is tried again
     const bool safe = attempt > 0 ? (s->h_flags[FLG_SKIN] && !(s->h_flags[FLG_ERR] & (ERR_CELL_CAP | ERR_NBR_CAP)))
                                   : s->safe_calls > 0;
     md_status st = upload_desc(s, dt_in, dt_outer);
@@ -1545,7 +1545,8 @@ md_status batch_build(md_batch* b) {
     r.trip0 = 0;
   }
   CK(cudaMemcpyAsync(b->d_sys, hs.data(), sizeof(SysDev) * ns, cudaMemcpyHostToDevice, b->stream));
-  // work items for every tick of the cycle (normal, and safe: a rebuild on every tick)
+  // work items for every tick of the cycle (normal, and safe: binning items on every tick, which the
+  // members' modes make conditional on their drift flags)
   std::vector<PItem> pit;
   std::vector<CItem> cit;
   std::vector<SItem> sit;
