@@ -71,3 +71,17 @@ def test_reference_arm_other_ranks_exit_without_work():
                        env=env, capture_output=True, text=True, timeout=120)
     assert p.returncode == 0, p.stderr
     assert p.stdout.strip() == ""
+
+
+def test_clock_summary_reads_both_sample_formats():
+    """The clock sampler's lines (NVML or nvidia-smi CSV): median SM clock, maximum, and the throttle
+    reasons that were active in any sample."""
+    import bench
+    lines = ["1995, 2070, , 0x4, Not Active, Not Active, Not Active, Active",
+             "2070, 2070, 512.3, 0x0, Not Active, Not Active, Not Active, Not Active",
+             "2070, 2070, 514.0, Not Active, Not Active, Not Active, Not Active, Not Active",
+             "garbage"]
+    c = bench.clock_summary(lines)
+    assert c["sm_mhz"] == 2070.0 and c["sm_max_mhz"] == 2070.0
+    assert c["reasons"] == ["sw_power_cap"] and c["samples"] == 3
+    assert bench.clock_summary([])["sm_mhz"] is None
