@@ -844,7 +844,11 @@ md_status tune_atm(md_system* s) {
   float best = 1e30f;
   int bestv = 0, bestper = s->rot_per;
   // candidates: (variant, bases per warp of the rotation kernel's work items)
+#ifdef R3B_ROT_SHAPE_ONLY  // build-time knob: a single rotation shape instead of the tuned choice
+  const int cand[][2] = {{0, 0}, {1, 0}, {2, R3B_ROT_SHAPE_ONLY}};
+#else
   const int cand[][2] = {{0, 0}, {1, 0}, {2, 4}, {2, 8}, {2, 16}};
+#endif
   for (const auto& c : cand) {
     const int v = c[0];
     if (!variant_allowed(s, v)) continue;
