@@ -58,3 +58,15 @@ def test_no_oracle_import_in_product_package():
                 src = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in src and "from oracle" not in src, f
                 assert "liboracle" not in src and "oracle/" not in src, f
+
+
+def test_binding_argument_counts_match_the_header():
+    """Every ctypes signature of the binding has as many arguments as the header's prototype."""
+    txt = open(os.path.join(ROOT, "include", "respa3b.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    protos = dict(re.findall(r"\b(md_[a-z_]+)\s*\(([^)]*)\)\s*;", txt))
+    assert protos
+    for name, params in protos.items():
+        params = params.strip()
+        n = 0 if params in ("", "void") else params.count(",") + 1
+        assert len(r3.SIGNATURES[name][1]) == n, name
