@@ -1,7 +1,8 @@
 // Host runtime and C ABI of respa3b: device state of a system, the launch
 // plan of Algorithm 2 (arXiv 2507.11172, Sec. 4.1) captured as CUDA graphs,
-// snapshot/replay when a particle outruns the pair-list skin, and the batched
-// ensemble / serving engine.
+// snapshot/replay when a particle outruns the pair-list skin (with adaptive
+// binning afterwards), the triplet-kernel autotuner, distance classes, and the
+// batched ensemble / serving engine.
 #include <math.h>
 #include <stdio.h>
 #include <string.h>

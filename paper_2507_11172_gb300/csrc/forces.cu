@@ -1,12 +1,16 @@
-// Force kernels of the r-RESPA hot path (arXiv 2507.11172):
+// Force and update kernels of the r-RESPA hot path (arXiv 2507.11172):
 //   k_lj      Lennard-Jones 12-6 pair forces (Sec. 2.1) from the Verlet pair
-//             list, fused with the inner velocity-Verlet kick/drift of
-//             Algorithm 2 (one launch per inner step).
+//             list (each thread one particle's force, no scatter).
+//   k_kick    the inner velocity-Verlet kick/drift of Algorithm 2 after each
+//             LJ evaluation (FP64, one thread per particle).
 //   k_atm     Axilrod-Teller-Muto triplet forces (Sec. 2.1) with the triplet
 //             cutoff "all three distances <= r_c" (Fig. 2 caption, Sec.
-//             4.2.2), each triplet evaluated once with Newton-3 scatter.
-//   k_combine per-particle sum of the triplet kernel's partial forces and the
-//             outer (three-body) kicks of Algorithm 2.
+//             4.2.2), one CTA per cell, each triplet evaluated once with
+//             Newton-3 scatter (cell kernel; the default is k_atm_rot).
+//   k_atm_pa  the same forces, each triplet evaluated from each member.
+//   k_combine per-particle sum of the triplet kernel's forces and the outer
+//             (three-body) kicks of Algorithm 2 (with distance classes: far
+//             and near kicks).
 //   k_start   opening half kicks and first drift of a call.
 #include <stdio.h>
 
