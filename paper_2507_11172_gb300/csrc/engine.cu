@@ -994,13 +994,17 @@ md_status do_call(md_system* s, int n_outer, int k, double dt_outer) {
 
 // caller-order AoS copy (out_aos, host) of a sorted SoA device array; the permutation runs on the
 // device (staged in snap_x, free between calls), the host only receives the result
-md_status fetch_sorted(md_system* s, const double* dsrc, double* out_aos, bool wrap) {
+// (two arrays at once when dsrc2 / out2 are given: staged in snap_x and snap_v, one synchronisation)
+md_status fetch_sorted(md_system* s, const double* dsrc, double* out_aos, bool wrap, const double* dsrc2 = nullptr,
+                       double* out2 = nullptr, bool wrap2 = false) {
   const size_t n = (size_t)s->n;
   Launch L{s->stream, s->d_sys};
   CK(cudaMemsetAsync(s->h.flags + FLG_STATE, 0, 4, s->stream));
   launch_take_state(L, (int)n, dsrc, s->snap_x, wrap ? 1 : 0);
+  if (dsrc2) launch_take_state(L, (int)n, dsrc2, s->snap_v, wrap2 ? 1 : 0);
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(out_aos, s->snap_x, 24 * n, cudaMemcpyDeviceToHost, s->stream));
+  if (dsrc2) CK(cudaMemcpyAsync(out2, s->snap_v, 24 * n, cudaMemcpyDeviceToHost, s->stream));
   CK(cudaMemcpyAsync(s->h_flags + FLG_STATE, s->h.flags + FLG_STATE, 4, cudaMemcpyDeviceToHost, s->stream));
   CK(cudaStreamSynchronize(s->stream));
   return s->h_flags[FLG_STATE] ? MD_ERR_STATE : MD_OK;
@@ -1205,14 +1209,9 @@ md_status md_get_forces(md_system* s, double* f2, double* f3) {
   if (s->batch) return MD_ERR_STATE;
   md_status st = ensure_forces(s);
   if (st != MD_OK) return st;
-  if (f2) {
-    st = fetch_sorted(s, s->h.f2, f2, false);
-    if (st != MD_OK) return st;
-  }
-  if (f3) {
-    st = fetch_sorted(s, s->h.f3, f3, false);
-    if (st != MD_OK) return st;
-  }
+  if (f2 && f3) return fetch_sorted(s, s->h.f2, f2, false, s->h.f3, f3, false);
+  if (f2) return fetch_sorted(s, s->h.f2, f2, false);
+  if (f3) return fetch_sorted(s, s->h.f3, f3, false);
   return MD_OK;
 }
 
@@ -1265,14 +1264,9 @@ md_status md_get_state(md_system* s, double* pos, double* vel) {
     if (vel) memcpy(vel, s->host_v.data(), 24 * (size_t)s->n);
     return MD_OK;
   }
-  if (pos) {
-    md_status st = fetch_sorted(s, s->h.X[s->cur], pos, true);
-    if (st != MD_OK) return st;
-  }
-  if (vel) {
-    md_status st = fetch_sorted(s, s->h.v, vel, false);
-    if (st != MD_OK) return st;
-  }
+  if (pos && vel) return fetch_sorted(s, s->h.X[s->cur], pos, true, s->h.v, vel, false);
+  if (pos) return fetch_sorted(s, s->h.X[s->cur], pos, true);
+  if (vel) return fetch_sorted(s, s->h.v, vel, false);
   return MD_OK;
 }
 
