@@ -170,3 +170,81 @@ def run3(state: State3, n_outer: int, k_inner: int, s_near: int, dt_outer: float
                 state.energies.append((kinetic(v, m), state.u2, state.u3n + state.u3f))
     state.x, state.v, state.f2, state.f3n, state.f3f = x, v, f2, f3n, f3f
     return state
+
+
+# ---------------------------------------------------------------------------------------------
+# Several distance classes (the outlook of Sec. 5 names several intermediate cutoffs, each class with
+# its own time step): cutoffs r_1 < r_2 < ... < r_C = r_c3 split the ATM triplets by their largest pair
+# distance, class c holding the triplets with r_{c-1} < max distance <= r_c (r_0 = 0).  Class c is
+# integrated with step-size factor s_c, s_1 | s_2 | ... | s_C = k_inner, written as one loop in the
+# manner of Algorithm 2: the class-c kicks dt s_c / (2m) F_c open and close every block of s_c
+# iterations, the LJ force drives every iteration.
+
+@dataclass
+class StateN:
+    x: np.ndarray
+    v: np.ndarray
+    L: float
+    mass: float = 1.0
+    f2: Optional[np.ndarray] = None
+    f3: Optional[list] = None          # per-class forces
+    u2: float = 0.0
+    u3: Optional[list] = None          # per-class energies
+    energies: list = field(default_factory=list)  # (e_kin, u2, sum of class energies) at each full step
+
+
+def band_forces(L: float, nu: float, cutoffs):
+    """Force fields x -> (F, U, W) of the classes r_{c-1} < max pair distance <= r_c, each the difference
+    of two brute-force sums with the triplet cutoffs r_c and r_{c-1}."""
+    cut = [float(c) for c in cutoffs]
+    if any(not (b > a) for a, b in zip(cut, cut[1:])) or not cut[0] > 0:
+        raise ValueError("cutoffs must increase from a positive value")
+
+    def make(c):
+        def f(x):
+            fa, ua, wa, _ = atm_brute(x, L, nu, cut[c])
+            if c == 0:
+                return fa, ua, wa
+            fb, ub, wb, _ = atm_brute(x, L, nu, cut[c - 1])
+            return fa - fb, ua - ub, wa - wb
+        return f
+    return [make(c) for c in range(len(cut))]
+
+
+def run_classes(state: StateN, n_outer: int, k_inner: int, s_list, dt_outer: float, f2b: ForceFn, fclass,
+                periodic: bool = True, record: bool = False) -> StateN:
+    """n_outer outer steps of k_inner iterations (dt = dt_outer / k_inner) with the classes' force fields
+    fclass[c] kicked every s_list[c] iterations; s_list increasing, each dividing the next, the last
+    equal to k_inner.  With two classes this is run3."""
+    s_list = [int(s) for s in s_list]
+    if (len(s_list) != len(fclass) or s_list[-1] != k_inner or any(s < 1 for s in s_list)
+            or any(b % a for a, b in zip(s_list, s_list[1:])) or n_outer < 0 or not dt_outer > 0):
+        raise ValueError("s_1 | s_2 | ... | s_C = k_inner, one factor per class, dt_outer > 0 required")
+    dt = dt_outer / k_inner
+    m = state.mass
+    C = len(s_list)
+    x, v = state.x, state.v
+    if state.f2 is None:
+        state.f2, state.u2, _ = f2b(x)
+    if state.f3 is None:
+        res = [f(x) for f in fclass]
+        state.f3, state.u3 = [r[0] for r in res], [r[1] for r in res]
+    f2, f3 = state.f2, list(state.f3)
+    for i in range(n_outer * k_inner):
+        for c in reversed(range(C)):  # opening kicks, slowest class first
+            if i % s_list[c] == 0:
+                v = v + (dt * s_list[c] / (2.0 * m)) * f3[c]
+        x_new = x + dt * v + (dt * dt / (2.0 * m)) * f2
+        if periodic:
+            x_new = wrap(x_new, state.L)
+        f2_new, state.u2, _ = f2b(x_new)
+        v = v + (dt / (2.0 * m)) * (f2 + f2_new)
+        x, f2 = x_new, f2_new
+        for c in range(C):  # closing kicks, fastest class first
+            if (i + 1) % s_list[c] == 0:
+                f3[c], state.u3[c], _ = fclass[c](x)
+                v = v + (dt * s_list[c] / (2.0 * m)) * f3[c]
+        if (i + 1) % k_inner == 0 and record:
+            state.energies.append((kinetic(v, m), state.u2, float(sum(state.u3))))
+    state.x, state.v, state.f2, state.f3 = x, v, f2, f3
+    return state

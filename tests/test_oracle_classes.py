@@ -1,7 +1,9 @@
-"""Pins of the distance-class r-RESPA oracle (three levels: LJ, near triplets, far triplets)."""
+"""Pins of the distance-class r-RESPA oracle (three levels: LJ, near triplets, far triplets; and
+several classes, each with its own step-size factor)."""
 import itertools
 
 import numpy as np
+import pytest
 
 import md_inputs
 import oracle
@@ -100,3 +102,94 @@ def test_time_reversibility():
     d = st.x - x
     d -= L * np.rint(d / L)
     assert np.abs(d).max() < 1e-10 and np.abs(st.v + v).max() < 1e-9
+
+
+# ---------------------------------------------------------------- several classes
+
+def test_two_classes_are_run3_bit_for_bit():
+    x, v, L = _system()
+    f2b, _ = respa.lj_atm_forces(L, 1.0, 1.0, 2.5, 0.4, 2.5)
+    near, far = respa.class_forces(L, 0.4, 1.9, 2.5)
+    a = respa.State3(x.copy(), v.copy(), L)
+    respa.run3(a, 3, 6, 2, 0.012, f2b, near, far)
+    b = respa.StateN(x.copy(), v.copy(), L)
+    respa.run_classes(b, 3, 6, [2, 6], 0.012, f2b, respa.band_forces(L, 0.4, [1.9, 2.5]))
+    assert np.array_equal(a.x, b.x) and np.array_equal(a.v, b.v)
+
+
+def test_three_bands_partition_the_triplets():
+    x, _, L = _system(40)
+    cut = [1.4, 1.9, 2.5]
+    fb = respa.band_forces(L, 0.3, cut)
+    fall, uall, _, _ = oracle.atm_brute(x, L, 0.3, 2.5)
+    fs = [f(x) for f in fb]
+    assert np.abs(sum(r[0] for r in fs) - fall).max() < 1e-12 * max(1.0, np.abs(fall).max())
+    assert abs(sum(r[1] for r in fs) - uall) < 1e-12 * max(1.0, abs(uall))
+    # the bands' triplet counts against a plain loop over all triples
+    d = x[:, None, :] - x[None, :, :]
+    d -= L * np.rint(d / L)
+    r = np.sqrt((d ** 2).sum(-1))
+    counts = [0, 0, 0]
+    for i, j, k in itertools.combinations(range(len(x)), 3):
+        mx = max(r[i, j], r[i, k], r[j, k])
+        for c, rc in enumerate(cut):
+            if mx <= rc:
+                counts[c] += 1
+                break
+    got = [oracle.atm_brute(x, L, 0.3, rc)[3] for rc in cut]
+    assert [got[0], got[1] - got[0], got[2] - got[1]] == counts
+
+
+def test_all_factors_equal_k_is_algorithm2():
+    x, v, L = _system()
+    f2b, f3b = respa.lj_atm_forces(L, 1.0, 1.0, 2.5, 0.4, 2.5)
+    a = respa.StateN(x.copy(), v.copy(), L)
+    respa.run_classes(a, 3, 4, [4, 4, 4], 0.008, f2b, respa.band_forces(L, 0.4, [1.4, 1.9, 2.5]))
+    b = respa.State(x.copy(), v.copy(), L)
+    respa.run(b, 3, 4, 0.008, f2b, f3b)
+    assert np.abs(a.x - b.x).max() < 1e-12 and np.abs(a.v - b.v).max() < 1e-11
+
+
+def test_four_spring_nested_matrix_product():
+    """1-D oscillator: spring k0 every step, k1 every s1, k2 every s2, k3 every k steps; one outer step is
+    K3 [K2 [K1 M0^s1 K1]^(s2/s1) K2]^(k/s2) K3 (nested loops of Sec. 2.3.1)."""
+    m, dt, s1, s2, k = 1.1, 0.02, 2, 4, 8
+    ks = [2.5, 0.9, 0.4, 0.1]
+
+    def kick(kk, h):
+        return np.array([[1.0, 0.0], [-kk * h / m, 1.0]])
+    drift = np.array([[1.0, dt], [0.0, 1.0]])
+    M0 = kick(ks[0], dt / 2) @ drift @ kick(ks[0], dt / 2)
+    M1 = kick(ks[1], s1 * dt / 2) @ np.linalg.matrix_power(M0, s1) @ kick(ks[1], s1 * dt / 2)
+    M2 = kick(ks[2], s2 * dt / 2) @ np.linalg.matrix_power(M1, s2 // s1) @ kick(ks[2], s2 * dt / 2)
+    M3 = kick(ks[3], k * dt / 2) @ np.linalg.matrix_power(M2, k // s2) @ kick(ks[3], k * dt / 2)
+    y0 = np.array([0.7, 0.2])
+    st = respa.StateN(np.array([[y0[0], 0.0, 0.0]]), np.array([[y0[1], 0.0, 0.0]]), 1e9, mass=m)
+    lin = lambda kk: (lambda x: (-kk * x, 0.5 * kk * float((x ** 2).sum()), 0.0))
+    respa.run_classes(st, 3, k, [s1, s2, k], k * dt, lin(ks[0]), [lin(ks[1]), lin(ks[2]), lin(ks[3])],
+                      periodic=False)
+    y = np.linalg.matrix_power(M3, 3) @ y0
+    assert abs(st.x[0, 0] - y[0]) < 1e-13 and abs(st.v[0, 0] - y[1]) < 1e-13
+
+
+def test_three_classes_time_reversible():
+    x, v, L = _system()
+    f2b, _ = respa.lj_atm_forces(L, 1.0, 1.0, 2.5, 0.4, 2.5)
+    fb = respa.band_forces(L, 0.4, [1.4, 1.9, 2.5])
+    st = respa.StateN(x.copy(), v.copy(), L)
+    respa.run_classes(st, 2, 4, [1, 2, 4], 0.008, f2b, fb)
+    st.v = -st.v
+    respa.run_classes(st, 2, 4, [1, 2, 4], 0.008, f2b, fb)
+    d = st.x - x
+    d -= L * np.rint(d / L)
+    assert np.abs(d).max() < 1e-10 and np.abs(st.v + v).max() < 1e-9
+
+
+def test_bad_class_factors_are_rejected():
+    x, v, L = _system()
+    f2b, _ = respa.lj_atm_forces(L, 1.0, 1.0, 2.5, 0.4, 2.5)
+    fb = respa.band_forces(L, 0.4, [1.9, 2.5])
+    with pytest.raises(ValueError):
+        respa.run_classes(respa.StateN(x.copy(), v.copy(), L), 1, 6, [4, 6], 0.012, f2b, fb)
+    with pytest.raises(ValueError):
+        respa.band_forces(L, 0.4, [2.5, 1.9])
