@@ -348,16 +348,22 @@ __global__ void __launch_bounds__(256) k_kick(const SysDev* __restrict__ sys, co
     const double c = S.dt_in * S.inv_mass;
     const double* __restrict__ X = S.X[it.buf];
     double* Xo = S.X[it.buf ^ 1];
-    double xn[3], rel[3], fn[3] = {0.0, 0.0, 0.0};
-    if (mode & M_NEAR) take_near<T>(S, i, fn);
-    const double cn = S.dt_near * S.inv_mass;
+    double xn[3], rel[3], vv[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) vv[a] = fma(c, S.f2[a * n + i], S.v[a * n + i]);
+    if (mode & M_NEAR) {  // block-uniform; FP64 instructions are costly on GB300: only where needed
+      double fn[3];
+      take_near<T>(S, i, fn);
+      const double cn = S.dt_near * S.inv_mass;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) vv[a] = fma(cn, fn[a], vv[a]);
+    }
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const double vv = fma(cn, fn[a], fma(c, S.f2[a * n + i], S.v[a * n + i]));
-      S.v[a * n + i] = vv;
-      xn[a] = fma(S.dt_in, vv, X[a * n + i]);
+      S.v[a * n + i] = vv[a];
+      xn[a] = fma(S.dt_in, vv[a], X[a * n + i]);
       Xo[a * n + i] = xn[a];
-      bad |= !finite_bits(vv);
+      bad |= !finite_bits(vv[a]);
     }
     cell_rel(S, S.pcell[i], xn, rel);
     store_pos<T>(S, it.buf ^ 1, i, rel, true);
@@ -1149,7 +1155,7 @@ __global__ void __launch_bounds__(256) k_combine(const SysDev* __restrict__ sys,
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       S.f3[a * n + p] = F[a];
-      bad |= !isfinite(F[a]);
+      bad |= !finite_bits(F[a]);
     }
     // distance classes: F holds near + far; the near part comes from the second evaluation
     const bool classes = S.f3n != nullptr;
@@ -1159,7 +1165,7 @@ __global__ void __launch_bounds__(256) k_combine(const SysDev* __restrict__ sys,
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         S.f3n[a * n + p] = Fn[a];
-        bad |= !isfinite(Fn[a]);
+        bad |= !finite_bits(Fn[a]);
       }
     }
     if (kind != CB_INIT) {
@@ -1189,7 +1195,7 @@ __global__ void __launch_bounds__(256) k_combine(const SysDev* __restrict__ sys,
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         S.v[a * n + p] = vv[a];
-        bad |= !isfinite(vv[a]);
+        bad |= !finite_bits(vv[a]);
       }
     }
     if (bad) atomicOr(&S.flags[FLG_ERR], ERR_NONFINITE);
@@ -1223,7 +1229,7 @@ __global__ void __launch_bounds__(256) k_start(const SysDev* __restrict__ sys, c
     S.v[a * n + p] = vv;
     xn[a] = X[a * n + p] + S.dt_in * vv;
     Xo[a * n + p] = xn[a];
-    bad |= !isfinite(vv);
+    bad |= !finite_bits(vv);
   }
   cell_rel(S, S.pcell[p], xn, rel);
   store_pos<T>(S, 0, p, rel, true);

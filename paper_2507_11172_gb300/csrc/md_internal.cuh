@@ -202,16 +202,23 @@ template <typename T> struct V4;
 template <> struct V4<float> { using type = float4; };
 template <> struct V4<double> { using type = double4_32a; };
 
+// Fold into [0, L).  Positions are folded at every binning and move far less than L in between, so
+// nearly every call finds x inside already (checked on the bit pattern with integer compares: for
+// L > 0, 0 <= x < L exactly when the pattern of x lies in [0, pattern of L)) or within one box length
+// of it (one exact addition or subtraction); the FP64 division, costly on GB300, is left for the rest.
 __device__ __forceinline__ double wrap_box(double x, double L) {
-  double y = x - L * floor(x / L);
+  const long long xb = __double_as_longlong(x);
+  if (xb >= 0 && xb < __double_as_longlong(L)) return x;
+  double y;
+  if (x >= L && x < L + L)
+    y = x - L;
+  else if (x < 0.0 && x >= -L)
+    y = x + L;
+  else
+    y = x - L * floor(x / L);
   if (y >= L) y -= L;
   if (y < 0.0) y = 0.0;
   return y;
-}
-
-__device__ __forceinline__ int cell_coord(double x, double inv_edge, int nc) {
-  int c = (int)floor(x * inv_edge);
-  return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
 }
 
 // Exact cutoff decision in IEEE double with the same operation order as the

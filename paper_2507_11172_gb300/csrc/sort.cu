@@ -13,32 +13,46 @@ namespace r3b {
 __global__ void k_bin_count(const SysDev* __restrict__ sys, const PItem* __restrict__ items) {
   const PItem it = items[blockIdx.x];
   const SysDev& S = sys[it.sys];
-  if (sort_idle(S, it.mode)) return;
-  int p = it.begin + threadIdx.x;
-  if (p >= S.n) return;
-  double* X = S.X[it.buf];
+  if (sort_idle(S, it.mode)) return;  // block-uniform
+  const int p = it.begin + threadIdx.x;
   const int n = S.n;
-  int c[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    double x = wrap_box(X[a * n + p], S.L);
-    X[a * n + p] = x;
-    c[a] = cell_coord(x, S.inv_edge, S.nc);
-  }
-  int cell = (c[2] * S.nc + c[1]) * S.nc + c[0];
-  S.cell_tmp[p] = cell;
-  S.rank[p] = atomicAdd(&S.count[cell], 1);
-  if (S.skey) {  // position within the cell on an 8 x 8 x 8 grid, bits interleaved (Morton order)
-    unsigned key = 0u;
+  const bool valid = p < n;  // no early return: every lane takes part in the match below
+  int cell = -1;
+  unsigned key = 0u;
+  if (valid) {
+    double* X = S.X[it.buf];
+    const double inv8 = S.inv_edge * 8.0;  // exact scaling
+    const int nc = S.nc;
+    int c[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const double f = (X[a * n + p] - c[a] * S.edge) * S.inv_edge * 8.0;
-      const unsigned q = (unsigned)min(7, max(0, (int)f));
+      const double x = wrap_box(X[a * n + p], S.L);
+      X[a * n + p] = x;
+      // floor(8 x / edge) >= 0: its top bits are the cell coordinate floor(x / edge) (x * 8/edge is
+      // exactly 8 (x / edge) rounded), its low three bits the position on the cell's 8 x 8 x 8 grid
+      const int q8 = max(0, __double2int_rz(x * inv8));
+      int q = q8 & 7;
+      c[a] = q8 >> 3;
+      if (c[a] >= nc) {
+        c[a] = nc - 1;
+        q = 7;
+      }
 #pragma unroll
-      for (int bit = 0; bit < 3; ++bit) key |= ((q >> bit) & 1u) << (3 * bit + a);
+      for (int bit = 0; bit < 3; ++bit) key |= ((unsigned)(q >> bit) & 1u) << (3 * bit + a);  // Morton order
     }
-    S.skey[p] = (int)key;
+    cell = (c[2] * nc + c[1]) * nc + c[0];
+    S.cell_tmp[p] = cell;
+    if (S.skey) S.skey[p] = (int)key;
   }
+  // arrival rank within the cell: one atomic per group of lanes with the same cell (consecutive
+  // particles mostly share a cell); only a bijection onto 0 .. count - 1 matters
+  const unsigned peers = __match_any_sync(0xffffffffu, cell);
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(peers) - 1;
+  int base = 0;
+  if (valid && lane == leader) base = atomicAdd(&S.count[cell], __popc(peers));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (valid) S.rank[p] = base + __popc(peers & ((1u << lane) - 1u));
 }
 
 // Order within each cell: every particle's slot in its cell's segment is replaced by its rank by
