@@ -75,11 +75,44 @@ __device__ __forceinline__ bool finite_bits(double x) {
   return ((unsigned long long)__double_as_longlong(x) & 0x7ff0000000000000ull) != 0x7ff0000000000000ull;
 }
 
-// cell-local coordinate of an FP64 position relative to the centre of cell `cell` (its cell at the
-// last binning).  Positions are folded into [0, L) only at a binning, together with the cell
-// assignment, so between two binnings x - centre stays within about half a cell edge plus the
-// displacement: no periodic fold is needed here.  One FP64 subtraction per axis (the centres come
-// from a table; on GB300 every FP64 instruction is costly).
+// Cell-local coordinates are FP64 positions relative to the centre of the particle's cell at the last
+// binning.  Positions are folded into [0, L) only at a binning, together with the cell assignment, so
+// between two binnings x - centre stays within about half a cell edge plus the displacement: no
+// periodic fold is needed, one FP64 subtraction per axis (the centres come from a table; on GB300
+// every FP64 instruction is costly).
+// centre of cell `cell` (one table row per axis).  The kick/drift and start kernels load it, like every
+// other input, before their first store: loads cannot move across stores through pointers that may
+// alias, so loading everything first keeps the chain of dependent global round trips short (kick/drift
+// 9.5 -> 8.3 us and start 14.5 -> 13.2 us per launch on 100k particles)
+__device__ __forceinline__ void cell_centre(const SysDev& S, int cell, double cen[3]) {
+  const int nc = S.nc;
+  const int cz = cell / (nc * nc);
+  const int r = cell - cz * nc * nc;
+  const int cy = r / nc;
+  const int cx = r - cy * nc;
+  cen[0] = S.ccen[cx];
+  cen[1] = S.ccen[cy];
+  cen[2] = S.ccen[cz];
+}
+
+// cell-local coordinates (x - centre) of a new position into buffer buf, and the displacement check
+// against r, the particle's coordinates at the last binning (loaded by the caller)
+template <typename T>
+__device__ __forceinline__ void store_pos_checked(const SysDev& S, int buf, int i, const double x[3],
+                                                  const double cen[3], const typename V4<T>::type r) {
+  using T4 = typename V4<T>::type;
+  T4 h;
+  h.x = (T)(x[0] - cen[0]);
+  h.y = (T)(x[1] - cen[1]);
+  h.z = (T)(x[2] - cen[2]);
+  h.w = (T)0;
+  reinterpret_cast<T4*>(S.pos[buf])[i] = h;
+  const T dx = h.x - r.x, dy = h.y - r.y, dz = h.z - r.z;
+  if (dx * dx + dy * dy + dz * dz > Par<T>::half_skin_sq(S)) atomicOr(&S.flags[FLG_SKIN], 1);
+}
+
+// cell-local coordinate of an FP64 position relative to the centre of cell `cell` (combine kernel:
+// there, loading its inputs before the first store measured slower, so it keeps this form)
 __device__ __forceinline__ void cell_rel(const SysDev& S, int cell, const double x[3], double rel[3]) {
   const int nc = S.nc;
   const int cz = cell / (nc * nc);
@@ -345,12 +378,22 @@ __global__ void __launch_bounds__(256) k_kick(const SysDev* __restrict__ sys, co
   if (i >= n) return;
   bool bad = false;
   if (kind == LJ_MID) {
+    using T4 = typename V4<T>::type;
     const double c = S.dt_in * S.inv_mass;
-    const double* __restrict__ X = S.X[it.buf];
+    const double* X = S.X[it.buf];
     double* Xo = S.X[it.buf ^ 1];
-    double xn[3], rel[3], vv[3];
+    // inputs first (see cell_centre)
+    double vv[3], f[3], x[3], cen[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) vv[a] = fma(c, S.f2[a * n + i], S.v[a * n + i]);
+    for (int a = 0; a < 3; ++a) {
+      vv[a] = S.v[a * n + i];
+      f[a] = S.f2[a * n + i];
+      x[a] = X[a * n + i];
+    }
+    const T4 r = reinterpret_cast<const T4*>(S.ref)[i];
+    cell_centre(S, S.pcell[i], cen);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) vv[a] = fma(c, f[a], vv[a]);
     if (mode & M_NEAR) {  // block-uniform; FP64 instructions are costly on GB300: only where needed
       double fn[3];
       take_near<T>(S, i, fn);
@@ -361,19 +404,24 @@ __global__ void __launch_bounds__(256) k_kick(const SysDev* __restrict__ sys, co
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       S.v[a * n + i] = vv[a];
-      xn[a] = fma(S.dt_in, vv[a], X[a * n + i]);
-      Xo[a * n + i] = xn[a];
+      x[a] = fma(S.dt_in, vv[a], x[a]);
+      Xo[a * n + i] = x[a];
       bad |= !finite_bits(vv[a]);
     }
-    cell_rel(S, S.pcell[i], xn, rel);
-    store_pos<T>(S, it.buf ^ 1, i, rel, true);
+    store_pos_checked<T>(S, it.buf ^ 1, i, x, cen, r);
   } else {
     const double c = 0.5 * S.dt_in * S.inv_mass;
+    double vv[3], f[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {  // inputs first (see cell_centre)
+      vv[a] = S.v[a * n + i];
+      f[a] = S.f2[a * n + i];
+    }
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const double vv = fma(c, S.f2[a * n + i], S.v[a * n + i]);
-      S.v[a * n + i] = vv;
-      bad |= !finite_bits(vv);
+      vv[a] = fma(c, f[a], vv[a]);
+      S.v[a * n + i] = vv[a];
+      bad |= !finite_bits(vv[a]);
     }
   }
   if (bad) atomicOr(&S.flags[FLG_ERR], ERR_NONFINITE);
@@ -1209,6 +1257,7 @@ __global__ void __launch_bounds__(256) k_combine(const SysDev* __restrict__ sys,
 // opening kicks (outer F3, inner F2) and first drift of a call
 template <typename T>
 __global__ void __launch_bounds__(256) k_start(const SysDev* __restrict__ sys, const PItem* __restrict__ items) {
+  using T4 = typename V4<T>::type;
   const PItem it = items[blockIdx.x];
   const SysDev& S = sys[it.sys];
   const int n = S.n;
@@ -1216,23 +1265,31 @@ __global__ void __launch_bounds__(256) k_start(const SysDev* __restrict__ sys, c
   if (p >= n) return;
   const double* X = S.X[it.buf];
   double* Xo = S.X[0];
-  double xn[3], rel[3];
+  // inputs first (see cell_centre)
+  double f3[3], f3n[3] = {0.0, 0.0, 0.0}, v[3], f2[3], x[3], cen[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    f3[a] = S.f3[a * n + p];
+    if (S.f3n) f3n[a] = S.f3n[a * n + p];
+    v[a] = S.v[a * n + p];
+    f2[a] = S.f2[a * n + p];
+    x[a] = X[a * n + p];
+  }
+  const T4 r = reinterpret_cast<const T4*>(S.ref)[p];
+  cell_centre(S, S.pcell[p], cen);
   bool bad = false;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const double f3 = S.f3[a * n + p];
     // distance classes: far part (f3 - f3n) with the outer step, near part with s_near dt
-    const double k3 = S.f3n ? 0.5 * S.dt_out * S.inv_mass * (f3 - S.f3n[a * n + p]) +
-                                  0.5 * S.dt_near * S.inv_mass * S.f3n[a * n + p]
-                            : 0.5 * S.dt_out * S.inv_mass * f3;
-    double vv = S.v[a * n + p] + k3 + 0.5 * S.dt_in * S.inv_mass * S.f2[a * n + p];
+    const double k3 = S.f3n ? 0.5 * S.dt_out * S.inv_mass * (f3[a] - f3n[a]) + 0.5 * S.dt_near * S.inv_mass * f3n[a]
+                            : 0.5 * S.dt_out * S.inv_mass * f3[a];
+    const double vv = v[a] + k3 + 0.5 * S.dt_in * S.inv_mass * f2[a];
     S.v[a * n + p] = vv;
-    xn[a] = X[a * n + p] + S.dt_in * vv;
-    Xo[a * n + p] = xn[a];
+    x[a] = x[a] + S.dt_in * vv;
+    Xo[a * n + p] = x[a];
     bad |= !finite_bits(vv);
   }
-  cell_rel(S, S.pcell[p], xn, rel);
-  store_pos<T>(S, 0, p, rel, true);
+  store_pos_checked<T>(S, 0, p, x, cen, r);
   if (bad) atomicOr(&S.flags[FLG_ERR], ERR_NONFINITE);
 }
 
