@@ -80,7 +80,8 @@ __device__ __forceinline__ bool finite_bits(double x) {
 // between two binnings x - centre stays within about half a cell edge plus the displacement: no
 // periodic fold is needed, one FP64 subtraction per axis (the centres come from a table; on GB300
 // every FP64 instruction is costly).
-// centre of cell `cell` (one table row per axis).  The kick/drift and start kernels load it, like every
+//
+// Centre of cell `cell` (one table row per axis).  The kick/drift and start kernels load it, like every
 // other input, before their first store: loads cannot move across stores through pointers that may
 // alias, so loading everything first keeps the chain of dependent global round trips short (kick/drift
 // 9.5 -> 8.3 us and start 14.5 -> 13.2 us per launch on 100k particles)
@@ -124,6 +125,8 @@ __device__ __forceinline__ void cell_rel(const SysDev& S, int cell, const double
   rel[2] = x[2] - S.ccen[cz];
 }
 
+// cell-local coordinates rel into buffer buf, optionally with the displacement check (loads the
+// coordinates at the last binning itself, after the store)
 template <typename T>
 __device__ __forceinline__ void store_pos(const SysDev& S, int buf, int i, const double rel[3], bool check_skin) {
   using T4 = typename V4<T>::type;
