@@ -1092,7 +1092,8 @@ md_status md_create_system(md_system** out, int64_t n, double box_L, const doubl
     return MD_ERR_ARG;
   for (int64_t i = 0; i < 3 * n; ++i)
     if (!isfinite(pos[i]) || (vel && !isfinite(vel[i]))) return MD_ERR_NONFINITE;
-  std::unique_ptr<md_system> s(new md_system());
+  // every early return (a failed CUDA call included) releases what was made so far
+  std::unique_ptr<md_system, md_status (*)(md_system*)> s(new md_system(), md_destroy_system);
   s->n = n;
   s->L = box_L;
   s->mass = mass;
