@@ -32,16 +32,69 @@ sys.path.insert(0, ROOT)
 
 METRIC = "triplets/s and r-RESPA steps/s, FP32 vs FP64 plain; p50/p99 replica latency"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# FP32 ALU peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.070 GHz maximum SM clock
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# Nominal FP32 ALU peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.070 GHz maximum SM clock.  The
+# roofline divides by the FMA throughput measured in the same run (md_measure_fma_peak); this figure
+# is reported beside it.
+FP32_PEAK_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # Algorithmic FP32 flops of one interacting triplet in the ATM kernel's formula (FMA = 2 flops),
 # counted from atm_triplet: d_jk 3, c 5, ab/q 2, rsqrt 1 + Newton 4, w/t3/t5 3, s/A/B/C 8,
 # AB/AC/BC/P 4, Pa/Pb/Pc 9, G 3, ia/ib/ic 5, nu*t5 1, pa2/pb2/pc2 12, F_i 9, F_j 9, F_k 3,
 # accumulation of F_i (3) and scatter of F_j, F_k (6)
-# DRAM bytes (read + write) of one launch of the rotation kernel on the 100k workload, from an ncu
-# capture of the current kernel (dram__bytes_read.sum + dram__bytes_write.sum; cold caches)
-ATM_ROT_TRAFFIC_BYTES = 29.475840e6 + 0.0
+PROFILES = os.path.join(ROOT, "profiles")
+# source files whose content decides each kernel's code: a profile's DRAM traffic counts only while
+# their hash is the one recorded beside it
+KERNEL_SOURCES = {
+    "k_atm_rot<float>": ["paper_2507_11172_gb300/csrc/atm_rot.cu", "paper_2507_11172_gb300/csrc/md_internal.cuh"],
+    "k_lj<float, 1>": ["paper_2507_11172_gb300/csrc/forces.cu", "paper_2507_11172_gb300/csrc/md_internal.cuh"],
+}
 ATM_FLOPS_PER_TRIPLET = 3 + 5 + 2 + 5 + 3 + 8 + 4 + 9 + 3 + 5 + 1 + 12 + 9 + 9 + 3 + 3 + 6
+
+
+def source_hash(kernel):
+    import hashlib
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel):
+    """DRAM bytes (read + write) per launch of `kernel` on the 100k workload from the ncu summary in
+    profiles/ (a line `traffic: {json}` with the kernel, the bytes and the source hash at capture), or
+    (None, reason) when there is none or the kernel's source has changed since."""
+    import glob
+    for path in sorted(glob.glob(os.path.join(PROFILES, "*.md"))):
+        for line in open(path):
+            line = line.strip()
+            if not line.startswith("traffic: {"):
+                continue
+            rec = json.loads(line[len("traffic: "):])
+            if rec.get("kernel") != kernel:
+                continue
+            if rec.get("source_sha256") != source_hash(kernel):
+                return None, f"stale: {os.path.basename(path)} was captured from other source"
+            return float(rec["dram_bytes_per_launch"]), os.path.basename(path)
+    return None, "no capture in profiles/"
+
+
+def measure_peaks(r3):
+    """FP32 (plain and packed FMA) and FP64 FMA throughput of this GPU, with clock samples taken
+    during the measurement (md_measure_fma_peak; each kind >= 60 ms per launch)."""
+    stop, samples = threading.Event(), []
+    th = threading.Thread(target=sample_clocks, args=(stop, samples), daemon=True)
+    th.start()
+    try:
+        f32, _ = r3.md_measure_fma_peak(0, 60.0)
+        f32x2, _ = r3.md_measure_fma_peak(1, 60.0)
+        f64, _ = r3.md_measure_fma_peak(2, 60.0)
+    finally:
+        stop.set()
+        th.join()
+    return {"fp32_tflops": max(f32, f32x2) / 1e12, "fp32_ffma_tflops": f32 / 1e12, "fp32_ffma2_tflops": f32x2 / 1e12,
+            "fp64_tflops": f64 / 1e12, "clocks": clock_summary(samples),
+            "how": "md_measure_fma_peak: one full wave of resident CTAs, 8 independent FMA chains per thread, "
+                   "best of 3 launches >= 60 ms (CUDA events)"}
 
 
 def _nvml_sampler():
@@ -150,6 +203,8 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     r3.load()
+    peaks_run = measure_peaks(r3)
+    fp32_peak = peaks_run["fp32_tflops"]
     w = workload(rank)  # weak scaling: every rank advances its own independent replica
     K, W = args.steps, args.warmup
     stream = torch.cuda.Stream()
@@ -270,13 +325,16 @@ def run_ours(args):
             r3.md_destroy_system(h)
 
     classes_line = run_classes(r3, w, stream, flush, K) if rank == 0 else None
-    large_line = run_large(r3, stream, flush) if (rank == 0 and args.large) else None
-    direct_line = run_direct(r3, stream) if rank == 0 else None
+    large_line = run_large(r3, stream, flush) if (rank == 0 and not args.no_large) else None
+    direct_line = run_direct(r3, stream, fp32_peak) if rank == 0 else None
 
     peaks = {}
     if os.path.exists(PEAKS_FILE):
         peaks = json.load(open(PEAKS_FILE))
     achieved_tflops = trip_per_eval * ATM_FLOPS_PER_TRIPLET / (atm_ms / 1e3) / 1e12
+    kname = {0: "k_atm<float>", 1: "k_atm_pa<float>", 2: "k_atm_rot<float>"}.get(q32["kernel"])
+    traffic, traffic_src = profiled_traffic(kname) if kname in KERNEL_SOURCES else (None, "no capture")
+    fp64_tflops = trip64 / k64 * ATM_FLOPS_PER_TRIPLET / (atm64_ms / 1e3) / 1e12 if atm64_ms > 0 else None
     line = {
         "metric": METRIC,
         "value": value,
@@ -288,7 +346,8 @@ def run_ours(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32 forces (compensated), f64 integrator",
+        "dtype": "f32 forces (LJ sums compensated by TwoSum, ATM sums in exact 64-bit fixed point), "
+                 "f64 integrator and energies",
         "data": "synthetic",
         "config": {"workload": "fcc100k_rho0.8: N=100000 FCC+jitter 0.05, LJ rc 2.5, ATM nu 0.073 rc 2.5, "
                                "r-RESPA k=10 dt_outer=0.02, one step = one outer step",
@@ -297,16 +356,23 @@ def run_ours(args):
         "rrespa_steps_per_s": steps_per_s,
         "triplets_per_atm_eval": trip_per_eval,
         "fp64_plain": {"triplets_per_s": trip64 / (ms64 / 1e3), "rrespa_steps_per_s": k64 / (ms64 / 1e3),
-                       "atm_kernel_ms": atm64_ms},
+                       "atm_kernel_ms": atm64_ms, "atm_achieved_tflops": fp64_tflops,
+                       "atm_frac_of_measured_fp64_peak": (fp64_tflops / peaks_run["fp64_tflops"]
+                                                          if fp64_tflops and peaks_run["fp64_tflops"] > 0 else None)},
         "atm_kernel_ms": atm_ms,
         "profiled_pass_ms_per_step": q32["ms"] / K,
-        "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved_tflops / FP32_PEAK_TFLOPS,
-                     "traffic": ATM_ROT_TRAFFIC_BYTES if q32["kernel"] == 2 else None,
-                     "kernel": {0: "k_atm<float>", 1: "k_atm_pa<float>", 2: "k_atm_rot<float>"}.get(q32["kernel"]),
+        "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": achieved_tflops / fp32_peak,
+                     "traffic": traffic, "traffic_source": traffic_src,
+                     "kernel": kname,
                      "bases_per_warp": q32["per"] if q32["kernel"] == 2 else None,
-                     "note": f"{ATM_FLOPS_PER_TRIPLET} flop per interacting triplet; peak = 152 SM x 128 "
-                             "FP32 lanes x 2 x 2.07 GHz"},
+                     "peak_source": "measured in this run (md_measure_fma_peak, FP32 FMA)",
+                     "peak_nominal": FP32_PEAK_NOMINAL_TFLOPS,
+                     "frac_of_nominal": achieved_tflops / FP32_PEAK_NOMINAL_TFLOPS,
+                     "note": f"{ATM_FLOPS_PER_TRIPLET} flop per interacting triplet (FMA = 2) x interacting "
+                             "triplets per launch / CUDA-event launch time; nominal peak = 152 SM x 128 FP32 "
+                             "lanes x 2 x 2.07 GHz"},
+        "fma_peaks": peaks_run,
         "clocks": clk,
         # per outer step: 2 LJ-phase launches (forces, kick/drift) per inner step, the sort (bin, scan,
         # cell order (2), scatter, listbuild), the triplet kernel and the combine; plus the opening
@@ -331,14 +397,17 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
-def run_large(r3, stream, flush, steps=50):
+def run_large(r3, stream, flush, steps=20):
     """Large single system (2,000,000 particles, random-sequential-addition start at density 0.75,
     T* = 1.2, FP32 forces, k = 10, dt_outer = 0.02) with triplet cutoffs 2.0 and 2.5: whole outer steps
     through the graph-replayed path, CUDA events, L2 flushed before each step."""
     import torch
     import md_inputs
     out = {}
+    t0 = time.perf_counter()
     w = md_inputs.rsa_2m(2.5)
+    out["input_generation_s"] = time.perf_counter() - t0
+    out["timed_outer_steps"] = steps
     for rc3 in (2.0, 2.5):
         h = r3.md_create_system(w.x, w.L, w.v, 1.0, r3.MD_FP32, stream.cuda_stream)
         try:
@@ -367,7 +436,7 @@ def run_large(r3, stream, flush, steps=50):
     return out
 
 
-def run_direct(r3, stream, n=4995, calls=2):
+def run_direct(r3, stream, fp32_peak, n=4995, calls=2):
     """All-triplet ATM forces (DirectSum, open boundaries, no cutoff) on the aluminium scenario's
     shape (Table 1: 4995 particles at density 4995 / 20^3, nu = 0.3095), FP32, through the C ABI with
     host buffers (the call copies 120 KB each way and is synchronous).  Each unordered triplet counts
@@ -387,7 +456,7 @@ def run_direct(r3, stream, n=4995, calls=2):
     trip = n * (n - 1) * (n - 2) / 6
     tflops = trip * ATM_FLOPS_PER_TRIPLET / (ms / 1e3) / 1e12
     return {"n": n, "ms_per_call": ms, "triplets_per_s": trip / (ms / 1e3), "achieved_tflops": tflops,
-            "frac_fp32_peak": tflops / FP32_PEAK_TFLOPS,
+            "frac_fp32_peak": tflops / fp32_peak,
             "note": f"{ATM_FLOPS_PER_TRIPLET} flop per unordered triplet (each evaluated from its 3 members)"}
 
 
@@ -613,8 +682,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=100_000,
                     help="particles in the oracle's timed per-particle pass (100000 = one full evaluation)")
     ap.add_argument("--no-batch", action="store_true", help="skip the ensemble and serving runs")
-    ap.add_argument("--large", action="store_true",
-                    help="also time the 2,000,000-particle system (its input takes about a minute to generate)")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the 2,000,000-particle system (its input takes about half a minute to generate)")
     ap.add_argument("--serve-seconds", type=float, default=3.0, help="arrival window of the serving run")
     args = ap.parse_args()
     if args.warmup < 3:

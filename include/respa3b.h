@@ -49,10 +49,12 @@ typedef enum {
   MD_ERR_OOM = -2,            /* device memory (or the batch's memory budget) exhausted */
   MD_ERR_BOX_TOO_SMALL = -3,  /* L <= 3 * max(r_c2 + skin, r_c3): minimum image not unique */
   MD_ERR_NONFINITE = -4,      /* a position, velocity, force or energy became NaN/Inf */
-  MD_ERR_DEVICE_TIMEOUT = -5, /* a bounded device-side wait gave up */
+  MD_ERR_DEVICE_TIMEOUT = -5, /* reserved, never returned: no kernel of this library waits on another
+                                launch or on the host (each launch runs to completion on its own) */
   MD_ERR_CUDA = -6,           /* a CUDA runtime call failed (message via md_last_error) */
   MD_ERR_STATE = -7,          /* call not valid in this state (e.g. ticket unknown) */
-  MD_ERR_CAPACITY = -8        /* a cell, neighbour list or triplet list exceeded its capacity */
+  MD_ERR_CAPACITY = -8,       /* a cell, neighbour list or triplet list exceeded its capacity */
+  MD_ERR_CANCELLED = -9       /* batch request cancelled by md_batch_cancel */
 } md_status;
 
 enum { MD_FP32 = 0, MD_FP64 = 1 };
@@ -78,11 +80,13 @@ typedef struct {
   uint64_t near_triplets_last; /* distance classes: near-class triplets found by the last near evaluation */
 } md_stats;
 
-/* Create a system of n >= 3 particles in a periodic cube of side box_L.
- * pos: n x 3, caller order, any real values (folded into [0, L));
- * vel: n x 3 or NULL for zeros; mass > 0 (the paper's m, usually 1).
- * precision: MD_FP32 (FP32 forces with compensated per-particle accumulation,
- * FP64 positions, velocities and energies) or MD_FP64 (everything in FP64).
+/* Create a system of n >= 3 particles in a periodic cube of side box_L: the input x0, v0 of
+ * Algorithm 2 (Sec. 4.1) and the periodic cutoff setting of Sec. 4.2.
+ * pos: n x 3, caller order, any finite values (folded into [0, L));
+ * vel: n x 3 or NULL for zeros; mass > 0 and finite (the paper's m, usually 1); box_L > 0 and finite.
+ * precision: MD_FP32 (FP32 forces; LJ per-particle sums compensated (TwoSum), triplet forces summed
+ * per particle in 64-bit fixed point (exact, order-independent); FP64 positions, velocities, energies)
+ * or MD_FP64 (everything in FP64).  Non-finite pos / vel: MD_ERR_NONFINITE.
  * cuda_stream: a cudaStream_t to run on, or NULL for a library-owned stream.
  * Potentials default to eps = sigma = 1, r_c2 = 2.5, nu = 0, r_c3 = 2.5
  * until md_set_potentials.  On error *out is NULL. */
@@ -90,8 +94,10 @@ md_status md_create_system(md_system **out, int64_t n, double box_L, const doubl
                            double mass, int precision, void *cuda_stream);
 
 /* LJ 12-6 (eps, sigma, pair cutoff rc_pair) and ATM (nu, triplet cutoff
- * rc_triplet), Sec. 2.1.  nu = 0 disables the three-body force.  Invalidates
- * the cached forces (Algorithm 2 recomputes F2b(x0) and F3b(x0)). */
+ * rc_triplet), Sec. 2.1; the cutoff rules of the Fig. 2 caption and Sec. 4.2.2.
+ * All five finite; eps, sigma, the cutoffs > 0, nu >= 0 (else MD_ERR_ARG); nu = 0
+ * disables the three-body force.  Invalidates the cached forces (Algorithm 2
+ * recomputes F2b(x0) and F3b(x0)). */
 md_status md_set_potentials(md_system *s, double lj_eps, double lj_sigma, double rc_pair, double atm_nu,
                             double rc_triplet);
 
@@ -110,13 +116,15 @@ md_status md_set_skin(md_system *s, double skin);
  * velocities are updated in place; forces are cached between calls. */
 md_status md_respa_step(md_system *s, int n_outer, int k_inner, double dt_outer);
 
-/* Current forces (caller order, n x 3): f2 = LJ, f3 = ATM, either may be NULL.
- * Evaluates them first if they are not cached. */
+/* Current forces (caller order, n x 3), F = -grad Phi (Eq. 1-3): f2 = LJ, f3 = ATM (Sec. 2.1),
+ * the F2b and F3b of Algorithm 2 at the current positions; either may be NULL.
+ * Evaluates them first if they are not cached.  MD_ERR_STATE while the system is in a batch. */
 md_status md_get_forces(md_system *s, double *f2, double *f3);
 
-/* Energies at the current state (a full step): kinetic 0.5 m sum v^2, LJ
- * energy, ATM energy and the virial W = sum over interactions of
- * sum r_a . F_a (pressure P = (2 e_kin + W) / (3 L^3)).  Any pointer may be
+/* Energies at the current state (a full step of Algorithm 2; only full iterations are meaningful,
+ * Sec. 4.1): kinetic 0.5 m sum v^2, LJ energy, ATM energy (Eq. 2-3, Sec. 2.1; the total energy of the
+ * RVITE metric, Eq. 4) and the virial W = sum over interactions of sum r_a . F_a (pressure
+ * P = (2 e_kin + W) / (3 L^3), the pressure of Sec. 4.2.2).  Reduced in FP64.  Any pointer may be
  * NULL. */
 md_status md_get_energy(md_system *s, double *e_kin, double *u2, double *u3, double *virial);
 
@@ -132,7 +140,9 @@ md_status md_get_energy(md_system *s, double *e_kin, double *u2, double *u3, dou
 md_status md_get_rdf(md_system *s, int nbins, double r_max, uint64_t *counts);
 
 /* Copy positions (folded into [0, L)) and velocities out / in, caller order,
- * n x 3 each; either may be NULL.  md_set_state invalidates cached forces; it
+ * n x 3 each; either may be NULL: the input x0, v0 and output of Algorithm 2 ("positions and
+ * velocities updated in place", Sec. 4.1), also the checkpoint / resume pair.  md_set_state
+ * invalidates cached forces; it
  * returns MD_ERR_NONFINITE, with nothing changed, if an input value is NaN/Inf.
  * Both copy straight between the caller's buffers and the device (pinned caller
  * memory moves by DMA) and permute to and from the sorted layout on the device. */
@@ -158,13 +168,15 @@ md_status md_set_distance_classes(md_system *s, double r_a, int s_near);
  * f3 is the whole ATM force (near + far).  MD_ERR_STATE if the classes are off. */
 md_status md_get_near_forces(md_system *s, double *f3near);
 
-/* Counters (see md_stats).  profile = 1 launches a call's kernels one by one
+/* Counters (see md_stats; the triplet counts are those of the cutoff rule of the Fig. 2 caption, the
+ * step counts those of Algorithm 2).  profile = 1 launches a call's kernels one by one
  * (instead of replaying a captured CUDA graph) with CUDA events recorded on
  * the system's stream around every ATM launch (atm_ms_total / atm_timed). */
 md_status md_get_stats(md_system *s, md_stats *out);
 md_status md_set_profiling(md_system *s, int profile);
 
-/* Triplet-kernel choice (an autotuning knob; results agree within the FP tolerance):
+/* Triplet-kernel choice (an autotuning knob, like the paper's node-level autotuning in AutoPas,
+ * Sec. 4.1; results agree within the FP tolerance):
  *   0  one CTA per base cell, shared-memory staging, each triplet evaluated once with
  *      Newton-3 scatter of the three forces;
  *   1  one warp per particle, neighbours from the pair list, only the force on that
@@ -172,18 +184,23 @@ md_status md_set_profiling(md_system *s, int profile);
  *   2  one warp per particle and its half list (its neighbours within r_c3 above it in the
  *      order: cell layer along z, fixed-point z, sorted index), every neighbour pair visited
  *      once by a cyclic rotation across the lanes, each triplet evaluated once (Newton 3)
- *      with its forces kept as edge weights; per-neighbour sums added with vector atomics
- *      (summation order varies from run to run at the FP32 rounding level);
+ *      with its forces kept as edge weights; per-neighbour terms added to per-particle sums
+ *      in 64-bit fixed point (FP32 path: bitwise reproducible) or with FP64 atomics (FP64);
  *      1 and 2 need r_c3 <= r_c2 + skin, else 0 is used;
  *  -1  (default) time the allowed kernels (the rotation kernel with 4, 8 and 16 bases per warp in
  *      a work item) on the system's first evaluation and keep the fastest.  A batch uses its
  *      members' common choice, else 2 where allowed, else 0. */
 md_status md_set_atm_kernel(md_system *s, int variant);
 
-/* Number of particles, box side and precision of a handle. */
+/* Number of particles, box side and precision of a handle (the inputs of Algorithm 2). */
 md_status md_get_info(md_system *s, int64_t *n, double *box_L, int *precision);
 
-/* Release all device memory of the handle; NULL is accepted. */
+/* Device memory of a handle in bytes: what it holds, or for a deferred system (MD_DEFERRED) what it
+ * will hold once resident -- the figure md_batch_create's budget admission counts.  No counterpart in
+ * the paper (serving, the batched ensemble of this library). */
+md_status md_get_memory(md_system *s, size_t *device_bytes);
+
+/* Release all device memory of the handle (the end of the run of Algorithm 2); NULL is accepted. */
 md_status md_destroy_system(md_system *s);
 
 /* Static string for a status code; message of the last failing CUDA call of
@@ -192,6 +209,8 @@ const char *md_status_string(md_status st);
 const char *md_last_error(void);
 
 /* ---------------- batched ensemble / continuous serving ----------------
+ * No counterpart in the paper, which runs one system at a time: many independent replicas of
+ * Algorithm 2 (Sec. 4.1), each exactly as md_respa_step would advance it.
  * A batch advances many independent systems together: on every inner "tick"
  * one launch per kernel covers all resident systems (uneven sizes, different
  * k_inner), captured as a CUDA graph per batch composition.  Systems are
@@ -219,6 +238,12 @@ md_status md_batch_pending(md_batch *b, int *queued, int *resident);
 /* Cycles run so far and how many of them were replayed from their start (a member's particle left its
  * skin, or a capacity grew); either pointer may be NULL. */
 md_status md_batch_cycles(md_batch *b, uint64_t *cycles, uint64_t *replayed);
+/* Cancel a request (call between md_batch_run calls).  A queued request is dropped and its system is
+ * left as it was; a resident one finishes the outer step it is in (so its state is a full step of
+ * Algorithm 2; md_batch_latency counts the steps done) and leaves at the end of the next cycle.  The
+ * ticket then polls done with MD_ERR_CANCELLED.  MD_ERR_STATE for an unknown ticket or one that has
+ * already finished, failed or been cancelled. */
+md_status md_batch_cancel(md_batch *b, uint64_t ticket);
 md_status md_batch_destroy(md_batch *b);
 
 /* ---------------- all-triplet (DirectSum) ATM forces ----------------
@@ -234,22 +259,36 @@ md_status md_batch_destroy(md_batch *b);
 md_status md_atm_direct(const double *pos, int64_t n, double atm_nu, int precision, double *f3, double *u3,
                         void *cuda_stream);
 
+/* ---------------- arithmetic peaks of the device ----------------
+ * No counterpart in the paper: the FP32 and FP64 fused multiply-add throughput of the current device,
+ * the denominators of the triplet kernel's roofline fraction (its work is plain FP32 arithmetic, not a
+ * dense contraction).  kind: 0 FP32 FMA, 1 packed FP32x2 FMA (two per instruction), 2 FP64 FMA.  Every
+ * resident thread of one full wave runs 8 independent FMA chains; the trip count grows until one launch
+ * lasts at least min_ms (0 < min_ms <= 1e4), then the best of three timed launches (CUDA events) gives
+ * *flops_per_s (2 flop per FMA) and *ms_out (may be NULL).  Runs on its own stream; allocates 4 bytes;
+ * synchronous.  Reads no clock setting and changes none: the rate is the one at the clock of the moment. */
+md_status md_measure_fma_peak(int kind, double min_ms, double *flops_per_s, double *ms_out);
+
 /* ---------------- allocation-free ATM forces ----------------
- * No counterpart in the paper: an entry point for callers that cannot
+ * No counterpart in the paper (the forces are those of Sec. 2.1 with the cutoff of the Fig. 2
+ * caption): an entry point for callers that cannot
  * allocate device memory (code living inside another framework's memory
  * pool, a process whose device allocator is locked down, or a caller that
  * must not trigger the device-wide synchronisation of cudaMalloc/cudaFree).
  *
  * Computes the ATM forces F3 (and energy, triplet count) of one configuration
- * with the FP32 path (FP32 forces, compensated per-particle combination),
- * the same kernels as md_get_forces.  It allocates nothing: every
- * intermediate array lives in a file-scope __device__ array of about 10 MiB
- * that each GPU loading the library holds until the process exits.
+ * with FP32 triplet arithmetic: the binning sort and the cell triplet kernel
+ * (md_set_atm_kernel variant 0; md_get_forces defaults to the autotuned choice,
+ * usually the rotation kernel), whose per-stencil partial forces are combined
+ * per particle with TwoSum and added in FP64.  It allocates nothing: every
+ * intermediate array lives in a file-scope __device__ array of 8.8 MiB (at most
+ * 9 MiB) that each GPU loading the library holds until the process exits.
  *   d_pos: device, n x 3 doubles, caller order;  d_f3: device, n x 3 output;
+ *   box_L, atm_nu >= 0, rc_triplet > 0: finite (MD_ERR_ARG otherwise);
  *   u3, triplets: host outputs or NULL;  cuda_stream: cudaStream_t or NULL.
  * Limits: 3 <= n <= MD_NOALLOC_MAX_N, L > 3 r_c (MD_ERR_BOX_TOO_SMALL), at most
  * 32^3 cells (coarser cells beyond that).  n above the limit returns
- * MD_ERR_CAPACITY before any device work.
+ * MD_ERR_CAPACITY before any device work.  Messages of failing calls go to md_last_error.
  * The first call on a device looks up the arrays' device addresses and
  * uploads the pair table (a synchronous copy), so make that first call before
  * any stream capture.  All calls share the arrays: calls that overlap on the

@@ -22,7 +22,8 @@ MD_FP64 = 1
 MD_DEFERRED = 0x100
 
 STATUS = {0: "MD_OK", -1: "MD_ERR_ARG", -2: "MD_ERR_OOM", -3: "MD_ERR_BOX_TOO_SMALL", -4: "MD_ERR_NONFINITE",
-          -5: "MD_ERR_DEVICE_TIMEOUT", -6: "MD_ERR_CUDA", -7: "MD_ERR_STATE", -8: "MD_ERR_CAPACITY"}
+          -5: "MD_ERR_DEVICE_TIMEOUT", -6: "MD_ERR_CUDA", -7: "MD_ERR_STATE", -8: "MD_ERR_CAPACITY",
+          -9: "MD_ERR_CANCELLED"}
 
 
 class MDError(RuntimeError):
@@ -64,6 +65,7 @@ SIGNATURES = {
     "md_set_distance_classes": (_I, [_P, _D, _I]),
     "md_get_near_forces": (_I, [_P, _P]),
     "md_get_info": (_I, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_D), ctypes.POINTER(_I)]),
+    "md_get_memory": (_I, [_P, ctypes.POINTER(ctypes.c_size_t)]),
     "md_destroy_system": (_I, [_P]),
     "md_status_string": (ctypes.c_char_p, [_I]),
     "md_last_error": (ctypes.c_char_p, []),
@@ -74,8 +76,10 @@ SIGNATURES = {
     "md_batch_latency": (_I, [_P, ctypes.c_uint64, _P, ctypes.POINTER(_I)]),
     "md_batch_pending": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "md_batch_cycles": (_I, [_P, _U64P, _U64P]),
+    "md_batch_cancel": (_I, [_P, ctypes.c_uint64]),
     "md_batch_destroy": (_I, [_P]),
     "md_atm_direct": (_I, [_P, _I64, _D, _I, _P, _P, _P]),
+    "md_measure_fma_peak": (_I, [_I, _D, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "md_atm_forces_noalloc": (_I, [_P, _I64, _D, _D, _D, _P, ctypes.POINTER(_D), _U64P, _P]),
 }
 
@@ -155,6 +159,13 @@ def md_get_info(h):
     n, L, p = _I64(), _D(), _I()
     _check(load().md_get_info(h, ctypes.byref(n), ctypes.byref(L), ctypes.byref(p)), "md_get_info")
     return int(n.value), float(L.value), int(p.value)
+
+
+def md_get_memory(h) -> int:
+    """Device bytes the handle holds (deferred: will hold once resident)."""
+    b = ctypes.c_size_t()
+    _check(load().md_get_memory(h, ctypes.byref(b)), "md_get_memory")
+    return int(b.value)
 
 
 def md_get_forces(h, f2=True, f3=True):
@@ -271,6 +282,10 @@ def md_batch_cycles(b):
     return int(c.value), int(r.value)
 
 
+def md_batch_cancel(b, ticket: int):
+    _check(load().md_batch_cancel(b, ctypes.c_uint64(ticket)), "md_batch_cancel")
+
+
 def md_batch_destroy(b):
     if b:
         _check(load().md_batch_destroy(b), "md_batch_destroy")
@@ -285,6 +300,14 @@ def md_atm_direct(pos, nu: float, precision: int = MD_FP32, stream=None):
     _check(load().md_atm_direct(_ptr(x), n, float(nu), int(precision), _ptr(f), ctypes.byref(u),
                                 stream if stream else None), "md_atm_direct")
     return f, u.value
+
+
+def md_measure_fma_peak(kind: int, min_ms: float = 50.0):
+    """FMA throughput of the device: kind 0 FP32, 1 packed FP32x2, 2 FP64.  Returns (flop/s, ms)."""
+    f, ms = _D(), _D()
+    _check(load().md_measure_fma_peak(int(kind), float(min_ms), ctypes.byref(f), ctypes.byref(ms)),
+           "md_measure_fma_peak")
+    return f.value, ms.value
 
 
 def md_atm_forces_noalloc(d_pos_ptr: int, n: int, box_L: float, nu: float, rc_triplet: float, d_f3_ptr: int,

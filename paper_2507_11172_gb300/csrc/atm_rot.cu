@@ -24,8 +24,9 @@
 // Node v collects a scalar W_v (its i-edge weights) and a vector G_v (its j-k edge forces); then
 // F_v = G_v - W_v d_v and F_i = sum_v W_v d_v.  The lane of node j keeps j's share in registers; the
 // partner's share goes to the partner's shared-memory slot (the rotation makes those writes distinct).
-// Per-(base, node) totals are added to the node's force with one vector atomic; the combine kernel
-// reads and clears the sums.
+// Per-(base, node) totals are added to the node's force sum: FP32 path, in 64-bit fixed point
+// (fix_red3: exact, order-independent sums, bitwise reproducible); FP64 path, with FP64 atomics.
+// The combine kernel reads and clears the sums.
 //
 // Squared-distance algebra (law of cosines; w = 1/(abc), u = w^(1/2), A = a + b - c, B = a - b + c,
 // C = -a + b + c, P = ABC = 8 abc cos(g_i) cos(g_j) cos(g_k)):
@@ -103,7 +104,8 @@ struct ZrK {
   unsigned long long* ctr;
   int* flags;
   double L, rc3sq, nu, edge;
-  T rcsq, g, fs;         // r_c3^2, guard half-width, 3/4 nu in the kernel's precision
+  T rcsq, g, fs;         // r_c3^2, guard half-width, 3/4 nu in the kernel's precision (FP64 path; the
+                         // FP32 path's fixed-point sums take unscaled terms)
   float qscale;          // L / 2^32
   int n;
 };
@@ -494,33 +496,50 @@ __device__ __forceinline__ T zr_sum4(T a, T b, T c, T d, int lane) {
   return k;
 }
 
+// one (base, node) force term to the node's sum: FP32, unscaled into the fixed-point sums (the
+// combine kernel applies 3/4 nu); FP64, scaled by 3/4 nu with FP64 atomics
 template <typename T>
-__device__ __forceinline__ void zr_atomic_add(void* f3acc, int j, T fx, T fy, T fz) {
+__device__ __forceinline__ void zr_atomic_add(const ZrK<T>& K, int j, T fx, T fy, T fz) {
   if constexpr (sizeof(T) == 4) {
-    atomicAdd(reinterpret_cast<float4*>(f3acc) + j, make_float4(fx, fy, fz, 0.f));
+    if (!fix_red3(K.f3acc, j, fx, fy, fz)) atomicOr(K.flags + FLG_ERR, ERR_NONFINITE);
   } else {
-    double* q = reinterpret_cast<double*>(f3acc) + 4 * (size_t)j;
-    atomicAdd(q, fx);
-    atomicAdd(q + 1, fy);
-    atomicAdd(q + 2, fz);
+    double* q = reinterpret_cast<double*>(K.f3acc) + 4 * (size_t)j;
+    atomicAdd(q, K.fs * fx);
+    atomicAdd(q + 1, K.fs * fy);
+    atomicAdd(q + 2, K.fs * fz);
   }
 }
 
-// node force F_v = (G_v - W_v d_v) * fs to its accumulator; W_v d_v (unscaled) into F_i
+// node force F_v = G_v - W_v d_v (unscaled) to its sum; W_v d_v into F_i
 template <typename T>
 __device__ __forceinline__ void zr_emit(const ZrK<T>& K, const typename V4<T>::type d, int j, T W, T Gx, T Gy, T Gz,
                                         T& fix, T& fiy, T& fiz) {
   fix = fma(W, d.x, fix);
   fiy = fma(W, d.y, fiy);
   fiz = fma(W, d.z, fiz);
-  zr_atomic_add<T>(K.f3acc, j, K.fs * fma(-W, d.x, Gx), K.fs * fma(-W, d.y, Gy), K.fs * fma(-W, d.z, Gz));
+  zr_atomic_add<T>(K, j, fma(-W, d.x, Gx), fma(-W, d.y, Gy), fma(-W, d.z, Gz));
 }
+
+// Per-lane energy sum across a warp's bases: FP32 path, a compensated (hi, lo) pair (TwoSum; no FP64
+// instruction per base, FP64 being scarce on GB300), converted to FP64 for the warp and CTA sums; FP64
+// path, a plain double.
+template <typename T> struct ZrU;
+template <> struct ZrU<float> {
+  CompF c{0.f, 0.f};
+  __device__ __forceinline__ void add(float t) { c.add(t); }
+  __device__ __forceinline__ double value() const { return c.value(); }
+};
+template <> struct ZrU<double> {
+  double c = 0.0;
+  __device__ __forceinline__ void add(double t) { c += t; }
+  __device__ __forceinline__ double value() const { return c; }
+};
 
 // All triplets owned by base x, whose half list (length m) is in w.pn / w.nidx.  Adds the forces to
 // the accumulators and the count and energy (per lane) to cnt_sum, u_sum.
 template <typename T, bool kE>
 __device__ __forceinline__ void zr_eval(const ZrK<T>& K, ZrSmem<T>& w, const int x, const int m, const int lane,
-                                        T& cnt_sum, T& u_sum) {
+                                        T& cnt_sum, ZrU<T>& u_sum) {
   using T4 = typename V4<T>::type;
   if (m > kZrMax) {
     if (lane == 0) atomicOr(K.flags + FLG_ERR, ERR_HALF_CAP);
@@ -545,7 +564,7 @@ __device__ __forceinline__ void zr_eval(const ZrK<T>& K, ZrSmem<T>& w, const int
       if (zr_self_f2<kE>(K, w, J, m, lane, r)) {
         done = true;
         cnt_sum += r.cnt;
-        if (kE) u_sum += r.u;
+        if (kE) u_sum.add(r.u);
         if (lane < m) zr_emit<T>(K, J, jid, r.W, r.Gx, r.Gy, r.Gz, fix, fiy, fiz);
       }
     }
@@ -554,7 +573,7 @@ __device__ __forceinline__ void zr_eval(const ZrK<T>& K, ZrSmem<T>& w, const int
       __syncwarp();
       zr_phase<T, kE>(K, w, J, jid, ZrPart{0, m}, 1, (m - 1) >> 1, (m & 1) ? 0 : (m >> 1), lane, A);
       cnt_sum += A.cnt;
-      if (kE) u_sum += A.u;
+      if (kE) u_sum.add(A.u);
       if (lane < m) {
         const T4 s = zr_add4<T>(zr_add4<T>(w.slot[0][lane], w.slot[1][lane]),
                                 zr_add4<T>(w.slot[0][lane + m], w.slot[1][lane + m]));
@@ -585,7 +604,7 @@ __device__ __forceinline__ void zr_eval(const ZrK<T>& K, ZrSmem<T>& w, const int
       else
         zr_phase<T, kE>(K, w, J, jid, pp, 0, ma - 1, 0, lane, A);
       cnt_sum += A.cnt;
-      if (kE) u_sum += A.u;
+      if (kE) u_sum.add(A.u);
       if (lane < own_n) {
         T4 o;
         o.x = A.Gx;
@@ -614,12 +633,12 @@ __device__ __forceinline__ void zr_eval(const ZrK<T>& K, ZrSmem<T>& w, const int
   // F_i = sum_v W_v d_v (scaled): warp sum
   const T k = zr_sum4<T>(fix, fiy, fiz, (T)0, lane);
   const T Fx = k, Fy = __shfl_sync(0xffffffffu, k, 8), Fz = __shfl_sync(0xffffffffu, k, 16);
-  if (lane == 0) zr_atomic_add<T>(K.f3acc, x, K.fs * Fx, K.fs * Fy, K.fs * Fz);
+  if (lane == 0) zr_atomic_add<T>(K, x, Fx, Fy, Fz);
 }
 
 template <typename T>
 __device__ __forceinline__ void zr_eval_any(const ZrK<T>& K, ZrSmem<T>& w, int x, int m, int lane, bool energy, T& cnt,
-                                            T& u) {
+                                            ZrU<T>& u) {
   if (energy)
     zr_eval<T, true>(K, w, x, m, lane, cnt, u);
   else
@@ -630,8 +649,8 @@ __device__ __forceinline__ void zr_eval_any(const ZrK<T>& K, ZrSmem<T>& w, int x
 // Work item: 4 per consecutive bases, per of them for each warp (the autotuner picks per; 8 by
 // default, kZrPer).  FP32: a two-stage cp.async pipeline per warp
 // copies the half list of base k + 2 and the positions of base k + 1 into shared memory while base k
-// is evaluated.  Counts and energy are summed per CTA (the last warp to finish adds them to the
-// system's totals with one atomic each).
+// is evaluated.  Counts and energy (compensated per lane, FP64 across lanes) are summed per CTA (the
+// last warp to finish adds them to the system's totals with one atomic each).
 template <typename T>
 __global__ void __launch_bounds__(32 * kZrWarps, sizeof(T) == 4 ? R3B_ROT_MINB : 4)
     k_atm_rot(const SysDev* __restrict__ sys, const PItem* __restrict__ items, const int per) {
@@ -673,7 +692,8 @@ __global__ void __launch_bounds__(32 * kZrWarps, sizeof(T) == 4 ? R3B_ROT_MINB :
   const int n = K.n;
   const int x0 = it.begin + warp * per;
   const int nb = max(0, min(per, n - x0));  // bases of this warp
-  T cnt = (T)0, u = (T)0;
+  T cnt = (T)0;
+  ZrU<T> u;
   if constexpr (sizeof(T) == 4) {
     if (nb > 0) {
       zr_fetch_row(K, w, 0, x0, lane);
@@ -709,7 +729,7 @@ __global__ void __launch_bounds__(32 * kZrWarps, sizeof(T) == 4 ? R3B_ROT_MINB :
   }
   // per-lane counts are exact small integers in T (integer warp reduction: no FP64 instructions)
   const unsigned c = __reduce_add_sync(0xffffffffu, (unsigned)cnt);
-  const double uu = energy ? (double)warp_sum_t<T>(u) : 0.0;
+  const double uu = energy ? warp_sum(u.value()) : 0.0;
   if (lane == 0) {
     atomicAdd(&s_cnt, (unsigned long long)c);
     if (energy) atomicAdd(&s_u, uu);
@@ -727,16 +747,10 @@ __global__ void __launch_bounds__(32 * kZrWarps, sizeof(T) == 4 ? R3B_ROT_MINB :
   }
 }
 
-// dynamic shared memory above the 48 KB default: set once per process and kernel
+// dynamic shared memory above the 48 KB default (per device, see raise_smem_attr)
 template <typename T>
 static bool zr_configure() {
-  static int done = 0;
-  if (!done) {
-    done = cudaFuncSetAttribute(k_atm_rot<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)zr_smem_bytes<T>()) == cudaSuccess ? 1 : -1;
-    if (done < 0) cudaGetLastError();
-  }
-  return done > 0;
+  return raise_smem_attr((const void*)k_atm_rot<T>, (int)zr_smem_bytes<T>());
 }
 
 template <typename T>

@@ -61,6 +61,8 @@ struct Arena {
 
 }  // namespace
 
+void r3b::set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
+
 // ====================================================================== system
 struct md_system {
   // description
@@ -196,7 +198,7 @@ md_status alloc_device(md_system* s) {
   size_t o_nbr = a.reserve(4 * (size_t)s->maxnb * n), o_nbc = a.reserve(4 * n);
   size_t o_half = a.reserve(4 * (size_t)kHalfCap * n), o_hc = a.reserve(4 * n);
   size_t o_part = a.reserve(tsz * 27 * 3 * n);
-  size_t o_f3a = a.reserve(4 * tsz * n);
+  size_t o_f3a = a.reserve(32 * n);  // [n][4] fixed-point (FP32) or double (FP64) sums
   size_t o_ipos = a.reserve(16 * n);
   size_t o_ccen = a.reserve(8 * (size_t)s->nc);
   size_t o_acc = a.reserve(8 * ACC_N), o_ctr = a.reserve(8 * CTR_N), o_flg = a.reserve(4 * FLG_N);
@@ -208,7 +210,7 @@ md_status alloc_device(md_system* s) {
     o_halfa = a.reserve(4 * (size_t)kHalfCap * n);
     o_hca = a.reserve(4 * n);
     o_f3n = a.reserve(24 * n);
-    o_f3na = a.reserve(4 * tsz * n);
+    o_f3na = a.reserve(32 * n);
     o_sf3n = a.reserve(24 * n);
   }
   char* m = nullptr;
@@ -308,7 +310,7 @@ size_t arena_bytes(const md_system* s0) {
   a.reserve(4 * (size_t)kHalfCap * n);
   a.reserve(4 * n);
   a.reserve(tsz * 27 * 3 * n);
-  a.reserve(4 * tsz * n);
+  a.reserve(32 * n);
   a.reserve(16 * n);
   a.reserve(8 * (size_t)tmp.nc);
   a.reserve(8 * ACC_N);
@@ -321,7 +323,7 @@ size_t arena_bytes(const md_system* s0) {
     a.reserve(4 * (size_t)kHalfCap * n);
     a.reserve(4 * n);
     a.reserve(24 * n);
-    a.reserve(4 * tsz * n);
+    a.reserve(32 * n);
     a.reserve(24 * n);
   }
   // work-item arrays (about 30 particle-block variants and 4 cell variants)
@@ -360,6 +362,7 @@ md_status upload_desc(md_system* s, double dt_in, double dt_out) {
   h.rasq = s->r_a * s->r_a;
   h.guarda = gfac * std::max(1.0, h.rasq);
   h.dt_near = s->s_near * dt_in;
+  h.fix_unit = 0.75 * s->nu / 4294967296.0;  // unscaled FP32 triplet terms, 2^32 units each
   h.f_rasq = (float)h.rasq;
   h.f_guarda = (float)h.guarda;
   h.f_nearcand = (float)((s->r_a + s->skin) * (s->r_a + s->skin) * (1.0 + 1e-4));
@@ -791,7 +794,6 @@ md_status status_from_flags(md_system* s) {
     return MD_ERR_CAPACITY;
   }
   if (err & (ERR_CELL_CAP | ERR_NBR_CAP | ERR_HALF_CAP)) return MD_ERR_CAPACITY;
-  if (err & ERR_TIMEOUT) return MD_ERR_DEVICE_TIMEOUT;
   return MD_OK;
 }
 
@@ -879,7 +881,7 @@ md_status tune_atm(md_system* s) {
   if (st != MD_OK) return st;
   s->profile = prof;
   // the rotation kernel's trial launches left sums that no combine cleared
-  CK(cudaMemsetAsync(s->h.f3acc, 0, (size_t)(s->precision ? 32 : 16) * (size_t)s->n, s->stream));
+  CK(cudaMemsetAsync(s->h.f3acc, 0, 32 * (size_t)s->n, s->stream));
   clear_graphs(s);
   s->forces_valid = false;  // recompute with the chosen kernel
   s->energy_valid = false;
@@ -1071,10 +1073,11 @@ const char* md_status_string(md_status st) {
     case MD_ERR_OOM: return "out of device memory";
     case MD_ERR_BOX_TOO_SMALL: return "box too small: L must exceed 3 * max(r_c2 + skin, r_c3)";
     case MD_ERR_NONFINITE: return "non-finite value in the state";
-    case MD_ERR_DEVICE_TIMEOUT: return "device-side wait timed out";
+    case MD_ERR_DEVICE_TIMEOUT: return "device-side wait timed out (reserved: never returned)";
     case MD_ERR_CUDA: return "CUDA error";
     case MD_ERR_STATE: return "invalid state for this call";
     case MD_ERR_CAPACITY: return "capacity exceeded";
+    case MD_ERR_CANCELLED: return "request cancelled";
   }
   return "unknown status";
 }
@@ -1087,8 +1090,8 @@ md_status md_create_system(md_system** out, int64_t n, double box_L, const doubl
   *out = nullptr;
   const bool deferred = (precision & MD_DEFERRED) != 0;
   precision &= ~MD_DEFERRED;
-  if (n < 3 || n >= (int64_t)kNbrMask || !pos || !(box_L > 0) || !(mass > 0) ||
-      (precision != MD_FP32 && precision != MD_FP64))
+  if (n < 3 || n >= (int64_t)kNbrMask || !pos || !(box_L > 0) || !isfinite(box_L) || !(mass > 0) ||
+      !isfinite(mass) || (precision != MD_FP32 && precision != MD_FP64))
     return MD_ERR_ARG;
   for (int64_t i = 0; i < 3 * n; ++i)
     if (!isfinite(pos[i]) || (vel && !isfinite(vel[i]))) return MD_ERR_NONFINITE;
@@ -1143,7 +1146,7 @@ md_status md_set_potentials(md_system* s, double lj_eps, double lj_sigma, double
                             double rc_triplet) {
   if (!s) return MD_ERR_ARG;
   if (!(lj_eps > 0) || !(lj_sigma > 0) || !(rc_pair > 0) || !(rc_triplet > 0) || !(atm_nu >= 0) ||
-      !isfinite(atm_nu))
+      !isfinite(lj_eps) || !isfinite(lj_sigma) || !isfinite(rc_pair) || !isfinite(rc_triplet) || !isfinite(atm_nu))
     return MD_ERR_ARG;
   double e0 = s->eps, s0 = s->sigma, r20 = s->rc2, nu0 = s->nu, r30 = s->rc3;
   s->eps = lj_eps;
@@ -1315,6 +1318,12 @@ md_status md_set_atm_kernel(md_system* s, int variant) {
   return MD_OK;
 }
 
+md_status md_get_memory(md_system* s, size_t* device_bytes) {
+  if (!s || !device_bytes) return MD_ERR_ARG;
+  *device_bytes = s->deferred ? arena_bytes(s) : s->mem_bytes;  // the figure batch admission uses
+  return MD_OK;
+}
+
 md_status md_get_info(md_system* s, int64_t* n, double* box_L, int* precision) {
   if (!s) return MD_ERR_ARG;
   if (n) *n = s->n;
@@ -1349,7 +1358,7 @@ md_status md_destroy_system(md_system* s) {
 namespace {
 
 enum { KT_SORT = 0, KT_LJ = 1, KT_ATM = 2, KT_COMB = 3, KT_N = 4 };
-enum { RQ_QUEUED = 0, RQ_RESIDENT = 1, RQ_DONE = 2, RQ_FAILED = 3 };
+enum { RQ_QUEUED = 0, RQ_RESIDENT = 1, RQ_DONE = 2, RQ_FAILED = 3, RQ_CANCELLED = 4 };
 
 struct Request {
   md_system* s = nullptr;
@@ -1358,6 +1367,7 @@ struct Request {
   double dt_outer = 0;
   int outer_done = 0;
   int state = RQ_QUEUED;
+  bool cancel = false;  // resident request cancelled: it leaves at the end of its current outer step
   md_status status = MD_OK;
   std::vector<double> lat_ms;
   unsigned long long trip0 = 0;
@@ -1792,6 +1802,9 @@ md_status batch_cycle(md_batch* b) {
     bool skin = false, cap = false, half = false;
     for (int j = 0; j < ns; ++j) {
       const int* f = b->h_flags + j * FLG_N;
+      // a member that went non-finite fails alone after this cycle: its other flags (a skin violation or
+      // a cell overflow, the usual company of a state blowing up) ask for no replay and no growth
+      if (f[FLG_ERR] & ERR_NONFINITE) continue;
       if (f[FLG_SKIN] && !safe) skin = true;
       if (f[FLG_ERR] & (ERR_CELL_CAP | ERR_NBR_CAP)) cap = true;
       if ((f[FLG_ERR] & ERR_HALF_CAP) && b->variant != 0) half = true;
@@ -1813,24 +1826,20 @@ md_status batch_cycle(md_batch* b) {
       std::vector<uint64_t> grow;
       for (int j = 0; j < ns; ++j) {
         const int* f = b->h_flags + j * FLG_N;
-        if (f[FLG_ERR] & (ERR_CELL_CAP | ERR_NBR_CAP)) grow.push_back(b->resident[j]);
+        if ((f[FLG_ERR] & (ERR_CELL_CAP | ERR_NBR_CAP)) && !(f[FLG_ERR] & ERR_NONFINITE))
+          grow.push_back(b->resident[j]);
       }
       for (uint64_t tk : grow) {
         md_system* s = b->req[tk].s;
         const int* f = b->h_flags + (std::find(b->resident.begin(), b->resident.end(), tk) - b->resident.begin()) * FLG_N;
         if (f[FLG_ERR] & ERR_CELL_CAP) s->cap_cell = std::max(s->cap_cell + 8, f[FLG_MAXCELL] + 8);
         if (f[FLG_ERR] & ERR_NBR_CAP) s->maxnb = s->maxnb * 3 / 2 + 16;
-        // the snapshot restored positions in buffer 0 with the cycle-start order
+        // The snapshot restored the cycle-start state (buffer 0, cycle-start order): inside an outer step,
+        // its opening kicks and first drift already applied, and the cached forces are no longer needed
+        // (the cycle's ticks compute every force they use).  The new arena keeps positions, velocities
+        // and order; the replay below starts in safe mode, which bins before its first tick.
         s->cur = 0;
         md_status st = rebuild(s, true);
-        if (st == MD_OK) st = ensure_forces(s);
-        if (st == MD_OK) {
-          const Request& r = b->req[tk];
-          st = upload_desc(s, r.dt_outer / r.k, r.dt_outer);
-          Plan Pl{s, Launch{s->stream, s->d_sys}};
-          if (s->precision) Pl.start<double>(s->cur); else Pl.start<float>(s->cur);
-          cudaStreamSynchronize(s->stream);
-        }
         if (st != MD_OK) return st;
       }
       md_status st = batch_build(b);
@@ -1872,6 +1881,10 @@ md_status batch_cycle(md_batch* b) {
       continue;
     }
     if (r.outer_done >= r.n_outer) {
+      if (r.cancel) {
+        r.state = RQ_CANCELLED;
+        r.status = MD_ERR_CANCELLED;
+      }
       const double* a = b->h_acc + j * ACC_N;
       s->e_kin = a[ACC_EK];
       s->u2 = a[ACC_U2];
@@ -1881,7 +1894,7 @@ md_status batch_cycle(md_batch* b) {
       s->energy_valid = true;
       s->forces_valid = true;
       s->cur = (r.k - 1) & 1;
-      r.state = RQ_DONE;
+      if (!r.cancel) r.state = RQ_DONE;
       leaving.push_back(r.ticket);
     }
   }
@@ -1946,9 +1959,34 @@ md_status md_batch_poll(md_batch* b, uint64_t ticket, int* done) {
   if (!b || !done) return MD_ERR_ARG;
   auto it = b->req.find(ticket);
   if (it == b->req.end()) return MD_ERR_STATE;
-  *done = (it->second.state == RQ_DONE) ? 1 : 0;
-  if (it->second.state == RQ_FAILED) return it->second.status;
+  const int state = it->second.state;
+  *done = (state == RQ_DONE || state == RQ_CANCELLED || state == RQ_FAILED) ? 1 : 0;
+  if (state == RQ_FAILED || state == RQ_CANCELLED) return it->second.status;
   return MD_OK;
+}
+
+md_status md_batch_cancel(md_batch* b, uint64_t ticket) {
+  if (!b) return MD_ERR_ARG;
+  auto it = b->req.find(ticket);
+  if (it == b->req.end()) return MD_ERR_STATE;
+  Request& r = it->second;
+  if (r.state == RQ_QUEUED) {  // never admitted: the system is untouched
+    b->queue.erase(std::find(b->queue.begin(), b->queue.end(), ticket));
+    r.state = RQ_CANCELLED;
+    r.status = MD_ERR_CANCELLED;
+    return MD_OK;
+  }
+  if (r.state == RQ_RESIDENT) {
+    // between md_batch_run calls every member stands at a cycle boundary, inside an outer step (its
+    // opening kicks and first drift are done): it finishes that step with the closing kicks, so its
+    // state is a full step of Algorithm 2, then leaves
+    if (!r.cancel) {
+      r.cancel = true;
+      r.n_outer = std::min(r.n_outer, r.outer_done + 1);
+    }
+    return MD_OK;
+  }
+  return MD_ERR_STATE;  // already finished, failed or cancelled
 }
 
 md_status md_batch_latency(md_batch* b, uint64_t ticket, double* ms, int* count) {

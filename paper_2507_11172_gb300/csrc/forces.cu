@@ -143,16 +143,11 @@ __device__ __forceinline__ void store_pos(const SysDev& S, int buf, int i, const
   }
 }
 
-// near-class force of particle p from the rotation kernel's sums (read and cleared)
+// near-class force of particle p from the near-class kernel's sums (read and cleared)
 template <typename T>
 __device__ __forceinline__ void take_near(const SysDev& S, int p, double f[3]) {
   if (sizeof(T) == 4) {
-    float4* a4 = reinterpret_cast<float4*>(S.f3nacc) + p;
-    const float4 a = *a4;
-    f[0] = (double)a.x;
-    f[1] = (double)a.y;
-    f[2] = (double)a.z;
-    *a4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    fix_take3(S.f3nacc, p, S.fix_unit, f);
   } else {
     double* a = reinterpret_cast<double*>(S.f3nacc) + 4 * (size_t)p;
     f[0] = a[0];
@@ -197,7 +192,7 @@ template <typename T, bool kE>
 __global__ void __launch_bounds__(kLjPer, R3B_LJ_THREADS_PER_SM / kLjPer) k_lj(const SysDev* __restrict__ sys, const PItem* __restrict__ items) {
   using T4 = typename V4<T>::type;
   __shared__ T4 s_off[64];
-  __shared__ T red_u[kLjPer / 32], red_w[kLjPer / 32];
+  __shared__ double red_u[kLjPer / 32], red_w[kLjPer / 32];
   const PItem it = items[blockIdx.x];
   const SysDev& S = sys[it.sys];
   const int mode = item_mode(S, it.mode);
@@ -221,7 +216,8 @@ __global__ void __launch_bounds__(kLjPer, R3B_LJ_THREADS_PER_SM / kLjPer) k_lj(c
   const T4* __restrict__ P = reinterpret_cast<const T4*>(S.pos[it.buf]);
   const double* __restrict__ X = S.X[it.buf];
   Acc3<T> f;
-  T uu = 0, ww = 0;  // energy and virial partials (FP32 path: FP32 sums are ample for the totals' tolerance)
+  T uu = 0, ww = 0;  // energy and virial of the current eight pair terms
+  AccS<T> ud, wd;    // the thread's energy and virial sums (FP32: compensated; FP64 across threads)
   if (active) {
     const T4 pi = P[i];
     const T rcsq = Par<T>::rc2sq(S), g2 = Par<T>::guard2(S);
@@ -284,6 +280,11 @@ __global__ void __launch_bounds__(kLjPer, R3B_LJ_THREADS_PER_SM / kLjPer) k_lj(c
         f.add(sx + px, sy + py, sz + pz);
         px = py = pz = (T)0;
         odd = false;
+        if (energy) {
+          ud.add(uu);
+          wd.add(ww);
+          uu = ww = (T)0;
+        }
       } else {
         px = sx;
         py = sy;
@@ -316,8 +317,8 @@ __global__ void __launch_bounds__(kLjPer, R3B_LJ_THREADS_PER_SM / kLjPer) k_lj(c
         const T g = eps24 * (sr12 + sr12 - sr6) * ir2;
         f.add(-g * dx, -g * dy, -g * dz);
         if (energy) {
-          uu += eps4 * (sr12 - sr6);
-          ww = fma(g, r2, ww);
+          ud.add(eps4 * (sr12 - sr6));
+          wd.add(g * r2);
         }
       }
     }
@@ -343,7 +344,7 @@ __global__ void __launch_bounds__(kLjPer, R3B_LJ_THREADS_PER_SM / kLjPer) k_lj(c
   }
   if (energy) {  // every pair appears in both members' lists: halve
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const T us = warp_sum_t<T>(uu), ws = warp_sum_t<T>(ww);
+    const double us = warp_sum(ud.get()), ws = warp_sum(wd.get());
     if (lane == 0) {
       red_u[warp] = us;
       red_w[warp] = ws;
@@ -353,8 +354,8 @@ __global__ void __launch_bounds__(kLjPer, R3B_LJ_THREADS_PER_SM / kLjPer) k_lj(c
       double ut = 0.0, wt = 0.0;
 #pragma unroll
       for (int q = 0; q < kLjPer / 32; ++q) {
-        ut += (double)red_u[q];
-        wt += (double)red_w[q];
+        ut += red_u[q];
+        wt += red_w[q];
       }
       atomicAdd(&S.acc[ACC_U2], 0.5 * ut);
       atomicAdd(&S.acc[ACC_W2], 0.5 * wt);
@@ -1176,12 +1177,7 @@ __global__ void __launch_bounds__(256) k_combine(const SysDev* __restrict__ sys,
     double F[3] = {f.get(0), f.get(1), f.get(2)};
     if (summed) {
       if (sizeof(T) == 4) {
-        float4* a4 = reinterpret_cast<float4*>(S.f3acc) + p;
-        const float4 a = *a4;
-        F[0] = (double)a.x;
-        F[1] = (double)a.y;
-        F[2] = (double)a.z;
-        *a4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        fix_take3(S.f3acc, p, S.fix_unit, F);
       } else {
         double* a = reinterpret_cast<double*>(S.f3acc) + 4 * (size_t)p;
         F[0] = a[0];
@@ -1330,25 +1326,14 @@ void atm_prepare_table(cudaStream_t s) {
   cudaStreamSynchronize(s);
 }
 
-// The dynamic shared-memory limit is a property of the kernel for the whole process, shared
-// by every system: it is only ever raised, never lowered below what another system needs.
-static int g_atm_smem_attr[2] = {0, 0};
-
+// The dynamic shared-memory limit of a kernel is shared by every system on a device: it is only
+// ever raised, never lowered below what another system needs (raise_smem_attr).
 int atm_configure(int smax, int precision, int* smem_bytes) {
   int bytes = (int)(precision ? atm_layout<double>(smax).total : atm_layout<float>(smax).total);
   *smem_bytes = bytes;
   int nb = 0;
-  const int p = precision ? 1 : 0;
-  if (bytes > g_atm_smem_attr[p]) {
-    cudaError_t e = precision
-                        ? cudaFuncSetAttribute(k_atm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
-                        : cudaFuncSetAttribute(k_atm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      return 0;
-    }
-    g_atm_smem_attr[p] = bytes;
-  }
+  const void* kern = precision ? (const void*)k_atm<double> : (const void*)k_atm<float>;
+  if (!raise_smem_attr(kern, bytes)) return 0;
   if (precision)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_atm<double>, kAtmThreads, bytes);
   else

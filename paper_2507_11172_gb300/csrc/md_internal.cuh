@@ -21,13 +21,23 @@ constexpr int kListWarps = R3B_LIST_WARPS;  // warps per CTA of the pair-list bu
 constexpr int kNearThreads = 128;   // owners (one thread each) per CTA of the near-class triplet kernel
 constexpr int kHalfCap = 64;        // triplet half list per particle (neighbours above it within r_c3)
 
+// Pair-list layout: blocks of 32 consecutive sorted particles; within a block, entry t of particle i
+// sits at int index ((i / 32) * (maxnb / 4) + t / 4) * 128 + (i % 32) * 4 + t % 4, so a warp reading
+// entries 4g .. 4g + 3 of its 32 particles reads one contiguous 512-byte group (maxnb is a multiple
+// of 4; the array holds ceil(n / 32) * 32 rows).
+__host__ __device__ __forceinline__ size_t nbr_slot(int maxnb, int i, int t) {
+  return ((size_t)(i >> 5) * (size_t)(maxnb >> 2) + (size_t)(t >> 2)) * 128u + (size_t)((i & 31) << 2) +
+         (size_t)(t & 3);
+}
+__host__ __device__ __forceinline__ size_t nbr_rows(size_t n) { return (n + 31) & ~size_t(31); }
+
 // error bits in SysDev::flags[0]
 enum : int {
   ERR_CELL_CAP = 1,   // a cell holds more particles than cap_cell
   ERR_NBR_CAP = 2,    // an LJ neighbour list overflowed
   ERR_HALF_CAP = 4,   // an ATM half list overflowed kMaxHalf
   ERR_NONFINITE = 8,  // NaN / Inf in positions, velocities or forces
-  ERR_TIMEOUT = 16,   // a bounded wait gave up
+  // 16: unused (no kernel of this library waits on another launch or on the host)
   ERR_NEAR_CAP = 32,  // distance classes: a near-class candidate list overflowed kHalfCap
 };
 
@@ -63,13 +73,14 @@ struct SysDev {
   // pair distances are <= r_a, integrated every s_near inner steps; far = the rest within r_c3
   double rasq, guarda;        // r_a^2 and the half-width of its FP64 re-decision band
   double dt_near;             // s_near * dt_in
+  double fix_unit;            // FP32 path: force per unit of the fixed-point sums f3acc / f3nacc (3/4 nu 2^-32)
   float f_rasq, f_guarda;
   float f_nearcand;           // (r_a + skin)^2 widened by 1e-4: near-class candidate test
   int pad2_;
   int *half_a, *half_a_cnt;   // [n][kHalfCap], [n]: near-class candidates of each particle (neighbours
                               // above it within r_a + skin at the last binning), from k_listbuild
   double *f3n;                // [3][n] cached near-class force (f3 holds near + far)
-  void *f3nacc;               // like f3acc, for the near-class evaluation
+  void *f3nacc;               // [n][4] like f3acc, for the near-class evaluation
   // state in cell-sorted order, double SoA [3][n] (x block, y block, z block)
   double *X[2];       // positions, ping-pong by inner-step parity
   double *v, *f2, *f3;
@@ -82,14 +93,15 @@ struct SysDev {
   int *cell_tmp, *rank;       // [n] binning scratch
   int *skey, *members;        // [n] binning scratch for the order within a cell (NULL: arrival order)
   int *count, *cell_start;    // [ncell], [ncell + 1]
-  int *nbr, *nbr_cnt;         // [n][maxnb] row-major, [n]
+  int *nbr, *nbr_cnt;         // pair list (layout: nbr_slot, ceil(n / 32) * 32 rows of maxnb), [n]
   int *half, *half_cnt;       // [n][kHalfCap] triplet half list of each particle (pair-list entries), [n]
   void *partial;              // T [27][3][n] per-stencil-slot ATM partial forces
   int4 *ipos;                 // [n] positions of the last binning in fixed point (box = 2^32 units;
                               // x, y, z as wrapping 32-bit integers), NULL where unused
   const double *ccen;         // [nc] cell centres along one axis: (c + 0.5) * edge
-  void *f3acc;                // [n] float4 (FP32) or double [n][4]: rotation-kernel ATM force sums,
-                              // zero between evaluations (the combine kernel clears what it reads)
+  void *f3acc;                // [n][4] rotation-kernel ATM force sums: 64-bit fixed point (FP32 path,
+                              // fix_red3) or double (FP64 path); zero between evaluations (the combine
+                              // kernel clears what it reads)
   double *acc;                // [ACC_N]
   unsigned long long *ctr;    // [CTR_N]
   int *flags;                 // [FLG_N]
@@ -243,6 +255,35 @@ __device__ __forceinline__ bool exact_within(const double* __restrict__ X, int n
   return r2 <= rcsq;
 }
 
+// ---------------------------------------------------------------- fixed-point force sums
+// The FP32 triplet kernels scatter one force term per (owner, member) to the member's sum.  Those
+// sums are kept in 64-bit fixed point (2^32 units per unit of the kernels' unscaled terms, which
+// carry no factor nu; after Le Grand, Goetz and Walker, "SPFP: Speed without compromise", Comput.
+// Phys. Commun. 184 (2013) 374): every FP32 term is rounded once to a multiple of 2^-32 and then
+// added exactly, so the sum of a particle's terms is the same integer in any order (bitwise
+// reproducible from run to run and whatever else shares the launch) and carries no accumulation
+// error.  A term of magnitude 2^22 or more (or NaN) is not added and raises ERR_NONFINITE: it would
+// take distances of about 0.2 sigma, and 2^9 such terms could overflow the sum.
+constexpr float kFixOne = 4294967296.0f;  // 2^32 fixed-point units per unit of a term
+constexpr float kFixLimit = 4194304.0f;   // 2^22: largest accepted term magnitude
+__device__ __forceinline__ bool fix_red3(void* acc, int j, float fx, float fy, float fz) {
+  if (!(fabsf(fx) < kFixLimit && fabsf(fy) < kFixLimit && fabsf(fz) < kFixLimit)) return false;
+  unsigned long long* q = reinterpret_cast<unsigned long long*>(acc) + 4 * (size_t)j;
+  atomicAdd(q, (unsigned long long)__float2ll_rn(fx * kFixOne));
+  atomicAdd(q + 1, (unsigned long long)__float2ll_rn(fy * kFixOne));
+  atomicAdd(q + 2, (unsigned long long)__float2ll_rn(fz * kFixOne));
+  return true;
+}
+// a particle's fixed-point sum as a force (times unit), then cleared for the next evaluation
+__device__ __forceinline__ void fix_take3(void* acc, int p, double unit, double f[3]) {
+  long long* q = reinterpret_cast<long long*>(acc) + 4 * (size_t)p;
+  const long long a = q[0], b = q[1], c = q[2];
+  q[0] = q[1] = q[2] = 0;
+  f[0] = (double)a * unit;
+  f[1] = (double)b * unit;
+  f[2] = (double)c * unit;
+}
+
 // error-free transformation s + e = a + b (Knuth TwoSum)
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = __fadd_rn(a, b);
@@ -367,6 +408,15 @@ __device__ __forceinline__ void stage_cells(const SysDev& S, int buf, const int*
     }
   }
 }
+
+// Raise a kernel's dynamic shared-memory limit to at least `bytes` on the current device.  The
+// attribute belongs to the device's context, so the largest value set so far is cached per (device,
+// kernel), behind a mutex (first calls may come from several threads); never lowered.  False if the
+// device refuses the size.
+bool raise_smem_attr(const void* kernel, int bytes);
+
+// message that md_last_error returns on this thread (engine.cu)
+void set_last_error(const char* msg);
 
 // ---------------------------------------------------------------- launchers
 struct Launch {

@@ -17,8 +17,8 @@
 //   w = 1/(abc), u = w^(1/2), A = a + b - c, B = a - b + c, C = -a + b + c, P = ABC,
 //   2 dphi/da = 3/4 nu u^5 (dP/da - bc (4 + 5/2 P w)),  dP/da = 2aC - AB (b, c alike),
 //   F_i = pa2 d_a + pb2 d_b,  F_a = -pa2 d_a + pc2 e,  F_b = -pb2 d_b - pc2 e,  e = d_b - d_a.
-// F_i and F_a stay in registers (one atomic each per owner / node), F_b goes out with one vector
-// atomic per triplet.  Cutoff decisions within the guard band around r_a^2 are re-decided in FP64
+// F_i and F_a stay in registers (one sum update each per owner / node), F_b goes out with one sum
+// update per triplet (FP32 path: 64-bit fixed-point sums, exact and order-independent).  Cutoff decisions within the guard band around r_a^2 are re-decided in FP64
 // from the FP64 positions with the CPU definition's operation order (exact_within).
 #include "md_internal.cuh"
 
@@ -32,10 +32,12 @@ __device__ __forceinline__ float nr_rsqrt(float q) {
 }
 __device__ __forceinline__ double nr_rsqrt(double q) { return 1.0 / sqrt(q); }
 
+// one force term to particle j's near-class sum: FP32, unscaled terms into the 64-bit fixed-point sums
+// (exact, order-independent; the reader applies 3/4 nu); FP64, terms scaled by 3/4 nu, FP64 atomics
 template <typename T>
-__device__ __forceinline__ void near_red(void* acc, int j, T fx, T fy, T fz) {
+__device__ __forceinline__ void near_red(const SysDev& S, void* acc, int j, T fx, T fy, T fz) {
   if constexpr (sizeof(T) == 4) {
-    atomicAdd(reinterpret_cast<float4*>(acc) + j, make_float4(fx, fy, fz, 0.f));
+    if (!fix_red3(acc, j, fx, fy, fz)) atomicOr(&S.flags[FLG_ERR], ERR_NONFINITE);
   } else {
     double* q = reinterpret_cast<double*>(acc) + 4 * (size_t)j;
     atomicAdd(q, fx);
@@ -114,7 +116,7 @@ __global__ void __launch_bounds__(kNearThreads) k_atm_near(const SysDev* __restr
     const T4 pi = P[i];
     const T edge = Par<T>::edge(S);
     const T ra = Par<T>::rasq(S), ga = Par<T>::guarda(S);
-    const T fs = (T)0.75 * Par<T>::nu(S);
+    const T fs = sizeof(T) == 4 ? (T)1 : (T)0.75 * Par<T>::nu(S);  // FP32: unscaled (fixed-point sums)
     // displacement of candidate entry e from i at the current positions
     auto node = [&](unsigned e, T& dx, T& dy, T& dz) {
       const T4 pj = P[e & kNbrMask];
@@ -163,10 +165,10 @@ __global__ void __launch_bounds__(kNearThreads) k_atm_near(const SysDev* __restr
           T fbx, fby, fbz;
           near_triplet<T>(fs, na.w, nb.w, cc, na.x, na.y, na.z, nb.x, nb.y, nb.z, ex, ey, ez, fix, fiy, fiz, fax,
                           fay, faz, fbx, fby, fbz);
-          near_red<T>(S.f3nacc, jb, fbx, fby, fbz);
+          near_red<T>(S, S.f3nacc, jb, fbx, fby, fbz);
           ++cnt;
         }
-        if (fax != (T)0 || fay != (T)0 || faz != (T)0) near_red<T>(S.f3nacc, ja, fax, fay, faz);
+        if (fax != (T)0 || fay != (T)0 || faz != (T)0) near_red<T>(S, S.f3nacc, ja, fax, fay, faz);
       }
     } else {
       // more near nodes than shared slots: every pair of candidates from global memory
@@ -193,13 +195,13 @@ __global__ void __launch_bounds__(kNearThreads) k_atm_near(const SysDev* __restr
           T fbx, fby, fbz;
           near_triplet<T>(fs, aa, bb, cc, ax, ay, az, bx, by, bz, ex, ey, ez, fix, fiy, fiz, fax, fay, faz, fbx,
                           fby, fbz);
-          near_red<T>(S.f3nacc, jb, fbx, fby, fbz);
+          near_red<T>(S, S.f3nacc, jb, fbx, fby, fbz);
           ++cnt;
         }
-        if (fax != (T)0 || fay != (T)0 || faz != (T)0) near_red<T>(S.f3nacc, ja, fax, fay, faz);
+        if (fax != (T)0 || fay != (T)0 || faz != (T)0) near_red<T>(S, S.f3nacc, ja, fax, fay, faz);
       }
     }
-    if (fix != (T)0 || fiy != (T)0 || fiz != (T)0) near_red<T>(S.f3nacc, i, fix, fiy, fiz);
+    if (fix != (T)0 || fiy != (T)0 || fiz != (T)0) near_red<T>(S, S.f3nacc, i, fix, fiy, fiz);
   }
   const unsigned c = __reduce_add_sync(0xffffffffu, cnt);
   if ((threadIdx.x & 31) == 0 && c) atomicAdd(&s_cnt, c);

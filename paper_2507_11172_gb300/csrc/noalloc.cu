@@ -58,7 +58,7 @@ constexpr size_t kOffPItems = up256(kOffNbrCnt + 4ull * kMaxN);
 constexpr size_t kOffCItems = up256(kOffPItems + sizeof(PItem) * ((kMaxN + 255) / 256));
 constexpr size_t kOffSItem = up256(kOffCItems + sizeof(CItem) * kMaxCells);
 constexpr size_t kScratchBytes = up256(kOffSItem + sizeof(SItem));
-static_assert(kScratchBytes <= (size_t)12 << 20, "the scratch array must stay modest (<= 12 MiB)");
+static_assert(kScratchBytes <= (size_t)9 << 20, "the scratch array must stay modest (at most 9 MiB; 8.8 MiB as laid out)");
 static_assert(kMaxItems > 0, "");
 
 }  // namespace
@@ -100,10 +100,11 @@ struct DeviceSetup {
 };
 std::mutex g_setup_mutex;
 DeviceSetup g_setup[64];
-thread_local std::string g_noalloc_error;
+// messages go to the string md_last_error returns
+void set_error(const std::string& msg) { set_last_error(msg.c_str()); }
 
 md_status fail(cudaError_t e, const char* what) {
-  g_noalloc_error = std::string(what) + ": " + cudaGetErrorString(e);
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
   return MD_ERR_CUDA;
 }
 
@@ -139,10 +140,11 @@ md_status setup_device(int dev, cudaStream_t stream, DeviceSetup** out) {
 extern "C" md_status md_atm_forces_noalloc(const double* d_pos, int64_t n, double box_L, double atm_nu,
                                            double rc_triplet, double* d_f3, double* u3, uint64_t* triplets,
                                            void* cuda_stream) {
-  if (!d_pos || !d_f3 || n < 3 || !(box_L > 0) || !(rc_triplet > 0) || !(atm_nu >= 0) || !isfinite(atm_nu))
+  if (!d_pos || !d_f3 || n < 3 || !(box_L > 0) || !isfinite(box_L) || !(rc_triplet > 0) || !isfinite(rc_triplet) ||
+      !(atm_nu >= 0) || !isfinite(atm_nu))
     return MD_ERR_ARG;
   if (n > kMaxN) {
-    g_noalloc_error = "md_atm_forces_noalloc: n exceeds MD_NOALLOC_MAX_N";
+    set_error("md_atm_forces_noalloc: n exceeds MD_NOALLOC_MAX_N");
     return MD_ERR_CAPACITY;
   }
   if (!(box_L > 3.0 * rc_triplet)) return MD_ERR_BOX_TOO_SMALL;
@@ -176,7 +178,7 @@ extern "C" md_status md_atm_forces_noalloc(const double* d_pos, int64_t n, doubl
     int smem = 0;
     const int per_sm = atm_configure(atm_stage_capacity(cap), MD_FP32, &smem);
     if (per_sm <= 0) {
-      g_noalloc_error = "md_atm_forces_noalloc: a cell holds more particles than shared memory can stage";
+      set_error("md_atm_forces_noalloc: a cell holds more particles than shared memory can stage");
       return MD_ERR_CAPACITY;
     }
     int sms = 0;
@@ -275,7 +277,7 @@ extern "C" md_status md_atm_forces_noalloc(const double* d_pos, int64_t n, doubl
       continue;
     }
     if (flags[FLG_ERR] & ERR_HALF_CAP) {
-      g_noalloc_error = "md_atm_forces_noalloc: a particle has more than 128 larger-index neighbours";
+      set_error("md_atm_forces_noalloc: a particle has more than 128 larger-index neighbours");
       return MD_ERR_CAPACITY;
     }
     if (flags[FLG_ERR] & ERR_NONFINITE) return MD_ERR_NONFINITE;
@@ -283,6 +285,6 @@ extern "C" md_status md_atm_forces_noalloc(const double* d_pos, int64_t n, doubl
     if (triplets) *triplets = ctr[CTR_TRIPLETS];
     return MD_OK;
   }
-  g_noalloc_error = "md_atm_forces_noalloc: cell capacity retries exhausted";
+  set_error("md_atm_forces_noalloc: cell capacity retries exhausted");
   return MD_ERR_CAPACITY;
 }

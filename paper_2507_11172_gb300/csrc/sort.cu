@@ -277,7 +277,6 @@ __global__ void __launch_bounds__(32 * kListWarps)
     const int i = i0 + ib;
     const T4 pi = sp[islot];
     int cnt = 0;
-    int* row = S.nbr + (size_t)i * S.maxnb;
     // pass 1: every staged particle within the list radius
     for (int t0 = 0; t0 < nstaged; t0 += 32) {
       const int t = t0 + lane;
@@ -289,7 +288,7 @@ __global__ void __launch_bounds__(32 * kListWarps)
       }
       const unsigned bal = __ballot_sync(0xffffffffu, ok);
       const int pos = cnt + __popc(bal & lt);
-      if (ok && pos < S.maxnb) row[pos] = sj[t];
+      if (ok && pos < S.maxnb) S.nbr[nbr_slot(S.maxnb, i, pos)] = sj[t];
       cnt += __popc(bal);
     }
     if (lane == 0) {
@@ -307,7 +306,7 @@ __global__ void __launch_bounds__(32 * kListWarps)
       bool half = false, band = false, cand = false;
       unsigned e = 0u;
       if (t < cnt) {
-        e = (unsigned)row[t];
+        e = (unsigned)S.nbr[nbr_slot(S.maxnb, i, t)];
         const unsigned code = e >> kNbrShift;
         const int l = (int)(code & 3u) + 3 * (int)((code >> 2) & 3u) + 9 * (int)(code >> 4);
         const int slot = (int)(e & kNbrMask) + st_delta[l];
@@ -446,22 +445,11 @@ void launch_listbuild(const Launch& L, const CItem* items, int nitems, int smax)
   const int bytes = (int)(smax * (sizeof(typename V4<T>::type) + 2 * sizeof(int)));
   k_listbuild<T><<<nitems, 32 * kListWarps, bytes, L.stream>>>(L.sys, items, smax);
 }
-// the kernel's dynamic shared-memory limit is process-wide: only ever raised
-static int g_list_smem_attr[2] = {0, 0};
-
+// the kernel's dynamic shared-memory limit is shared by every system on a device: only ever raised
 int listbuild_configure(int smax, int precision) {
   const int bytes = (int)(smax * ((precision ? sizeof(double4_32a) : sizeof(float4)) + 2 * sizeof(int)));
-  const int p = precision ? 1 : 0;
-  if (bytes <= g_list_smem_attr[p]) return bytes;
-  cudaError_t e = precision
-                      ? cudaFuncSetAttribute(k_listbuild<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
-                      : cudaFuncSetAttribute(k_listbuild<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return -1;
-  }
-  g_list_smem_attr[p] = bytes;
-  return bytes;
+  const void* kern = precision ? (const void*)k_listbuild<double> : (const void*)k_listbuild<float>;
+  return raise_smem_attr(kern, bytes) ? bytes : -1;
 }
 template void launch_scatter<float>(const Launch&, const PItem*, int, int);
 template void launch_scatter<double>(const Launch&, const PItem*, int, int);

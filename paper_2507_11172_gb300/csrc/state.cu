@@ -1,9 +1,32 @@
 // State transfer between the caller's order (n x 3 AoS, as the C ABI takes and returns it) and the
 // library's cell-sorted SoA layout, on the device: the host only copies the caller's buffers in and
 // out (directly, so pinned caller memory moves by DMA without staging).
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "md_internal.cuh"
 
 namespace r3b {
+
+bool raise_smem_attr(const void* kernel, int bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, int> raised;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  int& cur = raised[std::make_pair(dev, kernel)];
+  if (bytes <= cur) return true;
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  cur = bytes;
+  return true;
+}
 
 // position folded into [0, L), with the host definition's operation order (no contraction)
 __device__ __forceinline__ double fold_box(double x, double L) {

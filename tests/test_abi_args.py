@@ -46,6 +46,7 @@ def test_null_system_handle_is_rejected_everywhere(lib):
         "md_set_profiling": lambda: lib.md_set_profiling(None, 1),
         "md_set_atm_kernel": lambda: lib.md_set_atm_kernel(None, 2),
         "md_get_info": lambda: lib.md_get_info(None, ctypes.byref(i64), ctypes.byref(d), ctypes.byref(i32)),
+        "md_get_memory": lambda: lib.md_get_memory(None, ctypes.byref(ctypes.c_size_t())),
     }
     for name, call in calls.items():
         assert call() == ARG, name
@@ -63,6 +64,7 @@ def test_null_batch_handle_is_rejected_everywhere(lib):
     assert lib.md_batch_latency(None, 0, ctypes.byref(d), ctypes.byref(i32)) == ARG
     assert lib.md_batch_pending(None, ctypes.byref(i32), ctypes.byref(i32)) == ARG
     assert lib.md_batch_cycles(None, ctypes.byref(u), ctypes.byref(u)) == ARG
+    assert lib.md_batch_cancel(None, 1) == ARG
     assert lib.md_batch_destroy(None) == OK  # NULL-safe
 
 
@@ -74,7 +76,10 @@ def test_create_system_validation_before_any_device_work(lib):
     assert lib.md_create_system(ctypes.byref(h), n, 20.0, None, None, 1.0, 0, None) == ARG  # no positions
     assert lib.md_create_system(ctypes.byref(h), n, 0.0, pos, None, 1.0, 0, None) == ARG    # box length 0
     assert lib.md_create_system(ctypes.byref(h), n, math.nan, pos, None, 1.0, 0, None) == ARG
+    assert lib.md_create_system(ctypes.byref(h), n, math.inf, pos, None, 1.0, 0, None) == ARG  # infinite box
     assert lib.md_create_system(ctypes.byref(h), n, 20.0, pos, None, 0.0, 0, None) == ARG   # mass 0
+    assert lib.md_create_system(ctypes.byref(h), n, 20.0, pos, None, math.inf, 0, None) == ARG  # infinite mass
+    assert lib.md_create_system(ctypes.byref(h), n, 20.0, pos, None, math.nan, 0, None) == ARG
     assert lib.md_create_system(ctypes.byref(h), n, 20.0, pos, None, 1.0, 7, None) == ARG   # precision
     bad = _doubles([0.5 * q for q in range(3 * n)])
     bad[4] = math.inf
@@ -123,14 +128,29 @@ def test_noalloc_validation_before_any_device_work(lib):
     assert call(pos, n, 20.0, 0.073, 0.0, f3, ctypes.byref(u3), ctypes.byref(trip), None) == ARG
     assert call(pos, n, 20.0, -0.5, 2.5, f3, ctypes.byref(u3), ctypes.byref(trip), None) == ARG
     assert call(pos, n, 7.5, 0.073, 2.5, f3, ctypes.byref(u3), ctypes.byref(trip), None) == BOX  # L = 3 r_c
+    assert call(pos, n, math.inf, 0.073, 2.5, f3, ctypes.byref(u3), ctypes.byref(trip), None) == ARG
+    assert call(pos, n, math.nan, 0.073, 2.5, f3, ctypes.byref(u3), ctypes.byref(trip), None) == ARG
+    assert call(pos, n, 20.0, 0.073, math.inf, f3, ctypes.byref(u3), ctypes.byref(trip), None) == ARG
+    assert call(pos, n, 20.0, math.inf, 2.5, f3, ctypes.byref(u3), ctypes.byref(trip), None) == ARG
     big = 16385  # MD_NOALLOC_MAX_N + 1
     assert call(pos, big, 100.0, 0.073, 2.5, f3, ctypes.byref(u3), ctypes.byref(trip), None) == CAPACITY
+    # the rejection's message is the one md_last_error returns
+    assert b"MD_NOALLOC_MAX_N" in lib.md_last_error()
 
 
 def test_status_strings_cover_every_code(lib):
     seen = set()
-    for code in (OK, ARG, -2, BOX, NONFINITE, -5, -6, STATE, CAPACITY):
+    for code in (OK, ARG, -2, BOX, NONFINITE, -5, -6, STATE, CAPACITY, -9):
         s = lib.md_status_string(code)
         assert s and isinstance(s, bytes)
         seen.add(s)
-    assert len(seen) == 9  # distinct texts
+    assert len(seen) == 10  # distinct texts
+
+
+def test_peak_measurement_validation_before_any_device_work(lib):
+    f = ctypes.c_double()
+    assert lib.md_measure_fma_peak(3, 10.0, ctypes.byref(f), None) == ARG   # unknown kind
+    assert lib.md_measure_fma_peak(-1, 10.0, ctypes.byref(f), None) == ARG
+    assert lib.md_measure_fma_peak(0, 10.0, None, None) == ARG                # no output
+    assert lib.md_measure_fma_peak(0, 0.0, ctypes.byref(f), None) == ARG     # duration
+    assert lib.md_measure_fma_peak(0, math.nan, ctypes.byref(f), None) == ARG
