@@ -195,7 +195,7 @@ md_status alloc_device(md_system* s) {
   size_t o_pcell = a.reserve(4 * n), o_ctmp = a.reserve(4 * n), o_rank = a.reserve(4 * n);
   size_t o_skey = a.reserve(4 * n), o_memb = a.reserve(4 * n);
   size_t o_count = a.reserve(4 * (size_t)s->ncell), o_cstart = a.reserve(4 * ((size_t)s->ncell + 1));
-  size_t o_nbr = a.reserve(4 * (size_t)s->maxnb * n), o_nbc = a.reserve(4 * n);
+  size_t o_nbr = a.reserve(4 * (size_t)s->maxnb * nbr_rows(n)), o_nbc = a.reserve(4 * n);
   size_t o_half = a.reserve(4 * (size_t)kHalfCap * n), o_hc = a.reserve(4 * n);
   size_t o_part = a.reserve(tsz * 27 * 3 * n);
   size_t o_f3a = a.reserve(32 * n);  // [n][4] fixed-point (FP32) or double (FP64) sums
@@ -305,7 +305,7 @@ size_t arena_bytes(const md_system* s0) {
   for (int i = 0; i < 5; ++i) a.reserve(4 * n);
   a.reserve(4 * (size_t)tmp.ncell);
   a.reserve(4 * ((size_t)tmp.ncell + 1));
-  a.reserve(4 * (size_t)tmp.maxnb * n);
+  a.reserve(4 * (size_t)tmp.maxnb * nbr_rows(n));
   a.reserve(4 * n);
   a.reserve(4 * (size_t)kHalfCap * n);
   a.reserve(4 * n);

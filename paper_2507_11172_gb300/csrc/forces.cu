@@ -182,8 +182,6 @@ template <> __device__ __forceinline__ float recip_fast<float>(float x) {
 }
 template <> __device__ __forceinline__ double recip_fast<double>(double x) { return 1.0 / x; }
 
-constexpr unsigned kPadCode = 63u;  // code of a padding entry (offset far outside every cutoff)
-
 // kE = false: a launch whose items never ask for energies (compiled without the energy terms)
 template <typename T, bool kE>
 #ifndef R3B_LJ_THREADS_PER_SM
@@ -225,7 +223,7 @@ __global__ void __launch_bounds__(kLjPer, R3B_LJ_THREADS_PER_SM / kLjPer) k_lj(c
     const T sig2 = Par<T>::sig2(S);
     const T eps24 = Par<T>::eps24(S), eps4 = Par<T>::eps4(S);
     const int cnt = S.nbr_cnt[i];
-    const int4* __restrict__ row4 = reinterpret_cast<const int4*>(S.nbr + (size_t)i * S.maxnb);
+    const int4* __restrict__ row4 = reinterpret_cast<const int4*>(S.nbr + nbr_slot(S.maxnb, i, 0));
     const int4 pad = make_int4((int)(kPadCode << kNbrShift), (int)(kPadCode << kNbrShift),
                                (int)(kPadCode << kNbrShift), (int)(kPadCode << kNbrShift));
     // entries of a group, padded beyond the row's length
@@ -301,7 +299,7 @@ __global__ void __launch_bounds__(kLjPer, R3B_LJ_THREADS_PER_SM / kLjPer) k_lj(c
       // FP64 with the CPU definition's operation order; the ones inside the cutoff are added.
       for (int t = 0; t < cnt; ++t) {
         if ((t >> 2) % kLjTeam != h) continue;  // this thread's groups only
-        const unsigned e = (unsigned)S.nbr[(size_t)i * S.maxnb + t];
+        const unsigned e = (unsigned)S.nbr[nbr_slot(S.maxnb, i, t)];
         const int j = (int)(e & kNbrMask);
         const T4 pj = P[j];
         const T4 o = s_off[e >> kNbrShift];
@@ -998,7 +996,7 @@ __global__ void __launch_bounds__(32 * kPaWarps)
   if (sizeof(T) == 4) lx = PL[x];
   // 1. neighbours within r_c3 from the pair list (full-precision differences)
   const int cnt = S.nbr_cnt[x];
-  const int* __restrict__ row = S.nbr + (size_t)x * S.maxnb;
+  const int* __restrict__ row = S.nbr + nbr_slot(S.maxnb, x, 0);
   int m = 0;
   for (int t0 = 0; t0 < cnt; t0 += 32) {
     const int t = t0 + lane;

@@ -10,6 +10,8 @@ constexpr int kStencil = 27;        // 3 x 3 x 3 cells: cell edge >= every cutof
 constexpr int kMaxHalf = 128;       // per-particle ATM half list (neighbours with larger sorted index)
 constexpr int kNbrShift = 26;       // LJ list entry = j | (image code << 26), code = 2 bits per axis
 constexpr unsigned kNbrMask = (1u << kNbrShift) - 1u;
+constexpr unsigned kPadCode = 63u;  // image code of a padding entry: an offset far outside every cutoff
+constexpr int kNbrPad = (int)(kPadCode << kNbrShift);  // padding entry (index 0, code 63)
 constexpr int kPairTable = kMaxHalf * (kMaxHalf - 1) / 2;  // (j, k) pairs, k-major
 constexpr int kAtmWarps = 8;
 constexpr int kAtmThreads = 32 * kAtmWarps;
@@ -21,13 +23,10 @@ constexpr int kListWarps = R3B_LIST_WARPS;  // warps per CTA of the pair-list bu
 constexpr int kNearThreads = 128;   // owners (one thread each) per CTA of the near-class triplet kernel
 constexpr int kHalfCap = 64;        // triplet half list per particle (neighbours above it within r_c3)
 
-// Pair-list layout: blocks of 32 consecutive sorted particles; within a block, entry t of particle i
-// sits at int index ((i / 32) * (maxnb / 4) + t / 4) * 128 + (i % 32) * 4 + t % 4, so a warp reading
-// entries 4g .. 4g + 3 of its 32 particles reads one contiguous 512-byte group (maxnb is a multiple
-// of 4; the array holds ceil(n / 32) * 32 rows).
+// Pair-list layout: row-major, entry t of particle i at int index i * maxnb + t (maxnb is a multiple
+// of 4, so every row starts on a 16-byte boundary).
 __host__ __device__ __forceinline__ size_t nbr_slot(int maxnb, int i, int t) {
-  return ((size_t)(i >> 5) * (size_t)(maxnb >> 2) + (size_t)(t >> 2)) * 128u + (size_t)((i & 31) << 2) +
-         (size_t)(t & 3);
+  return (size_t)i * (size_t)maxnb + (size_t)t;
 }
 __host__ __device__ __forceinline__ size_t nbr_rows(size_t n) { return (n + 31) & ~size_t(31); }
 

@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(256) k_rdf(const SysDev* __restrict__ sys, con
     const double L = S.L, hL = S.half_L;
     const double rmax = __dmul_rn((double)nbins, dr);
     const int cnt = S.nbr_cnt[i];
-    const int* __restrict__ row = S.nbr + (size_t)i * S.maxnb;
+    const int* __restrict__ row = S.nbr + nbr_slot(S.maxnb, i, 0);
     for (int t = 0; t < cnt; ++t) {
       const int j = (int)((unsigned)row[t] & kNbrMask);
       if (j <= i) continue;  // each unordered pair once

@@ -277,6 +277,7 @@ __global__ void __launch_bounds__(32 * kListWarps)
     const int i = i0 + ib;
     const T4 pi = sp[islot];
     int cnt = 0;
+    int* const row = S.nbr + nbr_slot(S.maxnb, i, 0);
     // pass 1: every staged particle within the list radius
     for (int t0 = 0; t0 < nstaged; t0 += 32) {
       const int t = t0 + lane;
@@ -288,7 +289,7 @@ __global__ void __launch_bounds__(32 * kListWarps)
       }
       const unsigned bal = __ballot_sync(0xffffffffu, ok);
       const int pos = cnt + __popc(bal & lt);
-      if (ok && pos < S.maxnb) S.nbr[nbr_slot(S.maxnb, i, pos)] = sj[t];
+      if (ok && pos < S.maxnb) row[pos] = sj[t];
       cnt += __popc(bal);
     }
     if (lane == 0) {
@@ -306,7 +307,7 @@ __global__ void __launch_bounds__(32 * kListWarps)
       bool half = false, band = false, cand = false;
       unsigned e = 0u;
       if (t < cnt) {
-        e = (unsigned)S.nbr[nbr_slot(S.maxnb, i, t)];
+        e = (unsigned)row[t];
         const unsigned code = e >> kNbrShift;
         const int l = (int)(code & 3u) + 3 * (int)((code >> 2) & 3u) + 9 * (int)(code >> 4);
         const int slot = (int)(e & kNbrMask) + st_delta[l];
