@@ -78,6 +78,11 @@ typedef struct {
   int32_t atm_kernel;          /* triplet kernel in use: 0 cell, 1 per-particle, 2 rotation, -1 not chosen yet */
   int32_t atm_bases_per_warp;  /* rotation kernel: consecutive bases per warp in a work item (autotuned) */
   uint64_t near_triplets_last; /* distance classes: near-class triplets found by the last near evaluation */
+  int32_t lj_block;            /* LJ kernel: particles (threads) per block (autotuned: 32, 64 or 128) */
+  int32_t list_warps;          /* pair-list build: warps per CTA (autotuned: 2, 4 or 8) */
+  int32_t tuned_from_cache;    /* 1 if the last tuning reused the choices of an earlier system with the same
+                                  key (N bucket, density bucket, r_c2, r_c3, skin, precision, classes) */
+  int32_t reserved_;
 } md_stats;
 
 /* Create a system of n >= 3 particles in a periodic cube of side box_L: the input x0, v0 of
@@ -189,8 +194,19 @@ md_status md_set_profiling(md_system *s, int profile);
  *      1 and 2 need r_c3 <= r_c2 + skin, else 0 is used;
  *  -1  (default) time the allowed kernels (the rotation kernel with 4, 8 and 16 bases per warp in
  *      a work item) on the system's first evaluation and keep the fastest.  A batch uses its
- *      members' common choice, else 2 where allowed, else 0. */
+ *      members' common choice, else 2 where allowed, else 0.
+ * The same autotuner picks the LJ block size and the pair-list build's warps per CTA (md_stats), and
+ * caches every choice for the process under the key (device, N in half-octave buckets, density in
+ * steps of 0.025, r_c2, r_c3, skin, precision, distance classes on/off): a later system with the same
+ * key takes the cached choices without trials (md_stats.tuned_from_cache = 1). */
 md_status md_set_atm_kernel(md_system *s, int variant);
+
+/* Launch shapes fixed instead of autotuned (no counterpart in the paper; an autotuning knob like
+ * md_set_atm_kernel): lj_block 32, 64 or 128 particles per LJ block, list_warps 2, 4 or 8 warps per
+ * CTA of the pair-list build, rot_bases_per_warp 4, 8 or 16 (rotation kernel work items); 0 leaves a
+ * shape to the autotuner.  Every shape gives the same forces bit for bit.  Applied at the next call
+ * that evaluates forces; MD_ERR_ARG for other values, MD_ERR_STATE while the system is in a batch. */
+md_status md_set_shapes(md_system *s, int lj_block, int list_warps, int rot_bases_per_warp);
 
 /* Number of particles, box side and precision of a handle (the inputs of Algorithm 2). */
 md_status md_get_info(md_system *s, int64_t *n, double *box_L, int *precision);

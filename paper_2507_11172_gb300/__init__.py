@@ -38,7 +38,8 @@ class md_stats(ctypes.Structure):
                 ("replays", ctypes.c_uint64), ("guard_rechecks", ctypes.c_uint64), ("atm_ms_total", ctypes.c_double),
                 ("atm_timed", ctypes.c_uint64), ("max_cell_count", ctypes.c_int32),
                 ("cells_per_side", ctypes.c_int32), ("atm_kernel", ctypes.c_int32), ("atm_bases_per_warp", ctypes.c_int32),
-                ("near_triplets_last", ctypes.c_uint64)]
+                ("near_triplets_last", ctypes.c_uint64), ("lj_block", ctypes.c_int32), ("list_warps", ctypes.c_int32),
+                ("tuned_from_cache", ctypes.c_int32), ("reserved_", ctypes.c_int32)]
 
 
 _lib = None
@@ -62,6 +63,7 @@ SIGNATURES = {
     "md_get_stats": (_I, [_P, ctypes.POINTER(md_stats)]),
     "md_set_profiling": (_I, [_P, _I]),
     "md_set_atm_kernel": (_I, [_P, _I]),
+    "md_set_shapes": (_I, [_P, _I, _I, _I]),
     "md_set_distance_classes": (_I, [_P, _D, _I]),
     "md_get_near_forces": (_I, [_P, _P]),
     "md_get_info": (_I, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_D), ctypes.POINTER(_I)]),
@@ -216,6 +218,10 @@ def md_set_profiling(h, on: bool):
 
 def md_set_atm_kernel(h, variant: int):
     _check(load().md_set_atm_kernel(h, int(variant)), "md_set_atm_kernel")
+
+
+def md_set_shapes(h, lj_block: int = 0, list_warps: int = 0, rot_bases_per_warp: int = 0):
+    _check(load().md_set_shapes(h, int(lj_block), int(list_warps), int(rot_bases_per_warp)), "md_set_shapes")
 
 
 def md_set_distance_classes(h, r_a: float, s_near: int):

@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -103,6 +104,10 @@ struct md_system {
   int nblocks_pa = 0;
   int nblocks_rot = 0;
   int rot_per = rot_bases_per_item(0) / kRotWarps;  // rotation kernel: bases per warp in a work item
+  int lj_block = kLjPer;                 // LJ kernel: threads (particles) per block
+  int list_warps = kListWarpsDefault;    // pair-list build: warps per CTA
+  bool tuned_from_cache = false;         // the last tuning reused another system's choices
+  int lj_block_req = 0, list_warps_req = 0, rot_per_req = 0;  // md_set_shapes (0: autotuned)
   std::map<std::tuple<int, int, int, int, int>, cudaGraphExec_t> graphs;  // (n_outer, k, cur, safe, profile)
   // host mirrors
   int* h_flags = nullptr;       // pinned [FLG_N]
@@ -412,12 +417,12 @@ PItem* pitems_for(md_system* s, int tag, int mode, int buf) {
   auto it = s->pitems.find(key);
   if (it != s->pitems.end()) return it->second;
   std::vector<PItem> v;
-  const int per = (tag == T_LJ)      ? kLjParticles
+  const int per = (tag == T_LJ)      ? s->lj_block
                   : (tag == T_ATMPA)  ? kPaPerBlock
                   : (tag == T_ATMROT) ? kRotWarps * s->rot_per
                   : (tag == T_ATMNEAR) ? kNearThreads
                                       : kBlock;
-  const int nb = (tag == T_LJ)       ? (s->n + kLjParticles - 1) / kLjParticles
+  const int nb = (tag == T_LJ)       ? (int)((s->n + s->lj_block - 1) / s->lj_block)
                  : (tag == T_ATMPA)  ? s->nblocks_pa
                  : (tag == T_ATMROT) ? s->nblocks_rot
                  : (tag == T_ATMNEAR) ? (int)((s->n + kNearThreads - 1) / kNearThreads)
@@ -583,14 +588,14 @@ struct Plan {
     launch_scan(L, cond ? s->sitem_cond : s->sitem, 1);
     launch_cell_order(L, pitems_for(s, T_BIN, c, buf), s->nblocks, kBlock, citems_for(s, c, buf), s->ncell);
     launch_scatter<T>(L, pitems_for(s, T_SCATTER, c, buf), s->nblocks, kBlock);
-    launch_listbuild<T>(L, citems_for(s, c, buf), s->ncell, 27 * s->cap_cell);
+    launch_listbuild<T>(L, citems_for(s, c, buf), s->ncell, 27 * s->cap_cell, s->list_warps);
   }
   // LJ forces and the velocity-Verlet kick/drift; with near = true (distance classes, LJ_MID) the
   // near-class triplets are evaluated between the two and their kicks join the LJ kick
   template <typename T>
   void lj(int kind, int buf, bool energy, bool near = false) {
     launch_lj<T>(L, pitems_for(s, T_LJ, kind | (energy ? M_ENERGY : 0), buf),
-                 padded_blocks((s->n + kLjParticles - 1) / kLjParticles), energy);
+                 padded_blocks((int)((s->n + s->lj_block - 1) / s->lj_block)), energy, s->lj_block);
     if (near) atm_near<T>(buf);
     if (kind != LJ_INIT)
       launch_kick<T>(L, pitems_for(s, T_KICK, kind | (near ? M_NEAR : 0), buf), padded_blocks(s->nblocks));
@@ -822,18 +827,90 @@ md_status set_rot_per(md_system* s, int per) {
   return MD_OK;
 }
 
-// Autotuner for the triplet kernel: after one initial evaluation (binning, pair list, forces)
-// each allowed variant, and for the rotation kernel each work-item shape (4, 8 or 16 bases per warp),
-// is launched a few times on the same configuration with CUDA events around each launch; the fastest
-// is kept for the system.
-md_status tune_atm(md_system* s) {
-  const int req = s->atm_variant_req;
-  if (req >= 0) {
-    s->atm_variant = variant_allowed(s, req) ? req : 0;
-    return MD_OK;
+// LJ work items of `block` particles (the items of the previous size are dropped from the cache; their
+// memory is released with the other items)
+md_status set_lj_block(md_system* s, int block) {
+  if (block == s->lj_block) return MD_OK;
+  s->lj_block = block;
+  for (auto it = s->pitems.begin(); it != s->pitems.end();) {
+    if (std::get<0>(it->first) == T_LJ)
+      it = s->pitems.erase(it);
+    else
+      ++it;
   }
-  s->atm_variant = 0;
-  if (!variant_allowed(s, 1)) return MD_OK;
+  for (int b = 0; b < 2; ++b)
+    for (int e = 0; e < 2; ++e)
+      for (int kind : {LJ_INIT, LJ_MID, LJ_LAST})
+        if (!pitems_for(s, T_LJ, kind | (e ? M_ENERGY : 0), b)) return MD_ERR_OOM;
+  CK(cudaStreamSynchronize(s->stream));
+  clear_graphs(s);
+  return MD_OK;
+}
+
+// Autotuner (the paper's AutoPas tunes its traversal at run time, Sec. 4.1; here the launch shapes).
+// Choices: the triplet kernel (cell, per-particle or rotation kernel) and the rotation kernel's work-item
+// shape (4, 8 or 16 bases per warp), the LJ block size (32, 64 or 128 particles) and the pair-list
+// build's warps per CTA (2, 4 or 8).  None of them changes a result bit except the triplet kernel
+// variant (within the FP tolerance).  After one initial evaluation (binning, pair list, forces) each
+// candidate is launched four times on the same configuration with CUDA events around each launch
+// (the first launch warms caches) and the fastest is kept.  The choices are cached for the process,
+// keyed on (device, N in half-octave buckets, density in steps of 0.025, r_c2, r_c3, skin, precision,
+// distance classes on/off): a later system with the same key skips the trials.
+struct TuneChoice {
+  int variant, rot_per, lj_block, list_warps;
+};
+using TuneKey = std::tuple<int, int, int, int, int, int, int, int>;
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneChoice> g_tune_cache;
+
+TuneKey tune_key(const md_system* s) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) cudaGetLastError();
+  const double rho = (double)s->n / (s->L * s->L * s->L);
+  return std::make_tuple(dev, (int)floor(2.0 * log2((double)s->n)), (int)lround(rho * 40.0),
+                         (int)lround(s->rc2 * 1000.0), (int)lround(s->rc3 * 1000.0), (int)lround(s->skin * 1000.0),
+                         s->precision, s->r_a > 0 ? 1 : 0);
+}
+
+md_status tune_apply(md_system* s, const TuneChoice& c) {
+  const int req = s->atm_variant_req;
+  s->atm_variant = req >= 0 ? (variant_allowed(s, req) ? req : 0) : (variant_allowed(s, c.variant) ? c.variant : 0);
+  md_status st = set_rot_per(s, s->rot_per_req ? s->rot_per_req : c.rot_per);
+  if (st == MD_OK) st = set_lj_block(s, s->lj_block_req ? s->lj_block_req : c.lj_block);
+  if (st != MD_OK) return st;
+  s->list_warps = s->list_warps_req ? s->list_warps_req : c.list_warps;
+  clear_graphs(s);
+  return MD_OK;
+}
+
+// mean of launches 2-4 of `launch` (CUDA events on the system's stream)
+template <typename F>
+md_status time_launches(md_system* s, F launch, float* ms_out) {
+  float tot = 0.f;
+  for (int r = 0; r < 4; ++r) {
+    CK(cudaEventRecord(s->events[0], s->stream));
+    launch();
+    CK(cudaEventRecord(s->events[1], s->stream));
+    CK(cudaEventSynchronize(s->events[1]));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, s->events[0], s->events[1]));
+    if (r > 0) tot += ms;
+  }
+  *ms_out = tot / 3.f;
+  return MD_OK;
+}
+
+md_status tune(md_system* s) {
+  const TuneKey key = tune_key(s);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      s->tuned_from_cache = true;
+      return tune_apply(s, it->second);
+    }
+  }
+  s->tuned_from_cache = false;
   md_status st = upload_desc(s, 0.0, 0.0);
   if (st != MD_OK) return st;
   st = ensure_events(s, 2);
@@ -842,11 +919,12 @@ md_status tune_atm(md_system* s) {
   const bool prof = s->profile;
   s->profile = false;
   clear_graphs(s);
+  s->atm_variant = 0;
   st = run_plan(s, 0, 1, true, false);  // binning + pair list at the current positions
   if (st != MD_OK) return st;
-  float best = 1e30f;
-  int bestv = 0, bestper = s->rot_per;
-  // candidates: (variant, bases per warp of the rotation kernel's work items)
+  TuneChoice best{0, s->rot_per, s->lj_block, s->list_warps};
+  float tbest = 1e30f;
+  // triplet kernel: (variant, bases per warp of the rotation kernel's work items)
 #ifdef R3B_ROT_SHAPE_ONLY  // build-time knob: a single rotation shape instead of the tuned choice
   const int cand[][2] = {{0, 0}, {1, 0}, {2, R3B_ROT_SHAPE_ONLY}};
 #else
@@ -860,33 +938,63 @@ md_status tune_atm(md_system* s) {
       st = set_rot_per(s, c[1]);
       if (st != MD_OK) return st;
     }
-    float tot = 0.f;
-    for (int r = 0; r < 4; ++r) {
-      CK(cudaEventRecord(s->events[0], s->stream));
+    float ms = 0.f;
+    st = time_launches(s, [&] {
       if (s->precision) P.atm_all<double>(s->cur, false); else P.atm_all<float>(s->cur, false);
-      CK(cudaEventRecord(s->events[1], s->stream));
-      CK(cudaEventSynchronize(s->events[1]));
-      float ms = 0.f;
-      CK(cudaEventElapsedTime(&ms, s->events[0], s->events[1]));
-      if (r > 0) tot += ms;  // first launch warms caches
-    }
-    if (tot < best) {
-      best = tot;
-      bestv = v;
-      if (v == 2) bestper = c[1];
+    }, &ms);
+    if (st != MD_OK) return st;
+    if (ms < tbest) {
+      tbest = ms;
+      best.variant = v;
+      if (v == 2) best.rot_per = c[1];
     }
   }
-  s->atm_variant = bestv;
-  st = set_rot_per(s, bestper);
-  if (st != MD_OK) return st;
-  s->profile = prof;
   // the rotation kernel's trial launches left sums that no combine cleared
   CK(cudaMemsetAsync(s->h.f3acc, 0, 32 * (size_t)s->n, s->stream));
-  clear_graphs(s);
-  s->forces_valid = false;  // recompute with the chosen kernel
+  // LJ block size (forces only; every block size gives the same forces)
+  tbest = 1e30f;
+  for (int block : kLjBlocks) {
+    st = set_lj_block(s, block);
+    if (st != MD_OK) return st;
+    float ms = 0.f;
+    st = time_launches(s, [&] {
+      const PItem* items = pitems_for(s, T_LJ, LJ_INIT, s->cur);
+      const int nb = padded_blocks((int)((s->n + block - 1) / block));
+      if (s->precision) launch_lj<double>(P.L, items, nb, false, block); else launch_lj<float>(P.L, items, nb, false, block);
+    }, &ms);
+    if (st != MD_OK) return st;
+    if (ms < tbest) {
+      tbest = ms;
+      best.lj_block = block;
+    }
+  }
+  // pair-list build warps per CTA (the lists are the same for every choice)
+  tbest = 1e30f;
+  for (int wps : {2, 4, 8}) {
+    float ms = 0.f;
+    st = time_launches(s, [&] {
+      const CItem* items = citems_for(s, 0, s->cur);
+      if (s->precision)
+        launch_listbuild<double>(P.L, items, s->ncell, 27 * s->cap_cell, wps);
+      else
+        launch_listbuild<float>(P.L, items, s->ncell, 27 * s->cap_cell, wps);
+    }, &ms);
+    if (st != MD_OK) return st;
+    if (ms < tbest) {
+      tbest = ms;
+      best.list_warps = wps;
+    }
+  }
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache[key] = best;
+  }
+  st = tune_apply(s, best);
+  if (st != MD_OK) return st;
+  s->profile = prof;
+  s->forces_valid = false;  // recompute with the chosen kernels
   s->energy_valid = false;
-  st = read_flags(s);      // refresh the counter baseline (the trial launches counted triplets)
-  return st;
+  return read_flags(s);  // refresh the counter baseline (the trial launches counted triplets)
 }
 
 // one respa_step call with snapshot / replay
@@ -896,7 +1004,7 @@ md_status do_call(md_system* s, int n_outer, int k, double dt_outer) {
     return MD_ERR_ARG;
   }
   if (s->atm_variant < 0) {
-    md_status st = tune_atm(s);
+    md_status st = tune(s);
     if (st != MD_OK) return st;
   }
   const double dt_in = dt_outer / k;
@@ -1297,6 +1405,9 @@ md_status md_get_stats(md_system* s, md_stats* out) {
   if (!s || !out) return MD_ERR_ARG;
   s->stats.atm_kernel = s->atm_variant;
   s->stats.atm_bases_per_warp = s->rot_per;
+  s->stats.lj_block = s->lj_block;
+  s->stats.list_warps = s->list_warps;
+  s->stats.tuned_from_cache = s->tuned_from_cache ? 1 : 0;
   *out = s->stats;
   return MD_OK;
 }
@@ -1321,6 +1432,21 @@ md_status md_set_atm_kernel(md_system* s, int variant) {
 md_status md_get_memory(md_system* s, size_t* device_bytes) {
   if (!s || !device_bytes) return MD_ERR_ARG;
   *device_bytes = s->deferred ? arena_bytes(s) : s->mem_bytes;  // the figure batch admission uses
+  return MD_OK;
+}
+
+md_status md_set_shapes(md_system* s, int lj_block, int list_warps, int rot_bases_per_warp) {
+  if (!s) return MD_ERR_ARG;
+  if (lj_block != 0 && lj_block != 32 && lj_block != 64 && lj_block != 128) return MD_ERR_ARG;
+  if (list_warps != 0 && list_warps != 2 && list_warps != 4 && list_warps != 8) return MD_ERR_ARG;
+  if (rot_bases_per_warp != 0 && rot_bases_per_warp != 4 && rot_bases_per_warp != 8 && rot_bases_per_warp != 16)
+    return MD_ERR_ARG;
+  if (s->batch) return MD_ERR_STATE;
+  s->lj_block_req = lj_block;
+  s->list_warps_req = list_warps;
+  s->rot_per_req = rot_bases_per_warp;
+  s->atm_variant = -1;  // applied with the next tuning (the cached choices fill the rest)
+  clear_graphs(s);
   return MD_OK;
 }
 
@@ -1472,9 +1598,9 @@ void enqueue_cycle(md_batch* b, const std::vector<TickItems>& ticks, bool with_s
     chk("cell_order", t);
     launch_scatter<T>(L, b->d_pitems + it.bin, it.nbin, kBlock);
     chk("scatter", t);
-    launch_listbuild<T>(L, b->d_citems + it.list, it.nlist, b->smax_list);
+    launch_listbuild<T>(L, b->d_citems + it.list, it.nlist, b->smax_list, kListWarpsDefault);
     chk("listbuild", t);
-    launch_lj<T>(L, b->d_pitems + it.lj, it.nlj, true);  // members' modes decide the energy
+    launch_lj<T>(L, b->d_pitems + it.lj, it.nlj, true, kLjParticles);  // members' modes decide the energy
     chk("lj", t);
     launch_kick<T>(L, b->d_pitems + it.kick, it.nkick);
     chk("kick", t);

@@ -182,15 +182,17 @@ template <> __device__ __forceinline__ float recip_fast<float>(float x) {
 }
 template <> __device__ __forceinline__ double recip_fast<double>(double x) { return 1.0 / x; }
 
-// kE = false: a launch whose items never ask for energies (compiled without the energy terms)
-template <typename T, bool kE>
+// kE = false: a launch whose items never ask for energies (compiled without the energy terms);
+// kPer: threads per block (one per particle), a runtime choice of the autotuner
 #ifndef R3B_LJ_THREADS_PER_SM
 #define R3B_LJ_THREADS_PER_SM 896  // resident LJ threads per SM the register allocation is sized for
 #endif
-__global__ void __launch_bounds__(kLjPer, R3B_LJ_THREADS_PER_SM / kLjPer) k_lj(const SysDev* __restrict__ sys, const PItem* __restrict__ items) {
+template <typename T, bool kE, int kPer>
+__global__ void __launch_bounds__(kPer, R3B_LJ_THREADS_PER_SM / kPer) k_lj(const SysDev* __restrict__ sys, const PItem* __restrict__ items) {
+  static_assert(kPer % 32 == 0 && kLjTeam == 1, "LJ blocks of whole warps, one thread per particle");
   using T4 = typename V4<T>::type;
   __shared__ T4 s_off[64];
-  __shared__ double red_u[kLjPer / 32], red_w[kLjPer / 32];
+  __shared__ double red_u[kPer / 32], red_w[kPer / 32];
   const PItem it = items[blockIdx.x];
   const SysDev& S = sys[it.sys];
   const int mode = item_mode(S, it.mode);
@@ -351,7 +353,7 @@ __global__ void __launch_bounds__(kLjPer, R3B_LJ_THREADS_PER_SM / kLjPer) k_lj(c
     if (threadIdx.x == 0) {
       double ut = 0.0, wt = 0.0;
 #pragma unroll
-      for (int q = 0; q < kLjPer / 32; ++q) {
+      for (int q = 0; q < kPer / 32; ++q) {
         ut += red_u[q];
         wt += red_w[q];
       }
@@ -1340,13 +1342,23 @@ int atm_configure(int smax, int precision, int* smem_bytes) {
 }
 
 // ---------------------------------------------------------------- launchers
-template <typename T>
-void launch_lj(const Launch& L, const PItem* items, int nitems, bool energy) {
-  if (nitems <= 0) return;
+template <typename T, int kPer>
+void launch_lj_per(const Launch& L, const PItem* items, int nitems, bool energy) {
   if (energy)
-    k_lj<T, true><<<nitems, kLjPer, 0, L.stream>>>(L.sys, items);
+    k_lj<T, true, kPer><<<nitems, kPer, 0, L.stream>>>(L.sys, items);
   else
-    k_lj<T, false><<<nitems, kLjPer, 0, L.stream>>>(L.sys, items);
+    k_lj<T, false, kPer><<<nitems, kPer, 0, L.stream>>>(L.sys, items);
+}
+// items of `block` particles (kLjBlocks), one thread each
+template <typename T>
+void launch_lj(const Launch& L, const PItem* items, int nitems, bool energy, int block) {
+  if (nitems <= 0) return;
+  if (block == 32)
+    launch_lj_per<T, 32>(L, items, nitems, energy);
+  else if (block == 128)
+    launch_lj_per<T, 128>(L, items, nitems, energy);
+  else
+    launch_lj_per<T, 64>(L, items, nitems, energy);
 }
 template <typename T>
 void launch_atm(const Launch& L, const CItem* items, int nitems, int grid, int smax) {
@@ -1389,8 +1401,8 @@ void launch_kinetic(const Launch& L, const PItem* items, int nitems, int block) 
   if (nitems > 0) k_kinetic<<<nitems, block, 0, L.stream>>>(L.sys, items);
 }
 
-template void launch_lj<float>(const Launch&, const PItem*, int, bool);
-template void launch_lj<double>(const Launch&, const PItem*, int, bool);
+template void launch_lj<float>(const Launch&, const PItem*, int, bool, int);
+template void launch_lj<double>(const Launch&, const PItem*, int, bool, int);
 template void launch_combine<float>(const Launch&, const PItem*, int, int);
 template void launch_combine<double>(const Launch&, const PItem*, int, int);
 template void launch_start<float>(const Launch&, const PItem*, int, int);

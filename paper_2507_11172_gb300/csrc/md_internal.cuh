@@ -16,10 +16,7 @@ constexpr int kPairTable = kMaxHalf * (kMaxHalf - 1) / 2;  // (j, k) pairs, k-ma
 constexpr int kAtmWarps = 8;
 constexpr int kAtmThreads = 32 * kAtmWarps;
 constexpr int kQueue = 256;         // per-warp queue of accepted neighbour pairs (j, k)
-#ifndef R3B_LIST_WARPS
-#define R3B_LIST_WARPS 4
-#endif
-constexpr int kListWarps = R3B_LIST_WARPS;  // warps per CTA of the pair-list build
+constexpr int kListWarpsDefault = 4;  // warps per CTA of the pair-list build (autotuned: 2, 4 or 8)
 constexpr int kNearThreads = 128;   // owners (one thread each) per CTA of the near-class triplet kernel
 constexpr int kHalfCap = 64;        // triplet half list per particle (neighbours above it within r_c3)
 
@@ -436,7 +433,7 @@ void launch_put_state(const Launch& L, int n, const double* pos, const double* v
 void launch_take_state(const Launch& L, int n, const double* src, double* out, int fold);
 void launch_scan(const Launch& L, const SItem* items, int nitems);
 template <typename T> void launch_scatter(const Launch& L, const PItem* items, int nitems, int block);
-template <typename T> void launch_listbuild(const Launch& L, const CItem* items, int nitems, int smax);
+template <typename T> void launch_listbuild(const Launch& L, const CItem* items, int nitems, int smax, int warps);
 template <typename T> void launch_atm_near(const Launch& L, const PItem* items, int nitems);
 int listbuild_configure(int smax, int precision);
 // forces.cu
@@ -451,7 +448,8 @@ constexpr int kLjPer = R3B_LJ_PER;  // threads per block
 #endif
 constexpr int kLjTeam = R3B_LJ_TEAM;  // a power of two dividing 32
 constexpr int kLjParticles = kLjPer / kLjTeam;
-template <typename T> void launch_lj(const Launch& L, const PItem* items, int nitems, bool energy);
+constexpr int kLjBlocks[3] = {32, 64, 128};  // LJ block sizes the autotuner tries (kLjPer by default)
+template <typename T> void launch_lj(const Launch& L, const PItem* items, int nitems, bool energy, int block);
 template <typename T> void launch_atm(const Launch& L, const CItem* items, int nitems, int grid, int smax);
 // staged-particle capacity of an ATM CTA: the particles within r_c of a base cell (edge >= r_c)
 // occupy at most the volume of about 21 cells (16 cells plus margin is sized for the typical mean

@@ -204,7 +204,7 @@ __global__ void k_scatter(const SysDev* __restrict__ sys, const PItem* __restric
 // same pass keeps the near-class candidates (S.half_a): the entries above i within r_a + skin (a
 // superset test, widened by 1e-4).  The CTA also moves the permuted state of b's particles back into
 // place.
-template <typename T>
+template <typename T, int kListWarps>
 __global__ void __launch_bounds__(32 * kListWarps)
     k_listbuild(const SysDev* __restrict__ sys, const CItem* __restrict__ items, int smax) {
   using T4 = typename V4<T>::type;
@@ -440,21 +440,36 @@ template <typename T>
 void launch_scatter(const Launch& L, const PItem* items, int nitems, int block) {
   if (nitems > 0) k_scatter<T><<<nitems, block, 0, L.stream>>>(L.sys, items);
 }
+template <typename T, int kW>
+static void launch_listbuild_w(const Launch& L, const CItem* items, int nitems, int smax, int bytes) {
+  k_listbuild<T, kW><<<nitems, 32 * kW, bytes, L.stream>>>(L.sys, items, smax);
+}
+// warps: warps per CTA (kListWarpChoices), a runtime choice of the autotuner
 template <typename T>
-void launch_listbuild(const Launch& L, const CItem* items, int nitems, int smax) {
+void launch_listbuild(const Launch& L, const CItem* items, int nitems, int smax, int warps) {
   if (nitems <= 0) return;
   const int bytes = (int)(smax * (sizeof(typename V4<T>::type) + 2 * sizeof(int)));
-  k_listbuild<T><<<nitems, 32 * kListWarps, bytes, L.stream>>>(L.sys, items, smax);
+  if (warps == 2)
+    launch_listbuild_w<T, 2>(L, items, nitems, smax, bytes);
+  else if (warps == 8)
+    launch_listbuild_w<T, 8>(L, items, nitems, smax, bytes);
+  else
+    launch_listbuild_w<T, 4>(L, items, nitems, smax, bytes);
 }
-// the kernel's dynamic shared-memory limit is shared by every system on a device: only ever raised
+// the kernels' dynamic shared-memory limit is shared by every system on a device: only ever raised
 int listbuild_configure(int smax, int precision) {
   const int bytes = (int)(smax * ((precision ? sizeof(double4_32a) : sizeof(float4)) + 2 * sizeof(int)));
-  const void* kern = precision ? (const void*)k_listbuild<double> : (const void*)k_listbuild<float>;
-  return raise_smem_attr(kern, bytes) ? bytes : -1;
+  const void* kerns[2][3] = {{(const void*)k_listbuild<float, 2>, (const void*)k_listbuild<float, 4>,
+                              (const void*)k_listbuild<float, 8>},
+                             {(const void*)k_listbuild<double, 2>, (const void*)k_listbuild<double, 4>,
+                              (const void*)k_listbuild<double, 8>}};
+  for (const void* k : kerns[precision ? 1 : 0])
+    if (!raise_smem_attr(k, bytes)) return -1;
+  return bytes;
 }
 template void launch_scatter<float>(const Launch&, const PItem*, int, int);
 template void launch_scatter<double>(const Launch&, const PItem*, int, int);
-template void launch_listbuild<float>(const Launch&, const CItem*, int, int);
-template void launch_listbuild<double>(const Launch&, const CItem*, int, int);
+template void launch_listbuild<float>(const Launch&, const CItem*, int, int, int);
+template void launch_listbuild<double>(const Launch&, const CItem*, int, int, int);
 
 }  // namespace r3b

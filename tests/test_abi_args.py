@@ -47,6 +47,7 @@ def test_null_system_handle_is_rejected_everywhere(lib):
         "md_set_atm_kernel": lambda: lib.md_set_atm_kernel(None, 2),
         "md_get_info": lambda: lib.md_get_info(None, ctypes.byref(i64), ctypes.byref(d), ctypes.byref(i32)),
         "md_get_memory": lambda: lib.md_get_memory(None, ctypes.byref(ctypes.c_size_t())),
+        "md_set_shapes": lambda: lib.md_set_shapes(None, 64, 4, 8),
     }
     for name, call in calls.items():
         assert call() == ARG, name
