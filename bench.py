@@ -389,6 +389,8 @@ def run_ours(args):
     if rank == 0 and not args.no_batch:
         line["ensemble"] = run_ensemble(r3)
         line["serving"] = run_serving(r3, seconds=args.serve_seconds)
+        # below capacity (about 25 requests/s of this mix on one GB300): latencies without queueing
+        line["serving_subcapacity"] = run_serving(r3, seconds=5.0, rate=12.0)
     if not args.no_cpu and rank == 0:
         line["cpu_baseline"] = cpu_baseline(w, args.cpu_sample)
     if rank == 0:
@@ -595,7 +597,9 @@ def run_serving(r3, seconds=3.0, rate=50.0, n_outer=100, k=10, seed=None, atm_ke
         wall = time.perf_counter() - t0
         lat = np.concatenate(lat_all) if lat_all else np.zeros(1)
         cycles, replayed = r3.md_batch_cycles(b)
+        offered = float(sum(sizes)) * n_outer * 200.0 / seconds  # about 200 triplets per particle
         return {"requests": n_req, "arrival_rate_per_s": rate, "arrival_window_s": seconds,
+                "offered_triplets_per_s_estimate": offered,
                 "cycles": cycles, "replayed_cycles": replayed,
                 "outer_steps_each": n_outer, "k_inner": k, "wall_s": wall,
                 "triplets_per_s": trip_all / wall,
