@@ -95,6 +95,10 @@ struct md_system {
   // execution
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  // second stream of the captured plan: the closing LJ step of each outer step runs on it beside the
+  // triplet kernel (F2(x) and F3(x) do not depend on each other); fork / join events
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int cur = 0;               // position buffer holding the current state
   bool forces_valid = false;
   bool energy_valid = false;
@@ -593,12 +597,14 @@ struct Plan {
   // LJ forces and the velocity-Verlet kick/drift; with near = true (distance classes, LJ_MID) the
   // near-class triplets are evaluated between the two and their kicks join the LJ kick
   template <typename T>
-  void lj(int kind, int buf, bool energy, bool near = false) {
-    launch_lj<T>(L, pitems_for(s, T_LJ, kind | (energy ? M_ENERGY : 0), buf),
+  void lj(int kind, int buf, bool energy, bool near = false) { lj_on<T>(L, kind, buf, energy, near); }
+  template <typename T>
+  void lj_on(const Launch& Lx, int kind, int buf, bool energy, bool near = false) {
+    launch_lj<T>(Lx, pitems_for(s, T_LJ, kind | (energy ? M_ENERGY : 0), buf),
                  padded_blocks((int)((s->n + s->lj_block - 1) / s->lj_block)), energy, s->lj_block);
     if (near) atm_near<T>(buf);
     if (kind != LJ_INIT)
-      launch_kick<T>(L, pitems_for(s, T_KICK, kind | (near ? M_NEAR : 0), buf), padded_blocks(s->nblocks));
+      launch_kick<T>(Lx, pitems_for(s, T_KICK, kind | (near ? M_NEAR : 0), buf), padded_blocks(s->nblocks));
   }
   // distance classes: the near-class triplets at the current positions
   template <typename T>
@@ -667,13 +673,24 @@ void enqueue_steps(Plan& P, int n_outer, int k, int cur, bool safe, bool profile
         P.sort<T>(b);
       else if (safe)
         P.sort<T>(b, true);
-      if (t < k - 1)
-        P.lj<T>(LJ_MID, b, false, near);
-      else
-        P.lj<T>(LJ_LAST, b, last);
+      if (t < k - 1) P.lj<T>(LJ_MID, b, false, near);
     }
     const int b = (k - 1) & 1;
-    P.atm<T>(b, last, profile ? o : -1);  // (i+1) % s == 0: F3b(x^{i+1})
+    // F2b(x^{i+1}) with its closing half kick and F3b(x^{i+1}) ((i+1) % s == 0) are independent: the LJ
+    // step runs on the side stream beside the triplet kernel, joined before the outer kicks.  A profiled
+    // pass launches them one after the other, so the triplet kernel's events time it alone.
+    md_system* s = P.s;
+    if (profile) {
+      P.lj<T>(LJ_LAST, b, last);
+      P.atm<T>(b, last, o);
+    } else {
+      cudaEventRecord(s->ev_fork, P.L.stream);
+      cudaStreamWaitEvent(s->side, s->ev_fork, 0);
+      P.lj_on<T>(Launch{s->side, P.L.sys}, LJ_LAST, b, last);
+      cudaEventRecord(s->ev_join, s->side);
+      P.atm<T>(b, last, -1);
+      cudaStreamWaitEvent(P.L.stream, s->ev_join, 0);
+    }
     P.combine<T>(last ? CB_LAST : CB_CONT, b, last);
   }
 }
@@ -1219,6 +1236,9 @@ md_status md_create_system(md_system** out, int64_t n, double box_L, const doubl
     CK(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
     s->own_stream = true;
   }
+  CK(cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming));
   CK(cudaMallocHost(&s->h_flags, 4 * FLG_N));
   CK(cudaMallocHost(&s->h_acc, 8 * ACC_N));
   CK(cudaMallocHost(&s->h_ctr, 8 * CTR_N));
@@ -1466,6 +1486,10 @@ md_status md_destroy_system(md_system* s) {
   if (s->h_flags) cudaFreeHost(s->h_flags);
   if (s->h_acc) cudaFreeHost(s->h_acc);
   if (s->h_ctr) cudaFreeHost(s->h_ctr);
+  if (s->side) cudaStreamSynchronize(s->side);
+  if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+  if (s->ev_join) cudaEventDestroy(s->ev_join);
+  if (s->side) cudaStreamDestroy(s->side);
   if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
   delete s;
   return MD_OK;
