@@ -654,6 +654,7 @@ __device__ __forceinline__ void zr_eval_any(const ZrK<T>& K, ZrSmem<T>& w, int x
 template <typename T>
 __global__ void __launch_bounds__(32 * kZrWarps, sizeof(T) == 4 ? R3B_ROT_MINB : 4)
     k_atm_rot(const SysDev* __restrict__ sys, const PItem* __restrict__ items, const int per) {
+  pdl_wait();
   extern __shared__ __align__(32) unsigned char zr_raw[];
   __shared__ ZrK<T> K;
   __shared__ unsigned long long s_cnt;
@@ -756,7 +757,7 @@ static bool zr_configure() {
 template <typename T>
 void launch_atm_rot(const Launch& L, const PItem* items, int nitems, int per) {
   if (nitems > 0 && zr_configure<T>())
-    k_atm_rot<T><<<nitems, 32 * kZrWarps, zr_smem_bytes<T>(), L.stream>>>(L.sys, items, per);
+    launch_kernel(L, k_atm_rot<T>, nitems, 32 * kZrWarps, zr_smem_bytes<T>(), L.sys, items, per);
 }
 template void launch_atm_rot<float>(const Launch&, const PItem*, int, int);
 template void launch_atm_rot<double>(const Launch&, const PItem*, int, int);

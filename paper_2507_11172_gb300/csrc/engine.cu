@@ -749,6 +749,7 @@ md_status run_plan(md_system* s, int n_outer, int k, bool init, bool safe) {
   md_status st = ensure_events(s, 2 * nev);
   if (st != MD_OK) return st;
   Plan P{s, Launch{s->stream, s->d_sys}};
+  P.L.pdl = !prof;  // the captured plan: programmatic dependent launches (section "launchers")
   auto key = std::make_tuple(init ? -1 - n_outer : n_outer, k, s->cur, safe ? 1 : 0, prof ? 1 : 0);
   if (prof) {
     // profiling: direct launches so the ATM kernel can be timed with events recorded on the

@@ -189,6 +189,7 @@ template <> __device__ __forceinline__ double recip_fast<double>(double x) { ret
 #endif
 template <typename T, bool kE, int kPer>
 __global__ void __launch_bounds__(kPer, R3B_LJ_THREADS_PER_SM / kPer) k_lj(const SysDev* __restrict__ sys, const PItem* __restrict__ items) {
+  pdl_wait();
   static_assert(kPer % 32 == 0 && kLjTeam == 1, "LJ blocks of whole warps, one thread per particle");
   using T4 = typename V4<T>::type;
   __shared__ T4 s_off[64];
@@ -371,6 +372,7 @@ __global__ void __launch_bounds__(kPer, R3B_LJ_THREADS_PER_SM / kPer) k_lj(const
 // near-class kicks s_near dt/2 F3near / m closing this block and opening the next are added too.
 template <typename T>
 __global__ void __launch_bounds__(256) k_kick(const SysDev* __restrict__ sys, const PItem* __restrict__ items) {
+  pdl_wait();
   const PItem it = items[blockIdx.x];
   const SysDev& S = sys[it.sys];
   const int mode = item_mode(S, it.mode);
@@ -527,6 +529,7 @@ template <typename T>
 __global__ void __launch_bounds__(kAtmThreads, 3)
     k_atm(const SysDev* __restrict__ sys, const CItem* __restrict__ items, int nitems,
           const uint16_t* __restrict__ gtable, int smax) {
+  pdl_wait();
   using T4 = typename V4<T>::type;
   extern __shared__ __align__(16) unsigned char smem[];
   const AtmLayout Ly = atm_layout<T>(smax);
@@ -971,6 +974,7 @@ constexpr int kMaxFull = 128;  // neighbours within r_c3 of one particle
 template <typename T>
 __global__ void __launch_bounds__(32 * kPaWarps)
     k_atm_pa(const SysDev* __restrict__ sys, const PItem* __restrict__ items, const uint16_t* __restrict__ gtable) {
+  pdl_wait();
   using T4 = typename V4<T>::type;
   __shared__ T4 s_nd[kPaWarps][kMaxFull];
   __shared__ int s_idx[kPaWarps][kMaxFull];
@@ -1149,6 +1153,7 @@ __global__ void __launch_bounds__(32 * kPaWarps)
 // ============================================================== combine + outer kicks
 template <typename T>
 __global__ void __launch_bounds__(256) k_combine(const SysDev* __restrict__ sys, const PItem* __restrict__ items) {
+  pdl_wait();
   __shared__ double red[32];
   const PItem it = items[blockIdx.x];
   const SysDev& S = sys[it.sys];
@@ -1256,6 +1261,7 @@ __global__ void __launch_bounds__(256) k_combine(const SysDev* __restrict__ sys,
 // opening kicks (outer F3, inner F2) and first drift of a call
 template <typename T>
 __global__ void __launch_bounds__(256) k_start(const SysDev* __restrict__ sys, const PItem* __restrict__ items) {
+  pdl_wait();
   using T4 = typename V4<T>::type;
   const PItem it = items[blockIdx.x];
   const SysDev& S = sys[it.sys];
@@ -1293,6 +1299,7 @@ __global__ void __launch_bounds__(256) k_start(const SysDev* __restrict__ sys, c
 }
 
 __global__ void __launch_bounds__(256) k_kinetic(const SysDev* __restrict__ sys, const PItem* __restrict__ items) {
+  pdl_wait();
   __shared__ double red[32];
   const PItem it = items[blockIdx.x];
   const SysDev& S = sys[it.sys];
@@ -1345,9 +1352,9 @@ int atm_configure(int smax, int precision, int* smem_bytes) {
 template <typename T, int kPer>
 void launch_lj_per(const Launch& L, const PItem* items, int nitems, bool energy) {
   if (energy)
-    k_lj<T, true, kPer><<<nitems, kPer, 0, L.stream>>>(L.sys, items);
+    launch_kernel(L, k_lj<T, true, kPer>, nitems, kPer, 0, L.sys, items);
   else
-    k_lj<T, false, kPer><<<nitems, kPer, 0, L.stream>>>(L.sys, items);
+    launch_kernel(L, k_lj<T, false, kPer>, nitems, kPer, 0, L.sys, items);
 }
 // items of `block` particles (kLjBlocks), one thread each
 template <typename T>
@@ -1364,7 +1371,7 @@ template <typename T>
 void launch_atm(const Launch& L, const CItem* items, int nitems, int grid, int smax) {
   if (nitems <= 0) return;
   const int bytes = (int)atm_layout<T>(smax).total;
-  k_atm<T><<<grid, kAtmThreads, bytes, L.stream>>>(L.sys, items, nitems, g_table, smax);
+  launch_kernel(L, k_atm<T>, grid, kAtmThreads, bytes, L.sys, items, nitems, (const uint16_t*)g_table, smax);
 }
 // same launch with a caller-provided pair table (used by the allocation-free entry point)
 template <typename T>
@@ -1377,28 +1384,28 @@ template void launch_atm_table<float>(const Launch&, const CItem*, int, int, int
 
 template <typename T>
 void launch_atm_pa(const Launch& L, const PItem* items, int nitems) {
-  if (nitems > 0) k_atm_pa<T><<<nitems, 32 * kPaWarps, 0, L.stream>>>(L.sys, items, g_table);
+  if (nitems > 0) launch_kernel(L, k_atm_pa<T>, nitems, 32 * kPaWarps, 0, L.sys, items, (const uint16_t*)g_table);
 }
 template void launch_atm_pa<float>(const Launch&, const PItem*, int);
 template void launch_atm_pa<double>(const Launch&, const PItem*, int);
 
 template <typename T>
 void launch_kick(const Launch& L, const PItem* items, int nitems) {
-  if (nitems > 0) k_kick<T><<<nitems, 256, 0, L.stream>>>(L.sys, items);
+  if (nitems > 0) launch_kernel(L, k_kick<T>, nitems, 256, 0, L.sys, items);
 }
 template void launch_kick<float>(const Launch&, const PItem*, int);
 template void launch_kick<double>(const Launch&, const PItem*, int);
 
 template <typename T>
 void launch_combine(const Launch& L, const PItem* items, int nitems, int block) {
-  if (nitems > 0) k_combine<T><<<nitems, block, 0, L.stream>>>(L.sys, items);
+  if (nitems > 0) launch_kernel(L, k_combine<T>, nitems, block, 0, L.sys, items);
 }
 template <typename T>
 void launch_start(const Launch& L, const PItem* items, int nitems, int block) {
-  if (nitems > 0) k_start<T><<<nitems, block, 0, L.stream>>>(L.sys, items);
+  if (nitems > 0) launch_kernel(L, k_start<T>, nitems, block, 0, L.sys, items);
 }
 void launch_kinetic(const Launch& L, const PItem* items, int nitems, int block) {
-  if (nitems > 0) k_kinetic<<<nitems, block, 0, L.stream>>>(L.sys, items);
+  if (nitems > 0) launch_kernel(L, k_kinetic, nitems, block, 0, L.sys, items);
 }
 
 template void launch_lj<float>(const Launch&, const PItem*, int, bool, int);

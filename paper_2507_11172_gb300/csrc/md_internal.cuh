@@ -415,10 +415,37 @@ bool raise_smem_attr(const void* kernel, int bytes);
 void set_last_error(const char* msg);
 
 // ---------------------------------------------------------------- launchers
+// pdl: launch with programmatic dependent launch (the kernel's blocks may become resident while the
+// previous kernel of the stream drains; each such kernel starts with pdl_wait, which returns once
+// that kernel has completed and its memory is visible).  Used by the captured single-system plan.
 struct Launch {
   cudaStream_t stream;
   const SysDev* sys;  // device array of systems
+  bool pdl = false;
 };
+
+// first statement of every kernel of the plan: wait for the previous kernel of the stream (a hardware
+// dependency, no spin; a no-op when the kernel was launched without the PDL attribute)
+// (The next kernel is released implicitly as this grid's blocks exit: an explicit
+// griddepcontrol.launch_dependents at a kernel's start let waiting blocks of the next kernel take SM
+// slots and slowed the 100k outer step from 0.856 to 0.981 ms.)
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline void launch_kernel(const Launch& L, void (*kern)(KArgs...), unsigned grid, unsigned block, size_t smem,
+                          Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = L.stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = L.pdl ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
 
 // sort.cu
 void launch_bin_count(const Launch& L, const PItem* items, int nitems, int block);

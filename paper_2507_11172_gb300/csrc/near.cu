@@ -94,6 +94,7 @@ template <typename T> __host__ __device__ constexpr int near_slots() { return si
 
 template <typename T>
 __global__ void __launch_bounds__(kNearThreads) k_atm_near(const SysDev* __restrict__ sys, const PItem* __restrict__ items) {
+  pdl_wait();
   using T4 = typename V4<T>::type;
   constexpr int kSlots = near_slots<T>();
   __shared__ T4 s_nd[kSlots * kNearThreads];  // (d_x, d_y, d_z, |d|^2) of near node v at [v][thread]
@@ -211,7 +212,7 @@ __global__ void __launch_bounds__(kNearThreads) k_atm_near(const SysDev* __restr
 
 template <typename T>
 void launch_atm_near(const Launch& L, const PItem* items, int nitems) {
-  if (nitems > 0) k_atm_near<T><<<nitems, kNearThreads, 0, L.stream>>>(L.sys, items);
+  if (nitems > 0) launch_kernel(L, k_atm_near<T>, nitems, kNearThreads, 0, L.sys, items);
 }
 template void launch_atm_near<float>(const Launch&, const PItem*, int);
 template void launch_atm_near<double>(const Launch&, const PItem*, int);

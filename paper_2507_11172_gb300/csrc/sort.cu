@@ -11,6 +11,7 @@
 namespace r3b {
 
 __global__ void k_bin_count(const SysDev* __restrict__ sys, const PItem* __restrict__ items) {
+  pdl_wait();
   const PItem it = items[blockIdx.x];
   const SysDev& S = sys[it.sys];
   if (sort_idle(S, it.mode)) return;  // block-uniform
@@ -61,6 +62,7 @@ __global__ void k_bin_count(const SysDev* __restrict__ sys, const PItem* __restr
 // the order no longer depends on the arrival order of the binning's atomics.
 // Step 1 (per particle): the members of each cell, in arrival order.
 __global__ void k_cell_members(const SysDev* __restrict__ sys, const PItem* __restrict__ items) {
+  pdl_wait();
   const PItem it = items[blockIdx.x];
   const SysDev& S = sys[it.sys];
   if (sort_idle(S, it.mode)) return;
@@ -70,6 +72,7 @@ __global__ void k_cell_members(const SysDev* __restrict__ sys, const PItem* __re
 }
 // Step 2 (one warp per cell): rank of each member by (key, index) among its cell's members.
 __global__ void k_cell_rank(const SysDev* __restrict__ sys, const CItem* __restrict__ items, int nitems) {
+  pdl_wait();
   const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (w >= nitems) return;  // warp-uniform
   const CItem it = items[w];
@@ -96,6 +99,7 @@ __global__ void k_cell_rank(const SysDev* __restrict__ sys, const CItem* __restr
 // One 1024-thread CTA per system: exclusive scan of count[] into
 // cell_start[], count[] reset to zero, largest occupancy checked.
 __global__ void __launch_bounds__(1024) k_scan(const SysDev* __restrict__ sys, const SItem* __restrict__ items) {
+  pdl_wait();
   const SysDev& S = sys[items[blockIdx.x].sys];
   if (sort_idle(S, items[blockIdx.x].mode)) return;
   __shared__ int wsum[32];
@@ -156,6 +160,7 @@ __global__ void __launch_bounds__(1024) k_scan(const SysDev* __restrict__ sys, c
 
 template <typename T>
 __global__ void k_scatter(const SysDev* __restrict__ sys, const PItem* __restrict__ items) {
+  pdl_wait();
   using T4 = typename V4<T>::type;
   const PItem it = items[blockIdx.x];
   const SysDev& S = sys[it.sys];
@@ -207,6 +212,7 @@ __global__ void k_scatter(const SysDev* __restrict__ sys, const PItem* __restric
 template <typename T, int kListWarps>
 __global__ void __launch_bounds__(32 * kListWarps)
     k_listbuild(const SysDev* __restrict__ sys, const CItem* __restrict__ items, int smax) {
+  pdl_wait();
   using T4 = typename V4<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T4* sp = reinterpret_cast<T4*>(smem_raw);
@@ -402,11 +408,12 @@ __global__ void k_stamp(unsigned long long* out) {
 // skin / 2 since the last one (flag set by the drifts); the decision is taken once, for every kernel of
 // the binning, and the drift flag starts over.
 __global__ void k_sort_decide(const SysDev* __restrict__ sys) {
+  pdl_wait();
   const SysDev& S = sys[0];
   S.flags[FLG_DOSORT] = S.flags[FLG_SKIN] != 0 ? 1 : 0;
   S.flags[FLG_SKIN] = 0;
 }
-void launch_sort_decide(const Launch& L) { k_sort_decide<<<1, 1, 0, L.stream>>>(L.sys); }
+void launch_sort_decide(const Launch& L) { launch_kernel(L, k_sort_decide, 1, 1, 0, L.sys); }
 // the same for every member of a batch (one thread each)
 __global__ void k_sort_decide_all(const SysDev* __restrict__ sys, int ns) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -427,22 +434,22 @@ void launch_stamp(cudaStream_t s, unsigned long long* out) { k_stamp<<<1, 1, 0, 
 void launch_cell_order(const Launch& L, const PItem* pitems, int npitems, int block, const CItem* citems,
                        int ncitems) {
   if (npitems <= 0 || ncitems <= 0) return;
-  k_cell_members<<<npitems, block, 0, L.stream>>>(L.sys, pitems);
-  k_cell_rank<<<(ncitems + 7) / 8, 256, 0, L.stream>>>(L.sys, citems, ncitems);
+  launch_kernel(L, k_cell_members, npitems, block, 0, L.sys, pitems);
+  launch_kernel(L, k_cell_rank, (ncitems + 7) / 8, 256, 0, L.sys, citems, ncitems);
 }
 void launch_bin_count(const Launch& L, const PItem* items, int nitems, int block) {
-  if (nitems > 0) k_bin_count<<<nitems, block, 0, L.stream>>>(L.sys, items);
+  if (nitems > 0) launch_kernel(L, k_bin_count, nitems, block, 0, L.sys, items);
 }
 void launch_scan(const Launch& L, const SItem* items, int nitems) {
-  if (nitems > 0) k_scan<<<nitems, 1024, 0, L.stream>>>(L.sys, items);
+  if (nitems > 0) launch_kernel(L, k_scan, nitems, 1024, 0, L.sys, items);
 }
 template <typename T>
 void launch_scatter(const Launch& L, const PItem* items, int nitems, int block) {
-  if (nitems > 0) k_scatter<T><<<nitems, block, 0, L.stream>>>(L.sys, items);
+  if (nitems > 0) launch_kernel(L, k_scatter<T>, nitems, block, 0, L.sys, items);
 }
 template <typename T, int kW>
 static void launch_listbuild_w(const Launch& L, const CItem* items, int nitems, int smax, int bytes) {
-  k_listbuild<T, kW><<<nitems, 32 * kW, bytes, L.stream>>>(L.sys, items, smax);
+  launch_kernel(L, k_listbuild<T, kW>, nitems, 32 * kW, bytes, L.sys, items, smax);
 }
 // warps: warps per CTA (kListWarpChoices), a runtime choice of the autotuner
 template <typename T>
