@@ -49,8 +49,9 @@ typedef enum {
   MD_ERR_OOM = -2,            /* device memory (or the batch's memory budget) exhausted */
   MD_ERR_BOX_TOO_SMALL = -3,  /* L <= 3 * max(r_c2 + skin, r_c3): minimum image not unique */
   MD_ERR_NONFINITE = -4,      /* a position, velocity, force or energy became NaN/Inf */
-  MD_ERR_DEVICE_TIMEOUT = -5, /* reserved, never returned: no kernel of this library waits on another
-                                launch or on the host (each launch runs to completion on its own) */
+  MD_ERR_DEVICE_TIMEOUT = -5, /* a kernel's bounded wait for its own asynchronous shared-memory copies
+                                gave up (cell-tile LJ kernel); no kernel waits on another launch or on
+                                the host */
   MD_ERR_CUDA = -6,           /* a CUDA runtime call failed (message via md_last_error) */
   MD_ERR_STATE = -7,          /* call not valid in this state (e.g. ticket unknown) */
   MD_ERR_CAPACITY = -8,       /* a cell, neighbour list or triplet list exceeded its capacity */
@@ -82,6 +83,10 @@ typedef struct {
   int32_t list_warps;          /* pair-list build: warps per CTA (autotuned: 2, 4 or 8) */
   int32_t tuned_from_cache;    /* 1 if the last tuning reused the choices of an earlier system with the same
                                   key (N bucket, density bucket, r_c2, r_c3, skin, precision, classes) */
+  int32_t lj_kernel;           /* LJ kernel in use: 0 row kernel (one thread per particle, neighbour positions
+                                  gathered from global memory), 1 cell-tile kernel, 2 team kernel
+                                  (md_set_lj_kernel) */
+  int32_t lj_team;             /* team kernel: lanes per particle (autotuned: 4, 8 or 16) */
   int32_t reserved_;
 } md_stats;
 
@@ -207,6 +212,25 @@ md_status md_set_atm_kernel(md_system *s, int variant);
  * shape to the autotuner.  Every shape gives the same forces bit for bit.  Applied at the next call
  * that evaluates forces; MD_ERR_ARG for other values, MD_ERR_STATE while the system is in a batch. */
 md_status md_set_shapes(md_system *s, int lj_block, int list_warps, int rot_bases_per_warp);
+
+/* LJ kernel choice for the pair forces of Sec. 2.1 (LJ 12-6, every inner step of Algorithm 2; an
+ * autotuning knob like md_set_atm_kernel; both give the forces of the pair list within FP rounding):
+ *   0  row kernel: one thread per particle walks its pair-list row and gathers the neighbours'
+ *      positions from global memory (md_set_shapes' lj_block particles per block);
+ *   1  cell-tile kernel: one CTA per block of 2 x 2 x 2 cells copies the positions of the 4 x 4 x 4
+ *      cells around it into shared memory (bulk asynchronous copies completing on an mbarrier, waited
+ *      on with a bounded poll: MD_ERR_DEVICE_TIMEOUT if it gives up), then one thread per particle
+ *      walks its pair-list row against shared memory; used where that staging fits in shared memory
+ *      (about 52 cap_cell particles), else 0;
+ *   2  team kernel: 4, 8 or 16 adjacent lanes per particle share its row (consecutive entries read
+ *      together, neighbour positions gathered from global memory), their compensated partial sums
+ *      combined by TwoSum; more warps resident than with one thread per particle;
+ *  -1  (default) time all of them (the row kernel with 32, 64 and 128 particles per block, the team
+ *      kernel with 4, 8 and 16 lanes per particle) on the system's first evaluation and keep the
+ *      fastest (cached per key with the other choices).  Batches use the row kernel.
+ * Applied at the next call that evaluates forces (the cached forces are recomputed); MD_ERR_ARG for
+ * other values, MD_ERR_STATE while the system is in a batch. */
+md_status md_set_lj_kernel(md_system *s, int variant);
 
 /* Number of particles, box side and precision of a handle (the inputs of Algorithm 2). */
 md_status md_get_info(md_system *s, int64_t *n, double *box_L, int *precision);

@@ -39,7 +39,8 @@ class md_stats(ctypes.Structure):
                 ("atm_timed", ctypes.c_uint64), ("max_cell_count", ctypes.c_int32),
                 ("cells_per_side", ctypes.c_int32), ("atm_kernel", ctypes.c_int32), ("atm_bases_per_warp", ctypes.c_int32),
                 ("near_triplets_last", ctypes.c_uint64), ("lj_block", ctypes.c_int32), ("list_warps", ctypes.c_int32),
-                ("tuned_from_cache", ctypes.c_int32), ("reserved_", ctypes.c_int32)]
+                ("tuned_from_cache", ctypes.c_int32), ("lj_kernel", ctypes.c_int32),
+                ("lj_team", ctypes.c_int32), ("reserved_", ctypes.c_int32)]
 
 
 _lib = None
@@ -63,6 +64,7 @@ SIGNATURES = {
     "md_get_stats": (_I, [_P, ctypes.POINTER(md_stats)]),
     "md_set_profiling": (_I, [_P, _I]),
     "md_set_atm_kernel": (_I, [_P, _I]),
+    "md_set_lj_kernel": (_I, [_P, _I]),
     "md_set_shapes": (_I, [_P, _I, _I, _I]),
     "md_set_distance_classes": (_I, [_P, _D, _I]),
     "md_get_near_forces": (_I, [_P, _P]),
@@ -220,6 +222,10 @@ def md_set_atm_kernel(h, variant: int):
     _check(load().md_set_atm_kernel(h, int(variant)), "md_set_atm_kernel")
 
 
+def md_set_lj_kernel(h, variant: int):
+    _check(load().md_set_lj_kernel(h, int(variant)), "md_set_lj_kernel")
+
+
 def md_set_shapes(h, lj_block: int = 0, list_warps: int = 0, rot_bases_per_warp: int = 0):
     _check(load().md_set_shapes(h, int(lj_block), int(list_warps), int(rot_bases_per_warp)), "md_set_shapes")
 
@@ -338,7 +344,7 @@ class System:
 
     @classmethod
     def create(cls, pos, box_L, vel=None, mass=1.0, precision=MD_FP32, eps=1.0, sigma=1.0, rc_pair=2.5, nu=0.0,
-               rc_triplet=2.5, skin=None, atm_kernel=-1):
+               rc_triplet=2.5, skin=None, atm_kernel=-1, lj_kernel=-1):
         h = md_create_system(pos, box_L, vel, mass, precision)
         try:
             if skin is not None:
@@ -346,6 +352,8 @@ class System:
             md_set_potentials(h, eps, sigma, rc_pair, nu, rc_triplet)
             if atm_kernel != -1:
                 md_set_atm_kernel(h, atm_kernel)
+            if lj_kernel != -1:
+                md_set_lj_kernel(h, lj_kernel)
         except Exception:
             md_destroy_system(h)
             raise

@@ -108,7 +108,12 @@ struct md_system {
   int nblocks_pa = 0;
   int nblocks_rot = 0;
   int rot_per = rot_bases_per_item(0) / kRotWarps;  // rotation kernel: bases per warp in a work item
-  int lj_block = kLjPer;                 // LJ kernel: threads (particles) per block
+  int lj_block = kLjPer;                 // LJ row kernel: threads (particles) per block
+  int lj_kernel = 1;                     // LJ kernel: 0 row kernel (global gathers), 1 cell-tile kernel,
+                                         // 2 team kernel (lj_team lanes per particle)
+  int lj_kernel_req = -1;                // md_set_lj_kernel (-1: autotuned)
+  int lj_team = 8;                       // team kernel: lanes per particle (autotuned: 4, 8 or 16)
+  bool lj_tile_ok = false;               // the cell-tile kernel fits in shared memory for cap_cell
   int list_warps = kListWarpsDefault;    // pair-list build: warps per CTA
   bool tuned_from_cache = false;         // the last tuning reused another system's choices
   int lj_block_req = 0, list_warps_req = 0, rot_per_req = 0;  // md_set_shapes (0: autotuned)
@@ -124,6 +129,9 @@ struct md_system {
   double e_kin = 0, u2 = 0, u3 = 0, w2 = 0, w3 = 0;
   // batch membership
   md_batch* batch = nullptr;
+  // in a batch, or being admitted to one: LJ forces come from the batch's LJ kernel (the row kernel) from
+  // the admission's first evaluation on, so a request gives the same bits in any mix
+  bool batch_lj = false;
   // calls since the last skin replay that started in safe mode (0: start with the normal plan), and the
   // length of such a run before the normal plan is tried again
   int safe_calls = 0, safe_span = 4;
@@ -136,7 +144,10 @@ struct md_system {
 
 namespace {
 
-enum KTag { T_BIN = 1, T_SCATTER, T_LIST, T_LJ, T_COMB, T_START, T_KIN, T_ATMPA, T_ATMROT, T_KICK, T_ATMNEAR };
+enum KTag { T_BIN = 1, T_SCATTER, T_LIST, T_LJ, T_COMB, T_START, T_KIN, T_ATMPA, T_ATMROT, T_KICK, T_ATMNEAR, T_LJT,
+            T_LJM4, T_LJM8, T_LJM16 };  // T_LJM<team>: team LJ kernel items
+int ljm_tag(int team) { return team == 4 ? T_LJM4 : (team == 16 ? T_LJM16 : T_LJM8); }
+int ljm_per(int tag) { return kLjmThreads / (tag == T_LJM4 ? 4 : (tag == T_LJM16 ? 16 : 8)); }
 
 void free_items(md_system* s) {
   for (void* p : s->item_allocs) cudaFree(p);
@@ -422,16 +433,20 @@ PItem* pitems_for(md_system* s, int tag, int mode, int buf) {
   if (it != s->pitems.end()) return it->second;
   std::vector<PItem> v;
   const int per = (tag == T_LJ)      ? s->lj_block
+                  : (tag == T_LJT)    ? 1
+                  : (tag >= T_LJM4)   ? ljm_per(tag)
                   : (tag == T_ATMPA)  ? kPaPerBlock
                   : (tag == T_ATMROT) ? kRotWarps * s->rot_per
                   : (tag == T_ATMNEAR) ? kNearThreads
                                       : kBlock;
   const int nb = (tag == T_LJ)       ? (int)((s->n + s->lj_block - 1) / s->lj_block)
+                 : (tag == T_LJT)    ? lj_tile_blocks(s->nc)
+                 : (tag >= T_LJM4)   ? (int)((s->n + ljm_per(tag) - 1) / ljm_per(tag))
                  : (tag == T_ATMPA)  ? s->nblocks_pa
                  : (tag == T_ATMROT) ? s->nblocks_rot
                  : (tag == T_ATMNEAR) ? (int)((s->n + kNearThreads - 1) / kNearThreads)
                                      : s->nblocks;
-  if (tag == T_LJ || tag == T_ATMROT || tag == T_KICK || tag == T_ATMNEAR) {
+  if (tag == T_LJ || tag == T_ATMROT || tag == T_KICK || tag == T_ATMNEAR || tag >= T_LJM4) {
     // Gather kernels: the block scheduler hands consecutive blocks to different SMs, so blocks
     // b, b + nsm, b + 2 nsm, ... tend to share an SM.  Giving those blocks adjacent particle ranges
     // keeps each SM's neighbour gathers within one region of the box (L1 reuse); the order of the
@@ -479,6 +494,11 @@ md_status prepare_items(md_system* s) {
       pitems_for(s, T_LJ, LJ_INIT | E, b);
       pitems_for(s, T_LJ, LJ_MID | E, b);
       pitems_for(s, T_LJ, LJ_LAST | E, b);
+      pitems_for(s, T_LJT, LJ_INIT | E, b);
+      pitems_for(s, T_LJT, LJ_MID | E, b);
+      pitems_for(s, T_LJT, LJ_LAST | E, b);
+      for (int team : kLjTeams)
+        for (int kind : {LJ_INIT, LJ_MID, LJ_LAST}) pitems_for(s, ljm_tag(team), kind | E, b);
       pitems_for(s, T_KICK, LJ_MID, b);
       pitems_for(s, T_KICK, LJ_LAST, b);
       pitems_for(s, T_COMB, CB_INIT | E, b);
@@ -531,6 +551,9 @@ md_status configure_atm(md_system* s) {
     return MD_ERR_CAPACITY;
   }
   s->atm_grid = std::min(s->ncell, per_sm * device_sm_count());
+  // the cell-tile LJ kernel where its staging fits in shared memory (else the row kernel)
+  s->lj_tile_ok = lj_tile_configure(lj_tile_capacity(s->cap_cell), s->precision) > 0;
+  if (!s->lj_tile_ok) s->lj_kernel = 0;
   return MD_OK;
 }
 
@@ -600,8 +623,17 @@ struct Plan {
   void lj(int kind, int buf, bool energy, bool near = false) { lj_on<T>(L, kind, buf, energy, near); }
   template <typename T>
   void lj_on(const Launch& Lx, int kind, int buf, bool energy, bool near = false) {
-    launch_lj<T>(Lx, pitems_for(s, T_LJ, kind | (energy ? M_ENERGY : 0), buf),
-                 padded_blocks((int)((s->n + s->lj_block - 1) / s->lj_block)), energy, s->lj_block);
+    const int ljk = s->batch_lj ? 0 : s->lj_kernel;
+    if (ljk == 2) {
+      const int tag = ljm_tag(s->lj_team);
+      launch_lj_team<T>(Lx, pitems_for(s, tag, kind | (energy ? M_ENERGY : 0), buf),
+                        padded_blocks((int)((s->n + ljm_per(tag) - 1) / ljm_per(tag))), energy, s->lj_team);
+    } else if (ljk == 1)
+      launch_lj_tile<T>(Lx, pitems_for(s, T_LJT, kind | (energy ? M_ENERGY : 0), buf), lj_tile_blocks(s->nc), energy,
+                        lj_tile_capacity(s->cap_cell));
+    else
+      launch_lj<T>(Lx, pitems_for(s, T_LJ, kind | (energy ? M_ENERGY : 0), buf),
+                   padded_blocks((int)((s->n + s->lj_block - 1) / s->lj_block)), energy, s->lj_block);
     if (near) atm_near<T>(buf);
     if (kind != LJ_INIT)
       launch_kick<T>(Lx, pitems_for(s, T_KICK, kind | (near ? M_NEAR : 0), buf), padded_blocks(s->nblocks));
@@ -816,7 +848,11 @@ md_status status_from_flags(md_system* s) {
     g_last_error = "distance classes: more than 64 near-class candidates (neighbours above within r_a + skin)";
     return MD_ERR_CAPACITY;
   }
-  if (err & (ERR_CELL_CAP | ERR_NBR_CAP | ERR_HALF_CAP)) return MD_ERR_CAPACITY;
+  if (err & ERR_TIMEOUT) {
+    g_last_error = "LJ cell-tile kernel: a bounded wait for its shared-memory copies gave up";
+    return MD_ERR_DEVICE_TIMEOUT;
+  }
+  if (err & (ERR_CELL_CAP | ERR_NBR_CAP | ERR_HALF_CAP | ERR_STAGE_CAP)) return MD_ERR_CAPACITY;
   return MD_OK;
 }
 
@@ -875,7 +911,7 @@ md_status set_lj_block(md_system* s, int block) {
 // keyed on (device, N in half-octave buckets, density in steps of 0.025, r_c2, r_c3, skin, precision,
 // distance classes on/off): a later system with the same key skips the trials.
 struct TuneChoice {
-  int variant, rot_per, lj_block, list_warps;
+  int variant, rot_per, lj_block, list_warps, lj_kernel, lj_team;
 };
 using TuneKey = std::tuple<int, int, int, int, int, int, int, int>;
 std::mutex g_tune_mu;
@@ -897,6 +933,9 @@ md_status tune_apply(md_system* s, const TuneChoice& c) {
   if (st == MD_OK) st = set_lj_block(s, s->lj_block_req ? s->lj_block_req : c.lj_block);
   if (st != MD_OK) return st;
   s->list_warps = s->list_warps_req ? s->list_warps_req : c.list_warps;
+  s->lj_kernel = s->lj_kernel_req >= 0 ? s->lj_kernel_req : c.lj_kernel;
+  if (s->lj_kernel == 1 && !s->lj_tile_ok) s->lj_kernel = 0;
+  s->lj_team = c.lj_team;
   clear_graphs(s);
   return MD_OK;
 }
@@ -940,7 +979,7 @@ md_status tune(md_system* s) {
   s->atm_variant = 0;
   st = run_plan(s, 0, 1, true, false);  // binning + pair list at the current positions
   if (st != MD_OK) return st;
-  TuneChoice best{0, s->rot_per, s->lj_block, s->list_warps};
+  TuneChoice best{0, s->rot_per, s->lj_block, s->list_warps, 0, s->lj_team};
   float tbest = 1e30f;
   // triplet kernel: (variant, bases per warp of the rotation kernel's work items)
 #ifdef R3B_ROT_SHAPE_ONLY  // build-time knob: a single rotation shape instead of the tuned choice
@@ -986,6 +1025,47 @@ md_status tune(md_system* s) {
       best.lj_block = block;
     }
   }
+  // the cell-tile LJ kernel against the best row-kernel block (same forces within rounding)
+  if (s->lj_tile_ok) {
+    float ms = 0.f;
+    st = time_launches(s, [&] {
+      const PItem* items = pitems_for(s, T_LJT, LJ_INIT, s->cur);
+      const int smax = lj_tile_capacity(s->cap_cell);
+      if (s->precision)
+        launch_lj_tile<double>(P.L, items, lj_tile_blocks(s->nc), false, smax);
+      else
+        launch_lj_tile<float>(P.L, items, lj_tile_blocks(s->nc), false, smax);
+    }, &ms);
+    if (st != MD_OK) return st;
+    if (ms < tbest) {
+      tbest = ms;
+      best.lj_kernel = 1;
+    }
+  }
+  // the team kernel with 4, 8 and 16 lanes per particle (its fastest team is kept even where another
+  // kernel wins: md_set_lj_kernel(2) then uses it)
+  float tteam = 1e30f;
+  for (int team : kLjTeams) {
+    float ms = 0.f;
+    st = time_launches(s, [&] {
+      const int tag = ljm_tag(team);
+      const PItem* items = pitems_for(s, tag, LJ_INIT, s->cur);
+      const int nb = padded_blocks((int)((s->n + ljm_per(tag) - 1) / ljm_per(tag)));
+      if (s->precision)
+        launch_lj_team<double>(P.L, items, nb, false, team);
+      else
+        launch_lj_team<float>(P.L, items, nb, false, team);
+    }, &ms);
+    if (st != MD_OK) return st;
+    if (ms < tteam) {
+      tteam = ms;
+      best.lj_team = team;
+    }
+  }
+  if (tteam < tbest) {
+    tbest = tteam;
+    best.lj_kernel = 2;
+  }
   // pair-list build warps per CTA (the lists are the same for every choice)
   tbest = 1e30f;
   for (int wps : {2, 4, 8}) {
@@ -1029,7 +1109,8 @@ md_status do_call(md_system* s, int n_outer, int k, double dt_outer) {
   for (int attempt = 0; attempt < 6; ++attempt) {
     // after a skin replay the next calls start in safe mode (adaptive binning; a first attempt that
     // would be replayed anyway costs a whole call); after safe_span calls the normal plan is tried again
-    const bool safe = attempt > 0 ? (s->h_flags[FLG_SKIN] && !(s->h_flags[FLG_ERR] & (ERR_CELL_CAP | ERR_NBR_CAP)))
+    const bool safe = attempt > 0 ? (s->h_flags[FLG_SKIN] &&
+                                     !(s->h_flags[FLG_ERR] & (ERR_CELL_CAP | ERR_NBR_CAP | ERR_STAGE_CAP)))
                                   : s->safe_calls > 0;
     md_status st = upload_desc(s, dt_in, dt_outer);
     if (st != MD_OK) return st;
@@ -1050,7 +1131,7 @@ md_status do_call(md_system* s, int n_outer, int k, double dt_outer) {
     if (st != MD_OK) return st;
     const int err = s->h_flags[FLG_ERR];
     const bool skin_bad = s->h_flags[FLG_SKIN] != 0 && !safe;
-    const bool cap_bad = (err & (ERR_CELL_CAP | ERR_NBR_CAP)) != 0;
+    const bool cap_bad = (err & (ERR_CELL_CAP | ERR_NBR_CAP | ERR_STAGE_CAP)) != 0;
     // the rotation and per-particle kernels hold shorter half lists than the cell kernel
     const bool half_bad = (err & ERR_HALF_CAP) != 0 && s->atm_variant != 0;
     s->stats.max_cell_count = s->h_flags[FLG_MAXCELL];
@@ -1098,6 +1179,8 @@ md_status do_call(md_system* s, int n_outer, int k, double dt_outer) {
     if (cap_bad) {
       if (err & ERR_CELL_CAP) s->cap_cell = std::max(s->cap_cell + 8, s->h_flags[FLG_MAXCELL] + 8);
       if (err & ERR_NBR_CAP) s->maxnb = s->maxnb * 3 / 2 + 16;
+      if (err & ERR_STAGE_CAP)  // the cell-tile LJ staging follows cap_cell (lj_tile_capacity)
+        s->cap_cell = std::max(s->cap_cell + 8, (s->h_flags[FLG_LJSTAGE] - 64 + 51) / 52 + 8);
       st = rebuild(s, true);
       if (st != MD_OK) return st;
     } else if (half_bad) {
@@ -1427,6 +1510,8 @@ md_status md_get_stats(md_system* s, md_stats* out) {
   s->stats.atm_kernel = s->atm_variant;
   s->stats.atm_bases_per_warp = s->rot_per;
   s->stats.lj_block = s->lj_block;
+  s->stats.lj_kernel = s->lj_kernel;
+  s->stats.lj_team = s->lj_team;
   s->stats.list_warps = s->list_warps;
   s->stats.tuned_from_cache = s->tuned_from_cache ? 1 : 0;
   *out = s->stats;
@@ -1444,6 +1529,17 @@ md_status md_set_atm_kernel(md_system* s, int variant) {
   if (!s || variant < -1 || variant > 2) return MD_ERR_ARG;
   s->atm_variant_req = variant;
   s->atm_variant = -1;
+  clear_graphs(s);
+  s->forces_valid = false;
+  s->energy_valid = false;
+  return MD_OK;
+}
+
+md_status md_set_lj_kernel(md_system* s, int variant) {
+  if (!s || variant < -1 || variant > 2) return MD_ERR_ARG;
+  if (s->batch) return MD_ERR_STATE;
+  s->lj_kernel_req = variant;
+  s->atm_variant = -1;  // applied with the next tuning (the cached choices fill the rest)
   clear_graphs(s);
   s->forces_valid = false;
   s->energy_valid = false;
@@ -1875,6 +1971,11 @@ md_status batch_admit(md_batch* b) {
       break;
     }
     b->queue.erase(b->queue.begin());
+    if (!s->batch_lj) {
+      s->batch_lj = true;
+      s->forces_valid = false;  // forces from the batch's LJ kernel
+      clear_graphs(s);
+    }
     md_status st = ensure_resident(s);
     if (st == MD_OK) st = ensure_forces(s);
     if (st == MD_OK && r.n_outer > 0) {
@@ -1886,6 +1987,10 @@ md_status batch_admit(md_batch* b) {
         cudaError_t e = cudaStreamSynchronize(s->stream);
         if (e != cudaSuccess) st = cuda_fail(e, "batch start");
       }
+    }
+    if (st != MD_OK || r.n_outer == 0) {
+      s->batch_lj = false;
+      clear_graphs(s);
     }
     if (st != MD_OK) {
       r.state = RQ_FAILED;
@@ -1917,6 +2022,7 @@ void batch_retire(md_batch* b, std::vector<uint64_t>& leaving) {
   for (uint64_t tk : leaving) {
     Request& r = b->req[tk];
     r.s->batch = nullptr;
+    r.s->batch_lj = false;
     clear_graphs(r.s);
   }
   b->dirty = true;
@@ -2172,6 +2278,8 @@ md_status md_batch_destroy(md_batch* b) {
   for (uint64_t tk : b->resident) {
     Request& r = b->req[tk];
     r.s->batch = nullptr;
+    r.s->batch_lj = false;
+    clear_graphs(r.s);
     r.s->forces_valid = false;  // interrupted mid-request: the cached forces are not at a full step
     r.s->energy_valid = false;
   }

@@ -170,7 +170,30 @@ __device__ __forceinline__ void take_near(const SysDev& S, int p, double f[3]) {
 // velocity-Verlet kick/drift of Algorithm 2 follows in k_kick.
 
 // read-only cached load of a 4-vector (the position buffer read by a kernel is never written by it)
+#ifdef R3B_LJ_POS_EVICT_LAST
+__device__ __forceinline__ float4 ldg4(const float4* p) {
+  float4 v;
+  asm("ld.global.nc.L1::evict_last.v4.f32 {%0, %1, %2, %3}, [%4];"
+      : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+      : "l"(p));
+  return v;
+}
+#else
 __device__ __forceinline__ float4 ldg4(const float4* p) { return __ldg(p); }
+#endif
+// four pair-list entries: each row is streamed once per launch, so its lines are marked for early
+// eviction from L1 (the neighbour positions, reused by many threads of the SM, stay)
+__device__ __forceinline__ int4 ld_entries(const int4* p) {
+#ifdef R3B_LJ_LIST_PLAIN
+  return __ldg(p);
+#else
+  int4 v;
+  asm("ld.global.nc.L1::evict_first.v4.s32 {%0, %1, %2, %3}, [%4];"
+      : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+      : "l"(p));
+  return v;
+#endif
+}
 __device__ __forceinline__ double4_32a ldg4(const double4_32a* p) { return *p; }
 
 template <typename T> __device__ __forceinline__ T recip_fast(T x);
@@ -231,7 +254,7 @@ __global__ void __launch_bounds__(kPer, R3B_LJ_THREADS_PER_SM / kPer) k_lj(const
                                (int)(kPadCode << kNbrShift), (int)(kPadCode << kNbrShift));
     // entries of a group, padded beyond the row's length
     auto entries = [&](int t0) {
-      int4 e = t0 < cnt ? __ldg(row4 + (t0 >> 2)) : pad;
+      int4 e = t0 < cnt ? ld_entries(row4 + (t0 >> 2)) : pad;
       if (t0 + 1 >= cnt) e.y = pad.y;
       if (t0 + 2 >= cnt) e.z = pad.z;
       if (t0 + 3 >= cnt) e.w = pad.w;

@@ -33,8 +33,9 @@ enum : int {
   ERR_NBR_CAP = 2,    // an LJ neighbour list overflowed
   ERR_HALF_CAP = 4,   // an ATM half list overflowed kMaxHalf
   ERR_NONFINITE = 8,  // NaN / Inf in positions, velocities or forces
-  // 16: unused (no kernel of this library waits on another launch or on the host)
+  ERR_TIMEOUT = 16,   // a bounded wait on a CTA's own bulk copies gave up (cell-tile LJ kernel)
   ERR_NEAR_CAP = 32,  // distance classes: a near-class candidate list overflowed kHalfCap
+  ERR_STAGE_CAP = 64, // cell-tile LJ kernel: a block's region held more particles than its staging
 };
 
 // accumulator slots in SysDev::acc (double)
@@ -43,7 +44,8 @@ enum : int { ACC_U2 = 0, ACC_W2 = 1, ACC_U3 = 2, ACC_W3 = 3, ACC_EK = 4, ACC_N =
 enum : int { CTR_TRIPLETS = 0, CTR_GUARD = 1, CTR_NEAR = 2, CTR_N = 4 };  // CTR_NEAR: near-class triplets
 // flag slots in SysDev::flags (int)
 // FLG_STATE: state transfer; FLG_DOSORT: adaptive binning, a binning is due before the next LJ evaluation
-enum : int { FLG_ERR = 0, FLG_SKIN = 1, FLG_MAXCELL = 2, FLG_STATE = 3, FLG_DOSORT = 4, FLG_N = 8 };
+// FLG_LJSTAGE: largest staging need (particles + 1) of a cell-tile LJ block that overflowed
+enum : int { FLG_ERR = 0, FLG_SKIN = 1, FLG_MAXCELL = 2, FLG_STATE = 3, FLG_DOSORT = 4, FLG_LJSTAGE = 5, FLG_N = 8 };
 
 // Device-resident description of one system.  Kernels read it from global
 // memory at run time (never from constant memory) so graphs stay valid when
@@ -477,6 +479,36 @@ constexpr int kLjTeam = R3B_LJ_TEAM;  // a power of two dividing 32
 constexpr int kLjParticles = kLjPer / kLjTeam;
 constexpr int kLjBlocks[3] = {32, 64, 128};  // LJ block sizes the autotuner tries (kLjPer by default)
 template <typename T> void launch_lj(const Launch& L, const PItem* items, int nitems, bool energy, int block);
+// cell-tile LJ kernel (lj_tile.cu): one CTA of kLjtThreads threads per block of 2 x 2 x 2 cells, items
+// with begin = block index; smax staged slots (lj_tile_capacity)
+#ifndef R3B_LJT_THREADS
+#define R3B_LJT_THREADS 256
+#endif
+#ifndef R3B_LJT_MINB
+#define R3B_LJT_MINB 4
+#endif
+constexpr int kLjtThreads = R3B_LJT_THREADS;
+constexpr int kLjtMinBlocks = R3B_LJT_MINB;
+// staged slots of a block's 4^3 region cells: 64 cells of mean occupancy below 0.8 cap_cell, with a
+// margin of several standard deviations, plus the padding slot; more raises ERR_STAGE_CAP (and a
+// larger cap_cell)
+inline int lj_tile_capacity(int cap_cell) { return 52 * cap_cell + 64; }
+inline int lj_tile_blocks(int nc) {
+  const int nb = (nc + 1) / 2;
+  return nb * nb * nb;
+}
+template <typename T> void launch_lj_tile(const Launch& L, const PItem* items, int nitems, bool energy, int smax);
+// raises the kernels' dynamic shared-memory limit; bytes, or -1 if the device refuses the size
+int lj_tile_configure(int smax, int precision);
+// team LJ kernel (lj_tile.cu): team lanes (4, 8 or 16) per particle, blocks of kLjmThreads threads, items
+// of kLjmThreads / team particles
+constexpr int kLjmThreads = 256;
+#ifndef R3B_LJM_MINB
+#define R3B_LJM_MINB 8
+#endif
+constexpr int kLjmMinBlocks = R3B_LJM_MINB;  // resident blocks per SM the registers are sized for
+constexpr int kLjTeams[3] = {4, 8, 16};
+template <typename T> void launch_lj_team(const Launch& L, const PItem* items, int nitems, bool energy, int team);
 template <typename T> void launch_atm(const Launch& L, const CItem* items, int nitems, int grid, int smax);
 // staged-particle capacity of an ATM CTA: the particles within r_c of a base cell (edge >= r_c)
 // occupy at most the volume of about 21 cells (16 cells plus margin is sized for the typical mean

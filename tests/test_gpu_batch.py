@@ -204,12 +204,13 @@ def test_served_fp32_matches_the_oracle_and_equals_alone_bitwise(gpu_lib):
         (per-particle relative error <= 1e-5, every particle), and its energies (E_kin, U2, U3) agree
         within 1e-6 of E_kin + |U2| + |U3|;
       * every request's final state and forces equal the same request run alone bit for bit (the
-        triplet forces are summed in fixed point, so the order in which launches mix does not matter)."""
+        triplet forces are summed in fixed point, so the order in which launches mix does not matter;
+        batches use the row LJ kernel, so the lone run uses it too)."""
     r3 = gpu_lib
     ws = _served_mix(131)
     alone = []
     for w in ws:
-        with r3.System.create(w.x, w.L, w.v, precision=0, nu=NU, atm_kernel=2) as s:
+        with r3.System.create(w.x, w.L, w.v, precision=0, nu=NU, atm_kernel=2, lj_kernel=0) as s:
             s.step(w.n_outer, w.k_inner, w.dt_outer)
             alone.append((*s.state(), *s.forces()))
     hs = []

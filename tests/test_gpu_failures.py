@@ -30,7 +30,8 @@ def _w(n, rho, T, k, seed):
 
 
 def _alone(r3, w, n_outer):
-    with r3.System.create(w.x, w.L, w.v, precision=0, nu=NU, atm_kernel=2) as s:
+    # the LJ kernel batches use (row kernel): the same bits alone and in the batch
+    with r3.System.create(w.x, w.L, w.v, precision=0, nu=NU, atm_kernel=2, lj_kernel=0) as s:
         s.step(n_outer, w.k_inner, w.dt_outer)
         return s.state()
 
