@@ -510,14 +510,68 @@ __device__ __forceinline__ void zr_atomic_add(const ZrK<T>& K, int j, T fx, T fy
   }
 }
 
-// node force F_v = G_v - W_v d_v (unscaled) to its sum; W_v d_v into F_i
-template <typename T>
-__device__ __forceinline__ void zr_emit(const ZrK<T>& K, const typename V4<T>::type d, int j, T W, T Gx, T Gy, T Gz,
-                                        T& fix, T& fiy, T& fiz) {
-  fix = fma(W, d.x, fix);
-  fiy = fma(W, d.y, fiy);
-  fiz = fma(W, d.z, fiz);
-  zr_atomic_add<T>(K, j, fma(-W, d.x, Gx), fma(-W, d.y, Gy), fma(-W, d.z, Gz));
+// A lane's share of the base force F_i.  FP64: the sums of W_v d_v.  FP32: the sums of the lane's
+// fixed-point node terms; the triplet forces of a base add up to zero (Newton 3), so F_i is minus the
+// sum of its nodes' terms, taken exactly in fixed point (each base's terms then cancel exactly).
+template <typename T> struct ZrFi;
+template <> struct ZrFi<double> {
+  double x = 0.0, y = 0.0, z = 0.0;
+};
+template <> struct ZrFi<float> {
+  long long x = 0, y = 0, z = 0;
+};
+
+// node force F_v = G_v - W_v d_v (unscaled) to its sum, and its share of F_i
+__device__ __forceinline__ void zr_emit(const ZrK<double>& K, const double4_32a d, int j, double W, double Gx,
+                                        double Gy, double Gz, ZrFi<double>& fi) {
+  fi.x = fma(W, d.x, fi.x);
+  fi.y = fma(W, d.y, fi.y);
+  fi.z = fma(W, d.z, fi.z);
+  zr_atomic_add<double>(K, j, fma(-W, d.x, Gx), fma(-W, d.y, Gy), fma(-W, d.z, Gz));
+}
+__device__ __forceinline__ void zr_emit(const ZrK<float>& K, const float4 d, int j, float W, float Gx, float Gy,
+                                        float Gz, ZrFi<float>& fi) {
+  const float fx = fmaf(-W, d.x, Gx), fy = fmaf(-W, d.y, Gy), fz = fmaf(-W, d.z, Gz);
+  if (!(fabsf(fx) < kFixLimit && fabsf(fy) < kFixLimit && fabsf(fz) < kFixLimit)) {
+    atomicOr(K.flags + FLG_ERR, ERR_NONFINITE);
+    return;
+  }
+  const long long qx = __float2ll_rn(fx * kFixOne), qy = __float2ll_rn(fy * kFixOne), qz = __float2ll_rn(fz * kFixOne);
+  unsigned long long* q = reinterpret_cast<unsigned long long*>(K.f3acc) + 4 * (size_t)j;
+  atomicAdd(q, (unsigned long long)qx);
+  atomicAdd(q + 1, (unsigned long long)qy);
+  atomicAdd(q + 2, (unsigned long long)qz);
+  fi.x += qx;
+  fi.y += qy;
+  fi.z += qz;
+}
+
+// exact warp sum of 64-bit integers of magnitude below 2^58: three 21-bit limbs (the 32-bit warp
+// reductions of the two low limbs stay below 2^26, the signed high limb below 2^22)
+__device__ __forceinline__ long long zr_warp_sum64(long long q) {
+  const unsigned lo = (unsigned)q & 0x1FFFFFu;
+  const unsigned mid = (unsigned)(q >> 21) & 0x1FFFFFu;
+  const int hi = (int)(q >> 42);
+  const unsigned slo = __reduce_add_sync(0xffffffffu, lo);
+  const unsigned smid = __reduce_add_sync(0xffffffffu, mid);
+  const int shi = __reduce_add_sync(0xffffffffu, hi);
+  return (long long)shi * (1ll << 42) + (long long)smid * (1ll << 21) + (long long)slo;
+}
+
+// F_i of base x to its sum (every lane takes part)
+__device__ __forceinline__ void zr_emit_base(const ZrK<double>& K, int x, const ZrFi<double>& fi, int lane) {
+  const double k = zr_sum4<double>(fi.x, fi.y, fi.z, 0.0, lane);
+  const double Fx = k, Fy = __shfl_sync(0xffffffffu, k, 8), Fz = __shfl_sync(0xffffffffu, k, 16);
+  if (lane == 0) zr_atomic_add<double>(K, x, Fx, Fy, Fz);
+}
+__device__ __forceinline__ void zr_emit_base(const ZrK<float>& K, int x, const ZrFi<float>& fi, int lane) {
+  const long long Fx = -zr_warp_sum64(fi.x), Fy = -zr_warp_sum64(fi.y), Fz = -zr_warp_sum64(fi.z);
+  if (lane == 0) {
+    unsigned long long* q = reinterpret_cast<unsigned long long*>(K.f3acc) + 4 * (size_t)x;
+    atomicAdd(q, (unsigned long long)Fx);
+    atomicAdd(q + 1, (unsigned long long)Fy);
+    atomicAdd(q + 2, (unsigned long long)Fz);
+  }
 }
 
 // Per-lane energy sum across a warp's bases: FP32 path, a compensated (hi, lo) pair (TwoSum; no FP64
@@ -546,7 +600,7 @@ __device__ __forceinline__ void zr_eval(const ZrK<T>& K, ZrSmem<T>& w, const int
     return;
   }
   if (m < 2) return;
-  T fix = (T)0, fiy = (T)0, fiz = (T)0;
+  ZrFi<T> fi;
   ZrAcc<T> A;
   if (m <= 32) {
     // the list in place, doubled (pn[v + m] = pn[v]), then far dummies
@@ -565,7 +619,7 @@ __device__ __forceinline__ void zr_eval(const ZrK<T>& K, ZrSmem<T>& w, const int
         done = true;
         cnt_sum += r.cnt;
         if (kE) u_sum.add(r.u);
-        if (lane < m) zr_emit<T>(K, J, jid, r.W, r.Gx, r.Gy, r.Gz, fix, fiy, fiz);
+        if (lane < m) zr_emit(K, J, jid, r.W, r.Gx, r.Gy, r.Gz, fi);
       }
     }
     if (!done) {  // FP64 path, or a pair in the guard band: shared-memory rotation (exact repeat if needed)
@@ -577,7 +631,7 @@ __device__ __forceinline__ void zr_eval(const ZrK<T>& K, ZrSmem<T>& w, const int
       if (lane < m) {
         const T4 s = zr_add4<T>(zr_add4<T>(w.slot[0][lane], w.slot[1][lane]),
                                 zr_add4<T>(w.slot[0][lane + m], w.slot[1][lane + m]));
-        zr_emit<T>(K, J, jid, A.W + s.w, A.Gx + s.x, A.Gy + s.y, A.Gz + s.z, fix, fiy, fiz);
+        zr_emit(K, J, jid, A.W + s.w, A.Gx + s.x, A.Gy + s.y, A.Gz + s.z, fi);
       }
     }
   } else {
@@ -626,14 +680,11 @@ __device__ __forceinline__ void zr_eval(const ZrK<T>& K, ZrSmem<T>& w, const int
       const int v = lane + 32 * h;
       if (v < m) {
         const T4 t = w.tot[v];
-        zr_emit<T>(K, w.nd[v], w.nidx[v], t.w, t.x, t.y, t.z, fix, fiy, fiz);
+        zr_emit(K, w.nd[v], w.nidx[v], t.w, t.x, t.y, t.z, fi);
       }
     }
   }
-  // F_i = sum_v W_v d_v (scaled): warp sum
-  const T k = zr_sum4<T>(fix, fiy, fiz, (T)0, lane);
-  const T Fx = k, Fy = __shfl_sync(0xffffffffu, k, 8), Fz = __shfl_sync(0xffffffffu, k, 16);
-  if (lane == 0) zr_atomic_add<T>(K, x, Fx, Fy, Fz);
+  zr_emit_base(K, x, fi, lane);
 }
 
 template <typename T>

@@ -1282,7 +1282,7 @@ const char* md_status_string(md_status st) {
     case MD_ERR_OOM: return "out of device memory";
     case MD_ERR_BOX_TOO_SMALL: return "box too small: L must exceed 3 * max(r_c2 + skin, r_c3)";
     case MD_ERR_NONFINITE: return "non-finite value in the state";
-    case MD_ERR_DEVICE_TIMEOUT: return "device-side wait timed out (reserved: never returned)";
+    case MD_ERR_DEVICE_TIMEOUT: return "a kernel's bounded wait for its own shared-memory copies gave up";
     case MD_ERR_CUDA: return "CUDA error";
     case MD_ERR_STATE: return "invalid state for this call";
     case MD_ERR_CAPACITY: return "capacity exceeded";

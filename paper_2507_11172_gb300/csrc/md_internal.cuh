@@ -504,7 +504,7 @@ int lj_tile_configure(int smax, int precision);
 // of kLjmThreads / team particles
 constexpr int kLjmThreads = 256;
 #ifndef R3B_LJM_MINB
-#define R3B_LJM_MINB 8
+#define R3B_LJM_MINB 5
 #endif
 constexpr int kLjmMinBlocks = R3B_LJM_MINB;  // resident blocks per SM the registers are sized for
 constexpr int kLjTeams[3] = {4, 8, 16};
