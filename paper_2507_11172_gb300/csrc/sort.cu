@@ -249,22 +249,41 @@ __global__ void __launch_bounds__(32 * kListWarps)
   if (st_begin[27] > smax && threadIdx.x == 0) atomicOr(&S.flags[FLG_ERR], ERR_CELL_CAP);
   const T edge = (T)S.edge;
   const T4* __restrict__ P = reinterpret_cast<const T4*>(S.pos[it.buf]);
-  for (int l = warp; l < 27; l += kListWarps) {
-    const int cnt = st_cnt[l];
-    const int c0 = S.cell_start[st_cell[l]];
-    const T ox = (T)(l % 3 - 1) * edge, oy = (T)((l / 3) % 3 - 1) * edge, oz = (T)(l / 9 - 1) * edge;
-    for (int e = lane; e < cnt; e += 32) {
-      const int slot = st_begin[l] + e;
-      if (slot >= smax) break;
-      T4 h = P[c0 + e];
-      h.x += ox;
-      h.y += oy;
-      h.z += oz;
-      sp[slot] = h;
-      // image code: cell offset (dx, dy, dz) + 1 per axis in 2 bits each
-      const unsigned code = (unsigned)(l % 3) | ((unsigned)((l / 3) % 3) << 2) | ((unsigned)(l / 9) << 4);
-      sj[slot] = (int)((unsigned)(c0 + e) | (code << kNbrShift));
-      sqz[slot] = S.ipos[c0 + e].z;
+  // staging: thread t takes slots t, t + blockDim, ...; the loads of kU slots are issued together
+  // before their stores (one round trip to L2 for the kU slots instead of one per stencil cell)
+  {
+    constexpr int kU = 4;
+    __shared__ int st_c0[27];
+    if (threadIdx.x < 27) st_c0[threadIdx.x] = S.cell_start[st_cell[threadIdx.x]];
+    __syncthreads();
+    for (int s0 = threadIdx.x; s0 < nstaged; s0 += kU * (int)blockDim.x) {
+      T4 h[kU];
+      int qz[kU], l[kU], g[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int slot = s0 + u * (int)blockDim.x;
+        l[u] = slot < nstaged ? stencil_cell_of(st_begin, slot) : 0;
+        g[u] = st_c0[l[u]] + slot - st_begin[l[u]];
+        if (slot < nstaged) {
+          h[u] = P[g[u]];
+          qz[u] = S.ipos[g[u]].z;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int slot = s0 + u * (int)blockDim.x;
+        if (slot < nstaged) {
+          const int lu = l[u];
+          h[u].x += (T)(lu % 3 - 1) * edge;
+          h[u].y += (T)((lu / 3) % 3 - 1) * edge;
+          h[u].z += (T)(lu / 9 - 1) * edge;
+          sp[slot] = h[u];
+          // image code: cell offset (dx, dy, dz) + 1 per axis in 2 bits each
+          const unsigned code = (unsigned)(lu % 3) | ((unsigned)((lu / 3) % 3) << 2) | ((unsigned)(lu / 9) << 4);
+          sj[slot] = (int)((unsigned)g[u] | (code << kNbrShift));
+          sqz[slot] = qz[u];
+        }
+      }
     }
   }
   __syncthreads();
@@ -295,7 +314,10 @@ __global__ void __launch_bounds__(32 * kListWarps)
       }
       const unsigned bal = __ballot_sync(0xffffffffu, ok);
       const int pos = cnt + __popc(bal & lt);
-      if (ok && pos < S.maxnb) row[pos] = sj[t];
+      if (ok && pos < S.maxnb) {
+        const int e = sj[t];
+        row[pos] = e;
+      }
       cnt += __popc(bal);
     }
     if (lane == 0) {
