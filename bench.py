@@ -251,7 +251,9 @@ def run_ours(args):
                                         trip=s1["triplets_total"] - s0["triplets_total"],
                                         atm_ms=(s1["atm_ms_total"] - s0["atm_ms_total"]),
                                         atm_n=s1["atm_timed"] - s0["atm_timed"], clocks=clock_summary(samples),
-                                        kernel=s1["atm_kernel"], per=s1["atm_bases_per_warp"])
+                                        kernel=s1["atm_kernel"], per=s1["atm_bases_per_warp"],
+                                        tuned={k: s1[k] for k in ("atm_kernel", "atm_bases_per_warp", "lj_kernel",
+                                                                   "lj_team", "lj_block", "list_warps")})
             return out
         finally:
             r3.md_destroy_system(h)
@@ -372,6 +374,9 @@ def run_ours(args):
                      "note": f"{ATM_FLOPS_PER_TRIPLET} flop per interacting triplet (FMA = 2) x interacting "
                              "triplets per launch / CUDA-event launch time; nominal peak = 152 SM x 128 FP32 "
                              "lanes x 2 x 2.07 GHz"},
+        # the autotuner's choices for the timed system (LJ kernel 0 row, 1 cell tile, 2 team of lj_team
+        # lanes per particle; triplet kernel 2 rotation with atm_bases_per_warp bases per warp)
+        "autotuned": q32["tuned"],
         "fma_peaks": peaks_run,
         "clocks": clk,
         # per outer step: 2 LJ-phase launches (forces, kick/drift) per inner step, the sort (bin, scan,

@@ -232,6 +232,14 @@ md_status md_set_shapes(md_system *s, int lj_block, int list_warps, int rot_base
  * other values, MD_ERR_STATE while the system is in a batch. */
 md_status md_set_lj_kernel(md_system *s, int variant);
 
+/* Failure-detection test knob (no counterpart in the paper): from the next call on, the cell-tile LJ
+ * kernel (md_set_lj_kernel 1) announces `bytes` more to its copy barrier than its bulk copies deliver,
+ * so that barrier never completes; every copy it issues still completes, the kernel's bounded wait
+ * (0.1-0.3 s) runs out, the call fails with MD_ERR_DEVICE_TIMEOUT and the state is restored to the call's
+ * start, while the CUDA context stays usable.  0 <= bytes <= 4096 (MD_ERR_ARG otherwise); 0, the
+ * default, turns it off.  For tests of the timeout path only. */
+md_status md_inject_copy_shortfall(md_system *s, int bytes);
+
 /* Number of particles, box side and precision of a handle (the inputs of Algorithm 2). */
 md_status md_get_info(md_system *s, int64_t *n, double *box_L, int *precision);
 

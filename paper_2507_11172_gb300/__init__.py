@@ -65,6 +65,7 @@ SIGNATURES = {
     "md_set_profiling": (_I, [_P, _I]),
     "md_set_atm_kernel": (_I, [_P, _I]),
     "md_set_lj_kernel": (_I, [_P, _I]),
+    "md_inject_copy_shortfall": (_I, [_P, _I]),
     "md_set_shapes": (_I, [_P, _I, _I, _I]),
     "md_set_distance_classes": (_I, [_P, _D, _I]),
     "md_get_near_forces": (_I, [_P, _P]),
@@ -224,6 +225,10 @@ def md_set_atm_kernel(h, variant: int):
 
 def md_set_lj_kernel(h, variant: int):
     _check(load().md_set_lj_kernel(h, int(variant)), "md_set_lj_kernel")
+
+
+def md_inject_copy_shortfall(h, nbytes: int):
+    _check(load().md_inject_copy_shortfall(h, int(nbytes)), "md_inject_copy_shortfall")
 
 
 def md_set_shapes(h, lj_block: int = 0, list_warps: int = 0, rot_bases_per_warp: int = 0):

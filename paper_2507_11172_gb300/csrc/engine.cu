@@ -132,6 +132,7 @@ struct md_system {
   // in a batch, or being admitted to one: LJ forces come from the batch's LJ kernel (the row kernel) from
   // the admission's first evaluation on, so a request gives the same bits in any mix
   bool batch_lj = false;
+  int lj_tx_extra = 0;  // md_inject_copy_shortfall (failure-detection tests)
   // calls since the last skin replay that started in safe mode (0: start with the normal plan), and the
   // length of such a run before the normal plan is tried again
   int safe_calls = 0, safe_span = 4;
@@ -391,6 +392,7 @@ md_status upload_desc(md_system* s, double dt_in, double dt_out) {
   h.maxnb = s->maxnb;
   h.cap_stage = atm_stage_capacity(s->cap_cell);
   h.precision = s->precision;
+  h.lj_tx_extra = s->lj_tx_extra;
   {
     const double r = h.rc3 * (1.0 + 1e-5) + 1e-5;
     h.f_edge = (float)h.edge;
@@ -1543,6 +1545,12 @@ md_status md_set_lj_kernel(md_system* s, int variant) {
   clear_graphs(s);
   s->forces_valid = false;
   s->energy_valid = false;
+  return MD_OK;
+}
+
+md_status md_inject_copy_shortfall(md_system* s, int bytes) {
+  if (!s || bytes < 0 || bytes > 4096) return MD_ERR_ARG;
+  s->lj_tx_extra = bytes;
   return MD_OK;
 }
 

@@ -23,7 +23,7 @@ namespace r3b {
 
 namespace {
 
-constexpr int kLjtWaitLimit = 1 << 22;  // polls of the copy barrier (about 0.3 s) before giving up
+constexpr int kLjtWaitLimit = 1 << 19;  // polls of the copy barrier (0.1-0.3 s) before giving up
 
 __device__ __forceinline__ unsigned lt_smem(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -56,7 +56,7 @@ __device__ __forceinline__ bool lt_bar_done(unsigned long long* bar) {
 __device__ __forceinline__ bool lt_bar_wait(unsigned long long* bar) {
   for (int k = 0; k < kLjtWaitLimit; ++k) {
     if (lt_bar_done(bar)) return true;
-    if (k >= 16) __nanosleep(64);
+    if (k >= 16) __nanosleep(256);
   }
   return false;
 }
@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(kLjtThreads, kLjtMinBlocks)
     // one copy per non-empty cell (sorted ranges of 16- or 32-byte records: aligned, whole records)
     if (lane == 0) {
       lt_bar_init(&s_bar);
-      lt_bar_expect(&s_bar, (unsigned)total * (unsigned)sizeof(T4));
+      lt_bar_expect(&s_bar, (unsigned)total * (unsigned)sizeof(T4) + (unsigned)S.lj_tx_extra);
     }
     __syncwarp();
 #pragma unroll

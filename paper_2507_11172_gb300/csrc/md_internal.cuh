@@ -66,7 +66,8 @@ struct SysDev {
   float f_edge, f_edge_lo, f_half_edge, f_rc2sq, f_guard2, f_sig2, f_eps24, f_eps4;
   float f_rc3sq, f_guard3, f_nu, f_reach2, f_half_skin_sq, f_qscale;  // f_qscale = L / 2^32
   int precision;  // 0 = FP32 forces, 1 = FP64
-  int pad_;
+  int lj_tx_extra;  // failure-detection test knob: bytes the cell-tile LJ kernel announces to its copy
+                    // barrier beyond those it copies (0 in normal runs; md_inject_copy_shortfall)
   // distance classes of the three-body force (all NULL / zero when off): near = triplets whose three
   // pair distances are <= r_a, integrated every s_near inner steps; far = the rest within r_c3
   double rasq, guarda;        // r_a^2 and the half-width of its FP64 re-decision band

@@ -46,6 +46,7 @@ def test_null_system_handle_is_rejected_everywhere(lib):
         "md_set_profiling": lambda: lib.md_set_profiling(None, 1),
         "md_set_atm_kernel": lambda: lib.md_set_atm_kernel(None, 2),
         "md_set_lj_kernel": lambda: lib.md_set_lj_kernel(None, 1),
+        "md_inject_copy_shortfall": lambda: lib.md_inject_copy_shortfall(None, 16),
         "md_get_info": lambda: lib.md_get_info(None, ctypes.byref(i64), ctypes.byref(d), ctypes.byref(i32)),
         "md_get_memory": lambda: lib.md_get_memory(None, ctypes.byref(ctypes.c_size_t())),
         "md_set_shapes": lambda: lib.md_set_shapes(None, 64, 4, 8),

@@ -32,9 +32,10 @@ def test_second_system_with_the_same_key_takes_the_cached_choices(gpu_lib):
         s2.forces()
         st2 = s2.stats()
     assert st1["tuned_from_cache"] == 0 and st2["tuned_from_cache"] == 1
-    for k in ("atm_kernel", "atm_bases_per_warp", "lj_block", "list_warps"):
+    for k in ("atm_kernel", "atm_bases_per_warp", "lj_block", "list_warps", "lj_kernel", "lj_team"):
         assert st1[k] == st2[k], k
     assert st1["lj_block"] in (32, 64, 128) and st1["list_warps"] in (2, 4, 8)
+    assert st1["lj_kernel"] in (0, 1, 2) and st1["lj_team"] in (4, 8, 16)
     allp = np.arange(w1.n)
     r2, _ = oracle.lj_particles(w1.x, w1.L, allp, 1.0, 1.0, 2.5)
     r3f, _, _ = oracle.atm_particles(w1.x, w1.L, allp, NU, 2.5)

@@ -15,6 +15,7 @@ import numpy as np
 import pytest
 
 import md_inputs
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -155,3 +156,34 @@ def test_lone_system_going_non_finite_restores_its_state(gpu_lib):
         assert e.value.status == -4
         x, v = s.state()
         assert np.array_equal(x, x0) and np.array_equal(v, v1)
+
+
+def test_copy_barrier_timeout_is_reported_and_the_context_survives(gpu_lib):
+    """The cell-tile LJ kernel waits for its bulk shared-memory copies on an mbarrier with a bounded poll.
+    A host-side knob makes the kernel announce 16 bytes more than it copies: every copy completes, the
+    barrier's phase never does, the wait runs out and the call fails with MD_ERR_DEVICE_TIMEOUT; the state
+    is the call's start, and the same handle goes on normally once the knob is off (forces at the final
+    positions equal the oracle's)."""
+    r3 = gpu_lib
+    w = _w(1000, 0.8, 1.0, 4, 311)
+    with r3.System.create(w.x, w.L, w.v, precision=0, nu=NU, lj_kernel=1) as s:
+        s.step(1, w.k_inner, w.dt_outer)
+        assert s.stats()["lj_kernel"] == 1
+        x0, v0 = s.state()
+        r3.md_inject_copy_shortfall(s.handle, 16)
+        with pytest.raises(r3.MDError) as ei:
+            s.step(1, w.k_inner, w.dt_outer)
+        assert ei.value.status == -5  # MD_ERR_DEVICE_TIMEOUT
+        x1, v1 = s.state()
+        assert np.array_equal(x1, x0) and np.array_equal(v1, v0)
+        r3.md_inject_copy_shortfall(s.handle, 0)
+        s.step(2, w.k_inner, w.dt_outer)
+        x, _ = s.state()
+        f2, f3 = s.forces()
+    sel = np.arange(0, w.n, 7)
+    r2, _ = oracle.lj_particles(x, w.L, sel, 1.0, 1.0, 2.5)
+    r3f, _, _ = oracle.atm_particles(x, w.L, sel, NU, 2.5)
+    for got, ref in ((f2[sel], r2), (f3[sel], r3f)):
+        frms = np.sqrt((ref ** 2).sum(1).mean())
+        err = np.linalg.norm(got - ref, axis=1) / np.maximum(np.linalg.norm(ref, axis=1), frms)
+        assert err.max() <= 1e-5
