@@ -1979,9 +1979,8 @@ md_status batch_admit(md_batch* b) {
       break;
     }
     b->queue.erase(b->queue.begin());
-    if (!s->batch_lj) {
+    if (!s->batch_lj) {  // forces not yet computed are computed with the batch's LJ kernel
       s->batch_lj = true;
-      s->forces_valid = false;  // forces from the batch's LJ kernel
       clear_graphs(s);
     }
     md_status st = ensure_resident(s);
