@@ -15,6 +15,7 @@
 #include <stdio.h>
 
 #include "md_internal.cuh"
+#include "lj_common.cuh"
 
 namespace r3b {
 
@@ -164,8 +165,11 @@ __device__ __forceinline__ void take_near(const SysDev& S, int p, double f[3]) {
 // the neighbour positions of its next group are loaded while its current group is evaluated; a team's
 // partial forces are added in FP64 at the end.  On GB300 one thread per particle is fastest (teams of
 // 2 and 4 measured 3 % and 1 % slower per outer step on the 100k workload).
-// The offset of a neighbour's cell (entry code, one of 27) comes from a shared-memory table; list
-// padding uses code 63, whose offset is far outside every cutoff.  The plain sum of every eight pair
+// The offset of a neighbour's cell (entry code, one of 27) is computed from the code's bits in FP32
+// (off_unit: no shared-memory lookup, which would share the L1 pipe with the gathers; 0.81-0.84 ->
+// 0.79 ms per outer step on the 100k workload) and comes from a shared-memory table in FP64; list
+// padding uses code 63, whose offset (two cell edges per axis, or a far table entry) is beyond every
+// cutoff.  The plain sum of every eight pair
 // forces is added to a compensated (hi, lo) accumulator with an error-free TwoSum.  The
 // velocity-Verlet kick/drift of Algorithm 2 follows in k_kick.
 
@@ -248,6 +252,7 @@ __global__ void __launch_bounds__(kPer, R3B_LJ_THREADS_PER_SM / kPer) k_lj(const
     const T lo = rcsq - g2;
     const T sig2 = Par<T>::sig2(S);
     const T eps24 = Par<T>::eps24(S), eps4 = Par<T>::eps4(S);
+    const T edge = Par<T>::edge(S);
     const int cnt = S.nbr_cnt[i];
     const int4* __restrict__ row4 = reinterpret_cast<const int4*>(S.nbr + nbr_slot(S.maxnb, i, 0));
     const int4 pad = make_int4((int)(kPadCode << kNbrShift), (int)(kPadCode << kNbrShift),
@@ -280,10 +285,18 @@ __global__ void __launch_bounds__(kPer, R3B_LJ_THREADS_PER_SM / kPer) k_lj(const
       T sx = 0, sy = 0, sz = 0;
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const T4 o = s_off[e[u] >> kNbrShift];
-        const T dx = (pa[u].x - pi.x) + o.x;
-        const T dy = (pa[u].y - pi.y) + o.y;
-        const T dz = (pa[u].z - pi.z) + o.z;
+        T dx, dy, dz;
+        if (R3B_LJ_ARITH_OFF && sizeof(T) == 4) {  // padding (code 63): two edges per axis, beyond r_c
+          const unsigned cd = e[u] >> kNbrShift;
+          dx = fma((T)off_unit(cd & 3u), edge, pa[u].x - pi.x);
+          dy = fma((T)off_unit((cd >> 2) & 3u), edge, pa[u].y - pi.y);
+          dz = fma((T)off_unit(cd >> 4), edge, pa[u].z - pi.z);
+        } else {
+          const T4 o = s_off[e[u] >> kNbrShift];
+          dx = (pa[u].x - pi.x) + o.x;
+          dy = (pa[u].y - pi.y) + o.y;
+          dz = (pa[u].z - pi.z) + o.z;
+        }
         const T r2 = fma(dz, dz, fma(dy, dy, dx * dx));
         bmin = fmin(bmin, fabs(r2 - rcsq));
         const T ir2 = recip_fast<T>(r2);

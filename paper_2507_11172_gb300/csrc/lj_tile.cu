@@ -18,6 +18,7 @@
 // takes one subtraction, with an absolute error within a factor of about 1.2 of the row kernel's
 // (cell-local difference plus a cell offset, rounded at the same magnitudes).
 #include "md_internal.cuh"
+#include "lj_common.cuh"
 
 namespace r3b {
 
@@ -445,6 +446,7 @@ __global__ void __launch_bounds__(kLjmThreads, kLjmMinBlocks) k_lj_team(const Sy
     const T lo = rcsq - g2;
     const T sig2 = Par<T>::sig2(S);
     const T eps24 = Par<T>::eps24(S), eps4 = Par<T>::eps4(S);
+    const T edge = Par<T>::edge(S);
     const int cnt = S.nbr_cnt[i];
     const int* __restrict__ row = S.nbr + nbr_slot(S.maxnb, i, 0);
     T bmin = (T)1e30;
@@ -453,8 +455,18 @@ __global__ void __launch_bounds__(kLjmThreads, kLjmMinBlocks) k_lj_team(const Sy
     for (int t = h; t < cnt; t += kTeam) {
       const unsigned e = (unsigned)__ldg(row + t);
       const T4 pj = lt_ldg4(P + (e & kNbrMask));
-      const T4 o = s_off[e >> kNbrShift];
-      const T dx = (pj.x - pi.x) + o.x, dy = (pj.y - pi.y) + o.y, dz = (pj.z - pi.z) + o.z;
+      T dx, dy, dz;
+      if (R3B_LJ_ARITH_OFF && sizeof(T) == 4) {  // padding (code 63): two edges per axis, beyond r_c
+        const unsigned cd = e >> kNbrShift;
+        dx = fma((T)off_unit(cd & 3u), edge, pj.x - pi.x);
+        dy = fma((T)off_unit((cd >> 2) & 3u), edge, pj.y - pi.y);
+        dz = fma((T)off_unit(cd >> 4), edge, pj.z - pi.z);
+      } else {
+        const T4 o = s_off[e >> kNbrShift];
+        dx = (pj.x - pi.x) + o.x;
+        dy = (pj.y - pi.y) + o.y;
+        dz = (pj.z - pi.z) + o.z;
+      }
       const T r2 = fma(dz, dz, fma(dy, dy, dx * dx));
       bmin = fmin(bmin, fabs(r2 - rcsq));
       const T ir2 = lt_recip<T>(r2);
