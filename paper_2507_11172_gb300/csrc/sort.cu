@@ -8,6 +8,10 @@
 // copies the permuted state back into place).
 #include "md_internal.cuh"
 
+#ifndef R3B_LIST_PACKED
+#define R3B_LIST_PACKED 1  // pair-list build: two candidate chunks per iteration in packed FP32x2
+#endif
+
 namespace r3b {
 
 __global__ void k_bin_count(const SysDev* __restrict__ sys, const PItem* __restrict__ items) {
@@ -303,8 +307,30 @@ __global__ void __launch_bounds__(32 * kListWarps)
     const T4 pi = sp[islot];
     int cnt = 0;
     int* const row = S.nbr + nbr_slot(S.maxnb, i, 0);
-    // pass 1: every staged particle within the list radius
-    for (int t0 = 0; t0 < nstaged; t0 += 32) {
+    // pass 1: every staged particle within the list radius, in staging order; FP32: two chunks of 32
+    // candidates per iteration, their distance tests in packed FP32x2 arithmetic
+    auto compact = [&](const int t, const bool ok) {
+      const unsigned bal = __ballot_sync(0xffffffffu, ok);
+      const int pos = cnt + __popc(bal & lt);
+      if (ok && pos < S.maxnb) row[pos] = sj[t];
+      cnt += __popc(bal);
+    };
+    int t0 = 0;
+    if constexpr (sizeof(T) == 4 && R3B_LIST_PACKED) {
+      const float2 px = make_float2(-pi.x, -pi.x), py = make_float2(-pi.y, -pi.y), pz = make_float2(-pi.z, -pi.z);
+      for (; t0 + 32 < nstaged; t0 += 64) {
+        const int ta = t0 + lane, tb = ta + 32;
+        const float4 qa = sp[ta];
+        const float4 qb = tb < nstaged ? sp[tb] : make_float4(1e3f, 1e3f, 1e3f, 0.f);
+        const float2 dx = __fadd2_rn(make_float2(qa.x, qb.x), px);
+        const float2 dy = __fadd2_rn(make_float2(qa.y, qb.y), py);
+        const float2 dz = __fadd2_rn(make_float2(qa.z, qb.z), pz);
+        const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+        compact(ta, ta != islot && r2.x <= rl);
+        compact(tb, tb < nstaged && tb != islot && r2.y <= rl);
+      }
+    }
+    for (; t0 < nstaged; t0 += 32) {
       const int t = t0 + lane;
       bool ok = false;
       if (t < nstaged && t != islot) {
@@ -312,13 +338,7 @@ __global__ void __launch_bounds__(32 * kListWarps)
         const T dx = q.x - pi.x, dy = q.y - pi.y, dz = q.z - pi.z;
         ok = dx * dx + dy * dy + dz * dz <= rl;
       }
-      const unsigned bal = __ballot_sync(0xffffffffu, ok);
-      const int pos = cnt + __popc(bal & lt);
-      if (ok && pos < S.maxnb) {
-        const int e = sj[t];
-        row[pos] = e;
-      }
-      cnt += __popc(bal);
+      compact(t, ok);
     }
     if (lane == 0) {
       if (cnt > S.maxnb) atomicOr(&S.flags[FLG_ERR], ERR_NBR_CAP);
