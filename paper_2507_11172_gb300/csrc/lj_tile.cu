@@ -1,6 +1,8 @@
-// Lennard-Jones 12-6 pair forces (Sec. 2.1) from shared-memory tiles of cells (linked cells, Sec. 2.2).
+// Lennard-Jones 12-6 pair forces (Sec. 2.1): two alternatives to the row kernel k_lj (forces.cu), all
+// three timed by the autotuner.
 //
-//   k_lj_tile  one CTA per block of 2 x 2 x 2 cells.  The 4 x 4 x 4 cells around the block (every
+//   k_lj_team  4, 8 or 16 lanes per particle share its pair-list row (end of this file).
+//   k_lj_tile  one CTA per block of 2 x 2 x 2 cells (linked cells, Sec. 2.2).  The 4 x 4 x 4 cells around the block (every
 //              cell a pair-list entry of the block's particles can point to) are copied into shared
 //              memory by bulk asynchronous copies (cp.async.bulk, one per cell: each cell's particles
 //              are contiguous in the sorted order) that complete on an mbarrier, then shifted into one
