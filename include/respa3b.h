@@ -111,7 +111,8 @@ md_status md_create_system(md_system **out, int64_t n, double box_L, const doubl
 md_status md_set_potentials(md_system *s, double lj_eps, double lj_sigma, double rc_pair, double atm_nu,
                             double rc_triplet);
 
-/* Verlet-list skin for the pair list (default 0.3 sigma, thinner for boxes below
+/* Verlet-list skin for the pair list of the linked-cell neighbour search (Sec. 2.2, Sec. 4.1: the
+ * paper's linked cells; the skin is this library's, default 0.3 sigma, thinner for boxes below
  * 3 (r_c2 + 0.3) at creation).  The pair list is rebuilt at every outer step; if
  * any particle moves more than skin/2 within one, the call is replayed from its
  * start with a rebuild before every inner step at which some particle has moved
@@ -174,8 +175,9 @@ md_status md_set_state(md_system *s, const double *pos, const double *vel);
  * MD_ERR_CAPACITY.  Every near evaluation re-decides r_a exactly at the current positions. */
 md_status md_set_distance_classes(md_system *s, double r_a, int s_near);
 
-/* Cached near-class ATM forces F3near (n x 3, caller order) at the current positions; md_get_forces'
- * f3 is the whole ATM force (near + far).  MD_ERR_STATE if the classes are off. */
+/* Cached near-class ATM forces F3near (n x 3, caller order) at the current positions (the near distance
+ * class of the Sec. 5 outlook, ATM of Sec. 2.1); md_get_forces' f3 is the whole ATM force (near + far).
+ * MD_ERR_STATE if the classes are off. */
 md_status md_get_near_forces(md_system *s, double *f3near);
 
 /* Counters (see md_stats; the triplet counts are those of the cutoff rule of the Fig. 2 caption, the
@@ -251,9 +253,10 @@ md_status md_get_memory(md_system *s, size_t *device_bytes);
 /* Release all device memory of the handle (the end of the run of Algorithm 2); NULL is accepted. */
 md_status md_destroy_system(md_system *s);
 
-/* Static string for a status code; message of the last failing CUDA call of
- * this thread for MD_ERR_CUDA. */
+/* Static string for a status code (no counterpart in the paper: error reporting of this C ABI). */
 const char *md_status_string(md_status st);
+/* Message of this thread's last failing call (the failing CUDA call for MD_ERR_CUDA, the exceeded limit
+ * for MD_ERR_CAPACITY, ...); "" if none.  No counterpart in the paper. */
 const char *md_last_error(void);
 
 /* ---------------- batched ensemble / continuous serving ----------------
@@ -284,7 +287,8 @@ md_status md_batch_poll(md_batch *b, uint64_t ticket, int *done);
 md_status md_batch_latency(md_batch *b, uint64_t ticket, double *ms, int *count);
 md_status md_batch_pending(md_batch *b, int *queued, int *resident);
 /* Cycles run so far and how many of them were replayed from their start (a member's particle left its
- * skin, or a capacity grew); either pointer may be NULL. */
+ * skin, or a capacity grew); either pointer may be NULL.  No counterpart in the paper (serving
+ * monitoring of the batched ensemble). */
 md_status md_batch_cycles(md_batch *b, uint64_t *cycles, uint64_t *replayed);
 /* Cancel a request (call between md_batch_run calls).  A queued request is dropped and its system is
  * left as it was; a resident one finishes the outer step it is in (so its state is a full step of
@@ -308,7 +312,7 @@ md_status md_atm_direct(const double *pos, int64_t n, double atm_nu, int precisi
                         void *cuda_stream);
 
 /* ---------------- arithmetic peaks of the device ----------------
- * No counterpart in the paper: the FP32 and FP64 fused multiply-add throughput of the current device,
+ * No counterpart in the paper (it reports no throughput): the FP32 and FP64 fused multiply-add throughput of the current device,
  * the denominators of the triplet kernel's roofline fraction (its work is plain FP32 arithmetic, not a
  * dense contraction).  kind: 0 FP32 FMA, 1 packed FP32x2 FMA (two per instruction), 2 FP64 FMA.  Every
  * resident thread of one full wave runs 8 independent FMA chains; the trip count grows until one launch
