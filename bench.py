@@ -393,9 +393,9 @@ def run_ours(args):
         line["measured_peaks"] = {"hbm_gbs": peaks.get("hbm_gbs"), "bf16_tflops": peaks.get("bf16_tflops")}
     if rank == 0 and not args.no_batch:
         line["ensemble"] = run_ensemble(r3)
-        line["serving"] = run_serving(r3, seconds=args.serve_seconds)
+        line["serving"] = run_serving(r3, seconds=args.serve_seconds, max_particles=args.serve_max_particles)
         # below capacity (about 25 requests/s of this mix on one GB300): latencies without queueing
-        line["serving_subcapacity"] = run_serving(r3, seconds=5.0, rate=12.0)
+        line["serving_subcapacity"] = run_serving(r3, seconds=5.0, rate=12.0, max_particles=args.serve_max_particles)
     if not args.no_cpu and rank == 0:
         line["cpu_baseline"] = cpu_baseline(w, args.cpu_sample)
     if rank == 0:
@@ -557,11 +557,12 @@ def run_ensemble(r3, n_replicas=256, n_outer=20, seed=None, atm_kernel=2):
             r3.md_destroy_system(h)
 
 
-def run_serving(r3, seconds=3.0, rate=50.0, n_outer=100, k=10, seed=None, atm_kernel=2):
+def run_serving(r3, seconds=3.0, rate=50.0, n_outer=100, k=10, seed=None, atm_kernel=2, max_particles=2_000_000):
     """Poisson arrivals (rate per second) of replicas with N log-uniform in [1e3, 2e5] and rho
     U[0.7, 0.9]; each asks for n_outer outer steps at k inner steps; admitted by a device-memory
-    budget (80 % of free HBM), state resident, batched continuously; arrivals stop after
-    `seconds` and the loop drains the queue."""
+    budget (80 % of free HBM) and a bound on the resident particles (max_particles: the time of one
+    cycle, hence every request's outer-step latency), state resident, batched continuously; arrivals
+    stop after `seconds` and the loop drains the queue."""
     import torch
     import md_inputs
     seed = md_inputs.config_seed(5) if seed is None else seed
@@ -572,6 +573,8 @@ def run_serving(r3, seconds=3.0, rate=50.0, n_outer=100, k=10, seed=None, atm_ke
     dens = 0.7 + 0.2 * u[:, 2]
     free, _ = torch.cuda.mem_get_info()
     b = r3.md_batch_create(int(0.8 * free))
+    if max_particles:
+        r3.md_batch_set_limits(b, int(max_particles))
     live = {}
     lat_all, e2e, trip_all = [], [], 0
     t0 = time.perf_counter()
@@ -604,6 +607,7 @@ def run_serving(r3, seconds=3.0, rate=50.0, n_outer=100, k=10, seed=None, atm_ke
         cycles, replayed = r3.md_batch_cycles(b)
         offered = float(sum(sizes)) * n_outer * 200.0 / seconds  # about 200 triplets per particle
         return {"requests": n_req, "arrival_rate_per_s": rate, "arrival_window_s": seconds,
+                "max_resident_particles": int(max_particles),
                 "offered_triplets_per_s_estimate": offered,
                 "cycles": cycles, "replayed_cycles": replayed,
                 "outer_steps_each": n_outer, "k_inner": k, "wall_s": wall,
@@ -694,6 +698,8 @@ def main():
     ap.add_argument("--no-large", action="store_true",
                     help="skip the 2,000,000-particle system (its input takes about half a minute to generate)")
     ap.add_argument("--serve-seconds", type=float, default=3.0, help="arrival window of the serving run")
+    ap.add_argument("--serve-max-particles", type=int, default=2_000_000,
+                    help="bound on the particles resident in the serving batch (0: memory budget only)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -281,6 +281,13 @@ const char *md_last_error(void);
  *   ticket's request, measured from its admission; *count in/out.
  * md_batch_destroy: release the batch (systems stay valid; NULL accepted). */
 md_status md_batch_create(md_batch **out, size_t hbm_budget_bytes);
+/* Bound the particles of the resident systems (0, the default: no bound beyond the memory budget).
+ * Every resident system advances one outer step per cycle, so the particles resident set the time of
+ * a cycle and with it every request's outer-step latency; queued requests wait (in order) while the
+ * head of the queue would take the resident particles past the bound, and a request larger than the
+ * bound by itself runs alone.  Applies from the next admission.  MD_ERR_ARG for a negative bound.  No
+ * counterpart in the paper (serving). */
+md_status md_batch_set_limits(md_batch *b, int64_t max_resident_particles);
 md_status md_batch_submit(md_batch *b, md_system *s, int n_outer, int k_inner, double dt_outer, uint64_t *ticket);
 md_status md_batch_run(md_batch *b, int max_ticks);
 md_status md_batch_poll(md_batch *b, uint64_t ticket, int *done);

@@ -65,6 +65,7 @@ SIGNATURES = {
     "md_set_profiling": (_I, [_P, _I]),
     "md_set_atm_kernel": (_I, [_P, _I]),
     "md_set_lj_kernel": (_I, [_P, _I]),
+    "md_batch_set_limits": (_I, [_P, ctypes.c_int64]),
     "md_inject_copy_shortfall": (_I, [_P, _I]),
     "md_set_shapes": (_I, [_P, _I, _I, _I]),
     "md_set_distance_classes": (_I, [_P, _D, _I]),
@@ -259,6 +260,10 @@ def md_batch_create(hbm_budget_bytes: int = 0):
     h = _P()
     _check(load().md_batch_create(ctypes.byref(h), int(hbm_budget_bytes)), "md_batch_create")
     return h
+
+
+def md_batch_set_limits(b, max_resident_particles: int):
+    _check(load().md_batch_set_limits(b, int(max_resident_particles)), "md_batch_set_limits")
 
 
 def md_batch_submit(b, sys_h, n_outer: int, k_inner: int, dt_outer: float) -> int:

@@ -1637,6 +1637,7 @@ struct TickItems {
 
 struct md_batch {
   size_t budget = 0;
+  int64_t max_particles = 0;  // md_batch_set_limits: resident particles admitted (0: no bound)
   int precision = -1;
   std::map<uint64_t, Request> req;
   std::vector<uint64_t> queue, resident;
@@ -1964,10 +1965,17 @@ void batch_fill_modes(md_batch* b, bool safe) {
 
 md_status batch_admit(md_batch* b) {
   size_t used = 0;
-  for (uint64_t tk : b->resident) used += b->req[tk].s->mem_bytes;
+  int64_t used_n = 0;
+  for (uint64_t tk : b->resident) {
+    used += b->req[tk].s->mem_bytes;
+    used_n += b->req[tk].s->n;
+  }
   while (!b->queue.empty()) {
     Request& r = b->req[b->queue.front()];
     md_system* s = r.s;
+    // particle bound (a latency target, not a capacity): the head of the queue waits while it would take
+    // the resident particles past it, and runs alone if it is larger than the bound by itself
+    if (b->max_particles > 0 && !b->resident.empty() && used_n + s->n > b->max_particles) break;
     const size_t need = s->deferred ? arena_bytes(s) : s->mem_bytes;
     if (b->budget && used + need > b->budget) {
       if (b->resident.empty()) {  // can never fit: fail the request
@@ -2013,6 +2021,7 @@ md_status batch_admit(md_batch* b) {
     r.state = RQ_RESIDENT;
     r.s->skin_carry = false;
     used += s->mem_bytes;
+    used_n += s->n;
     b->resident.push_back(r.ticket);
     b->dirty = true;
   }
@@ -2177,6 +2186,12 @@ md_status md_batch_create(md_batch** out, size_t hbm_budget_bytes) {
   b->budget = hbm_budget_bytes;
   CK(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
   *out = b.release();
+  return MD_OK;
+}
+
+md_status md_batch_set_limits(md_batch* b, int64_t max_resident_particles) {
+  if (!b || max_resident_particles < 0) return MD_ERR_ARG;
+  b->max_particles = max_resident_particles;
   return MD_OK;
 }
 

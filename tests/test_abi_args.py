@@ -68,6 +68,7 @@ def test_null_batch_handle_is_rejected_everywhere(lib):
     assert lib.md_batch_pending(None, ctypes.byref(i32), ctypes.byref(i32)) == ARG
     assert lib.md_batch_cycles(None, ctypes.byref(u), ctypes.byref(u)) == ARG
     assert lib.md_batch_cancel(None, 1) == ARG
+    assert lib.md_batch_set_limits(None, 1000) == ARG
     assert lib.md_batch_destroy(None) == OK  # NULL-safe
 
 

@@ -287,3 +287,47 @@ def test_served_fp64_follows_algorithm2(gpu_lib):
         r3.md_batch_destroy(b)
         for h in hs:
             r3.md_destroy_system(h)
+
+
+def test_particle_bound_holds_requests_back(gpu_lib):
+    """md_batch_set_limits: with a bound of 1800 resident particles, requests of 800 and 900 particles
+    are admitted together and one of 1000 waits in the queue until they finish; a request of 2000 (more
+    than the bound by itself) then runs alone.  Every request's final state equals the same request run
+    alone bit for bit (FP32, rotation triplet kernel, the batch's row LJ kernel)."""
+    r3 = gpu_lib
+    specs = [(800, 0.8, 1.0, 4), (900, 0.8, 1.1, 4), (1000, 0.75, 1.0, 4), (2000, 0.8, 1.0, 4)]
+    ws = []
+    for i, (n, rho, T, k) in enumerate(specs):
+        w = md_inputs.fcc_system(n, rho, T, 0.05, 731 + i)
+        w.k_inner, w.dt_outer = k, 0.002 * k
+        ws.append(w)
+    n_outer = 3
+    alone = []
+    for w in ws:
+        with r3.System.create(w.x, w.L, w.v, precision=0, nu=NU, atm_kernel=2, lj_kernel=0) as s:
+            s.step(n_outer, w.k_inner, w.dt_outer)
+            alone.append(s.state())
+    hs = []
+    for w in ws:
+        h = r3.md_create_system(w.x, w.L, w.v, 1.0, r3.MD_FP32 | r3.MD_DEFERRED)
+        r3.md_set_potentials(h, 1.0, 1.0, 2.5, NU, 2.5)
+        r3.md_set_atm_kernel(h, 2)
+        hs.append(h)
+    b = r3.md_batch_create(0)
+    try:
+        with pytest.raises(r3.MDError):
+            r3.md_batch_set_limits(b, -1)
+        r3.md_batch_set_limits(b, 1800)
+        tickets = [r3.md_batch_submit(b, h, n_outer, w.k_inner, w.dt_outer) for w, h in zip(ws[:3], hs[:3])]
+        r3.md_batch_run(b, 4)  # one cycle of the first admission
+        assert r3.md_batch_pending(b) == (1, 2)  # 800 + 900 resident, 1000 queued
+        tickets.append(r3.md_batch_submit(b, hs[3], n_outer, ws[3].k_inner, ws[3].dt_outer))
+        r3.md_batch_run(b, 0)
+        for w, h, t, (xa, va) in zip(ws, hs, tickets, alone):
+            assert r3.md_batch_poll(b, t)
+            x, v = r3.md_get_state(h)
+            assert np.array_equal(x, xa) and np.array_equal(v, va)
+    finally:
+        r3.md_batch_destroy(b)
+        for h in hs:
+            r3.md_destroy_system(h)
