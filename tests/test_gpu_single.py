@@ -242,6 +242,27 @@ def test_long_half_lists_fall_back_to_the_cell_kernel(gpu_lib):
     assert force_err(f3, f3r) <= 1e-5
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_long_pair_rows(gpu_lib, prec):
+    """With r_c2 = 3.5 at density 1.15 a pair-list row (list radius 3.8) holds about 260 entries, four
+    times the benchmark's rows, and the triplet half lists (r_c3 = 2.5) are built from the first part of
+    each row's distance range only.  LJ and ATM forces, the energies and the exact triplet count must
+    match the oracle."""
+    x, L = md_inputs.fcc_jitter(5324, 1.15, 0.05, 95)  # 4 cells per side of edge 4.17
+    d = x[:200, None, :] - x[None, :, :]
+    d -= L * np.rint(d / L)
+    assert ((d ** 2).sum(2) <= 3.5 ** 2).sum(1).min() > 190
+    f2r, u2r, _ = oracle.lj_brute(x, L, 1.0, 1.0, 3.5)
+    f3r, u3r, _, cnt = oracle.atm_brute(x, L, NU, 2.5)
+    with gpu_lib.System.create(x, L, None, precision=prec, nu=NU, rc_pair=3.5, rc_triplet=2.5, skin=0.3) as s:
+        f2, f3 = s.forces()
+        _, u2, u3, _ = s.energy()
+        assert s.stats()["triplets_last"] == cnt
+    assert force_err(f2, f2r) <= TOL[prec] and force_err(f3, f3r) <= TOL[prec]
+    etol = 1e-6 if prec == 0 else 1e-12
+    assert abs(u2 - u2r) <= etol * abs(u2r) and abs(u3 - u3r) <= etol * abs(u3r)
+
+
 def test_errors_are_reported(gpu_lib, cfg1):
     r3 = gpu_lib
     bad = cfg1.x.copy()
