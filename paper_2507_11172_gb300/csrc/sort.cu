@@ -212,9 +212,9 @@ __global__ void k_scatter(const SysDev* __restrict__ sys, const PItem* __restric
 // owner of every triplet whose other two members are in that list.  With distance classes on, the
 // same pass keeps the near-class candidates (S.half_a): the entries above i within r_a + skin (a
 // superset test, widened by 1e-4).  The CTA also moves the permuted state of b's particles back into
-// place.
+// place.  FP32: registers sized for 1024 resident threads per SM (64 per thread).
 template <typename T, int kListWarps>
-__global__ void __launch_bounds__(32 * kListWarps)
+__global__ void __launch_bounds__(32 * kListWarps, sizeof(T) == 4 ? 32 / kListWarps : 1)
     k_listbuild(const SysDev* __restrict__ sys, const CItem* __restrict__ items, int smax) {
   pdl_wait();
   using T4 = typename V4<T>::type;
@@ -301,6 +301,7 @@ __global__ void __launch_bounds__(32 * kListWarps)
   if (threadIdx.x < 27) st_delta[threadIdx.x] = st_begin[threadIdx.x] - S.cell_start[st_cell[threadIdx.x]];
   __syncthreads();
   const T rc3 = (T)S.rc3sq, g3 = (T)S.guard3;
+  const int b9 = st_begin[9];  // first staged slot of the base cell's own layer
   for (int ib = warp; ib < nbase; ib += kListWarps) {
     const int islot = st_begin[13] + ib;
     const int i = i0 + ib;
@@ -308,17 +309,19 @@ __global__ void __launch_bounds__(32 * kListWarps)
     int cnt = 0;
     int* const row = S.nbr + nbr_slot(S.maxnb, i, 0);
     // pass 1: every staged particle within the list radius, in staging order; FP32: two chunks of 32
-    // candidates per iteration, their distance tests in packed FP32x2 arithmetic
+    // candidates per iteration, their distance tests in packed FP32x2 arithmetic.  The row starts with
+    // the entries of the lower cell layer (staged slots below b9), none of which is above i: cnt0, the
+    // entries from the chunks that lie wholly below b9, is where pass 2 may start.
     auto compact = [&](const int t, const bool ok) {
       const unsigned bal = __ballot_sync(0xffffffffu, ok);
       const int pos = cnt + __popc(bal & lt);
       if (ok && pos < S.maxnb) row[pos] = sj[t];
       cnt += __popc(bal);
     };
-    int t0 = 0;
+    int t0 = 0, cnt0 = 0;
     if constexpr (sizeof(T) == 4 && R3B_LIST_PACKED) {
       const float2 px = make_float2(-pi.x, -pi.x), py = make_float2(-pi.y, -pi.y), pz = make_float2(-pi.z, -pi.z);
-      for (; t0 + 32 < nstaged; t0 += 64) {
+      auto two = [&](const int t0) {
         const int ta = t0 + lane, tb = ta + 32;
         const float4 qa = sp[ta];
         const float4 qb = tb < nstaged ? sp[tb] : make_float4(1e3f, 1e3f, 1e3f, 0.f);
@@ -328,9 +331,12 @@ __global__ void __launch_bounds__(32 * kListWarps)
         const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
         compact(ta, ta != islot && r2.x <= rl);
         compact(tb, tb < nstaged && tb != islot && r2.y <= rl);
-      }
+      };
+      for (; t0 + 32 < nstaged && t0 + 64 <= b9; t0 += 64) two(t0);
+      cnt0 = cnt;
+      for (; t0 + 32 < nstaged; t0 += 64) two(t0);
     }
-    for (; t0 < nstaged; t0 += 32) {
+    auto one = [&](const int t0) {
       const int t = t0 + lane;
       bool ok = false;
       if (t < nstaged && t != islot) {
@@ -339,18 +345,24 @@ __global__ void __launch_bounds__(32 * kListWarps)
         ok = dx * dx + dy * dy + dz * dz <= rl;
       }
       compact(t, ok);
+    };
+    if constexpr (!(sizeof(T) == 4 && R3B_LIST_PACKED)) {
+      for (; t0 < nstaged && t0 + 32 <= b9; t0 += 32) one(t0);
+      cnt0 = cnt;
     }
+    for (; t0 < nstaged; t0 += 32) one(t0);
     if (lane == 0) {
       if (cnt > S.maxnb) atomicOr(&S.flags[FLG_ERR], ERR_NBR_CAP);
       S.nbr_cnt[i] = min(cnt, S.maxnb);
     }
     cnt = min(cnt, S.maxnb);
+    cnt0 = min(cnt0, cnt);
     __syncwarp();  // the row written above is read back below by other lanes
     // pass 2: the triplet half list among the list entries
     const int qzi = sqz[islot];
     int* hrow = S.half + (size_t)i * kHalfCap;
     int mh = 0, ma = 0;
-    for (int t0 = 0; t0 < cnt; t0 += 32) {
+    for (int t0 = cnt0; t0 < cnt; t0 += 32) {
       const int t = t0 + lane;
       bool half = false, band = false, cand = false;
       unsigned e = 0u;
