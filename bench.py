@@ -221,6 +221,8 @@ def run_ours(args):
         h = r3.md_create_system(w.x, w.L, w.v, 1.0, precision, stream.cuda_stream)
         try:
             r3.md_set_potentials(h, 1.0, 1.0, w.rc2, w.nu, w.rc3)
+            if args.lj_kernel >= 0:  # pinned LJ kernel (row / cell-tile / team) instead of the autotuner's
+                r3.md_set_lj_kernel(h, args.lj_kernel)
             with torch.cuda.stream(stream):
                 r3.md_respa_step(h, 0, w.k_inner, w.dt_outer)  # initial forces F2b(x0), F3b(x0)
                 for _ in range(warmup):
@@ -692,6 +694,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--lj-kernel", type=int, default=-1, choices=[-1, 0, 1, 2],
+                    help="LJ kernel of the main runs: -1 autotuned, 0 row, 1 cell-tile, 2 team")
     ap.add_argument("--cpu-sample", type=int, default=100_000,
                     help="particles in the oracle's timed per-particle pass (100000 = one full evaluation)")
     ap.add_argument("--no-batch", action="store_true", help="skip the ensemble and serving runs")
