@@ -329,7 +329,8 @@ def run_ours(args):
             r3.md_destroy_system(h)
 
     classes_line = run_classes(r3, w, stream, flush, K) if rank == 0 else None
-    large_line = run_large(r3, stream, flush) if (rank == 0 and not args.no_large) else None
+    w2m = large_workload() if (rank == 0 and not args.no_large) else None
+    large_line = run_large(r3, stream, flush, *w2m) if w2m else None
     direct_line = run_direct(r3, stream, fp32_peak) if rank == 0 else None
 
     peaks = {}
@@ -400,22 +401,28 @@ def run_ours(args):
         line["serving_subcapacity"] = run_serving(r3, seconds=5.0, rate=12.0, max_particles=args.serve_max_particles)
     if not args.no_cpu and rank == 0:
         line["cpu_baseline"] = cpu_baseline(w, args.cpu_sample)
+        line["cpu_linked_cell"] = cpu_linked_cell(w, w2m[0] if w2m else None)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
 
 
-def run_large(r3, stream, flush, steps=20):
+def large_workload():
+    """The 2,000,000-particle random-sequential-addition start and the seconds its generation took."""
+    import md_inputs
+    t0 = time.perf_counter()
+    w = md_inputs.rsa_2m(2.5)
+    return w, time.perf_counter() - t0
+
+
+def run_large(r3, stream, flush, w, gen_s, steps=20):
     """Large single system (2,000,000 particles, random-sequential-addition start at density 0.75,
     T* = 1.2, FP32 forces, k = 10, dt_outer = 0.02) with triplet cutoffs 2.0 and 2.5: whole outer steps
     through the graph-replayed path, CUDA events, L2 flushed before each step."""
     import torch
-    import md_inputs
     out = {}
-    t0 = time.perf_counter()
-    w = md_inputs.rsa_2m(2.5)
-    out["input_generation_s"] = time.perf_counter() - t0
+    out["input_generation_s"] = gen_s
     out["timed_outer_steps"] = steps
     for rc3 in (2.0, 2.5):
         h = r3.md_create_system(w.x, w.L, w.v, 1.0, r3.MD_FP32, stream.cuda_stream)
@@ -621,6 +628,47 @@ def run_serving(r3, seconds=3.0, rate=50.0, n_outer=100, k=10, seed=None, atm_ke
         r3.md_batch_destroy(b)
         for h, _ in live.values():
             r3.md_destroy_system(h)
+
+
+def _cpu_model():
+    try:
+        r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10)
+        for line in r.stdout.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return None
+
+
+def cpu_linked_cell(w, w2m=None):
+    """The linked-cell FP64 CPU code (cpu_cells/: the paper's Cutoff traversal, OpenMP over particles,
+    no Newton 3) running Algorithm 2 on the workloads of the GPU runs, on every host core: the CPU
+    throughput figure beside the GPU's (the oracle's figure, `cpu_baseline`, is a deliberately simple
+    per-particle pass).  Whole outer steps after the initial forces; triplets/s = interacting triplets
+    evaluated / wall time of the steps."""
+    import cpu_cells
+    import md_inputs
+
+    def steps(x, v, L, rc3, k, dt_outer, n_outer):
+        st = cpu_cells.State(x, v, L, rc2=w.rc2, nu=w.nu, rc3=rc3)
+        st.run(0, k, dt_outer)  # F2b(x0), F3b(x0)
+        r = st.run(n_outer, k, dt_outer)
+        sec = r["seconds"]
+        return {"n": int(x.shape[0]), "rc3": rc3, "k_inner": k, "timed_outer_steps": n_outer,
+                "ms_per_outer_step": sec / n_outer * 1e3, "rrespa_steps_per_s": n_outer / sec,
+                "triplets_per_s": r["triplets"] / sec, "triplets_per_eval": r["triplets"] / max(1, r["atm_evals"]),
+                "lj_share": r["lj_s"] / sec, "atm_share": r["atm_s"] / sec}
+
+    out = {"kind": "linked-cell FP64, OpenMP over particles, no Newton 3 (cpu_cells/)", "cores": cpu_cells.threads(),
+           "cpu_model": _cpu_model()}
+    w1 = md_inputs.small_fcc_1k()
+    out["fcc1k"] = steps(w1.x, w1.v, w1.L, 2.5, w1.k_inner, w1.dt_outer, w1.n_outer)
+    out["fcc100k"] = steps(w.x, w.v, w.L, w.rc3, w.k_inner, w.dt_outer, 2)
+    if w2m is not None:
+        for rc3 in (2.0, 2.5):
+            out[f"rsa2m_rc3_{rc3}"] = steps(w2m.x, w2m.v, w2m.L, rc3, w2m.k_inner, w2m.dt_outer, 1)
+    return out
 
 
 def cpu_baseline(w, nsample):
