@@ -16,6 +16,7 @@
 
 #include "md_internal.cuh"
 #include "lj_common.cuh"
+#include "sys_stage.cuh"
 
 namespace r3b {
 
@@ -216,13 +217,21 @@ template <> __device__ __forceinline__ double recip_fast<double>(double x) { ret
 #endif
 template <typename T, bool kE, int kPer>
 __global__ void __launch_bounds__(kPer, R3B_LJ_THREADS_PER_SM / kPer) k_lj(const SysDev* __restrict__ sys, const PItem* __restrict__ items) {
-  pdl_wait();
   static_assert(kPer % 32 == 0 && kLjTeam == 1, "LJ blocks of whole warps, one thread per particle");
   using T4 = typename V4<T>::type;
   __shared__ T4 s_off[64];
   __shared__ double red_u[kPer / 32], red_w[kPer / 32];
   const PItem it = items[blockIdx.x];
+#if R3B_STAGE_SYS
+  __shared__ StagedSys s_sys;
+  stage_sys(s_sys, sys, it.sys);
+  pdl_wait();
+  __syncthreads();
+  const SysDev& S = s_sys.get();
+#else
+  pdl_wait();
   const SysDev& S = sys[it.sys];
+#endif
   const int mode = item_mode(S, it.mode);
   if (mode & M_SKIP) return;  // block-uniform: a block belongs to one system
   const bool energy = kE && (mode & M_ENERGY) != 0;
@@ -408,9 +417,17 @@ __global__ void __launch_bounds__(kPer, R3B_LJ_THREADS_PER_SM / kPer) k_lj(const
 // near-class kicks s_near dt/2 F3near / m closing this block and opening the next are added too.
 template <typename T>
 __global__ void __launch_bounds__(256) k_kick(const SysDev* __restrict__ sys, const PItem* __restrict__ items) {
-  pdl_wait();
   const PItem it = items[blockIdx.x];
+#if R3B_STAGE_SYS
+  __shared__ StagedSys s_sys;
+  stage_sys(s_sys, sys, it.sys);
+  pdl_wait();
+  __syncthreads();
+  const SysDev& S = s_sys.get();
+#else
+  pdl_wait();
   const SysDev& S = sys[it.sys];
+#endif
   const int mode = item_mode(S, it.mode);
   if (mode & M_SKIP) return;
   const int kind = mode & M_KIND_MASK;

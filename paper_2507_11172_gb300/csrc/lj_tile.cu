@@ -21,6 +21,7 @@
 // (cell-local difference plus a cell offset, rounded at the same magnitudes).
 #include "md_internal.cuh"
 #include "lj_common.cuh"
+#include "sys_stage.cuh"
 
 namespace r3b {
 
@@ -413,13 +414,21 @@ __device__ __forceinline__ double4_32a lt_ldg4(const double4_32a* p) { return *p
 // items: PItem.begin = first particle of the block (kLjmThreads / kTeam particles per block)
 template <typename T, bool kE, int kTeam>
 __global__ void __launch_bounds__(kLjmThreads, kLjmMinBlocks) k_lj_team(const SysDev* __restrict__ sys, const PItem* __restrict__ items) {
-  pdl_wait();
   static_assert(kTeam == 4 || kTeam == 8 || kTeam == 16, "team of 4, 8 or 16 lanes");
   using T4 = typename V4<T>::type;
   __shared__ T4 s_off[64];
   __shared__ double red_u[kLjmThreads / 32], red_w[kLjmThreads / 32];
   const PItem it = items[blockIdx.x];
+#if R3B_STAGE_SYS
+  __shared__ StagedSys s_sys;
+  stage_sys(s_sys, sys, it.sys);
+  pdl_wait();
+  __syncthreads();
+  const SysDev& S = s_sys.get();
+#else
+  pdl_wait();
   const SysDev& S = sys[it.sys];
+#endif
   const int mode = item_mode(S, it.mode);
   if (mode & M_SKIP) return;  // block-uniform
   const bool energy = kE && (mode & M_ENERGY) != 0;
