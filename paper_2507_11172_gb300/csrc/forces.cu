@@ -1206,10 +1206,18 @@ __global__ void __launch_bounds__(32 * kPaWarps)
 // ============================================================== combine + outer kicks
 template <typename T>
 __global__ void __launch_bounds__(256) k_combine(const SysDev* __restrict__ sys, const PItem* __restrict__ items) {
-  pdl_wait();
   __shared__ double red[32];
   const PItem it = items[blockIdx.x];
+#if R3B_STAGE_SYS
+  __shared__ StagedSys s_sys;
+  stage_sys(s_sys, sys, it.sys);
+  pdl_wait();
+  __syncthreads();
+  const SysDev& S = s_sys.get();
+#else
+  pdl_wait();
   const SysDev& S = sys[it.sys];
+#endif
   const int mode = item_mode(S, it.mode);
   if (mode & M_SKIP) return;
   const int kind = mode & M_KIND_MASK;
@@ -1314,10 +1322,18 @@ __global__ void __launch_bounds__(256) k_combine(const SysDev* __restrict__ sys,
 // opening kicks (outer F3, inner F2) and first drift of a call
 template <typename T>
 __global__ void __launch_bounds__(256) k_start(const SysDev* __restrict__ sys, const PItem* __restrict__ items) {
-  pdl_wait();
   using T4 = typename V4<T>::type;
   const PItem it = items[blockIdx.x];
+#if R3B_STAGE_SYS
+  __shared__ StagedSys s_sys;
+  stage_sys(s_sys, sys, it.sys);
+  pdl_wait();
+  __syncthreads();
+  const SysDev& S = s_sys.get();
+#else
+  pdl_wait();
   const SysDev& S = sys[it.sys];
+#endif
   const int n = S.n;
   const int p = it.begin + threadIdx.x;
   if (p >= n) return;

@@ -7,6 +7,7 @@
 // coordinates used by the force kernels) -> listbuild (pair list with skin,
 // copies the permuted state back into place).
 #include "md_internal.cuh"
+#include "sys_stage.cuh"
 
 #ifndef R3B_LIST_PACKED
 #define R3B_LIST_PACKED 1  // pair-list build: two candidate chunks per iteration in packed FP32x2
@@ -15,9 +16,17 @@
 namespace r3b {
 
 __global__ void k_bin_count(const SysDev* __restrict__ sys, const PItem* __restrict__ items) {
-  pdl_wait();
   const PItem it = items[blockIdx.x];
+#if R3B_STAGE_SYS
+  __shared__ StagedSys s_sys;
+  stage_sys(s_sys, sys, it.sys);
+  pdl_wait();
+  __syncthreads();
+  const SysDev& S = s_sys.get();
+#else
+  pdl_wait();
   const SysDev& S = sys[it.sys];
+#endif
   if (sort_idle(S, it.mode)) return;  // block-uniform
   const int p = it.begin + threadIdx.x;
   const int n = S.n;
@@ -66,9 +75,17 @@ __global__ void k_bin_count(const SysDev* __restrict__ sys, const PItem* __restr
 // the order no longer depends on the arrival order of the binning's atomics.
 // Step 1 (per particle): the members of each cell, in arrival order.
 __global__ void k_cell_members(const SysDev* __restrict__ sys, const PItem* __restrict__ items) {
-  pdl_wait();
   const PItem it = items[blockIdx.x];
+#if R3B_STAGE_SYS
+  __shared__ StagedSys s_sys;
+  stage_sys(s_sys, sys, it.sys);
+  pdl_wait();
+  __syncthreads();
+  const SysDev& S = s_sys.get();
+#else
+  pdl_wait();
   const SysDev& S = sys[it.sys];
+#endif
   if (sort_idle(S, it.mode)) return;
   const int p = it.begin + threadIdx.x;
   if (p >= S.n) return;
@@ -164,10 +181,18 @@ __global__ void __launch_bounds__(1024) k_scan(const SysDev* __restrict__ sys, c
 
 template <typename T>
 __global__ void k_scatter(const SysDev* __restrict__ sys, const PItem* __restrict__ items) {
-  pdl_wait();
   using T4 = typename V4<T>::type;
   const PItem it = items[blockIdx.x];
+#if R3B_STAGE_SYS
+  __shared__ StagedSys s_sys;
+  stage_sys(s_sys, sys, it.sys);
+  pdl_wait();
+  __syncthreads();
+  const SysDev& S = s_sys.get();
+#else
+  pdl_wait();
   const SysDev& S = sys[it.sys];
+#endif
   if (sort_idle(S, it.mode)) return;
   int p = it.begin + threadIdx.x;
   if (p >= S.n) return;

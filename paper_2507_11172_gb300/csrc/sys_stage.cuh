@@ -1,6 +1,7 @@
 // Staging of a work item's system descriptor in shared memory, ahead of the wait for the previous
-// kernel of the stream.  The kernels that use it (LJ, kick/drift) load their work item and descriptor
-// before pdl_wait instead of after it; the rest of their loads still follow the wait.
+// kernel of the stream.  The kernels that use it (LJ, kick/drift, start, combine, binning, cell order
+// and scatter) load their work item and descriptor before pdl_wait instead of after it; the rest of
+// their loads still follow the wait.
 #pragma once
 
 namespace r3b {
