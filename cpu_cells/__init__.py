@@ -13,6 +13,7 @@ import ctypes
 import os
 import subprocess
 import threading
+import time
 
 import numpy as np
 
@@ -100,7 +101,6 @@ class State:
         interacting triplets summed over the ATM evaluations, and the seconds spent in the LJ and ATM
         evaluations and in the whole call."""
         out = np.zeros(6)
-        import time
         t0 = time.perf_counter()
         st = _load().cells_respa(self.x.shape[0], _p(self.x), _p(self.v), self.L, self.mass, self.eps, self.sigma,
                                  self.rc2, self.nu, self.rc3, int(n_outer), int(k_inner), float(dt_outer),

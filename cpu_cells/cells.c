@@ -54,8 +54,8 @@ static int grid_build(int64_t n, const double *x, double L, double reach, Grid *
   g->edge = L / nc;
   const int64_t ncell = (int64_t)nc * nc * nc;
   g->start = (int *)calloc((size_t)ncell + 1, sizeof(int));
-  g->idx = (int *)malloc((size_t)n * sizeof(int));
-  g->cell = (int *)malloc((size_t)n * sizeof(int));
+  g->idx = (int *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int));
+  g->cell = (int *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int));
   g->xs = (double *)malloc((size_t)(n > 0 ? 3 * n : 1) * sizeof(double));
   if (!g->start || !g->idx || !g->cell || !g->xs) {
     grid_free(g);
@@ -162,7 +162,7 @@ static int atm_pass(int64_t n, double L, const Grid *g, double nu, double rc, do
   const int64_t ncell = (int64_t)g->nc * g->nc * g->nc;
   for (int64_t c = 0; c < ncell; ++c)
     if (g->start[c + 1] - g->start[c] > maxc) maxc = g->start[c + 1] - g->start[c];
-  const int cap = 27 * maxc;  /* at most every particle of the 27 cells */
+  const int cap = maxc > 0 ? 27 * maxc : 1;  /* at most every particle of the 27 cells */
   double usum = 0.0;
   int64_t csum = 0;
   int bad = 0;

@@ -64,3 +64,12 @@ def test_box_of_fewer_than_three_cells_is_rejected():
     x, L = md_inputs.fcc_jitter(32, 0.8, 0.05, 3)
     with pytest.raises(ValueError):
         cpu_cells.forces(x, L)
+
+
+def test_empty_system():
+    f2, f3, o = cpu_cells.forces(np.zeros((0, 3)), 10.0)
+    assert f2.shape == (0, 3) and f3.shape == (0, 3)
+    assert o["triplets"] == 0 and o["u2"] == 0.0 and o["u3"] == 0.0
+    st = cpu_cells.State(np.zeros((0, 3)), np.zeros((0, 3)), 10.0)
+    r = st.run(2, 3, 0.01)
+    assert r["triplets"] == 0 and r["atm_evals"] == 2
