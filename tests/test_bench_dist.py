@@ -85,3 +85,24 @@ def test_clock_summary_reads_both_sample_formats():
     assert c["sm_mhz"] == 2070.0 and c["sm_max_mhz"] == 2070.0
     assert c["reasons"] == ["sw_power_cap"] and c["samples"] == 3
     assert bench.clock_summary([])["sm_mhz"] is None
+
+
+def test_profiled_traffic_counts_only_for_the_captured_source(tmp_path, monkeypatch):
+    """roofline.traffic comes from a profile summary only while the kernel's source hash is the one
+    recorded at capture; any later change to the source makes it stale (reported as null)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    src = tmp_path / "kernel.cu"
+    src.write_text("__global__ void k() {}\n")
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "PROFILES", str(prof))
+    monkeypatch.setattr(bench, "KERNEL_SOURCES", {"k": ["kernel.cu"]})
+    assert bench.profiled_traffic("k") == (None, "no capture in profiles/")
+    rec = {"kernel": "k", "dram_bytes_per_launch": 1234, "source_sha256": bench.source_hash("k")}
+    (prof / "k_case.md").write_text("# k\n\ntraffic: " + json.dumps(rec) + "\n")
+    assert bench.profiled_traffic("k") == (1234.0, "k_case.md")
+    src.write_text("__global__ void k() { /* changed */ }\n")
+    val, why = bench.profiled_traffic("k")
+    assert val is None and why.startswith("stale")
