@@ -658,6 +658,7 @@ def cpu_linked_cell(w, w2m=None):
         return {"n": int(x.shape[0]), "rc3": rc3, "k_inner": k, "timed_outer_steps": n_outer,
                 "ms_per_outer_step": sec / n_outer * 1e3, "rrespa_steps_per_s": n_outer / sec,
                 "triplets_per_s": r["triplets"] / sec, "triplets_per_eval": r["triplets"] / max(1, r["atm_evals"]),
+                "atm_only_triplets_per_s": r["triplets"] / r["atm_s"] if r["atm_s"] > 0 else None,
                 "lj_share": r["lj_s"] / sec, "atm_share": r["atm_s"] / sec}
 
     out = {"kind": "linked-cell FP64, OpenMP over particles, no Newton 3 (cpu_cells/)", "cores": cpu_cells.threads(),
