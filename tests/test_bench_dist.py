@@ -106,3 +106,21 @@ def test_profiled_traffic_counts_only_for_the_captured_source(tmp_path, monkeypa
     src.write_text("__global__ void k() { /* changed */ }\n")
     val, why = bench.profiled_traffic("k")
     assert val is None and why.startswith("stale")
+
+
+def test_cpu_linked_cell_line_on_a_small_workload():
+    """The bench's linked-cell CPU entry: its configuration keys, rates and a plausible triplet count
+    per evaluation (averaged over the run; the exact count is pinned in tests/test_cpu_cells.py)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import md_inputs
+    import oracle
+    w = md_inputs.small_fcc_1k()
+    line = bench.cpu_linked_cell(w)
+    assert line["cores"] >= 1 and set(line) >= {"kind", "cores", "cpu_model", "fcc1k", "fcc100k"}
+    for key in ("fcc1k", "fcc100k"):
+        r = line[key]
+        assert r["n"] == 1000 and r["triplets_per_s"] > 0 and r["rrespa_steps_per_s"] > 0
+        assert 0 < r["lj_share"] < 1 and 0 < r["atm_share"] < 1 and r["atm_only_triplets_per_s"] > 0
+    _, _, _, cnt = oracle.atm_brute(w.x, w.L, w.nu, w.rc3)
+    assert abs(line["fcc1k"]["triplets_per_eval"] - cnt) < 0.05 * cnt  # the lattice start relaxes: a few %
